@@ -1,0 +1,946 @@
+/*
+ * PSLR oracle (FP64, single-threaded, plain C).  TEST INFRASTRUCTURE ONLY: the
+ * product path never loads this file.  See pslr_oracle.h for the notation and
+ * the list of what each routine restates.
+ *
+ * Parity status of each part (what pins it is in tests/test_oracle_*.py):
+ *   partition / reordering / blocks ..... pinned (brute force, reassembly)
+ *   ILU(0), exact LU ..................... pinned (pattern identity, P L U = B)
+ *   series, E_rr(m), Arnoldi, G ......... pinned (closed forms, Theorem 2)
+ *   Algorithm 3 apply and transpose ...... pinned (dense formulas, identity case)
+ *   FGMRES ............................... pinned (dense solve, M = I reduction)
+ */
+#include "pslr_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t nr, nc;
+    int32_t *rp, *ci;
+    double *v;
+} ocsr;
+
+struct orc_ctx {
+    int32_t n, s, p, q, factor;
+    int32_t *part, *iface, *perm, *iperm; /* perm[new] = old, iperm[old] = new */
+    int32_t *ioff, *goff;                 /* per subdomain: interior / interface offsets (s+1) */
+    ocsr A, B, E, F, C, C0, Cg;           /* blocks in the permuted numbering */
+    ocsr luB, luC;                        /* ILU(0): strictly lower = L (unit), upper = U */
+    double **dB, **dC;                    /* exact LU: per subdomain dense factors (row-major) */
+    int32_t **pvB, **pvC;                 /* exact LU: row swap at each elimination step */
+    int32_t m, r;
+    double *V, *H, *G;                    /* q x r, r x r, r x r (column-major) */
+};
+
+/* ------------------------------------------------------------------ helpers */
+
+static void csr_free(ocsr *a) {
+    free(a->rp);
+    free(a->ci);
+    free(a->v);
+    memset(a, 0, sizeof(*a));
+}
+
+static ocsr csr_copy(const ocsr *a) {
+    ocsr b = *a;
+    int32_t nnz = a->rp[a->nr];
+    b.rp = malloc(sizeof(int32_t) * (a->nr + 1));
+    b.ci = malloc(sizeof(int32_t) * (nnz ? nnz : 1));
+    b.v = malloc(sizeof(double) * (nnz ? nnz : 1));
+    memcpy(b.rp, a->rp, sizeof(int32_t) * (a->nr + 1));
+    memcpy(b.ci, a->ci, sizeof(int32_t) * nnz);
+    memcpy(b.v, a->v, sizeof(double) * nnz);
+    return b;
+}
+
+/* y = M x */
+static void spmv(const ocsr *M, const double *x, double *y) {
+    for (int32_t i = 0; i < M->nr; ++i) {
+        double acc = 0.0;
+        for (int32_t k = M->rp[i]; k < M->rp[i + 1]; ++k) acc += M->v[k] * x[M->ci[k]];
+        y[i] = acc;
+    }
+}
+
+/* y = M^T x  (column sweep over the rows of M) */
+static void spmv_t(const ocsr *M, const double *x, double *y) {
+    for (int32_t j = 0; j < M->nc; ++j) y[j] = 0.0;
+    for (int32_t i = 0; i < M->nr; ++i)
+        for (int32_t k = M->rp[i]; k < M->rp[i + 1]; ++k) y[M->ci[k]] += M->v[k] * x[i];
+}
+
+static double dot(int32_t n, const double *a, const double *b) {
+    double s = 0.0;
+    for (int32_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+static double nrm2(int32_t n, const double *a) { return sqrt(dot(n, a, a)); }
+
+/* Triplets -> CSR with columns ascending in every row. */
+typedef struct {
+    int32_t r, c;
+    double v;
+} trip;
+
+static int trip_cmp(const void *a, const void *b) {
+    const trip *x = a, *y = b;
+    if (x->r != y->r) return x->r < y->r ? -1 : 1;
+    if (x->c != y->c) return x->c < y->c ? -1 : 1;
+    return 0;
+}
+
+static ocsr csr_from_trips(int32_t nr, int32_t nc, trip *t, int32_t nt) {
+    ocsr a;
+    a.nr = nr;
+    a.nc = nc;
+    qsort(t, nt, sizeof(trip), trip_cmp);
+    a.rp = calloc(nr + 1, sizeof(int32_t));
+    a.ci = malloc(sizeof(int32_t) * (nt ? nt : 1));
+    a.v = malloc(sizeof(double) * (nt ? nt : 1));
+    for (int32_t k = 0; k < nt; ++k) {
+        a.rp[t[k].r + 1]++;
+        a.ci[k] = t[k].c;
+        a.v[k] = t[k].v;
+    }
+    for (int32_t i = 0; i < nr; ++i) a.rp[i + 1] += a.rp[i];
+    return a;
+}
+
+/* ------------------------------------------------ Section 2: reordering */
+
+typedef struct {
+    int32_t iface, part, idx;
+} okey;
+
+static int key_cmp(const void *a, const void *b) {
+    const okey *x = a, *y = b;
+    if (x->iface != y->iface) return x->iface - y->iface;
+    if (x->part != y->part) return x->part - y->part;
+    return x->idx - y->idx;
+}
+
+/*
+ * Section 2: an edge-separator ("vertex-based") partition into s subdomains,
+ * interior unknowns labelled subdomain by subdomain, interface unknowns last.
+ * The geometric split stands in for the paper's METIS call: node (i,j,k) of an
+ * Nx x Ny x Nz grid (x fastest) goes to part floor(i Px/Nx) + Px (floor(j Py/Ny)
+ * + Py floor(k Pz/Nz)).  A node is an interface node iff it is coupled (in the
+ * pattern of A + A^T) to a node of another part.
+ */
+static void reorder(orc_ctx *c, const int32_t dims[3], const int32_t splits[3],
+                    const int32_t *upart) {
+    int32_t n = c->n;
+    c->part = malloc(sizeof(int32_t) * n);
+    c->iface = calloc(n, sizeof(int32_t));
+    c->perm = malloc(sizeof(int32_t) * n);
+    c->iperm = malloc(sizeof(int32_t) * n);
+    if (upart) {
+        int32_t mx = 0;
+        for (int32_t v = 0; v < n; ++v) {
+            c->part[v] = upart[v];
+            if (upart[v] > mx) mx = upart[v];
+        }
+        c->s = mx + 1;
+    } else {
+        int32_t Nx = dims[0], Ny = dims[1], Nz = dims[2];
+        int32_t Px = splits[0], Py = splits[1], Pz = splits[2];
+        for (int32_t v = 0; v < n; ++v) {
+            int32_t i = v % Nx, j = (v / Nx) % Ny, k = v / (Nx * Ny);
+            c->part[v] = (i * Px) / Nx + Px * ((j * Py) / Ny + Py * ((k * Pz) / Nz));
+        }
+        c->s = Px * Py * Pz;
+    }
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t k = c->A.rp[v]; k < c->A.rp[v + 1]; ++k) {
+            int32_t w = c->A.ci[k];
+            if (w != v && c->part[w] != c->part[v]) {
+                c->iface[v] = 1;
+                c->iface[w] = 1;
+            }
+        }
+    okey *keys = malloc(sizeof(okey) * n);
+    for (int32_t v = 0; v < n; ++v) {
+        keys[v].iface = c->iface[v];
+        keys[v].part = c->part[v];
+        keys[v].idx = v;
+    }
+    qsort(keys, n, sizeof(okey), key_cmp);
+    c->p = 0;
+    for (int32_t t = 0; t < n; ++t) {
+        c->perm[t] = keys[t].idx;
+        c->iperm[keys[t].idx] = t;
+        if (!keys[t].iface) c->p++;
+    }
+    c->q = n - c->p;
+    free(keys);
+    c->ioff = calloc(c->s + 1, sizeof(int32_t));
+    c->goff = calloc(c->s + 1, sizeof(int32_t));
+    for (int32_t v = 0; v < n; ++v) {
+        if (c->iface[v]) c->goff[c->part[v] + 1]++;
+        else c->ioff[c->part[v] + 1]++;
+    }
+    for (int32_t i = 0; i < c->s; ++i) {
+        c->ioff[i + 1] += c->ioff[i];
+        c->goff[i + 1] += c->goff[i];
+    }
+}
+
+/* Eq. 2.1 and Eq. 3.1: split P A P^T into B (p x p), E (p x q), F (q x p),
+ * C (q x q); C0 keeps the entries of C inside one subdomain, C_g = C - C0. */
+static void extract_blocks(orc_ctx *c) {
+    int32_t n = c->n, p = c->p, q = c->q;
+    int32_t nnz = c->A.rp[n];
+    trip *tb = malloc(sizeof(trip) * (nnz + 1)), *te = malloc(sizeof(trip) * (nnz + 1));
+    trip *tf = malloc(sizeof(trip) * (nnz + 1)), *tc = malloc(sizeof(trip) * (nnz + 1));
+    trip *t0 = malloc(sizeof(trip) * (nnz + 1)), *tg = malloc(sizeof(trip) * (nnz + 1));
+    int32_t nb = 0, ne = 0, nf = 0, nc = 0, n0 = 0, ng = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        int32_t r = c->iperm[v];
+        for (int32_t k = c->A.rp[v]; k < c->A.rp[v + 1]; ++k) {
+            int32_t w = c->A.ci[k], cc = c->iperm[w];
+            double a = c->A.v[k];
+            if (r < p && cc < p) tb[nb++] = (trip){r, cc, a};
+            else if (r < p) te[ne++] = (trip){r, cc - p, a};
+            else if (cc < p) tf[nf++] = (trip){r - p, cc, a};
+            else {
+                tc[nc++] = (trip){r - p, cc - p, a};
+                if (c->part[v] == c->part[w]) t0[n0++] = (trip){r - p, cc - p, a};
+                else tg[ng++] = (trip){r - p, cc - p, a};
+            }
+        }
+    }
+    c->B = csr_from_trips(p, p, tb, nb);
+    c->E = csr_from_trips(p, q, te, ne);
+    c->F = csr_from_trips(q, p, tf, nf);
+    c->C = csr_from_trips(q, q, tc, nc);
+    c->C0 = csr_from_trips(q, q, t0, n0);
+    c->Cg = csr_from_trips(q, q, tg, ng);
+    free(tb); free(te); free(tf); free(tc); free(t0); free(tg);
+}
+
+/* ------------------------------------- Algorithm 1, steps 2-5: local factors */
+
+/*
+ * ILU(0) in the IKJ order (Saad, Iterative Methods, Sec. 10.3.2), natural order,
+ * no pivoting.  The block-diagonal matrix is factored as a whole, which is the
+ * same computation as factoring each diagonal block separately because no
+ * entry couples two blocks.  Result: strictly lower part = L (unit diagonal
+ * implied), upper part including the diagonal = U, on the pattern of M.
+ */
+static int32_t ilu0(ocsr *M) {
+    int32_t n = M->nr;
+    int32_t *pos = malloc(sizeof(int32_t) * (n ? n : 1));
+    int32_t *dg = malloc(sizeof(int32_t) * (n ? n : 1));
+    for (int32_t j = 0; j < n; ++j) pos[j] = -1;
+    for (int32_t i = 0; i < n; ++i) {
+        dg[i] = -1;
+        for (int32_t k = M->rp[i]; k < M->rp[i + 1]; ++k)
+            if (M->ci[k] == i) dg[i] = k;
+        if (dg[i] < 0) {
+            free(pos); free(dg);
+            return ORC_ERR_ZERO_PIVOT;
+        }
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t k = M->rp[i]; k < M->rp[i + 1]; ++k) pos[M->ci[k]] = k;
+        for (int32_t k = M->rp[i]; k < M->rp[i + 1]; ++k) {
+            int32_t kk = M->ci[k];
+            if (kk >= i) break;
+            double piv = M->v[dg[kk]];
+            if (piv == 0.0) {
+                free(pos); free(dg);
+                return ORC_ERR_ZERO_PIVOT;
+            }
+            M->v[k] /= piv; /* l_{i,kk} */
+            for (int32_t t = dg[kk] + 1; t < M->rp[kk + 1]; ++t) {
+                int32_t j = M->ci[t];
+                if (pos[j] >= 0) M->v[pos[j]] -= M->v[k] * M->v[t];
+            }
+        }
+        if (M->v[dg[i]] == 0.0) {
+            free(pos); free(dg);
+            return ORC_ERR_ZERO_PIVOT;
+        }
+        for (int32_t k = M->rp[i]; k < M->rp[i + 1]; ++k) pos[M->ci[k]] = -1;
+    }
+    free(pos);
+    free(dg);
+    return ORC_OK;
+}
+
+/* Dense LU with partial pivoting (largest |a|, ties -> smallest row) of the
+ * diagonal block rows/cols [lo, hi) of M.  a is row-major nb x nb. */
+static int32_t dense_lu_block(const ocsr *M, int32_t lo, int32_t hi, double **out, int32_t **piv) {
+    int32_t nb = hi - lo;
+    double *a = calloc((size_t)nb * nb + 1, sizeof(double));
+    int32_t *pv = malloc(sizeof(int32_t) * (nb ? nb : 1));
+    for (int32_t i = lo; i < hi; ++i)
+        for (int32_t k = M->rp[i]; k < M->rp[i + 1]; ++k)
+            a[(size_t)(i - lo) * nb + (M->ci[k] - lo)] = M->v[k];
+    for (int32_t k = 0; k < nb; ++k) {
+        int32_t pr = k;
+        double best = fabs(a[(size_t)k * nb + k]);
+        for (int32_t i = k + 1; i < nb; ++i)
+            if (fabs(a[(size_t)i * nb + k]) > best) {
+                best = fabs(a[(size_t)i * nb + k]);
+                pr = i;
+            }
+        pv[k] = pr;
+        if (best == 0.0) {
+            free(a); free(pv);
+            return ORC_ERR_ZERO_PIVOT;
+        }
+        if (pr != k)
+            for (int32_t j = 0; j < nb; ++j) {
+                double t = a[(size_t)k * nb + j];
+                a[(size_t)k * nb + j] = a[(size_t)pr * nb + j];
+                a[(size_t)pr * nb + j] = t;
+            }
+        for (int32_t i = k + 1; i < nb; ++i) {
+            double l = a[(size_t)i * nb + k] / a[(size_t)k * nb + k];
+            a[(size_t)i * nb + k] = l;
+            for (int32_t j = k + 1; j < nb; ++j) a[(size_t)i * nb + j] -= l * a[(size_t)k * nb + j];
+        }
+    }
+    *out = a;
+    *piv = pv;
+    return ORC_OK;
+}
+
+/* x = (L U)^{-1} b for the combined ILU(0) factor: forward, then backward. */
+static void ilu_solve(const ocsr *LU, const double *b, double *x) {
+    int32_t n = LU->nr;
+    for (int32_t i = 0; i < n; ++i) {
+        double acc = b[i];
+        for (int32_t k = LU->rp[i]; k < LU->rp[i + 1] && LU->ci[k] < i; ++k)
+            acc -= LU->v[k] * x[LU->ci[k]];
+        x[i] = acc;
+    }
+    for (int32_t i = n - 1; i >= 0; --i) {
+        double acc = x[i], d = 0.0;
+        for (int32_t k = LU->rp[i]; k < LU->rp[i + 1]; ++k) {
+            int32_t j = LU->ci[k];
+            if (j > i) acc -= LU->v[k] * x[j];
+            else if (j == i) d = LU->v[k];
+        }
+        x[i] = acc / d;
+    }
+}
+
+/* x = (L U)^{-T} b = L^{-T} U^{-T} b: U^T is lower triangular, L^T unit upper;
+ * both are swept column by column over the rows of the stored factor. */
+static void ilu_solve_t(const ocsr *LU, const double *b, double *x) {
+    int32_t n = LU->nr;
+    for (int32_t i = 0; i < n; ++i) x[i] = b[i];
+    for (int32_t i = 0; i < n; ++i) { /* U^T z = b */
+        double d = 0.0;
+        for (int32_t k = LU->rp[i]; k < LU->rp[i + 1]; ++k)
+            if (LU->ci[k] == i) d = LU->v[k];
+        x[i] /= d;
+        for (int32_t k = LU->rp[i]; k < LU->rp[i + 1]; ++k)
+            if (LU->ci[k] > i) x[LU->ci[k]] -= LU->v[k] * x[i];
+    }
+    for (int32_t i = n - 1; i >= 0; --i) /* L^T y = z */
+        for (int32_t k = LU->rp[i]; k < LU->rp[i + 1] && LU->ci[k] < i; ++k)
+            x[LU->ci[k]] -= LU->v[k] * x[i];
+}
+
+/* Solve with one dense pivoted LU block: P B = L U. */
+static void dense_solve(int32_t nb, const double *a, const int32_t *pv, const double *b, double *x) {
+    for (int32_t i = 0; i < nb; ++i) x[i] = b[i];
+    for (int32_t k = 0; k < nb; ++k)
+        if (pv[k] != k) {
+            double t = x[k];
+            x[k] = x[pv[k]];
+            x[pv[k]] = t;
+        }
+    for (int32_t i = 0; i < nb; ++i)
+        for (int32_t j = 0; j < i; ++j) x[i] -= a[(size_t)i * nb + j] * x[j];
+    for (int32_t i = nb - 1; i >= 0; --i) {
+        for (int32_t j = i + 1; j < nb; ++j) x[i] -= a[(size_t)i * nb + j] * x[j];
+        x[i] /= a[(size_t)i * nb + i];
+    }
+}
+
+/* B^T = U^T L^T P  =>  x = P^T L^{-T} U^{-T} b. */
+static void dense_solve_t(int32_t nb, const double *a, const int32_t *pv, const double *b, double *x) {
+    for (int32_t i = 0; i < nb; ++i) x[i] = b[i];
+    for (int32_t i = 0; i < nb; ++i) { /* U^T */
+        for (int32_t j = 0; j < i; ++j) x[i] -= a[(size_t)j * nb + i] * x[j];
+        x[i] /= a[(size_t)i * nb + i];
+    }
+    for (int32_t i = nb - 1; i >= 0; --i) /* L^T, unit diagonal */
+        for (int32_t j = i + 1; j < nb; ++j) x[i] -= a[(size_t)j * nb + i] * x[j];
+    for (int32_t k = nb - 1; k >= 0; --k)
+        if (pv[k] != k) {
+            double t = x[k];
+            x[k] = x[pv[k]];
+            x[pv[k]] = t;
+        }
+}
+
+/* ------------------------------------------------------------- set-up */
+
+orc_ctx *orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                   const int32_t dims[3], const int32_t splits[3], const int32_t *part,
+                   int32_t factor, int32_t *status) {
+    *status = ORC_ERR_ARG;
+    if (n <= 0 || !rowptr || !col || !val) return NULL;
+    if (!part && (!dims || !splits || (int64_t)dims[0] * dims[1] * dims[2] != n)) return NULL;
+    if (!part)
+        for (int d = 0; d < 3; ++d)
+            if (splits[d] < 1 || splits[d] > dims[d]) return NULL;
+    orc_ctx *c = calloc(1, sizeof(orc_ctx));
+    c->n = n;
+    c->factor = factor;
+    ocsr A = {n, n, (int32_t *)rowptr, (int32_t *)col, (double *)val};
+    c->A = csr_copy(&A);
+    reorder(c, dims, splits, part);
+    extract_blocks(c);
+    int32_t st = ORC_OK;
+    if (factor == 0) {
+        c->luB = csr_copy(&c->B);
+        c->luC = csr_copy(&c->C0);
+        st = ilu0(&c->luB);
+        if (st == ORC_OK) st = ilu0(&c->luC);
+    } else {
+        c->dB = calloc(c->s, sizeof(double *));
+        c->dC = calloc(c->s, sizeof(double *));
+        c->pvB = calloc(c->s, sizeof(int32_t *));
+        c->pvC = calloc(c->s, sizeof(int32_t *));
+        for (int32_t i = 0; i < c->s && st == ORC_OK; ++i) {
+            st = dense_lu_block(&c->B, c->ioff[i], c->ioff[i + 1], &c->dB[i], &c->pvB[i]);
+            if (st == ORC_OK)
+                st = dense_lu_block(&c->C0, c->goff[i], c->goff[i + 1], &c->dC[i], &c->pvC[i]);
+        }
+    }
+    if (st != ORC_OK) {
+        *status = st;
+        orc_destroy(c);
+        return NULL;
+    }
+    *status = ORC_OK;
+    return c;
+}
+
+void orc_destroy(orc_ctx *c) {
+    if (!c) return;
+    free(c->part); free(c->iface); free(c->perm); free(c->iperm);
+    free(c->ioff); free(c->goff);
+    csr_free(&c->A); csr_free(&c->B); csr_free(&c->E); csr_free(&c->F);
+    csr_free(&c->C); csr_free(&c->C0); csr_free(&c->Cg);
+    csr_free(&c->luB); csr_free(&c->luC);
+    if (c->dB)
+        for (int32_t i = 0; i < c->s; ++i) {
+            free(c->dB[i]); free(c->dC[i]); free(c->pvB[i]); free(c->pvC[i]);
+        }
+    free(c->dB); free(c->dC); free(c->pvB); free(c->pvC);
+    free(c->V); free(c->H); free(c->G);
+    free(c);
+}
+
+void orc_sizes(const orc_ctx *c, int32_t *n, int32_t *s, int32_t *p, int32_t *q) {
+    *n = c->n; *s = c->s; *p = c->p; *q = c->q;
+}
+
+void orc_maps(const orc_ctx *c, int32_t *part, int32_t *is_interface, int32_t *perm) {
+    memcpy(part, c->part, sizeof(int32_t) * c->n);
+    memcpy(is_interface, c->iface, sizeof(int32_t) * c->n);
+    memcpy(perm, c->perm, sizeof(int32_t) * c->n);
+}
+
+void orc_offsets(const orc_ctx *c, int32_t *interior_off, int32_t *interface_off) {
+    memcpy(interior_off, c->ioff, sizeof(int32_t) * (c->s + 1));
+    memcpy(interface_off, c->goff, sizeof(int32_t) * (c->s + 1));
+}
+
+static const ocsr *pick(const orc_ctx *c, int32_t which) {
+    switch (which) {
+    case ORC_B: return &c->B;
+    case ORC_E: return &c->E;
+    case ORC_F: return &c->F;
+    case ORC_C: return &c->C;
+    case ORC_C0: return &c->C0;
+    case ORC_CG: return &c->Cg;
+    case ORC_LU_B: return c->factor == 0 ? &c->luB : NULL;
+    case ORC_LU_C0: return c->factor == 0 ? &c->luC : NULL;
+    }
+    return NULL;
+}
+
+int32_t orc_block_nnz(const orc_ctx *c, int32_t which) {
+    const ocsr *m = pick(c, which);
+    return m ? m->rp[m->nr] : -1;
+}
+
+void orc_get_block(const orc_ctx *c, int32_t which, int32_t *rowptr, int32_t *col, double *val) {
+    const ocsr *m = pick(c, which);
+    if (!m) return;
+    memcpy(rowptr, m->rp, sizeof(int32_t) * (m->nr + 1));
+    memcpy(col, m->ci, sizeof(int32_t) * m->rp[m->nr]);
+    memcpy(val, m->v, sizeof(double) * m->rp[m->nr]);
+}
+
+/* ------------------------------------------ B~^{-1}, C0~^{-1} and transposes */
+
+void orc_solve_B(const orc_ctx *c, const double *in, double *out) {
+    if (c->factor == 0) {
+        ilu_solve(&c->luB, in, out);
+        return;
+    }
+    for (int32_t i = 0; i < c->s; ++i) {
+        int32_t lo = c->ioff[i], nb = c->ioff[i + 1] - lo;
+        dense_solve(nb, c->dB[i], c->pvB[i], in + lo, out + lo);
+    }
+}
+
+void orc_solve_BT(const orc_ctx *c, const double *in, double *out) {
+    if (c->factor == 0) {
+        ilu_solve_t(&c->luB, in, out);
+        return;
+    }
+    for (int32_t i = 0; i < c->s; ++i) {
+        int32_t lo = c->ioff[i], nb = c->ioff[i + 1] - lo;
+        dense_solve_t(nb, c->dB[i], c->pvB[i], in + lo, out + lo);
+    }
+}
+
+void orc_solve_C0(const orc_ctx *c, const double *in, double *out) {
+    if (c->factor == 0) {
+        ilu_solve(&c->luC, in, out);
+        return;
+    }
+    for (int32_t i = 0; i < c->s; ++i) {
+        int32_t lo = c->goff[i], nb = c->goff[i + 1] - lo;
+        dense_solve(nb, c->dC[i], c->pvC[i], in + lo, out + lo);
+    }
+}
+
+void orc_solve_C0T(const orc_ctx *c, const double *in, double *out) {
+    if (c->factor == 0) {
+        ilu_solve_t(&c->luC, in, out);
+        return;
+    }
+    for (int32_t i = 0; i < c->s; ++i) {
+        int32_t lo = c->goff[i], nb = c->goff[i + 1] - lo;
+        dense_solve_t(nb, c->dC[i], c->pvC[i], in + lo, out + lo);
+    }
+}
+
+/* ------------------------------------------- Sec. 3.1: splitting and series */
+
+/* E_s w = F B^{-1} E w - C_g w   (Eq. 3.1 with E_s = (C0 - C) + F B^{-1} E) */
+void orc_Es(const orc_ctx *c, const double *in, double *out) {
+    double *a = malloc(sizeof(double) * (c->p + 1)), *u = malloc(sizeof(double) * (c->p + 1));
+    double *g = malloc(sizeof(double) * (c->q + 1));
+    spmv(&c->E, in, a);
+    orc_solve_B(c, a, u);
+    spmv(&c->F, u, out);
+    spmv(&c->Cg, in, g);
+    for (int32_t i = 0; i < c->q; ++i) out[i] -= g[i];
+    free(a); free(u); free(g);
+}
+
+/* E_s^T w = E^T B^{-T} F^T w - C_g^T w */
+void orc_EsT(const orc_ctx *c, const double *in, double *out) {
+    double *a = malloc(sizeof(double) * (c->p + 1)), *u = malloc(sizeof(double) * (c->p + 1));
+    double *g = malloc(sizeof(double) * (c->q + 1));
+    spmv_t(&c->F, in, a);
+    orc_solve_BT(c, a, u);
+    spmv_t(&c->E, u, out);
+    spmv_t(&c->Cg, in, g);
+    for (int32_t i = 0; i < c->q; ++i) out[i] -= g[i];
+    free(a); free(u); free(g);
+}
+
+/*
+ * Eq. 3.3: P_m t = sum_{i=0}^{m} (C0^{-1} E_s)^i C0^{-1} t, m+1 terms, summed as
+ * w_0 = C0^{-1} t, w_i = C0^{-1} E_s w_{i-1}, out = w_0 + w_1 + ... + w_m.
+ */
+void orc_series(const orc_ctx *c, int32_t m, const double *in, double *out) {
+    int32_t q = c->q;
+    double *w = malloc(sizeof(double) * (q + 1)), *e = malloc(sizeof(double) * (q + 1));
+    orc_solve_C0(c, in, w);
+    for (int32_t k = 0; k < q; ++k) out[k] = w[k];
+    for (int32_t i = 1; i <= m; ++i) {
+        orc_Es(c, w, e);
+        orc_solve_C0(c, e, w);
+        for (int32_t k = 0; k < q; ++k) out[k] += w[k];
+    }
+    free(w); free(e);
+}
+
+/* P_m^T h = sum_{i=0}^{m} C0^{-T} (E_s^T C0^{-T})^i h, same recurrence with the
+ * transposed operators: w_0 = C0^{-T} h, w_i = C0^{-T} E_s^T w_{i-1}. */
+void orc_seriesT(const orc_ctx *c, int32_t m, const double *in, double *out) {
+    int32_t q = c->q;
+    double *w = malloc(sizeof(double) * (q + 1)), *e = malloc(sizeof(double) * (q + 1));
+    orc_solve_C0T(c, in, w);
+    for (int32_t k = 0; k < q; ++k) out[k] = w[k];
+    for (int32_t i = 1; i <= m; ++i) {
+        orc_EsT(c, w, e);
+        orc_solve_C0T(c, e, w);
+        for (int32_t k = 0; k < q; ++k) out[k] += w[k];
+    }
+    free(w); free(e);
+}
+
+/* Sec. 3.2.1, Eq. 3.19: E_rr(m) v = (E_s C0^{-1})^{m+1} v. */
+void orc_Err(const orc_ctx *c, int32_t m, const double *in, double *out) {
+    int32_t q = c->q;
+    double *t = malloc(sizeof(double) * (q + 1));
+    for (int32_t k = 0; k < q; ++k) out[k] = in[k];
+    for (int32_t i = 0; i <= m; ++i) {
+        orc_solve_C0(c, out, t);
+        orc_Es(c, t, out);
+    }
+    free(t);
+}
+
+/* ------------------------------------------ Sec. 3.2: low-rank correction */
+
+double orc_splitmix_uniform(uint64_t seed, uint64_t j) {
+    uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+/* Classical Gram-Schmidt against the first k columns of V, applied twice;
+ * h (length k) receives the summed coefficients. */
+static void cgs2(int32_t q, int32_t k, const double *V, double *w, double *h) {
+    double *t = malloc(sizeof(double) * (k + 1));
+    for (int32_t i = 0; i < k; ++i) h[i] = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int32_t i = 0; i < k; ++i) t[i] = dot(q, V + (size_t)i * q, w);
+        for (int32_t i = 0; i < k; ++i)
+            for (int32_t l = 0; l < q; ++l) w[l] -= t[i] * V[(size_t)i * q + l];
+        for (int32_t i = 0; i < k; ++i) h[i] += t[i];
+    }
+    free(t);
+}
+
+/* G = (I - H)^{-1} - I by LU with partial pivoting of I - H (Eq. 3.17). */
+static int32_t compute_G(int32_t r, const double *H, double *G) {
+    double *a = malloc(sizeof(double) * (r * r + 1)), *x = malloc(sizeof(double) * (r + 1));
+    int32_t *pv = malloc(sizeof(int32_t) * (r + 1));
+    double amax = 0.0;
+    for (int32_t i = 0; i < r; ++i) /* row-major copy of I - H (H column-major) */
+        for (int32_t j = 0; j < r; ++j) {
+            a[i * r + j] = (i == j ? 1.0 : 0.0) - H[j * r + i];
+            if (fabs(a[i * r + j]) > amax) amax = fabs(a[i * r + j]);
+        }
+    for (int32_t k = 0; k < r; ++k) {
+        int32_t pr = k;
+        double best = fabs(a[k * r + k]);
+        for (int32_t i = k + 1; i < r; ++i)
+            if (fabs(a[i * r + k]) > best) {
+                best = fabs(a[i * r + k]);
+                pr = i;
+            }
+        pv[k] = pr;
+        if (best <= 1e-14 * amax) {
+            free(a); free(x); free(pv);
+            return ORC_ERR_SINGULAR_IMH;
+        }
+        if (pr != k)
+            for (int32_t j = 0; j < r; ++j) {
+                double t = a[k * r + j];
+                a[k * r + j] = a[pr * r + j];
+                a[pr * r + j] = t;
+            }
+        for (int32_t i = k + 1; i < r; ++i) {
+            double l = a[i * r + k] / a[k * r + k];
+            a[i * r + k] = l;
+            for (int32_t j = k + 1; j < r; ++j) a[i * r + j] -= l * a[k * r + j];
+        }
+    }
+    for (int32_t j = 0; j < r; ++j) { /* column j of (I - H)^{-1} */
+        for (int32_t i = 0; i < r; ++i) x[i] = (i == j) ? 1.0 : 0.0;
+        for (int32_t k = 0; k < r; ++k)
+            if (pv[k] != k) {
+                double t = x[k];
+                x[k] = x[pv[k]];
+                x[pv[k]] = t;
+            }
+        for (int32_t i = 0; i < r; ++i)
+            for (int32_t l = 0; l < i; ++l) x[i] -= a[i * r + l] * x[l];
+        for (int32_t i = r - 1; i >= 0; --i) {
+            for (int32_t l = i + 1; l < r; ++l) x[i] -= a[i * r + l] * x[l];
+            x[i] /= a[i * r + i];
+        }
+        for (int32_t i = 0; i < r; ++i) G[j * r + i] = x[i] - (i == j ? 1.0 : 0.0);
+    }
+    free(a); free(x); free(pv);
+    return ORC_OK;
+}
+
+/*
+ * Algorithm 1 steps 6-8 with Eq. 3.16-3.17.  Arnoldi on E_rr(m):
+ * v_1 = u / ||u||, u_l = U[-1,1) from SplitMix64(seed) output l; for j = 1..r:
+ * w = E_rr(m) v_j, h_{1:j,j} by classical Gram-Schmidt twice, h_{j+1,j} = ||w||,
+ * v_{j+1} = w / h_{j+1,j}.  H is the leading r x r block (h_{r+1,r} dropped).
+ * Breakdown, h_{j+1,j} <= 1e-12 ||H(1:j+1,1:j)||_F with j < r: truncate to rank
+ * j, or (full_rank) start a fresh SplitMix64 vector (outputs t*q .. t*q+q-1 for
+ * the t-th vector) orthogonalised against V, with h_{j+1,j} = 0.
+ */
+int32_t orc_build_lowrank(orc_ctx *c, int32_t m, int32_t rank, uint64_t seed, int32_t full_rank,
+                          int32_t *rank_out) {
+    int32_t q = c->q;
+    free(c->V); free(c->H); free(c->G);
+    c->V = c->H = c->G = NULL;
+    c->m = m;
+    c->r = 0;
+    *rank_out = 0;
+    if (rank > q) rank = q;
+    if (rank <= 0 || q == 0) return ORC_OK;
+    int32_t r = rank;
+    double *V = calloc((size_t)q * (r + 1), sizeof(double));
+    double *Hb = calloc((size_t)(r + 1) * r, sizeof(double)); /* (r+1) x r, column-major */
+    double *w = malloc(sizeof(double) * q), *h = malloc(sizeof(double) * (r + 1));
+    int32_t tvec = 0;
+    for (int32_t l = 0; l < q; ++l) V[l] = orc_splitmix_uniform(seed, (uint64_t)l);
+    double nu = nrm2(q, V);
+    for (int32_t l = 0; l < q; ++l) V[l] /= nu;
+    int32_t kept = r;
+    double hf2 = 0.0;
+    for (int32_t j = 0; j < r; ++j) {
+        orc_Err(c, m, V + (size_t)j * q, w);
+        cgs2(q, j + 1, V, w, h);
+        double hn = nrm2(q, w);
+        for (int32_t i = 0; i <= j; ++i) {
+            Hb[(size_t)j * (r + 1) + i] = h[i];
+            hf2 += h[i] * h[i];
+        }
+        hf2 += hn * hn;
+        if (j == r - 1) break;
+        if (hn <= 1e-12 * sqrt(hf2)) {
+            if (!full_rank) {
+                kept = j + 1;
+                break;
+            }
+            /* fresh direction orthogonal to V(:, 0..j) */
+            double *vn = V + (size_t)(j + 1) * q;
+            ++tvec;
+            for (int32_t l = 0; l < q; ++l)
+                vn[l] = orc_splitmix_uniform(seed, (uint64_t)tvec * q + l);
+            cgs2(q, j + 1, V, vn, h);
+            double nn = nrm2(q, vn);
+            for (int32_t l = 0; l < q; ++l) vn[l] /= nn;
+            Hb[(size_t)j * (r + 1) + j + 1] = 0.0;
+        } else {
+            Hb[(size_t)j * (r + 1) + j + 1] = hn;
+            for (int32_t l = 0; l < q; ++l) V[(size_t)(j + 1) * q + l] = w[l] / hn;
+        }
+    }
+    c->V = malloc(sizeof(double) * (size_t)q * kept);
+    c->H = malloc(sizeof(double) * (size_t)kept * kept);
+    c->G = malloc(sizeof(double) * (size_t)kept * kept);
+    memcpy(c->V, V, sizeof(double) * (size_t)q * kept);
+    for (int32_t j = 0; j < kept; ++j)
+        for (int32_t i = 0; i < kept; ++i) c->H[j * kept + i] = Hb[(size_t)j * (r + 1) + i];
+    free(V); free(Hb); free(w); free(h);
+    c->r = kept;
+    *rank_out = kept;
+    int32_t st = compute_G(kept, c->H, c->G);
+    if (st != ORC_OK) {
+        free(c->V); free(c->H); free(c->G);
+        c->V = c->H = c->G = NULL;
+        c->r = 0;
+        *rank_out = 0;
+        return st;
+    }
+    return kept < rank ? ORC_ERR_BREAKDOWN : ORC_OK;
+}
+
+void orc_get_lowrank(const orc_ctx *c, double *V, double *H, double *G) {
+    if (c->r == 0) return;
+    if (V) memcpy(V, c->V, sizeof(double) * (size_t)c->q * c->r);
+    if (H && c->H) memcpy(H, c->H, sizeof(double) * (size_t)c->r * c->r);
+    if (G) memcpy(G, c->G, sizeof(double) * (size_t)c->r * c->r);
+}
+
+int32_t orc_set_lowrank(orc_ctx *c, int32_t m, int32_t rank, const double *V, const double *G) {
+    free(c->V); free(c->H); free(c->G);
+    c->V = c->H = c->G = NULL;
+    c->m = m;
+    c->r = rank;
+    if (rank <= 0) {
+        c->r = 0;
+        return ORC_OK;
+    }
+    c->V = malloc(sizeof(double) * (size_t)c->q * rank);
+    c->G = malloc(sizeof(double) * (size_t)rank * rank);
+    memcpy(c->V, V, sizeof(double) * (size_t)c->q * rank);
+    memcpy(c->G, G, sizeof(double) * (size_t)rank * rank);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------ Algorithm 3 and transpose */
+
+/* t <- t + V op(G) V^T t, op(G) = G or G^T. */
+static void lowrank_update(const orc_ctx *c, double *t, int transpose) {
+    int32_t q = c->q, r = c->r;
+    if (r == 0) return;
+    double *u = malloc(sizeof(double) * r), *d = malloc(sizeof(double) * r);
+    for (int32_t i = 0; i < r; ++i) u[i] = dot(q, c->V + (size_t)i * q, t);
+    for (int32_t i = 0; i < r; ++i) {
+        double acc = 0.0;
+        for (int32_t j = 0; j < r; ++j)
+            acc += (transpose ? c->G[i * r + j] : c->G[j * r + i]) * u[j];
+        d[i] = acc;
+    }
+    for (int32_t i = 0; i < r; ++i)
+        for (int32_t l = 0; l < q; ++l) t[l] += c->V[(size_t)i * q + l] * d[i];
+    free(u); free(d);
+}
+
+/*
+ * Algorithm 3 (Eq. 3.24): b = (f; g) in the reordered numbering;
+ *   t = g - F B^{-1} f,  t <- t + V G V^T t,  y = P_m t,  x = B^{-1}(f - E y),
+ *   z = (x; y), scattered back to the original numbering.
+ */
+void orc_apply(const orc_ctx *c, const double *b, double *z) {
+    int32_t p = c->p, q = c->q;
+    double *f = malloc(sizeof(double) * (p + 1)), *u = malloc(sizeof(double) * (p + 1));
+    double *t = malloc(sizeof(double) * (q + 1)), *y = malloc(sizeof(double) * (q + 1));
+    double *x = malloc(sizeof(double) * (p + 1));
+    for (int32_t i = 0; i < p; ++i) f[i] = b[c->perm[i]];
+    orc_solve_B(c, f, u);
+    spmv(&c->F, u, t);
+    for (int32_t i = 0; i < q; ++i) t[i] = b[c->perm[p + i]] - t[i];
+    lowrank_update(c, t, 0);
+    orc_series(c, c->m, t, y);
+    spmv(&c->E, y, u);
+    for (int32_t i = 0; i < p; ++i) u[i] = f[i] - u[i];
+    orc_solve_B(c, u, x);
+    for (int32_t i = 0; i < p; ++i) z[c->perm[i]] = x[i];
+    for (int32_t i = 0; i < q; ++i) z[c->perm[p + i]] = y[i];
+    free(f); free(u); free(t); free(y); free(x);
+}
+
+/*
+ * Exact transpose of Algorithm 3 (not in the paper; derived from the block
+ * form M^{-1} = [[B^{-1} + B^{-1} E K F B^{-1}, -B^{-1} E K], [-K F B^{-1}, K]]
+ * with K = P_m (I + V G V^T)).  For b = (f; g):
+ *   h = g - E^T B^{-T} f,  w = (I + V G^T V^T) P_m^T h,  x = B^{-T}(f - F^T w).
+ */
+void orc_apply_T(const orc_ctx *c, const double *b, double *z) {
+    int32_t p = c->p, q = c->q;
+    double *f = malloc(sizeof(double) * (p + 1)), *u = malloc(sizeof(double) * (p + 1));
+    double *h = malloc(sizeof(double) * (q + 1)), *w = malloc(sizeof(double) * (q + 1));
+    double *x = malloc(sizeof(double) * (p + 1));
+    for (int32_t i = 0; i < p; ++i) f[i] = b[c->perm[i]];
+    orc_solve_BT(c, f, u);
+    spmv_t(&c->E, u, h);
+    for (int32_t i = 0; i < q; ++i) h[i] = b[c->perm[p + i]] - h[i];
+    orc_seriesT(c, c->m, h, w);
+    lowrank_update(c, w, 1);
+    spmv_t(&c->F, w, u);
+    for (int32_t i = 0; i < p; ++i) u[i] = f[i] - u[i];
+    orc_solve_BT(c, u, x);
+    for (int32_t i = 0; i < p; ++i) z[c->perm[i]] = x[i];
+    for (int32_t i = 0; i < q; ++i) z[c->perm[p + i]] = w[i];
+    free(f); free(u); free(h); free(w); free(x);
+}
+
+/* -------------------------------------------------------------- FGMRES */
+
+static void op_A(const orc_ctx *c, int transpose, const double *x, double *y) {
+    if (transpose) spmv_t(&c->A, x, y);
+    else spmv(&c->A, x, y);
+}
+
+static void op_M(const orc_ctx *c, int prec, int transpose, const double *x, double *y) {
+    if (!prec) {
+        memcpy(y, x, sizeof(double) * c->n);
+        return;
+    }
+    if (transpose) orc_apply_T(c, x, y);
+    else orc_apply(c, x, y);
+}
+
+/*
+ * Flexible GMRES (Saad, Iterative Methods, Alg. 9.6), right preconditioned,
+ * x0 = 0, restart length `restart`, Section 4's stopping rule
+ * ||b - A x|| <= rtol ||b|| (checked on the least-squares residual |gamma_{j+1}|
+ * inside a cycle and confirmed on the true residual at the end of a cycle).
+ * prec bit 0: PSLR preconditioner on; bit 1: solve with A^T and M^T.
+ */
+int32_t orc_fgmres(const orc_ctx *c, int32_t prec, const double *b, double *x, double rtol,
+                   int32_t restart, int32_t maxit, int32_t *iters, double *relres) {
+    int32_t n = c->n, k = restart;
+    int use_m = prec & 1, tr = (prec >> 1) & 1;
+    double *V = malloc(sizeof(double) * (size_t)n * (k + 1));
+    double *Z = malloc(sizeof(double) * (size_t)n * k);
+    double *H = calloc((size_t)(k + 1) * k, sizeof(double)); /* column-major (k+1) x k */
+    double *cs = malloc(sizeof(double) * k), *sn = malloc(sizeof(double) * k);
+    double *gam = malloc(sizeof(double) * (k + 1)), *y = malloc(sizeof(double) * k);
+    double *r = malloc(sizeof(double) * n), *w = malloc(sizeof(double) * n);
+    double *hc = malloc(sizeof(double) * (k + 1));
+    double bn = nrm2(n, b);
+    int32_t its = 0, st = ORC_ERR_NOT_CONVERGED;
+    for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
+    *relres = 0.0;
+    if (bn == 0.0) {
+        *iters = 0;
+        st = ORC_OK;
+        goto done;
+    }
+    for (int32_t i = 0; i < n; ++i) r[i] = b[i];
+    double rn = bn;
+    while (its < maxit) {
+        for (int32_t i = 0; i < n; ++i) V[i] = r[i] / rn;
+        gam[0] = rn;
+        int32_t j, jdone = 0;
+        for (j = 0; j < k && its < maxit; ++j) {
+            op_M(c, use_m, tr, V + (size_t)j * n, Z + (size_t)j * n);
+            op_A(c, tr, Z + (size_t)j * n, w);
+            cgs2(n, j + 1, V, w, hc);
+            double hn = nrm2(n, w);
+            ++its;
+            for (int32_t i = 0; i <= j; ++i) H[(size_t)j * (k + 1) + i] = hc[i];
+            H[(size_t)j * (k + 1) + j + 1] = hn;
+            if (hn > 0.0)
+                for (int32_t i = 0; i < n; ++i) V[(size_t)(j + 1) * n + i] = w[i] / hn;
+            for (int32_t i = 0; i < j; ++i) { /* previous rotations */
+                double a = H[(size_t)j * (k + 1) + i], bb = H[(size_t)j * (k + 1) + i + 1];
+                H[(size_t)j * (k + 1) + i] = cs[i] * a + sn[i] * bb;
+                H[(size_t)j * (k + 1) + i + 1] = -sn[i] * a + cs[i] * bb;
+            }
+            double a = H[(size_t)j * (k + 1) + j], bb = H[(size_t)j * (k + 1) + j + 1];
+            double den = sqrt(a * a + bb * bb);
+            cs[j] = den > 0.0 ? a / den : 1.0;
+            sn[j] = den > 0.0 ? bb / den : 0.0;
+            H[(size_t)j * (k + 1) + j] = den;
+            H[(size_t)j * (k + 1) + j + 1] = 0.0;
+            gam[j + 1] = -sn[j] * gam[j];
+            gam[j] = cs[j] * gam[j];
+            jdone = j + 1;
+            if (fabs(gam[j + 1]) <= rtol * bn || hn == 0.0) break;
+        }
+        for (int32_t i = jdone - 1; i >= 0; --i) { /* H y = gamma */
+            double acc = gam[i];
+            for (int32_t l = i + 1; l < jdone; ++l) acc -= H[(size_t)l * (k + 1) + i] * y[l];
+            y[i] = acc / H[(size_t)i * (k + 1) + i];
+        }
+        for (int32_t l = 0; l < jdone; ++l)
+            for (int32_t i = 0; i < n; ++i) x[i] += Z[(size_t)l * n + i] * y[l];
+        op_A(c, tr, x, w);
+        for (int32_t i = 0; i < n; ++i) r[i] = b[i] - w[i];
+        rn = nrm2(n, r);
+        *relres = rn / bn;
+        if (rn <= rtol * bn) {
+            st = ORC_OK;
+            break;
+        }
+    }
+    *iters = its;
+done:
+    free(V); free(Z); free(H); free(cs); free(sn); free(gam); free(y); free(r); free(w); free(hc);
+    return st;
+}

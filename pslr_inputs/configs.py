@@ -1,0 +1,111 @@
+"""Named synthetic workloads (the paper's Section-4 problem families at GB300 sizes).
+
+Every workload is a dict with the PSLR parameters (subdomain split, local
+factor kind, series order m, rank r) and a ``build()`` that returns the matrix
+and right-hand side(s).  Seeds: 0 for right-hand sides, kappa fields and the
+batch's random sizes; 1 for the differentiable problem's target field.
+
+Workloads (names say what they are):
+
+``lap2d_32_2x2_exact``    2D 5-pt Laplacian 32x32, sigma for exactly 4 negative
+                          eigenvalues, 2x2 split, exact dense local LU, m=3, r=8.
+``lap3d_64_4x4x2_ilu0``   3D 7-pt Laplacian 64^3, sigma for 20 negative
+                          eigenvalues, 4x4x2 split, ILU(0), m=3, r=16.
+``batch2d_64sys``         64 shifted 2D Laplacians, side ~ U{64..256}, 4 rhs each.
+``kappa3d_48_3x3x3``      3D 48^3 variable-kappa operator, 3x3x3 split, m=3, r=16.
+``cd3d_128_8x8x4_ilu0``   3D 128^3 upwinded convection-diffusion, Pe=50, sigma for
+                          20 negative eigenvalues of the shifted operator, 8x8x4
+                          split, ILU(0), m=5, r=32.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import generators as G
+
+FACTOR_ILU0 = 0
+FACTOR_EXACT_LU = 1
+
+
+def _lap(dims, K):
+    sig, k = G.sigma_for_negative_count([G.laplacian_1d_eigs(d) for d in dims], K)
+    return G.shifted_laplacian(dims, sig), sig, k
+
+
+def lap2d_32_2x2_exact():
+    A, sig, k = _lap((32, 32), 4)
+    return dict(name="lap2d_32_2x2_exact", A=A, sigma=sig, nneg=k, ndim=2, dims=(32, 32, 1),
+                splits=(2, 2, 1), factor=FACTOR_EXACT_LU, m=3, rank=8)
+
+
+def lap3d_64_4x4x2_ilu0():
+    A, sig, k = _lap((64, 64, 64), 20)
+    return dict(name="lap3d_64_4x4x2_ilu0", A=A, sigma=sig, nneg=k, ndim=3, dims=(64, 64, 64),
+                splits=(4, 4, 2), factor=FACTOR_ILU0, m=3, rank=16)
+
+
+def cd3d_128_8x8x4_ilu0(N=128, splits=(8, 8, 4), m=5, rank=32, K=20):
+    pe = 50.0
+    a = pe / (N + 1.0)
+    sig, k = G.sigma_for_negative_count([G.convdiff_1d_eigs(N, a)] * 3, K)
+    A = G.convection_diffusion((N, N, N), pe, sig)
+    return dict(name=f"cd3d_{N}_{splits[0]}x{splits[1]}x{splits[2]}_ilu0", A=A, sigma=sig, nneg=k,
+                ndim=3, dims=(N, N, N), splits=tuple(splits), factor=FACTOR_ILU0, m=m, rank=rank)
+
+
+def kappa3d_48_3x3x3(N=48, splits=(3, 3, 3), m=3, rank=16, K=10):
+    dims = (N, N, N)
+    sig, k = G.sigma_for_negative_count([G.laplacian_1d_eigs(N)] * 3, K)
+    kap = G.kappa_field(dims, 0.5, seed=0)
+    A = G.variable_kappa(dims, kap, sig)
+    return dict(name=f"kappa3d_{N}_{splits[0]}x{splits[1]}x{splits[2]}", A=A, sigma=sig, nneg=k,
+                ndim=3, dims=dims, splits=tuple(splits), factor=FACTOR_ILU0, m=m, rank=rank,
+                kappa=kap)
+
+
+def batch2d_64sys(nsys=64, lo=64, hi=256, nrhs=4, seed=0):
+    """The batched workload: per system side N ~ U{lo..hi}, split ceil(N/32) per
+    side clipped to [4, 8], m ~ U{2..5}, r ~ {8, 16, 32}, sigma for 4 negative
+    eigenvalues, ILU(0)."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(lo, hi + 1, nsys)
+    ms = rng.integers(2, 6, nsys)
+    ranks = rng.choice(np.array([8, 16, 32]), nsys)
+    systems = []
+    for N, m, r in zip(sides.tolist(), ms.tolist(), ranks.tolist()):
+        sp = int(min(8, max(4, -(-N // 32))))
+        A, sig, k = _lap((N, N), 4)
+        systems.append(dict(A=A, sigma=sig, nneg=k, ndim=2, dims=(N, N, 1), splits=(sp, sp, 1),
+                            factor=FACTOR_ILU0, m=int(m), rank=int(r)))
+    return dict(name=f"batch2d_{nsys}sys", systems=systems, nrhs=nrhs)
+
+
+WORKLOADS = {
+    "lap2d_32_2x2_exact": lap2d_32_2x2_exact,
+    "lap3d_64_4x4x2_ilu0": lap3d_64_4x4x2_ilu0,
+    "batch2d_64sys": batch2d_64sys,
+    "kappa3d_48_3x3x3": kappa3d_48_3x3x3,
+    "cd3d_128_8x8x4_ilu0": cd3d_128_8x8x4_ilu0,
+}
+
+
+def small_problem(kind, dims, splits, factor=FACTOR_ILU0, m=3, rank=4, K=2, seed=0):
+    """A small problem of any family, for tests that must span several tiles and
+    ragged tails while the oracle finishes in seconds."""
+    nd = len(dims)
+    if kind == "lap":
+        A, sig, k = _lap(dims, K)
+    elif kind == "cd":
+        N = dims[0]
+        a = 50.0 / (N + 1.0)
+        sig, k = G.sigma_for_negative_count([G.convdiff_1d_eigs(N, a)] * nd, K)
+        A = G.convection_diffusion(dims, 50.0, sig)
+    elif kind == "kappa":
+        sig, k = G.sigma_for_negative_count([G.laplacian_1d_eigs(d) for d in dims], K)
+        A = G.variable_kappa(dims, G.kappa_field(dims, 0.5, seed), sig)
+    else:
+        raise ValueError(kind)
+    d3 = tuple(dims) + (1,) * (3 - nd)
+    s3 = tuple(splits) + (1,) * (3 - nd)
+    return dict(name=f"{kind}{nd}d_{'x'.join(map(str, dims))}", A=A, sigma=sig, nneg=k, ndim=nd,
+                dims=d3, splits=s3, factor=factor, m=m, rank=rank)
