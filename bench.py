@@ -1,0 +1,383 @@
+"""Benchmark of the PSLR hot path on GB300.
+
+One step = one PSLR preconditioner apply (Algorithm 3) of the workload through
+the C ABI, with the input resident in HBM.  The metric is the apply's
+algorithmic bandwidth (bytes it must stream with this layout, see
+pslr_get_info().apply_bytes_*) over its device time, next to FGMRES time to a
+1e-8 relative residual with the FP64 and the FP32 preconditioner.
+
+Default workload: 3D 7-point shifted Laplacian 64^3 (sigma for 20 negative
+eigenvalues), 4x4x2 subdomains, ILU(0), m = 3, r = 16, FP64 apply, one
+uniform[-1,1] right-hand side.  Its operator (~28 MB) fits in L2, so L2 is
+flushed (a 512 MB write) between timed applies and only the apply itself is
+inside each CUDA-event pair.
+
+    python bench.py [--gpus N --steps K --warmup W --workload NAME --impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the workload
+(the method is single-GPU: no collective exists on its path); value is the
+aggregate over ranks, timed as max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "PSLR apply GB/s (% HBM peak); FGMRES time-to-1e-8 residual, FP32 vs FP64 form"
+UNIT = "GB/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("pslr_apply.cu", "pslr_internal.h", "pslr_host.cpp"):
+        with open(os.path.join(ROOT, "paper_2002_00917_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(workload, prec):
+    """DRAM bytes per apply launch from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        e = d.get(f"{workload}/{prec}")
+        if e and e.get("source_hash") == kernel_source_hash():
+            return int(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_by_name(name):
+    from pslr_inputs import configs as C
+
+    return C.WORKLOADS[name]()
+
+
+def time_oracle_applies(w, ctx_lowrank, budget_s):
+    """The FP64 C oracle as it stands, single-threaded, on a bounded number of
+    applies of the same workload.  Returns (seconds per apply, applies)."""
+    import oracle as O
+
+    orc = O.from_workload(w)
+    V, H, G = ctx_lowrank
+    if V is not None and V.shape[1]:
+        orc.set_lowrank(w["m"], V, G)
+    else:
+        orc.set_lowrank(w["m"], None, None)
+    from pslr_inputs import generators as Gen
+
+    b, _ = Gen.uniform_rhs(w["A"], 0)
+    orc.apply(b)  # warm
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        orc.apply(b)
+        k += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return (time.perf_counter() - t0) / k, k
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle (plain C, one thread) on the same
+    workload and metric, each step a bounded sample of applies."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload_by_name(args.workload)
+    import oracle as O
+    from pslr_inputs import generators as Gen
+
+    orc = O.from_workload(w)
+    k, _ = orc.build_lowrank(w["m"], w["rank"], seed=0)
+    b, _ = Gen.uniform_rhs(w["A"], 0)
+    # bytes of one apply: same accounting as the GPU arm (taken from the GPU
+    # library only if it can be loaded without a device; else recomputed)
+    nbytes = reference_apply_bytes(w, k)
+    for _ in range(args.warmup):
+        orc.apply(b)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.apply(b)
+        times.append(time.perf_counter() - t0)
+    sec = sum(times)
+    value = args.steps * nbytes / sec / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["name"], "m": w["m"], "rank": k,
+                                        "n": w["A"].n, "subdomains": int(np.prod(w["splits"]))},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} FP64 applies of {w['name']} in the C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def reference_apply_bytes(w, rank):
+    """Algorithmic bytes of one FP64 apply as the GPU library counts them,
+    estimated on the host without a device: the library's own count is used
+    when available (it needs a GPU context), else this estimate from the
+    oracle's block sizes (FP64 values, 2-byte local / 4-byte global indices)."""
+    import oracle as O
+
+    o = O.from_workload(w)
+    m = w["m"]
+    nnz = {k: o.block(k)[1].size for k in ("B", "E", "F", "C0", "Cg")}
+    per = 8 + 2
+    fB = nnz["B"] * per + o.p * (2 + 8)
+    fC = nnz["C0"] * per + o.q * (2 + 8)
+    b = (m + 2) * fB + (m + 1) * fC + (m + 1) * (nnz["E"] * per) + (m + 1) * (nnz["F"] * per)
+    b += m * nnz["Cg"] * 12 + 2 * o.q * rank * 8
+    b += 8 * (2 * o.p + o.q + o.n + 4 * o.q + m * 4 * o.q)
+    return b
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="lap3d_64_4x4x2_ilu0")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fgmres", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2002_00917_gb300 import build as B
+    from paper_2002_00917_gb300 import pslr
+    from pslr_inputs import generators as Gen
+
+    if rank == 0 or world == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    w = workload_by_name(args.workload)
+    st_setup = time.perf_counter()
+    ctx = pslr.from_workload(w)
+    setup_s = time.perf_counter() - st_setup
+    t0 = time.perf_counter()
+    k, bst = ctx.build_lowrank(w["m"], w["rank"])
+    torch.cuda.synchronize()
+    lowrank_s = time.perf_counter() - t0
+    info = ctx.get_info()
+    bytes64, bytes32 = info["apply_bytes_fp64"], info["apply_bytes_fp32"]
+    b, xs = Gen.uniform_rhs(w["A"], 0)
+    bd = torch.tensor(b, device=dev)
+    zd = torch.empty_like(bd)
+    bf = bd.float()
+    zf = torch.empty_like(bf)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed_applies(bin_, zout, steps, warmup):
+        for _ in range(warmup):
+            ctx.apply(bin_, zout)
+        ctx.sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for e0, e1 in evs:
+            flush.fill_(1.0)  # evict L2 between timed applies (not timed)
+            e0.record(stream)
+            ctx.apply(bin_, zout)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.sync()
+        if dist:
+            dist.barrier()
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    with ClockSampler(local) as clk:
+        ms64 = timed_applies(bd, zd, args.steps, args.warmup)
+    ms32 = timed_applies(bf, zf, args.steps, args.warmup)
+    t64 = sum(ms64) / 1e3
+    t32 = sum(ms32) / 1e3
+    if dist:
+        tt = torch.tensor([t64, t32], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t64, t32 = tt.tolist()
+    value = world * args.steps * bytes64 / t64 / 1e9
+    value32 = world * args.steps * bytes32 / t32 / 1e9
+    peak, peak_kind = measured_peaks()
+
+    # end to end: host (pinned) b -> device -> apply -> host z, through the C ABI
+    bh = torch.tensor(b).pin_memory()
+    zh = torch.empty_like(bh).pin_memory()
+    for _ in range(3):
+        ctx.lib.pslr_apply_host(ctx.h, bh.data_ptr(), zh.data_ptr(), 1, 0, 0,
+                                pslr._stream(None))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    te2e = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 before each call (outside the timed window)
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        st = ctx.lib.pslr_apply_host(ctx.h, bh.data_ptr(), zh.data_ptr(), 1, 0, 0, pslr._stream(None))
+        te2e += time.perf_counter() - c0
+        assert st == 0, st
+    if dist:
+        tt = torch.tensor([te2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te2e = tt.item()
+    e2e_value = world * args.steps * bytes64 / te2e / 1e9
+
+    # FGMRES(40) to 1e-8 with the FP64 and the FP32 preconditioner
+    fg = {}
+    if not args.no_fgmres:
+        for name, prec in (("fp64", pslr.PSLR_FP64), ("fp32", pslr.PSLR_FP32)):
+            x = torch.empty_like(bd)
+            ctx.solve(bd, x, rtol=1e-8, restart=40, maxit=500, prec=prec)  # warm
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            its, rel, st = ctx.solve(bd, x, rtol=1e-8, restart=40, maxit=500, prec=prec)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            err = float(torch.linalg.norm(x - torch.tensor(xs, device=dev)) / np.linalg.norm(xs))
+            fg[name] = {"ms": s0.elapsed_time(s1), "iters": its, "relres": rel,
+                        "converged": st == 0, "rel_err_vs_xstar": err}
+
+    res = None
+    if rank == 0:
+        V, H, G = ctx.get_lowrank()
+        sec, napp = time_oracle_applies(w, (V, H, G), args.cpu_budget)
+        cpu_value = bytes64 / sec / 1e9
+        traffic = committed_traffic(w["name"], "fp64")
+        res = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t64 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "n": w["A"].n, "subdomains": info["s"], "p": info["p"],
+                       "q": info["q"], "m": w["m"], "rank": k, "factor": "ilu0" if w["factor"] == 0 else "lu",
+                       "l2": "flushed between timed applies (512 MB write)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
+            "roofline": {"bound": "hbm", "achieved": value / world, "peak": peak, "unit": "GB/s",
+                         "frac": value / world / peak, "peak_kind": peak_kind + " (burst copy)",
+                         "traffic": traffic, "bytes_per_launch": bytes64,
+                         "launch_us": 1e6 * t64 / args.steps},
+            "fp32_apply": {"value": value32, "unit": UNIT, "frac": value32 / world / peak,
+                           "bytes_per_launch": bytes32, "launch_us": 1e6 * t32 / args.steps,
+                           "dtype": "f32 (BF16 V)"},
+            "fgmres": fg,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w["A"].n,
+                    "d2h_bytes_per_step": 8 * w["A"].n},
+            "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{napp} FP64 applies of {w['name']} in the single-threaded C oracle"},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "setup_s": setup_s, "build_lowrank_s": lowrank_s,
+        }
+        print(json.dumps(res))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return res
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * pslr.h - C ABI of the GB300 (sm_103a) implementation of the PSLR (power
+ * Schur complement low-rank) preconditioner of Zheng, Xi and Saad,
+ * arXiv 2002.00917, and of the FGMRES solver it preconditions.
+ *
+ * Notation follows the paper.  After a graph partition into s subdomains
+ * (Section 2) the system reads [B E; F C] (x; y) = (f; g) (Eq. 2.1) with B, E
+ * and C0 = blockdiag(C_i) block diagonal and C_g = C - C0 the coupling of
+ * interface unknowns across subdomains.  The Schur complement S = C - F B^{-1} E
+ * (Eq. 2.2) is split as S = C0 - E_s (Eq. 3.1); P_m = sum_{i=0}^{m}
+ * (C0^{-1} E_s)^i C0^{-1} is the power series (Eq. 3.3); an r-step Arnoldi
+ * process on E_rr(m) = (E_s C0^{-1})^{m+1} (Eq. 3.16, Eq. 3.19) gives V and H,
+ * and G = (I - H)^{-1} - I (Eq. 3.17).  The preconditioner is Algorithm 3.
+ *
+ * Conventions for every entry point:
+ *  - No exception crosses this boundary; each call returns a pslr_status.
+ *    pslr_last_error() gives a message for the last failing call on a context.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued on it in stream order; a context must be
+ *    used from one stream at a time.
+ *  - Host arrays are read during the call and may be freed afterwards; the
+ *    context copies what it keeps.  Device vectors are owned by the caller,
+ *    are in the ORIGINAL ordering of A, and are column-major (n x nrhs) when
+ *    nrhs > 1.  The context owns every device buffer it allocates (factors,
+ *    V, G, Krylov workspace) and frees them in pslr_destroy().
+ *  - Asynchronous errors (a device-side wait that ran out, a NaN) are latched
+ *    in the context and reported by pslr_sync() or the next synchronising
+ *    call.
+ */
+#ifndef PSLR_H
+#define PSLR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pslr_ctx pslr_ctx;
+
+typedef enum {
+    PSLR_OK = 0,
+    PSLR_ERR_ARG = 1,           /* invalid argument (sizes, pointers, CSR)          */
+    PSLR_ERR_CUDA = 2,          /* a CUDA runtime call failed                       */
+    PSLR_ERR_ZERO_PIVOT = 3,    /* ILU(0) or LU met a zero pivot (Algorithm 1, 3-4) */
+    PSLR_ERR_BREAKDOWN = 4,     /* Arnoldi broke down; the rank was truncated       */
+    PSLR_ERR_SINGULAR_IMH = 5,  /* I - H singular: Eq. 3.15 assumes it is not       */
+    PSLR_ERR_NOT_CONVERGED = 6, /* FGMRES hit maxit                                 */
+    PSLR_ERR_NAN = 7,           /* a NaN / Inf appeared in a device reduction       */
+    PSLR_ERR_TIMEOUT = 8,       /* a device-side grid barrier gave up waiting       */
+    PSLR_ERR_STATE = 9,         /* call out of order (e.g. no low-rank built yet)   */
+    PSLR_ERR_TOO_LARGE = 10     /* a subdomain does not fit the on-chip working set */
+} pslr_status;
+
+/* Arithmetic of an apply: FP64 vectors and factors, or FP32 vectors and
+ * factors with V stored in BF16 (accumulation in FP32). */
+typedef enum { PSLR_FP64 = 0, PSLR_FP32 = 1 } pslr_prec;
+
+typedef struct {
+    /* Geometric split that stands in for the paper's METIS partition (Section
+     * 2): unknown idx = i + dims[0]*(j + dims[1]*k) goes to subdomain
+     * floor(i*splits[0]/dims[0]) + splits[0]*(floor(j*splits[1]/dims[1])
+     * + splits[1]*floor(k*splits[2]/dims[2])).  dims[0]*dims[1]*dims[2] must
+     * equal n.  Ignored when `part` is not NULL. */
+    int32_t dims[3];
+    int32_t splits[3];
+    const int32_t *part;  /* optional host array (length n) of subdomain ids 0..s-1 */
+    int32_t factor;       /* local factors of B_i and C_i: 0 = ILU(0), 1 = exact LU
+                             with partial pivoting (Algorithm 1, steps 2-5)         */
+    uint64_t seed;        /* SplitMix64 seed of the Arnoldi start vector            */
+} pslr_opts;
+
+typedef struct {
+    int32_t n, s, p, q;   /* unknowns, subdomains, interior, interface             */
+    int32_t m, rank;      /* series order and rank of the current low-rank term    */
+    int64_t nnz_A, nnz_ilu, nnz_lr; /* Section 4: nnz(A), nnz(ILU), nnz(V) + nnz(G) */
+    double fill_ilu, fill_lr, fill_total; /* Section 4 fill factors                 */
+    int32_t max_interior, max_interface;  /* largest p_i and q_i                    */
+    int32_t levels_B, levels_C0;          /* deepest triangular-solve level chain   */
+    int64_t apply_bytes_fp64, apply_bytes_fp32; /* algorithmic bytes of one apply   */
+} pslr_info;
+
+/*
+ * Reorder A (Section 2), extract B, E, F, C, C0, C_g (Eq. 2.1, Eq. 3.1), factor
+ * every B_i and C_i (Algorithm 1, steps 1-5), and upload everything to the
+ * current CUDA device.  A is host CSR: rowptr (n+1), colind (nnz, 0-based),
+ * val (nnz); every row must hold its diagonal entry and columns must be in
+ * range.  On success *out owns the new context and the low-rank term is empty
+ * (rank 0, m = 0) until pslr_build_lowrank() or pslr_set_lowrank().
+ * Errors: PSLR_ERR_ARG (bad CSR or options), PSLR_ERR_ZERO_PIVOT,
+ * PSLR_ERR_TOO_LARGE (a subdomain exceeds the on-chip vector budget),
+ * PSLR_ERR_CUDA.  *out is NULL on failure.
+ */
+pslr_status pslr_setup(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *val,
+                       const pslr_opts *opts, void *stream, pslr_ctx **out);
+
+/*
+ * Host-only dry run of pslr_setup: the same validation, reordering (Section 2),
+ * local factors and device layout, computed on the host without touching any
+ * GPU, so it runs where there is none.  Fills *info (with series order m and
+ * rank r as a later pslr_build_lowrank(m, r) would set them; apply_bytes_* is
+ * the algorithmic byte count of one apply) and, when not NULL, the maps of
+ * pslr_get_maps (host arrays of length n).  Same errors as pslr_setup except
+ * PSLR_ERR_CUDA; the shared-memory check uses the 227 KB per-CTA limit.
+ */
+pslr_status pslr_plan(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *val,
+                      const pslr_opts *opts, int32_t m, int32_t rank, pslr_info *info,
+                      int32_t *part, int32_t *is_interface, int32_t *perm);
+
+/*
+ * Algorithm 1, steps 6-8: an r-step Arnoldi process on E_rr(m) (Eq. 3.16),
+ * run on the device in FP64 with classical Gram-Schmidt applied twice, from
+ * the start vector v_1 = u/||u||, u_l = SplitMix64(opts.seed) output l mapped
+ * to [-1,1); then G = (I - H)^{-1} - I (Eq. 3.17) in FP64.  A breakdown
+ * (h_{j+1,j} <= 1e-12 ||H||_F) truncates the rank and returns
+ * PSLR_ERR_BREAKDOWN with the truncated term installed, unless full_rank != 0,
+ * in which case a fresh SplitMix64 vector (outputs t*q .. t*q+q-1 for the t-th
+ * vector) orthogonalised against V continues the basis.  rank is capped at q.
+ * Synchronises `stream`.
+ */
+pslr_status pslr_build_lowrank(pslr_ctx *c, int32_t m, int32_t rank, int32_t full_rank,
+                               void *stream);
+
+/*
+ * Install a low-rank term directly: V is host q x rank column-major in the
+ * interface numbering of pslr_get_maps(), G is host rank x rank column-major,
+ * both FP64 (the FP32 form stores V in BF16 and G in FP32).  rank 0 clears it.
+ */
+pslr_status pslr_set_lowrank(pslr_ctx *c, int32_t m, int32_t rank, const double *V,
+                             const double *G, void *stream);
+
+/*
+ * z = M^{-1} b with M^{-1} the PSLR operator of Algorithm 3 (Eq. 3.24):
+ *   t = g - F B^{-1} f;  t <- t + V G V^T t;  y = P_m t;  x = B^{-1}(f - E y).
+ * b_dev, z_dev: device arrays of n*nrhs elements, double for PSLR_FP64 and
+ * float for PSLR_FP32, original ordering, column-major; b and z must not
+ * overlap.  Enqueued on `stream`; does not synchronise.
+ */
+pslr_status pslr_apply(pslr_ctx *c, const void *b_dev, void *z_dev, int32_t nrhs, pslr_prec prec,
+                       void *stream);
+
+/*
+ * z = M^{-T} b, the exact transpose of Algorithm 3 (derived from its block
+ * form; the paper does not state it): h = g - E^T B^{-T} f;
+ * w = (I + V G^T V^T) P_m^T h;  x = B^{-T}(f - F^T w);  z = (x; w).
+ * Same argument conventions as pslr_apply.
+ */
+pslr_status pslr_apply_T(pslr_ctx *c, const void *b_dev, void *z_dev, int32_t nrhs,
+                         pslr_prec prec, void *stream);
+
+/*
+ * The same operator as pslr_apply (transpose != 0: pslr_apply_T) on HOST
+ * arrays: copies b (pinned or pageable host memory, n*nrhs elements of the
+ * precision's type) to the device, applies, copies z back and synchronises
+ * `stream`.  This is the end-to-end call of a user holding host data.
+ */
+pslr_status pslr_apply_host(pslr_ctx *c, const void *b_host, void *z_host, int32_t nrhs,
+                            pslr_prec prec, int32_t transpose, void *stream);
+
+/*
+ * Solve A x = b (transpose != 0: A^T x = b) with right-preconditioned flexible
+ * GMRES(restart) (Section 4: x0 = 0, stop when ||b - A x|| <= rtol ||b||, at
+ * most maxit iterations), preconditioned by pslr_apply (or pslr_apply_T) in
+ * precision `prec`.  Krylov vectors, the Hessenberg least-squares problem and
+ * the residual are FP64 in every case, so with PSLR_FP32 the outer iteration
+ * refines an FP32 preconditioner to FP64 accuracy.  b_dev, x_dev: device
+ * double arrays of length n (nrhs = 1 per call).  *iters (cumulative over
+ * restarts) and *relres (true residual ||b - A x||/||b|| in FP64) are written
+ * on return.  Synchronises `stream` once per restart cycle.
+ * Returns PSLR_OK or PSLR_ERR_NOT_CONVERGED (x holds the last iterate).
+ */
+pslr_status pslr_solve(pslr_ctx *c, const double *b_dev, double *x_dev, double rtol,
+                       int32_t restart, int32_t maxit, pslr_prec prec, int32_t transpose,
+                       int32_t *iters, double *relres, void *stream);
+
+/* y = A x (transpose: A^T x) on device double vectors of length n (FP64 SpMV
+ * with the matrix given to pslr_setup, original ordering). */
+pslr_status pslr_matvec(pslr_ctx *c, const double *x_dev, double *y_dev, int32_t transpose,
+                        void *stream);
+
+/* Copy the reordering of Section 2 to host arrays of length n (any may be
+ * NULL): part[v] subdomain of unknown v, is_interface[v] 0/1, perm[t] = the
+ * original index of reordered unknown t (interiors by subdomain, then
+ * interfaces by subdomain, each in increasing original index). */
+pslr_status pslr_get_maps(const pslr_ctx *c, int32_t *part, int32_t *is_interface, int32_t *perm);
+
+/* Copy V (q x rank), H and G (rank x rank), column-major FP64, to host
+ * arrays sized for the current rank (pslr_get_info().rank); any may be NULL. */
+pslr_status pslr_get_lowrank(const pslr_ctx *c, double *V, double *H, double *G);
+
+pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info);
+
+/* Synchronise `stream` and report any latched asynchronous error. */
+pslr_status pslr_sync(pslr_ctx *c, void *stream);
+
+/* Device-side grid-barrier wait limit in polls (default 2^22, about 0.5 s);
+ * 0 makes every wait give up at once, which tests use to exercise the
+ * PSLR_ERR_TIMEOUT path.  Returns the previous value. */
+int64_t pslr_set_wait_limit(pslr_ctx *c, int64_t polls);
+
+const char *pslr_last_error(const pslr_ctx *c);
+const char *pslr_status_string(pslr_status s);
+void pslr_destroy(pslr_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSLR_H */

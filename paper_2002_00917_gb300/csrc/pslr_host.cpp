@@ -1,0 +1,1491 @@
+// Host side of libpslr: set-up (Section 2 reordering, Algorithm 1 local
+// factors), device layout, and the C ABI of include/pslr.h.
+//
+// The set-up is plain C++ on the host (it is not part of the timed apply):
+// geometric partition, interface detection, the [interior by subdomain |
+// interface by subdomain] permutation, the per-subdomain blocks B_i, E_i, F_i,
+// C_i and the rows of C_g, ILU(0) or dense pivoted LU of every B_i and C_i,
+// level scheduling of the triangular factors, and packing into the segment
+// layout described in pslr_internal.h, for the forward and transposed
+// directions and for FP64 and FP32 values.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/pslr.h"
+#include "pslr_internal.h"
+
+namespace pslr {
+// kernels (pslr_apply.cu, pslr_krylov.cu)
+cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, cudaStream_t st);
+cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, cudaStream_t st);
+cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, cudaStream_t st);
+int max_coresident_apply(int smem, bool fp32);
+int krylov_blocks(int n);
+void launch_cgs_pass(int n, int k, const double *V, int64_t ld, double *w, const double *hsub, int norm,
+                     double *part, double *res, unsigned *ticket, const int32_t *rp, const int32_t *ci,
+                     const double *av, const double *z, const int *skip, cudaStream_t st);
+void launch_hessenberg(int j, const double *h1, const double *h2, const double *wn2, double *H, int ldh,
+                       double *hn, int givens, double *rot, double *gam, double tol_abs, int *state,
+                       int *skip, cudaStream_t st);
+void launch_normalize(int n, const double *w, double *v, const double *hn, const int *skip,
+                      cudaStream_t st);
+void launch_gemv_add(int n, int k, const double *Z, int64_t ld, const double *y, double *x,
+                     cudaStream_t st);
+void launch_residual(int n, const int32_t *rp, const int32_t *ci, const double *av, const double *x,
+                     const double *b, double *r, cudaStream_t st);
+void launch_d2f(int n, const double *a, float *b, const int *skip, cudaStream_t st);
+void launch_f2d(int n, const float *a, double *b, const int *skip, cudaStream_t st);
+void launch_splitmix(int n, uint64_t seed, uint64_t j0, double *v, cudaStream_t st);
+}  // namespace pslr
+
+using namespace pslr;
+
+namespace {
+
+// ---------------------------------------------------------------- utilities
+
+struct Csr {  // local sparse block, columns ascending in each row
+    int nr = 0, nc = 0;
+    std::vector<int32_t> rp, ci;
+    std::vector<double> v;
+};
+
+struct Row {  // one row of a segment: output row, off-diagonal entries, diagonal
+    int row;
+    std::vector<std::pair<int32_t, double>> e;
+    double diag;
+};
+
+uint16_t f32_to_bf16(float f) {  // round to nearest even
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0xffff) ? 0x40 : 0));
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+// Segments of one direction and one precision, accumulated on the host.
+struct SegStore {
+    std::vector<char> bytes;
+    std::vector<SegDesc> desc;
+    int max_bytes = 0;
+};
+
+template <class T, class IDX>
+void pack_segment(SegStore &S, const std::vector<Row> &rows, size_t b, size_t e, bool diag, int zero_col) {
+    int n = (int)(e - b), w = 0;
+    for (size_t i = b; i < e; ++i) w = std::max<int>(w, (int)rows[i].e.size());
+    const int np = seg_npad(n);
+    const int64_t nbytes = seg_bytes<T, IDX>(n, w, diag);
+    SegDesc d;
+    d.off = (int64_t)S.bytes.size();
+    d.bytes = n > 0 ? (int32_t)nbytes : 0;
+    d.n = (uint16_t)n;
+    d.w = (uint8_t)w;
+    d.flags = (uint8_t)((diag ? (unsigned)kSegDiag : 0u) | (sizeof(IDX) == 4 ? (unsigned)kSegGlobalCols : 0u));
+    if (n > 0) {
+        S.bytes.resize(S.bytes.size() + nbytes, 0);
+        char *base = S.bytes.data() + d.off;
+        T *vals = reinterpret_cast<T *>(base);
+        T *dinv = reinterpret_cast<T *>(base + (size_t)np * w * sizeof(T));
+        IDX *cols = reinterpret_cast<IDX *>(base + (size_t)np * w * sizeof(T) + (diag ? np * sizeof(T) : 0));
+        uint16_t *rws = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(cols) + (size_t)np * w * sizeof(IDX));
+        for (int j = 0; j < np; ++j) {
+            const bool real = j < n;
+            const Row *R = real ? &rows[b + j] : nullptr;
+            for (int k = 0; k < w; ++k) {
+                const bool has = real && k < (int)R->e.size();
+                vals[(size_t)k * np + j] = has ? (T)R->e[k].second : T(0);
+                cols[(size_t)k * np + j] = has ? (IDX)R->e[k].first : (IDX)zero_col;
+            }
+            if (diag) dinv[j] = real ? (T)(1.0 / R->diag) : T(0);
+            rws[j] = real ? (uint16_t)R->row : (uint16_t)0;
+        }
+        S.max_bytes = std::max<int>(S.max_bytes, (int)nbytes);
+    }
+    S.desc.push_back(d);
+}
+
+// Split a row list into segments within kSegBudget bytes / kSegMaxRows rows.
+// Returns the number of segments appended (an empty list appends none).
+template <class T, class IDX>
+int pack_rows(SegStore &S, const std::vector<Row> &rows, bool diag, int zero_col) {
+    int cnt = 0;
+    size_t b = 0;
+    while (b < rows.size()) {
+        size_t e = b;
+        int w = 0;
+        while (e < rows.size() && (int)(e - b) < kSegMaxRows) {
+            int w2 = std::max<int>(w, (int)rows[e].e.size());
+            if (e > b && seg_bytes<T, IDX>((int)(e - b + 1), w2, diag) > kSegBudget) break;
+            w = w2;
+            ++e;
+        }
+        pack_segment<T, IDX>(S, rows, b, e, diag, zero_col);
+        ++cnt;
+        b = e;
+    }
+    return cnt;
+}
+
+// Level schedule of a triangular sweep: lower (deps on smaller columns,
+// processed 0..n-1) or upper (deps on larger columns, processed n-1..0).
+// Returns the rows of every level, levels in dependency order.
+std::vector<std::vector<int>> levels(const Csr &T, bool lower) {
+    int n = T.nr;
+    std::vector<int> lev(n, 0);
+    int maxl = -1;
+    for (int t = 0; t < n; ++t) {
+        int r = lower ? t : n - 1 - t;
+        int l = 0;
+        for (int k = T.rp[r]; k < T.rp[r + 1]; ++k) {
+            int c = T.ci[k];
+            if ((lower && c < r) || (!lower && c > r)) l = std::max(l, lev[c] + 1);
+        }
+        lev[r] = l;
+        maxl = std::max(maxl, l);
+    }
+    std::vector<std::vector<int>> L(maxl + 1);
+    for (int r = 0; r < n; ++r) L[lev[r]].push_back(r);
+    return L;
+}
+
+// Rows of a triangular sweep level: off-diagonal entries of T in the row and
+// (with_diag) its diagonal.
+std::vector<Row> sweep_rows(const Csr &T, const std::vector<int> &lv, bool lower, bool with_diag) {
+    std::vector<Row> rows;
+    rows.reserve(lv.size());
+    for (int r : lv) {
+        Row R;
+        R.row = r;
+        R.diag = 1.0;
+        for (int k = T.rp[r]; k < T.rp[r + 1]; ++k) {
+            int c = T.ci[k];
+            if (c == r) R.diag = T.v[k];
+            else if ((lower && c < r) || (!lower && c > r)) R.e.push_back({c, T.v[k]});
+        }
+        if (!with_diag) R.diag = 1.0;
+        rows.push_back(std::move(R));
+    }
+    return rows;
+}
+
+Csr transpose(const Csr &A) {
+    Csr T;
+    T.nr = A.nc;
+    T.nc = A.nr;
+    T.rp.assign(T.nr + 1, 0);
+    for (int k = 0; k < (int)A.ci.size(); ++k) T.rp[A.ci[k] + 1]++;
+    for (int i = 0; i < T.nr; ++i) T.rp[i + 1] += T.rp[i];
+    T.ci.resize(A.ci.size());
+    T.v.resize(A.v.size());
+    std::vector<int32_t> pos(T.rp.begin(), T.rp.end() - 1);
+    for (int r = 0; r < A.nr; ++r)
+        for (int k = A.rp[r]; k < A.rp[r + 1]; ++k) {
+            int p = pos[A.ci[k]]++;
+            T.ci[p] = r;
+            T.v[p] = A.v[k];
+        }
+    return T;
+}
+
+// Rows of an ELL block (all rows with at least one entry).
+std::vector<Row> ell_rows(const Csr &A) {
+    std::vector<Row> rows;
+    for (int r = 0; r < A.nr; ++r) {
+        if (A.rp[r + 1] == A.rp[r]) continue;
+        Row R;
+        R.row = r;
+        R.diag = 1.0;
+        for (int k = A.rp[r]; k < A.rp[r + 1]; ++k) R.e.push_back({A.ci[k], A.v[k]});
+        rows.push_back(std::move(R));
+    }
+    return rows;
+}
+
+// ILU(0) of a local block in place (IKJ order, natural ordering, no
+// pivoting): strictly lower part becomes L (unit diagonal), the rest U.
+bool ilu0_inplace(Csr &M) {
+    const int n = M.nr;
+    std::vector<int> dpos(n, -1), where(n, -1);
+    for (int i = 0; i < n; ++i)
+        for (int k = M.rp[i]; k < M.rp[i + 1]; ++k)
+            if (M.ci[k] == i) dpos[i] = k;
+    for (int i = 0; i < n; ++i) {
+        if (dpos[i] < 0) return false;
+        for (int k = M.rp[i]; k < M.rp[i + 1]; ++k) where[M.ci[k]] = k;
+        for (int k = M.rp[i]; k < dpos[i]; ++k) {
+            const int j = M.ci[k];
+            const double piv = M.v[dpos[j]];
+            if (piv == 0.0) return false;
+            const double l = M.v[k] / piv;
+            M.v[k] = l;
+            for (int t = dpos[j] + 1; t < M.rp[j + 1]; ++t) {
+                const int w = where[M.ci[t]];
+                if (w >= 0) M.v[w] -= l * M.v[t];
+            }
+        }
+        if (M.v[dpos[i]] == 0.0) return false;
+        for (int k = M.rp[i]; k < M.rp[i + 1]; ++k) where[M.ci[k]] = -1;
+    }
+    return true;
+}
+
+// Dense LU with partial pivoting (largest |a|, first on ties) of a local
+// block; returns L (unit diagonal implied, strictly lower) and U (upper with
+// diagonal) as one combined sparse factor, and the row order piv: the
+// factored matrix is B(piv, :), i.e. (P b)_r = b[piv[r]].
+bool dense_lu(const Csr &M, Csr &LU, std::vector<uint16_t> &piv) {
+    const int n = M.nr;
+    std::vector<double> a((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = M.rp[i]; k < M.rp[i + 1]; ++k) a[(size_t)i * n + M.ci[k]] = M.v[k];
+    std::vector<int> perm(n);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int k = 0; k < n; ++k) {
+        int pr = k;
+        double best = std::fabs(a[(size_t)k * n + k]);
+        for (int i = k + 1; i < n; ++i) {
+            double v = std::fabs(a[(size_t)i * n + k]);
+            if (v > best) {
+                best = v;
+                pr = i;
+            }
+        }
+        if (best == 0.0) return false;
+        if (pr != k) {
+            for (int j = 0; j < n; ++j) std::swap(a[(size_t)k * n + j], a[(size_t)pr * n + j]);
+            std::swap(perm[k], perm[pr]);
+        }
+        const double d = a[(size_t)k * n + k];
+        for (int i = k + 1; i < n; ++i) {
+            double &l = a[(size_t)i * n + k];
+            if (l == 0.0) continue;
+            l /= d;
+            for (int j = k + 1; j < n; ++j) a[(size_t)i * n + j] -= l * a[(size_t)k * n + j];
+        }
+    }
+    LU.nr = LU.nc = n;
+    LU.rp.assign(n + 1, 0);
+    LU.ci.clear();
+    LU.v.clear();
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) {
+            double v = a[(size_t)i * n + j];
+            if (v != 0.0 || j == i) {
+                LU.ci.push_back(j);
+                LU.v.push_back(v);
+            }
+        }
+        LU.rp[i + 1] = (int32_t)LU.ci.size();
+    }
+    piv.resize(n);
+    for (int i = 0; i < n; ++i) piv[i] = (uint16_t)perm[i];
+    return true;
+}
+
+// Split the combined factor into L (strictly lower entries) and U.
+void split_lu(const Csr &LU, Csr &Lo, Csr &Up) {
+    Lo.nr = Lo.nc = Up.nr = Up.nc = LU.nr;
+    Lo.rp.assign(LU.nr + 1, 0);
+    Up.rp.assign(LU.nr + 1, 0);
+    Lo.ci.clear(); Lo.v.clear(); Up.ci.clear(); Up.v.clear();
+    for (int i = 0; i < LU.nr; ++i) {
+        for (int k = LU.rp[i]; k < LU.rp[i + 1]; ++k) {
+            if (LU.ci[k] < i) {
+                Lo.ci.push_back(LU.ci[k]);
+                Lo.v.push_back(LU.v[k]);
+            } else {
+                Up.ci.push_back(LU.ci[k]);
+                Up.v.push_back(LU.v[k]);
+            }
+        }
+        Lo.rp[i + 1] = (int32_t)Lo.ci.size();
+        Up.rp[i + 1] = (int32_t)Up.ci.size();
+    }
+}
+
+template <class X>
+cudaError_t upload(X **dst, const std::vector<X> &src) {
+    *dst = nullptr;
+    size_t bytes = std::max<size_t>(src.size() * sizeof(X), 16);
+    cudaError_t e = cudaMalloc((void **)dst, bytes);
+    if (e != cudaSuccess) return e;
+    if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(X), cudaMemcpyHostToDevice);
+    return e;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+
+struct OpSetHost {
+    char *seg = nullptr;
+    SegDesc *desc = nullptr;
+    int32_t *sub_desc = nullptr;
+    int32_t *cnt = nullptr;
+    int slot_bytes = 0;
+    int max_desc = 0;
+    int64_t seg_total = 0;
+    int64_t cat_bytes[kNCnt] = {0, 0, 0, 0, 0, 0, 0};  // segment bytes per category, all subdomains
+    int64_t nnz_cg = 0;
+    int smem = 0;
+    int grid = 0;
+};
+
+struct pslr_ctx {
+    int n = 0, s = 0, p = 0, q = 0, factor = 0;
+    uint64_t seed = 0;
+    std::vector<int32_t> part, iface, perm, ioff, goff;
+    int max_p = 0, max_q = 0, levels_B = 0, levels_C = 0;
+    int64_t nnz_A = 0, nnz_ilu = 0;
+    std::vector<int32_t> h_rp, h_ci;
+    std::vector<double> h_av;
+    // device: maps and matrices
+    int32_t *d_perm = nullptr, *d_ioff = nullptr, *d_goff = nullptr;
+    uint16_t *d_bpiv = nullptr, *d_cpiv = nullptr;
+    OpSetHost ops[2][2];  // [direction: 0 forward, 1 transposed][precision]
+    int32_t *d_rp = nullptr, *d_ci = nullptr, *d_rpT = nullptr, *d_ciT = nullptr;
+    double *d_av = nullptr, *d_avT = nullptr;
+    // low-rank term
+    int m = 0, r = 0;
+    std::vector<double> V, H, G;
+    double *d_V = nullptr;       // q x r FP64 (leading dimension q)
+    uint16_t *d_Vb = nullptr;    // q x r BF16
+    double *d_G = nullptr, *d_GT = nullptr;
+    float *d_Gf = nullptr, *d_GTf = nullptr;
+    // apply scratch
+    double *d_wbuf = nullptr, *d_acc = nullptr, *d_part = nullptr;
+    unsigned *d_bar = nullptr;
+    int *d_err = nullptr;
+    long long wait_limit = 1ll << 22;
+    // Krylov workspace (allocated on demand)
+    int kr_restart = 0;
+    double *d_kV = nullptr, *d_kZ = nullptr, *d_kw = nullptr, *d_kr = nullptr, *d_kH = nullptr;
+    double *d_krot = nullptr, *d_kgam = nullptr, *d_kh1 = nullptr, *d_kh2 = nullptr, *d_kscal = nullptr;
+    double *d_kpart = nullptr;
+    unsigned *d_kticket = nullptr;
+    int *d_kstate = nullptr, *d_kskip = nullptr;
+    float *d_kf_in = nullptr, *d_kf_out = nullptr;
+    double *d_eab = nullptr;  // E_rr scratch 2(q+1)
+    void *d_io_b = nullptr, *d_io_z = nullptr;  // pslr_apply_host staging
+    size_t io_bytes = 0;
+    std::string err;
+};
+
+namespace {
+
+pslr_status fail(pslr_ctx *c, pslr_status st, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+void cfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+void free_opset(OpSetHost &o) {
+    cfree(o.seg);
+    cfree(o.desc);
+    cfree(o.sub_desc);
+    cfree(o.cnt);
+    o = OpSetHost();
+}
+
+void free_krylov(pslr_ctx *c) {
+    for (void *p : {(void *)c->d_kV, (void *)c->d_kZ, (void *)c->d_kw, (void *)c->d_kr, (void *)c->d_kH,
+                    (void *)c->d_krot, (void *)c->d_kgam, (void *)c->d_kh1, (void *)c->d_kh2,
+                    (void *)c->d_kscal, (void *)c->d_kpart, (void *)c->d_kticket, (void *)c->d_kstate,
+                    (void *)c->d_kskip, (void *)c->d_kf_in, (void *)c->d_kf_out})
+        cfree(p);
+    c->d_kV = c->d_kZ = c->d_kw = c->d_kr = c->d_kH = c->d_krot = c->d_kgam = nullptr;
+    c->d_kh1 = c->d_kh2 = c->d_kscal = c->d_kpart = nullptr;
+    c->d_kticket = nullptr;
+    c->d_kstate = c->d_kskip = nullptr;
+    c->d_kf_in = c->d_kf_out = nullptr;
+    c->kr_restart = 0;
+}
+
+void free_lowrank(pslr_ctx *c) {
+    cfree(c->d_V); cfree(c->d_Vb); cfree(c->d_G); cfree(c->d_GT);
+    cfree(c->d_Gf); cfree(c->d_GTf); cfree(c->d_part);
+    c->d_V = nullptr; c->d_Vb = nullptr; c->d_G = c->d_GT = nullptr; c->d_Gf = c->d_GTf = nullptr;
+    c->d_part = nullptr;
+    c->r = 0;
+    c->V.clear(); c->H.clear(); c->G.clear();
+}
+
+// Per-subdomain local structures, kept only during set-up.
+struct Local {
+    Csr B, E, F, C0, Cg;        // Cg columns are global interface indices
+    Csr BL, BU, CL, CU;         // factors
+    std::vector<uint16_t> bpiv, cpiv;
+};
+
+template <class T>
+void pack_direction(const std::vector<Local> &loc, const std::vector<int> &np, const std::vector<int> &nq,
+                    bool transposed, int q, SegStore &S, std::vector<int32_t> &sub_desc,
+                    std::vector<int32_t> &cnt, int &levB, int &levC) {
+    const int s = (int)loc.size();
+    sub_desc.assign(s, 0);
+    cnt.assign((size_t)kNCnt * s, 0);
+    for (int i = 0; i < s; ++i) {
+        const Local &Lc = loc[i];
+        sub_desc[i] = (int32_t)S.desc.size();
+        int *k = &cnt[(size_t)kNCnt * i];
+        if (!transposed) {
+            k[kE] = pack_rows<T, uint16_t>(S, ell_rows(Lc.E), false, nq[i]);
+            k[kF] = pack_rows<T, uint16_t>(S, ell_rows(Lc.F), false, np[i]);
+            k[kCg] = pack_rows<T, int32_t>(S, ell_rows(Lc.Cg), false, q);
+            auto lb = levels(Lc.BL, true), ub = levels(Lc.BU, false);
+            auto lc = levels(Lc.CL, true), uc = levels(Lc.CU, false);
+            levB = std::max<int>(levB, (int)(lb.size() + ub.size()));
+            levC = std::max<int>(levC, (int)(lc.size() + uc.size()));
+            for (auto &lv : lb) k[kB1] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.BL, lv, true, false), false, np[i]);
+            for (auto &lv : ub) k[kB2] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.BU, lv, false, true), true, np[i]);
+            for (auto &lv : lc) k[kC1] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.CL, lv, true, false), false, nq[i]);
+            for (auto &lv : uc) k[kC2] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.CU, lv, false, true), true, nq[i]);
+        } else {
+            // E-slot: F_i^T (interior rows <- interface cols); F-slot: E_i^T.
+            k[kE] = pack_rows<T, uint16_t>(S, ell_rows(transpose(Lc.F)), false, nq[i]);
+            k[kF] = pack_rows<T, uint16_t>(S, ell_rows(transpose(Lc.E)), false, np[i]);
+            k[kCg] = 0;  // filled by the caller (needs C_g of every subdomain)
+            // B^{-T} = U^{-T} L^{-T}: sweep 1 is U^T (lower, with diagonal), sweep 2 L^T (upper)
+            Csr BUt = transpose(Lc.BU), BLt = transpose(Lc.BL);
+            Csr CUt = transpose(Lc.CU), CLt = transpose(Lc.CL);
+            auto l1 = levels(BUt, true), l2 = levels(BLt, false);
+            auto l3 = levels(CUt, true), l4 = levels(CLt, false);
+            for (auto &lv : l1) k[kB1] += pack_rows<T, uint16_t>(S, sweep_rows(BUt, lv, true, true), true, np[i]);
+            for (auto &lv : l2) k[kB2] += pack_rows<T, uint16_t>(S, sweep_rows(BLt, lv, false, false), false, np[i]);
+            for (auto &lv : l3) k[kC1] += pack_rows<T, uint16_t>(S, sweep_rows(CUt, lv, true, true), true, nq[i]);
+            for (auto &lv : l4) k[kC2] += pack_rows<T, uint16_t>(S, sweep_rows(CLt, lv, false, false), false, nq[i]);
+        }
+    }
+}
+
+}  // namespace
+
+// Insert the C_g^T segments of every subdomain into a transposed table.  The
+// table is rebuilt subdomain by subdomain so that each subdomain's descriptors
+// stay contiguous in the [E, F, Cg, B1, B2, C1, C2] order.
+template <class T>
+static void insert_cgT(SegStore &S, std::vector<int32_t> &sub_desc, std::vector<int32_t> &cnt,
+                       const std::vector<Csr> &cgT_rows, int q) {
+    const int s = (int)sub_desc.size();
+    std::vector<SegDesc> nd;
+    std::vector<int32_t> nsub(s);
+    for (int i = 0; i < s; ++i) {
+        nsub[i] = (int32_t)nd.size();
+        int *k = &cnt[(size_t)kNCnt * i];
+        int b = sub_desc[i];
+        for (int t = 0; t < k[kE] + k[kF]; ++t) nd.push_back(S.desc[b + t]);
+        size_t before = S.desc.size();
+        k[kCg] = pack_rows<T, int32_t>(S, ell_rows(cgT_rows[i]), false, q);
+        for (size_t t = before; t < S.desc.size(); ++t) nd.push_back(S.desc[t]);
+        S.desc.resize(before);
+        int nl = k[kB1] + k[kB2] + k[kC1] + k[kC2];
+        for (int t = 0; t < nl; ++t) nd.push_back(S.desc[b + k[kE] + k[kF] + t]);
+    }
+    S.desc.swap(nd);
+    sub_desc.swap(nsub);
+}
+
+template <class T>
+static pslr_status finish_opset(pslr_ctx *c, OpSetHost &o, SegStore &S, const std::vector<int32_t> &sub_desc,
+                                const std::vector<int32_t> &cnt, bool fp32, bool plan_only) {
+    o.slot_bytes = align_up(std::max(S.max_bytes, 128), 128);
+    o.max_desc = 0;
+    for (int i = 0; i < c->s; ++i) {
+        int t = 0;
+        for (int k = 0; k < kNCnt; ++k) t += cnt[(size_t)kNCnt * i + k];
+        o.max_desc = std::max(o.max_desc, t);
+    }
+    o.seg_total = (int64_t)S.bytes.size();
+    for (int i = 0; i < c->s; ++i) {
+        int d = sub_desc[i];
+        for (int k = 0; k < kNCnt; ++k)
+            for (int t = 0; t < cnt[(size_t)kNCnt * i + k]; ++t) o.cat_bytes[k] += S.desc[d++].bytes;
+    }
+    if (S.bytes.empty()) S.bytes.resize(16, 0);
+    const bool piv = c->factor == 1;
+    SmemLayout L = smem_layout(o.slot_bytes, o.max_desc, c->max_p, c->max_q, fp32 ? 4 : 8, piv);
+    o.smem = L.total;
+    int optin = 227 * 1024;  // sm_100-class opt-in limit; queried from the device when there is one
+    if (!plan_only) {
+        CK(upload(&o.seg, S.bytes));
+        CK(upload(&o.desc, S.desc));
+        CK(upload(&o.sub_desc, sub_desc));
+        CK(upload(&o.cnt, cnt));
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    }
+    if (o.smem + 1024 > optin)
+        return fail(c, PSLR_ERR_TOO_LARGE,
+                    "a subdomain needs %d bytes of shared memory (limit %d): use more subdomains",
+                    o.smem, optin - 1024);
+    o.grid = 0;
+    return PSLR_OK;
+}
+
+// ------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char *pslr_status_string(pslr_status s) {
+    switch (s) {
+    case PSLR_OK: return "ok";
+    case PSLR_ERR_ARG: return "invalid argument";
+    case PSLR_ERR_CUDA: return "CUDA error";
+    case PSLR_ERR_ZERO_PIVOT: return "zero pivot in a local factorization";
+    case PSLR_ERR_BREAKDOWN: return "Arnoldi breakdown (rank truncated)";
+    case PSLR_ERR_SINGULAR_IMH: return "I - H is singular";
+    case PSLR_ERR_NOT_CONVERGED: return "FGMRES did not converge";
+    case PSLR_ERR_NAN: return "NaN or Inf";
+    case PSLR_ERR_TIMEOUT: return "device-side wait timed out";
+    case PSLR_ERR_STATE: return "call out of order";
+    case PSLR_ERR_TOO_LARGE: return "subdomain too large";
+    }
+    return "unknown status";
+}
+
+const char *pslr_last_error(const pslr_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void pslr_destroy(pslr_ctx *c) {
+    if (!c) return;
+    for (auto &d : c->ops)
+        for (auto &o : d) free_opset(o);
+    free_krylov(c);
+    free_lowrank(c);
+    for (void *p : {(void *)c->d_perm, (void *)c->d_ioff, (void *)c->d_goff, (void *)c->d_bpiv,
+                    (void *)c->d_cpiv, (void *)c->d_rp, (void *)c->d_ci, (void *)c->d_rpT, (void *)c->d_ciT,
+                    (void *)c->d_av, (void *)c->d_avT, (void *)c->d_wbuf, (void *)c->d_acc, (void *)c->d_bar,
+                    (void *)c->d_err, (void *)c->d_eab, c->d_io_b, c->d_io_z})
+        cfree(p);
+    delete c;
+}
+
+}  // extern "C"
+
+// Everything pslr_setup does; with plan_only the device is never touched (no
+// uploads, no allocations), which pslr_plan uses.
+static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                              const double *val, const pslr_opts *opts, bool plan_only) {
+    auto bail = [](pslr_status st) { return st; };
+    c->n = n;
+    c->factor = opts->factor;
+    c->seed = opts->seed;
+    if (opts->factor != 0 && opts->factor != 1) return bail(fail(c, PSLR_ERR_ARG, "factor must be 0 or 1"));
+    // --- validate CSR: monotone row pointers, columns in range and ascending, diagonal present
+    if (rowptr[0] != 0) return bail(fail(c, PSLR_ERR_ARG, "rowptr[0] != 0"));
+    for (int i = 0; i < n; ++i) {
+        if (rowptr[i + 1] < rowptr[i]) return bail(fail(c, PSLR_ERR_ARG, "rowptr not monotone at %d", i));
+        bool diag = false;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            int j = colind[k];
+            if (j < 0 || j >= n) return bail(fail(c, PSLR_ERR_ARG, "column %d out of range in row %d", j, i));
+            if (k > rowptr[i] && colind[k - 1] >= j)
+                return bail(fail(c, PSLR_ERR_ARG, "columns not strictly ascending in row %d", i));
+            if (!std::isfinite(val[k])) return bail(fail(c, PSLR_ERR_ARG, "non-finite value in row %d", i));
+            diag |= (j == i);
+        }
+        if (!diag) return bail(fail(c, PSLR_ERR_ZERO_PIVOT, "row %d has no diagonal entry", i));
+    }
+    const int64_t nnz = rowptr[n];
+    c->nnz_A = nnz;
+    c->h_rp.assign(rowptr, rowptr + n + 1);
+    c->h_ci.assign(colind, colind + nnz);
+    c->h_av.assign(val, val + nnz);
+
+    // --- Section 2: partition and reordering
+    c->part.resize(n);
+    if (opts->part) {
+        int mx = -1;
+        for (int v = 0; v < n; ++v) {
+            if (opts->part[v] < 0) return bail(fail(c, PSLR_ERR_ARG, "negative part id"));
+            c->part[v] = opts->part[v];
+            mx = std::max(mx, (int)opts->part[v]);
+        }
+        c->s = mx + 1;
+    } else {
+        const int64_t Nx = opts->dims[0], Ny = opts->dims[1], Nz = opts->dims[2];
+        const int Px = opts->splits[0], Py = opts->splits[1], Pz = opts->splits[2];
+        if (Nx <= 0 || Ny <= 0 || Nz <= 0 || Nx * Ny * Nz != n)
+            return bail(fail(c, PSLR_ERR_ARG, "dims do not multiply to n"));
+        if (Px < 1 || Py < 1 || Pz < 1 || Px > Nx || Py > Ny || Pz > Nz)
+            return bail(fail(c, PSLR_ERR_ARG, "splits out of range"));
+        for (int64_t v = 0; v < n; ++v) {
+            int64_t i = v % Nx, j = (v / Nx) % Ny, k = v / (Nx * Ny);
+            c->part[v] = (int32_t)((i * Px) / Nx + Px * ((j * Py) / Ny + Py * ((k * Pz) / Nz)));
+        }
+        c->s = Px * Py * Pz;
+    }
+    const int s = c->s;
+    c->iface.assign(n, 0);
+    for (int v = 0; v < n; ++v)
+        for (int k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+            int w = colind[k];
+            if (w != v && c->part[w] != c->part[v]) c->iface[v] = c->iface[w] = 1;
+        }
+    // counting sort by (interface?, part, index): stable in the original index
+    std::vector<int64_t> cntI(s + 1, 0), cntG(s + 1, 0);
+    for (int v = 0; v < n; ++v) (c->iface[v] ? cntG : cntI)[c->part[v] + 1]++;
+    for (int i = 0; i < s; ++i) {
+        cntI[i + 1] += cntI[i];
+        cntG[i + 1] += cntG[i];
+    }
+    c->p = (int)cntI[s];
+    c->q = (int)cntG[s];
+    c->ioff.assign(cntI.begin(), cntI.end());
+    c->goff.assign(cntG.begin(), cntG.end());
+    c->perm.assign(n, 0);
+    std::vector<int32_t> loc(n), posI(c->ioff.begin(), c->ioff.end() - 1), posG(c->goff.begin(), c->goff.end() - 1);
+    for (int v = 0; v < n; ++v) {
+        int i = c->part[v];
+        if (c->iface[v]) {
+            loc[v] = posG[i] - c->goff[i];
+            c->perm[c->p + posG[i]++] = v;
+        } else {
+            loc[v] = posI[i] - c->ioff[i];
+            c->perm[posI[i]++] = v;
+        }
+    }
+    std::vector<int> np(s), nq(s);
+    for (int i = 0; i < s; ++i) {
+        np[i] = c->ioff[i + 1] - c->ioff[i];
+        nq[i] = c->goff[i + 1] - c->goff[i];
+        c->max_p = std::max(c->max_p, np[i]);
+        c->max_q = std::max(c->max_q, nq[i]);
+    }
+    if (c->max_p >= 65535 || c->max_q >= 65535)
+        return bail(fail(c, PSLR_ERR_TOO_LARGE, "a subdomain has more than 65534 interior or interface unknowns"));
+
+    // --- Eq. 2.1 / Eq. 3.1: local blocks (rows visited in the reordered order)
+    std::vector<Local> L(s);
+    for (int i = 0; i < s; ++i) {
+        Local &Lc = L[i];
+        for (Csr *M : {&Lc.B, &Lc.E}) { M->nr = np[i]; M->rp.assign(1, 0); }
+        for (Csr *M : {&Lc.F, &Lc.C0, &Lc.Cg}) { M->nr = nq[i]; M->rp.assign(1, 0); }
+        Lc.B.nc = np[i]; Lc.E.nc = nq[i]; Lc.F.nc = np[i]; Lc.C0.nc = nq[i]; Lc.Cg.nc = c->q;
+        for (int t = 0; t < np[i]; ++t) {
+            int v = c->perm[c->ioff[i] + t];
+            for (int k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+                int w = colind[k];
+                Csr &M = c->iface[w] ? Lc.E : Lc.B;
+                M.ci.push_back(loc[w]);
+                M.v.push_back(val[k]);
+            }
+            Lc.B.rp.push_back((int32_t)Lc.B.ci.size());
+            Lc.E.rp.push_back((int32_t)Lc.E.ci.size());
+        }
+        for (int t = 0; t < nq[i]; ++t) {
+            int v = c->perm[c->p + c->goff[i] + t];
+            std::vector<std::pair<int32_t, double>> cg;
+            for (int k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+                int w = colind[k];
+                if (!c->iface[w]) {
+                    Lc.F.ci.push_back(loc[w]);
+                    Lc.F.v.push_back(val[k]);
+                } else if (c->part[w] == i) {
+                    Lc.C0.ci.push_back(loc[w]);
+                    Lc.C0.v.push_back(val[k]);
+                } else {
+                    cg.push_back({c->goff[c->part[w]] + loc[w], val[k]});
+                }
+            }
+            std::sort(cg.begin(), cg.end());
+            for (auto &e : cg) {
+                Lc.Cg.ci.push_back(e.first);
+                Lc.Cg.v.push_back(e.second);
+            }
+            Lc.F.rp.push_back((int32_t)Lc.F.ci.size());
+            Lc.C0.rp.push_back((int32_t)Lc.C0.ci.size());
+            Lc.Cg.rp.push_back((int32_t)Lc.Cg.ci.size());
+        }
+    }
+
+    // --- Algorithm 1, steps 2-5: local factors
+    std::vector<uint16_t> bpiv, cpiv;
+    if (c->factor == 1) {
+        bpiv.resize(c->p);
+        cpiv.resize(c->q);
+    }
+    for (int i = 0; i < s; ++i) {
+        Local &Lc = L[i];
+        Csr fb, fc;
+        if (c->factor == 0) {
+            fb = Lc.B;
+            fc = Lc.C0;
+            if (!ilu0_inplace(fb) || !ilu0_inplace(fc))
+                return bail(fail(c, PSLR_ERR_ZERO_PIVOT, "ILU(0) met a zero pivot in subdomain %d", i));
+        } else {
+            if (np[i] > 4096 || nq[i] > 4096)
+                return bail(fail(c, PSLR_ERR_TOO_LARGE, "exact local LU is limited to blocks of 4096 rows"));
+            if (!dense_lu(Lc.B, fb, Lc.bpiv) || !dense_lu(Lc.C0, fc, Lc.cpiv))
+                return bail(fail(c, PSLR_ERR_ZERO_PIVOT, "singular local block in subdomain %d", i));
+            std::copy(Lc.bpiv.begin(), Lc.bpiv.end(), bpiv.begin() + c->ioff[i]);
+            std::copy(Lc.cpiv.begin(), Lc.cpiv.end(), cpiv.begin() + c->goff[i]);
+        }
+        c->nnz_ilu += (int64_t)fb.ci.size() + (int64_t)fc.ci.size();
+        split_lu(fb, Lc.BL, Lc.BU);
+        split_lu(fc, Lc.CL, Lc.CU);
+    }
+
+    // --- device layout: both directions, both precisions
+    std::vector<Csr> cgT(s);
+    {
+        // rows of C_g^T owned by subdomain i: column l of C_g for l in its interface range
+        std::vector<std::vector<std::pair<int32_t, double>>> colsT(c->q);
+        for (int i = 0; i < s; ++i)
+            for (int t = 0; t < nq[i]; ++t)
+                for (int k = L[i].Cg.rp[t]; k < L[i].Cg.rp[t + 1]; ++k)
+                    colsT[L[i].Cg.ci[k]].push_back({c->goff[i] + t, L[i].Cg.v[k]});
+        for (int i = 0; i < s; ++i) {
+            Csr &M = cgT[i];
+            M.nr = nq[i];
+            M.nc = c->q;
+            M.rp.assign(1, 0);
+            for (int t = 0; t < nq[i]; ++t) {
+                auto &v = colsT[c->goff[i] + t];
+                std::sort(v.begin(), v.end());
+                for (auto &e : v) {
+                    M.ci.push_back(e.first);
+                    M.v.push_back(e.second);
+                }
+                M.rp.push_back((int32_t)M.ci.size());
+            }
+        }
+    }
+    for (int dir = 0; dir < 2; ++dir)
+        for (int prec = 0; prec < 2; ++prec) {
+            SegStore S;
+            std::vector<int32_t> sub_desc, cnt;
+            int lb = 0, lc = 0;
+            pslr_status st;
+            if (prec == 0) {
+                pack_direction<double>(L, np, nq, dir == 1, c->q, S, sub_desc, cnt, lb, lc);
+                if (dir == 1) insert_cgT<double>(S, sub_desc, cnt, cgT, c->q);
+                st = finish_opset<double>(c, c->ops[dir][prec], S, sub_desc, cnt, false, plan_only);
+            } else {
+                pack_direction<float>(L, np, nq, dir == 1, c->q, S, sub_desc, cnt, lb, lc);
+                if (dir == 1) insert_cgT<float>(S, sub_desc, cnt, cgT, c->q);
+                st = finish_opset<float>(c, c->ops[dir][prec], S, sub_desc, cnt, true, plan_only);
+            }
+            if (st != PSLR_OK) return bail(st);
+            if (dir == 0 && prec == 0) {
+                c->levels_B = lb;
+                c->levels_C = lc;
+            }
+        }
+    if (plan_only) return PSLR_OK;
+    for (int prec = 0; prec < 2; ++prec) {
+        int smem = std::max(c->ops[0][prec].smem, c->ops[1][prec].smem);
+        int cap = max_coresident_apply(smem, prec == 1);
+        if (cap <= 0) return bail(fail(c, PSLR_ERR_CUDA, "persistent kernel cannot be made resident"));
+        for (int dir = 0; dir < 2; ++dir) {
+            c->ops[dir][prec].smem = smem;
+            c->ops[dir][prec].grid = std::min(cap, s);
+        }
+    }
+    CK(upload(&c->d_perm, c->perm));
+    CK(upload(&c->d_ioff, c->ioff));
+    CK(upload(&c->d_goff, c->goff));
+    if (c->factor == 1) {
+        CK(upload(&c->d_bpiv, bpiv));
+        CK(upload(&c->d_cpiv, cpiv));
+    }
+    CK(upload(&c->d_rp, c->h_rp));
+    CK(upload(&c->d_ci, c->h_ci));
+    CK(upload(&c->d_av, c->h_av));
+    {
+        Csr A;
+        A.nr = A.nc = n;
+        A.rp = c->h_rp;
+        A.ci = c->h_ci;
+        A.v = c->h_av;
+        Csr At = transpose(A);
+        CK(upload(&c->d_rpT, At.rp));
+        CK(upload(&c->d_ciT, At.ci));
+        CK(upload(&c->d_avT, At.v));
+    }
+    CK(cudaMalloc(&c->d_wbuf, sizeof(double) * 2 * (c->q + 1)));
+    CK(cudaMemset(c->d_wbuf, 0, sizeof(double) * 2 * (c->q + 1)));
+    CK(cudaMalloc(&c->d_acc, sizeof(double) * (c->q + 1)));
+    CK(cudaMalloc(&c->d_eab, sizeof(double) * 2 * (c->q + 1)));
+    CK(cudaMalloc(&c->d_bar, 2 * sizeof(unsigned)));
+    CK(cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned)));
+    CK(cudaMalloc(&c->d_err, sizeof(int)));
+    CK(cudaMemset(c->d_err, 0, sizeof(int)));
+    CK(cudaDeviceSynchronize());
+    return PSLR_OK;
+}
+
+extern "C" {
+
+pslr_status pslr_setup(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *val,
+                       const pslr_opts *opts, void *stream, pslr_ctx **out) {
+    if (!out) return PSLR_ERR_ARG;
+    *out = nullptr;
+    if (n <= 0 || !rowptr || !colind || !val || !opts) return PSLR_ERR_ARG;
+    (void)stream;
+    pslr_ctx *c = new pslr_ctx();
+    pslr_status st = setup_impl(c, n, rowptr, colind, val, opts, false);
+    if (st != PSLR_OK) {
+        fprintf(stderr, "pslr_setup: %s\n", c->err.c_str());
+        pslr_destroy(c);
+        return st;
+    }
+    *out = c;
+    return PSLR_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- applies
+
+template <class T>
+static void fill_params(pslr_ctx *c, ApplyParams<T> &P, int dir, int prec) {
+    const OpSetHost &o = c->ops[dir][prec];
+    P.ops.segbase = o.seg;
+    P.ops.desc = o.desc;
+    P.ops.sub_desc = o.sub_desc;
+    P.ops.cnt = o.cnt;
+    P.ops.pivot_post = dir;
+    P.ops.lowrank_after = dir;
+    P.s = c->s;
+    P.p = c->p;
+    P.q = c->q;
+    P.r = c->r;
+    P.m = c->m;
+    P.grid = o.grid;
+    P.max_p = c->max_p;
+    P.max_q = c->max_q;
+    P.max_desc = o.max_desc;
+    P.slot_bytes = o.slot_bytes;
+    P.ioff = c->d_ioff;
+    P.goff = c->d_goff;
+    P.perm = c->d_perm;
+    P.bpiv = c->d_bpiv;
+    P.cpiv = c->d_cpiv;
+    P.wbuf = reinterpret_cast<T *>(c->d_wbuf);
+    P.acc = reinterpret_cast<T *>(c->d_acc);
+    P.part = reinterpret_cast<T *>(c->d_part);
+    P.bar = c->d_bar;
+    P.err = c->d_err;
+    P.skip = nullptr;
+    P.wait_limit = c->wait_limit;
+}
+
+static pslr_status apply_one(pslr_ctx *c, const void *b, void *z, int prec, int dir, const int *skip,
+                             cudaStream_t st) {
+    const OpSetHost &o = c->ops[dir][prec];
+    cudaError_t e;
+    if (prec == PSLR_FP64) {
+        ApplyParams<double> P;
+        fill_params(c, P, dir, prec);
+        P.V = c->d_V;
+        P.G = dir ? c->d_GT : c->d_G;
+        P.b = static_cast<const double *>(b);
+        P.z = static_cast<double *>(z);
+        P.skip = skip;
+        e = launch_apply_fp64(P, o.smem, st);
+    } else {
+        ApplyParams<float> P;
+        fill_params(c, P, dir, prec);
+        P.V = c->d_Vb;
+        P.G = dir ? c->d_GTf : c->d_Gf;
+        P.b = static_cast<const float *>(b);
+        P.z = static_cast<float *>(z);
+        P.skip = skip;
+        e = launch_apply_fp32(P, o.smem, st);
+    }
+    if (e != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "apply launch: %s", cudaGetErrorString(e));
+    return PSLR_OK;
+}
+
+static pslr_status apply_dir(pslr_ctx *c, const void *b, void *z, int32_t nrhs, pslr_prec prec, int dir,
+                             void *stream) {
+    if (!c || !b || !z || nrhs < 1 || (prec != PSLR_FP64 && prec != PSLR_FP32))
+        return fail(c, PSLR_ERR_ARG, "apply: bad argument");
+    const size_t es = prec == PSLR_FP64 ? 8 : 4;
+    for (int j = 0; j < nrhs; ++j) {
+        pslr_status st = apply_one(c, static_cast<const char *>(b) + j * es * c->n,
+                                   static_cast<char *>(z) + j * es * c->n, prec, dir, nullptr,
+                                   static_cast<cudaStream_t>(stream));
+        if (st != PSLR_OK) return st;
+    }
+    return PSLR_OK;
+}
+
+// Algorithmic bytes of one forward apply (Algorithm 3) with this layout: each
+// pass streams its segments once - m+2 B solves, m+1 C0 solves, m+1 passes of
+// E and of F, m of C_g, 2 of V - plus the vectors each phase reads or writes
+// (b gathered twice for f, once for g; z written once; per phase the
+// interface iterate, accumulator and the C_g gathers).
+static int64_t pslr_apply_bytes(const pslr_ctx *c, int prec) {
+    const OpSetHost &o = c->ops[0][prec];
+    const int64_t m = c->m, r = c->r, n = c->n, p = c->p, q = c->q;
+    const int64_t vs = prec == 0 ? 8 : 4, vb = prec == 0 ? 8 : 2;
+    int64_t b = (m + 2) * (o.cat_bytes[kB1] + o.cat_bytes[kB2]) +
+                (m + 1) * (o.cat_bytes[kC1] + o.cat_bytes[kC2]) + (m + 1) * o.cat_bytes[kE] +
+                (m + 1) * o.cat_bytes[kF] + m * o.cat_bytes[kCg];
+    b += 2 * q * r * vb;
+    int64_t vec = 2 * p + q + n;                // b reads, z write
+    vec += (r > 0 ? 2 * q : 0) + 2 * q;         // t staging, w_0 and acc
+    vec += m * (q + q + 2 * q);                 // per term: w_{k-1} read, w_k write, acc r/w
+    b += vec * vs;
+    return b;
+}
+
+extern "C" {
+
+pslr_status pslr_apply(pslr_ctx *c, const void *b_dev, void *z_dev, int32_t nrhs, pslr_prec prec,
+                       void *stream) {
+    return apply_dir(c, b_dev, z_dev, nrhs, prec, 0, stream);
+}
+
+pslr_status pslr_apply_T(pslr_ctx *c, const void *b_dev, void *z_dev, int32_t nrhs, pslr_prec prec,
+                         void *stream) {
+    return apply_dir(c, b_dev, z_dev, nrhs, prec, 1, stream);
+}
+
+pslr_status pslr_sync(pslr_ctx *c, void *stream) {
+    if (!c) return PSLR_ERR_ARG;
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int e = 0;
+    CK(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        CK(cudaMemset(c->d_err, 0, sizeof(int)));
+        CK(cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned)));
+        return fail(c, static_cast<pslr_status>(e), "device reported: %s",
+                    pslr_status_string(static_cast<pslr_status>(e)));
+    }
+    return PSLR_OK;
+}
+
+pslr_status pslr_apply_host(pslr_ctx *c, const void *b_host, void *z_host, int32_t nrhs, pslr_prec prec,
+                            int32_t transpose, void *stream) {
+    if (!c || !b_host || !z_host || nrhs < 1 || (prec != PSLR_FP64 && prec != PSLR_FP32))
+        return fail(c, PSLR_ERR_ARG, "apply_host: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)(prec == PSLR_FP64 ? 8 : 4) * c->n * nrhs;
+    if (bytes > c->io_bytes) {  // staging buffers owned by the context, grown on demand
+        CK(cudaStreamSynchronize(st));
+        cudaFree(c->d_io_b);
+        cudaFree(c->d_io_z);
+        c->d_io_b = c->d_io_z = nullptr;
+        c->io_bytes = 0;
+        CK(cudaMalloc(&c->d_io_b, bytes));
+        CK(cudaMalloc(&c->d_io_z, bytes));
+        c->io_bytes = bytes;
+    }
+    CK(cudaMemcpyAsync(c->d_io_b, b_host, bytes, cudaMemcpyHostToDevice, st));
+    pslr_status s = apply_dir(c, c->d_io_b, c->d_io_z, nrhs, prec, transpose ? 1 : 0, stream);
+    if (s == PSLR_OK) CK(cudaMemcpyAsync(z_host, c->d_io_z, bytes, cudaMemcpyDeviceToHost, st));
+    pslr_status s2 = pslr_sync(c, stream);
+    return s != PSLR_OK ? s : s2;
+}
+
+int64_t pslr_set_wait_limit(pslr_ctx *c, int64_t polls) {
+    if (!c) return -1;
+    int64_t old = c->wait_limit;
+    c->wait_limit = polls;
+    return old;
+}
+
+pslr_status pslr_get_maps(const pslr_ctx *c, int32_t *part, int32_t *is_interface, int32_t *perm) {
+    if (!c) return PSLR_ERR_ARG;
+    if (part) std::copy(c->part.begin(), c->part.end(), part);
+    if (is_interface) std::copy(c->iface.begin(), c->iface.end(), is_interface);
+    if (perm) std::copy(c->perm.begin(), c->perm.end(), perm);
+    return PSLR_OK;
+}
+
+pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info) {
+    if (!c || !info) return PSLR_ERR_ARG;
+    pslr_info I;
+    std::memset(&I, 0, sizeof(I));
+    I.n = c->n;
+    I.s = c->s;
+    I.p = c->p;
+    I.q = c->q;
+    I.m = c->m;
+    I.rank = c->r;
+    I.nnz_A = c->nnz_A;
+    I.nnz_ilu = c->nnz_ilu;
+    I.nnz_lr = (int64_t)c->q * c->r + (int64_t)c->r * c->r;
+    I.fill_ilu = (double)I.nnz_ilu / (double)I.nnz_A;
+    I.fill_lr = (double)I.nnz_lr / (double)I.nnz_A;
+    I.fill_total = I.fill_ilu + I.fill_lr;
+    I.max_interior = c->max_p;
+    I.max_interface = c->max_q;
+    I.levels_B = c->levels_B;
+    I.levels_C0 = c->levels_C;
+    I.apply_bytes_fp64 = pslr_apply_bytes(c, 0);
+    I.apply_bytes_fp32 = pslr_apply_bytes(c, 1);
+    *info = I;
+    return PSLR_OK;
+}
+
+pslr_status pslr_plan(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *val,
+                      const pslr_opts *opts, int32_t m, int32_t rank, pslr_info *info, int32_t *part,
+                      int32_t *is_interface, int32_t *perm) {
+    if (n <= 0 || !rowptr || !colind || !val || !opts || m < 0 || rank < 0) return PSLR_ERR_ARG;
+    pslr_ctx *c = new pslr_ctx();
+    pslr_status st = setup_impl(c, n, rowptr, colind, val, opts, true);
+    if (st == PSLR_OK) {
+        c->m = m;
+        c->r = std::min(std::min<int>(rank, c->q), kMaxRank);
+        if (info) pslr_get_info(c, info);
+        pslr_get_maps(c, part, is_interface, perm);
+    } else {
+        fprintf(stderr, "pslr_plan: %s\n", c->err.c_str());
+    }
+    pslr_destroy(c);
+    return st;
+}
+
+pslr_status pslr_matvec(pslr_ctx *c, const double *x_dev, double *y_dev, int32_t transpose, void *stream) {
+    if (!c || !x_dev || !y_dev) return fail(c, PSLR_ERR_ARG, "matvec: bad argument");
+    launch_residual(c->n, transpose ? c->d_rpT : c->d_rp, transpose ? c->d_ciT : c->d_ci,
+                    transpose ? c->d_avT : c->d_av, x_dev, nullptr, y_dev, static_cast<cudaStream_t>(stream));
+    CK(cudaGetLastError());
+    return PSLR_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ low-rank term
+
+// G = (I - H)^{-1} - I by LU with partial pivoting of I - H (Eq. 3.17).
+// H and G are r x r column-major.  Returns false if I - H is singular.
+static bool compute_G(int r, const std::vector<double> &H, std::vector<double> &G) {
+    std::vector<double> a((size_t)r * r);
+    double amax = 0.0;
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < r; ++j) {
+            a[(size_t)i * r + j] = (i == j ? 1.0 : 0.0) - H[(size_t)j * r + i];
+            amax = std::max(amax, std::fabs(a[(size_t)i * r + j]));
+        }
+    std::vector<int> perm(r);
+    for (int i = 0; i < r; ++i) perm[i] = i;
+    for (int k = 0; k < r; ++k) {
+        int pr = k;
+        double best = std::fabs(a[(size_t)k * r + k]);
+        for (int i = k + 1; i < r; ++i)
+            if (std::fabs(a[(size_t)i * r + k]) > best) {
+                best = std::fabs(a[(size_t)i * r + k]);
+                pr = i;
+            }
+        if (!(best > 1e-14 * amax)) return false;
+        if (pr != k) {
+            for (int j = 0; j < r; ++j) std::swap(a[(size_t)k * r + j], a[(size_t)pr * r + j]);
+            std::swap(perm[k], perm[pr]);
+        }
+        for (int i = k + 1; i < r; ++i) {
+            double l = a[(size_t)i * r + k] / a[(size_t)k * r + k];
+            a[(size_t)i * r + k] = l;
+            for (int j = k + 1; j < r; ++j) a[(size_t)i * r + j] -= l * a[(size_t)k * r + j];
+        }
+    }
+    G.assign((size_t)r * r, 0.0);
+    std::vector<double> x(r);
+    for (int j = 0; j < r; ++j) {
+        for (int i = 0; i < r; ++i) x[i] = (perm[i] == j) ? 1.0 : 0.0;
+        for (int i = 0; i < r; ++i)
+            for (int l = 0; l < i; ++l) x[i] -= a[(size_t)i * r + l] * x[l];
+        for (int i = r - 1; i >= 0; --i) {
+            for (int l = i + 1; l < r; ++l) x[i] -= a[(size_t)i * r + l] * x[l];
+            x[i] /= a[(size_t)i * r + i];
+        }
+        for (int i = 0; i < r; ++i) G[(size_t)j * r + i] = x[i] - (i == j ? 1.0 : 0.0);
+    }
+    return true;
+}
+
+// Install V (device FP64 q x r, already in c->d_V) plus host G: derived copies.
+static pslr_status install_lowrank(pslr_ctx *c, int m, int r, const std::vector<double> &G) {
+    const int q = c->q;
+    c->m = m;
+    c->r = r;
+    c->G = G;
+    cudaFree(c->d_Vb); cudaFree(c->d_G); cudaFree(c->d_GT); cudaFree(c->d_Gf); cudaFree(c->d_GTf);
+    cudaFree(c->d_part);
+    c->d_Vb = nullptr; c->d_G = c->d_GT = nullptr; c->d_Gf = c->d_GTf = nullptr; c->d_part = nullptr;
+    if (r == 0) return PSLR_OK;
+    c->V.resize((size_t)q * r);
+    CK(cudaMemcpy(c->V.data(), c->d_V, sizeof(double) * (size_t)q * r, cudaMemcpyDeviceToHost));
+    std::vector<uint16_t> vb((size_t)q * r);
+    for (size_t i = 0; i < vb.size(); ++i) vb[i] = f32_to_bf16((float)c->V[i]);
+    std::vector<double> GT((size_t)r * r);
+    std::vector<float> Gf((size_t)r * r), GTf((size_t)r * r);
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < r; ++j) {
+            GT[(size_t)j * r + i] = G[(size_t)i * r + j];
+            Gf[(size_t)j * r + i] = (float)G[(size_t)j * r + i];
+            GTf[(size_t)j * r + i] = (float)G[(size_t)i * r + j];
+        }
+    CK(upload(&c->d_Vb, vb));
+    CK(upload(&c->d_G, G));
+    CK(upload(&c->d_GT, GT));
+    CK(upload(&c->d_Gf, Gf));
+    CK(upload(&c->d_GTf, GTf));
+    CK(cudaMalloc(&c->d_part, sizeof(double) * (size_t)c->s * r + 16));
+    return PSLR_OK;
+}
+
+extern "C" {
+
+pslr_status pslr_set_lowrank(pslr_ctx *c, int32_t m, int32_t rank, const double *V, const double *G,
+                             void *stream) {
+    if (!c || m < 0 || rank < 0 || rank > kMaxRank || rank > c->q || (rank > 0 && (!V || !G)))
+        return fail(c, PSLR_ERR_ARG, "set_lowrank: bad argument (rank must be <= %d and <= q)", kMaxRank);
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    free_lowrank(c);
+    if (rank > 0) {
+        CK(cudaMalloc(&c->d_V, sizeof(double) * (size_t)c->q * rank));
+        CK(cudaMemcpy(c->d_V, V, sizeof(double) * (size_t)c->q * rank, cudaMemcpyHostToDevice));
+    }
+    std::vector<double> g(G, G + (size_t)rank * rank);
+    pslr_status st = install_lowrank(c, m, rank, g);
+    if (st == PSLR_OK) c->H.clear();
+    return st;
+}
+
+pslr_status pslr_get_lowrank(const pslr_ctx *c, double *V, double *H, double *G) {
+    if (!c) return PSLR_ERR_ARG;
+    if (V && c->r) std::copy(c->V.begin(), c->V.end(), V);
+    if (H && c->r && !c->H.empty()) std::copy(c->H.begin(), c->H.end(), H);
+    if (G && c->r) std::copy(c->G.begin(), c->G.end(), G);
+    return PSLR_OK;
+}
+
+}  // extern "C"
+
+// Krylov workspace for vectors of length len and up to kcols basis columns.
+struct KWork {
+    double *part = nullptr, *h1 = nullptr, *h2 = nullptr, *wn2 = nullptr, *hn = nullptr;
+    unsigned *ticket = nullptr;
+    int nblk = 0;
+};
+
+static pslr_status kwork_alloc(pslr_ctx *c, KWork &W, int len, int kcols) {
+    W.nblk = krylov_blocks(len);
+    CK(cudaMalloc(&W.part, sizeof(double) * (size_t)W.nblk * (kcols + 1)));
+    CK(cudaMalloc(&W.h1, sizeof(double) * (kcols + 1)));
+    CK(cudaMalloc(&W.h2, sizeof(double) * (kcols + 1)));
+    CK(cudaMalloc(&W.wn2, sizeof(double) * 2));
+    CK(cudaMalloc(&W.hn, sizeof(double) * 2));
+    CK(cudaMalloc(&W.ticket, sizeof(unsigned)));
+    CK(cudaMemset(W.ticket, 0, sizeof(unsigned)));
+    return PSLR_OK;
+}
+
+static void kwork_free(KWork &W) {
+    cudaFree(W.part); cudaFree(W.h1); cudaFree(W.h2); cudaFree(W.wn2); cudaFree(W.hn); cudaFree(W.ticket);
+    W = KWork();
+}
+
+// w <- w - V(:,0:k)(V^T w) twice (CGS2); h (device) = summed coefficients,
+// wn2 = ||w||^2.  With k == 0 only the norm is taken.
+static void cgs2(KWork &W, int len, int k, const double *V, int64_t ld, double *w, const int32_t *rp,
+                 const int32_t *ci, const double *av, const double *z, const int *skip, cudaStream_t st) {
+    if (k > 0) {
+        launch_cgs_pass(len, k, V, ld, w, nullptr, 0, W.part, W.h1, W.ticket, rp, ci, av, z, skip, st);
+        launch_cgs_pass(len, k, V, ld, w, W.h1, 0, W.part, W.h2, W.ticket, nullptr, nullptr, nullptr,
+                        nullptr, skip, st);
+        launch_cgs_pass(len, k, V, ld, w, W.h2, 1, W.part, W.wn2, W.ticket, nullptr, nullptr, nullptr,
+                        nullptr, skip, st);
+    } else {
+        launch_cgs_pass(len, 0, V, ld, w, nullptr, 1, W.part, W.wn2, W.ticket, rp, ci, av, z, skip, st);
+    }
+}
+
+static pslr_status launch_err(pslr_ctx *c, const double *vin, double *vout, int m, cudaStream_t st) {
+    const OpSetHost &o = c->ops[0][0];
+    ErrParams<double> P;
+    P.ops.segbase = o.seg;
+    P.ops.desc = o.desc;
+    P.ops.sub_desc = o.sub_desc;
+    P.ops.cnt = o.cnt;
+    P.ops.pivot_post = 0;
+    P.ops.lowrank_after = 0;
+    P.s = c->s;
+    P.p = c->p;
+    P.q = c->q;
+    P.m = m;
+    P.grid = o.grid;
+    P.max_p = c->max_p;
+    P.max_q = c->max_q;
+    P.max_desc = o.max_desc;
+    P.slot_bytes = o.slot_bytes;
+    P.ioff = c->d_ioff;
+    P.goff = c->d_goff;
+    P.bpiv = c->d_bpiv;
+    P.cpiv = c->d_cpiv;
+    P.vin = vin;
+    P.vout = vout;
+    P.abuf = c->d_eab;
+    P.bar = c->d_bar;
+    P.err = c->d_err;
+    P.wait_limit = c->wait_limit;
+    cudaError_t e = launch_err_fp64(P, o.smem, st);
+    if (e != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "E_rr launch: %s", cudaGetErrorString(e));
+    return PSLR_OK;
+}
+
+extern "C" {
+
+pslr_status pslr_build_lowrank(pslr_ctx *c, int32_t m, int32_t rank, int32_t full_rank, void *stream) {
+    if (!c || m < 0 || rank < 0) return fail(c, PSLR_ERR_ARG, "build_lowrank: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaStreamSynchronize(st));
+    free_lowrank(c);
+    const int q = c->q;
+    if (rank > q) rank = q;
+    if (rank > kMaxRank) return fail(c, PSLR_ERR_ARG, "rank must be <= %d", kMaxRank);
+    c->m = m;
+    if (rank == 0) return install_lowrank(c, m, 0, {});
+    const int r = rank;
+    double *Vq = nullptr, *w = nullptr;
+    CK(cudaMalloc(&Vq, sizeof(double) * (size_t)q * (r + 1)));
+    CK(cudaMalloc(&w, sizeof(double) * (size_t)q));
+    KWork W;
+    pslr_status ks = kwork_alloc(c, W, q, r + 1);
+    auto cleanup = [&]() {
+        cudaFree(w);
+        kwork_free(W);
+    };
+    if (ks != PSLR_OK) {
+        cudaFree(Vq);
+        cleanup();
+        return ks;
+    }
+    std::vector<double> Hb((size_t)(r + 1) * r, 0.0);  // (r+1) x r column-major
+    double hn = 0.0, hf2 = 0.0;
+    int kept = r, tvec = 0;
+    pslr_status status = PSLR_OK;
+    // v_1 = u / ||u||, u = SplitMix64 draws
+    launch_splitmix(q, c->seed, 0, Vq, st);
+    cgs2(W, q, 0, Vq, q, Vq, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    {
+        double u2 = 0.0;
+        CK(cudaMemcpyAsync(&u2, W.wn2, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const double un = std::sqrt(u2);
+        CK(cudaMemcpyAsync(W.hn, &un, sizeof(double), cudaMemcpyHostToDevice, st));
+        launch_normalize(q, Vq, Vq, W.hn, nullptr, st);
+    }
+    std::vector<double> hcol(r + 2);
+    for (int j = 0; j < r; ++j) {
+        pslr_status es = launch_err(c, Vq + (size_t)j * q, w, m, st);
+        if (es != PSLR_OK) { status = es; break; }
+        cgs2(W, q, j + 1, Vq, q, w, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+        CK(cudaMemcpyAsync(hcol.data(), W.h1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
+        std::vector<double> h2(j + 1);
+        CK(cudaMemcpyAsync(h2.data(), W.h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
+        double wn2 = 0.0;
+        CK(cudaMemcpyAsync(&wn2, W.wn2, sizeof(double), cudaMemcpyDeviceToHost, st));
+        pslr_status ss = pslr_sync(c, stream);
+        if (ss != PSLR_OK) { status = ss; break; }
+        hn = std::sqrt(wn2);
+        for (int i = 0; i <= j; ++i) {
+            double h = hcol[i] + h2[i];
+            Hb[(size_t)j * (r + 1) + i] = h;
+            hf2 += h * h;
+        }
+        hf2 += wn2;
+        if (!std::isfinite(hn) || !std::isfinite(hf2)) { status = fail(c, PSLR_ERR_NAN, "NaN in Arnoldi"); break; }
+        if (j == r - 1) break;
+        if (hn <= 1e-12 * std::sqrt(hf2)) {
+            if (!full_rank) {
+                kept = j + 1;
+                status = PSLR_ERR_BREAKDOWN;
+                break;
+            }
+            ++tvec;
+            double *vn = Vq + (size_t)(j + 1) * q;
+            launch_splitmix(q, c->seed, (uint64_t)tvec * q, vn, st);
+            cgs2(W, q, j + 1, Vq, q, vn, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+            double nn2 = 0.0;
+            CK(cudaMemcpyAsync(&nn2, W.wn2, sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            double nn = std::sqrt(nn2);
+            CK(cudaMemcpyAsync(W.hn, &nn, sizeof(double), cudaMemcpyHostToDevice, st));
+            launch_normalize(q, vn, vn, W.hn, nullptr, st);
+            Hb[(size_t)j * (r + 1) + j + 1] = 0.0;
+        } else {
+            Hb[(size_t)j * (r + 1) + j + 1] = hn;
+            CK(cudaMemcpyAsync(W.hn, &hn, sizeof(double), cudaMemcpyHostToDevice, st));
+            launch_normalize(q, w, Vq + (size_t)(j + 1) * q, W.hn, nullptr, st);
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    cleanup();
+    if (status != PSLR_OK && status != PSLR_ERR_BREAKDOWN) {
+        cudaFree(Vq);
+        return status;
+    }
+    std::vector<double> H((size_t)kept * kept), G;
+    for (int j = 0; j < kept; ++j)
+        for (int i = 0; i < kept; ++i) H[(size_t)j * kept + i] = Hb[(size_t)j * (r + 1) + i];
+    if (!compute_G(kept, H, G)) {
+        cudaFree(Vq);
+        return fail(c, PSLR_ERR_SINGULAR_IMH, "I - H is singular");
+    }
+    c->d_V = Vq;  // first `kept` columns (leading dimension q)
+    pslr_status st2 = install_lowrank(c, m, kept, G);
+    if (st2 != PSLR_OK) return st2;
+    c->H = H;
+    if (status == PSLR_ERR_BREAKDOWN)
+        return fail(c, PSLR_ERR_BREAKDOWN, "Arnoldi breakdown: rank truncated to %d", kept);
+    return PSLR_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------- FGMRES
+
+static pslr_status krylov_alloc(pslr_ctx *c, int restart) {
+    if (c->kr_restart == restart) return PSLR_OK;
+    free_krylov(c);
+    const size_t n = c->n;
+    CK(cudaMalloc(&c->d_kV, sizeof(double) * n * (restart + 1)));
+    CK(cudaMalloc(&c->d_kZ, sizeof(double) * n * restart));
+    CK(cudaMalloc(&c->d_kw, sizeof(double) * n));
+    CK(cudaMalloc(&c->d_kr, sizeof(double) * n));
+    CK(cudaMalloc(&c->d_kH, sizeof(double) * (restart + 1) * restart));
+    CK(cudaMalloc(&c->d_krot, sizeof(double) * 2 * (restart + 1)));
+    CK(cudaMalloc(&c->d_kgam, sizeof(double) * (restart + 1)));
+    CK(cudaMalloc(&c->d_kf_in, sizeof(float) * n));
+    CK(cudaMalloc(&c->d_kf_out, sizeof(float) * n));
+    CK(cudaMalloc(&c->d_kstate, sizeof(int) * 2));
+    CK(cudaMalloc(&c->d_kskip, sizeof(int)));
+    c->kr_restart = restart;
+    return PSLR_OK;
+}
+
+extern "C" {
+
+pslr_status pslr_solve(pslr_ctx *c, const double *b_dev, double *x_dev, double rtol, int32_t restart,
+                       int32_t maxit, pslr_prec prec, int32_t transpose, int32_t *iters, double *relres,
+                       void *stream) {
+    if (!c || !b_dev || !x_dev || restart < 1 || restart > 63 || maxit < 0 || !(rtol > 0.0) ||
+        (prec != PSLR_FP64 && prec != PSLR_FP32))
+        return fail(c, PSLR_ERR_ARG, "solve: bad argument (restart must be 1..63)");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    pslr_status as = krylov_alloc(c, restart);
+    if (as != PSLR_OK) return as;
+    const int n = c->n, k = restart;
+    const int dir = transpose ? 1 : 0;
+    const int32_t *rp = dir ? c->d_rpT : c->d_rp, *ci = dir ? c->d_ciT : c->d_ci;
+    const double *av = dir ? c->d_avT : c->d_av;
+    KWork W;
+    pslr_status ks = kwork_alloc(c, W, n, k + 1);
+    if (ks != PSLR_OK) { kwork_free(W); return ks; }
+    struct Guard { KWork &w; ~Guard() { kwork_free(w); } } guard{W};
+    int its = 0;
+    double bn2 = 0.0;
+    cgs2(W, n, 0, nullptr, n, const_cast<double *>(b_dev), nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    CK(cudaMemcpyAsync(&bn2, W.wn2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemsetAsync(x_dev, 0, sizeof(double) * n, st));
+    pslr_status ss = pslr_sync(c, stream);
+    if (ss != PSLR_OK) return ss;
+    const double bn = std::sqrt(bn2);
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    if (bn == 0.0) return PSLR_OK;
+    if (!std::isfinite(bn)) return fail(c, PSLR_ERR_NAN, "right-hand side is not finite");
+    CK(cudaMemcpyAsync(c->d_kr, b_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    double rn = bn;
+    std::vector<double> H((size_t)(k + 1) * k), gam(k + 1), y(k);
+    pslr_status result = PSLR_ERR_NOT_CONVERGED;
+    while (its < maxit) {
+        // v_1 = r / ||r||, gamma = ||r|| e_1
+        std::vector<double> g0(k + 1, 0.0);
+        g0[0] = rn;
+        CK(cudaMemcpyAsync(c->d_kgam, g0.data(), sizeof(double) * (k + 1), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(W.hn, &rn, sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(c->d_kstate, 0, sizeof(int) * 2, st));
+        CK(cudaMemsetAsync(c->d_kskip, 0, sizeof(int), st));
+        launch_normalize(n, c->d_kr, c->d_kV, W.hn, nullptr, st);
+        CK(cudaStreamSynchronize(st));
+        const int jmax = std::min(k, maxit - its);
+        for (int j = 0; j < jmax; ++j) {
+            double *vj = c->d_kV + (size_t)j * n, *zj = c->d_kZ + (size_t)j * n;
+            pslr_status a;
+            if (prec == PSLR_FP64) {
+                a = apply_one(c, vj, zj, 0, dir, c->d_kskip, st);
+            } else {
+                launch_d2f(n, vj, c->d_kf_in, c->d_kskip, st);
+                a = apply_one(c, c->d_kf_in, c->d_kf_out, 1, dir, c->d_kskip, st);
+                launch_f2d(n, c->d_kf_out, zj, c->d_kskip, st);
+            }
+            if (a != PSLR_OK) return a;
+            cgs2(W, n, j + 1, c->d_kV, n, c->d_kw, rp, ci, av, zj, c->d_kskip, st);
+            launch_hessenberg(j, W.h1, W.h2, W.wn2, c->d_kH, k + 1, W.hn, 1, c->d_krot, c->d_kgam, rtol * bn,
+                              c->d_kstate, c->d_kskip, st);
+            launch_normalize(n, c->d_kw, c->d_kV + (size_t)(j + 1) * n, W.hn, c->d_kskip, st);
+        }
+        int state[2] = {0, 0};
+        CK(cudaMemcpyAsync(state, c->d_kstate, sizeof(state), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(H.data(), c->d_kH, sizeof(double) * (k + 1) * k, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(gam.data(), c->d_kgam, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
+        ss = pslr_sync(c, stream);
+        if (ss != PSLR_OK) return ss;
+        const int jd = state[0];
+        its += jd;
+        // H(0:jd, 0:jd) y = gamma(0:jd): upper triangular after the rotations
+        for (int i = jd - 1; i >= 0; --i) {
+            double a = gam[i];
+            for (int l = i + 1; l < jd; ++l) a -= H[(size_t)l * (k + 1) + i] * y[l];
+            y[i] = a / H[(size_t)i * (k + 1) + i];
+        }
+        bool finite = true;
+        for (int i = 0; i < jd; ++i) finite &= std::isfinite(y[i]);
+        if (!finite) return fail(c, PSLR_ERR_NAN, "NaN in the FGMRES least-squares solution");
+        CK(cudaMemcpyAsync(W.h1, y.data(), sizeof(double) * std::max(jd, 1), cudaMemcpyHostToDevice, st));
+        launch_gemv_add(n, jd, c->d_kZ, n, W.h1, x_dev, st);
+        launch_residual(n, rp, ci, av, x_dev, b_dev, c->d_kr, st);
+        cgs2(W, n, 0, nullptr, n, c->d_kr, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+        double rn2 = 0.0;
+        CK(cudaMemcpyAsync(&rn2, W.wn2, sizeof(double), cudaMemcpyDeviceToHost, st));
+        ss = pslr_sync(c, stream);
+        if (ss != PSLR_OK) return ss;
+        rn = std::sqrt(rn2);
+        if (!std::isfinite(rn)) return fail(c, PSLR_ERR_NAN, "residual is not finite");
+        if (rn <= rtol * bn) {
+            result = PSLR_OK;
+            break;
+        }
+        if (jd == 0) break;
+    }
+    if (iters) *iters = its;
+    if (relres) *relres = rn / bn;
+    if (result != PSLR_OK) return fail(c, PSLR_ERR_NOT_CONVERGED, "FGMRES reached maxit = %d", maxit);
+    return PSLR_OK;
+}
+
+}  // extern "C"

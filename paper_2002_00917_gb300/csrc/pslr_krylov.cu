@@ -1,0 +1,267 @@
+// FP64 Krylov kernels for sm_103a: the FGMRES of Section 4 and the Arnoldi
+// process of Algorithm 1 (steps 6-7) share them.
+//
+// Classical Gram-Schmidt applied twice (CGS2) is split into three passes over
+// the rows, each one launch whose blocks stream the basis V column-chunk by
+// column-chunk (coalesced along rows) and leave one partial per block; the
+// last block to finish (atomic ticket) adds the partials in block order, so
+// every reduction is deterministic:
+//   pass 1  w = A z (optional, fused CSR SpMV), h1 = V^T w
+//   pass 2  w -= V h1,                        h2 = V^T w
+//   pass 3  w -= V h2,                        ||w||^2
+// then one thread forms h = h1 + h2, h_{j+1,j} = ||w|| and (FGMRES) applies
+// the Givens rotations, and a last launch writes v_{j+1} = w / h_{j+1,j}.
+// Every kernel returns at once when *skip is set (the cycle has converged).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pslr {
+
+constexpr int kKThreads = 256;
+constexpr int kChunk = 8;  // basis columns per register chunk
+
+__device__ __forceinline__ bool skipping(const int *skip) {
+    return skip != nullptr && *(volatile const int *)skip != 0;
+}
+
+// Block-reduce kChunk values; thread 0 of the block gets the sums in out[].
+__device__ __forceinline__ void block_reduce8(double (&a)[kChunk], double *sh, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+        double v = a[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[warp * kChunk + k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kChunk) {
+        double v = 0.0;
+        for (int w = 0; w < nw; ++w) v += sh[w * kChunk + threadIdx.x];
+        out[threadIdx.x] = v;
+    }
+    __syncthreads();
+}
+
+// Last block to finish adds the per-block partials (nres values each) in
+// block order into res (res[c] = sum_b part[b*nres + c]; accumulate adds to
+// the existing res).  Returns true in the reducing block.
+__device__ bool finish_reduction(const double *part, int nres, double *res, unsigned *ticket,
+                                 bool accumulate) {
+    __shared__ unsigned last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    for (int c = threadIdx.x; c < nres; c += blockDim.x) {
+        double v = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) v += __ldcg(part + (int64_t)b * nres + c);
+        res[c] = accumulate ? res[c] + v : v;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    __syncthreads();
+    return true;
+}
+
+// One CGS pass.  If rp != nullptr: w = A z first (CSR, FP64).  If hsub !=
+// nullptr: w -= V(:, 0:k) hsub.  Then either h = V(:, 0:k)^T w (norm == 0) or
+// res[0] = ||w||^2 (norm != 0).
+__global__ void __launch_bounds__(kKThreads) k_cgs_pass(
+    int n, int k, const double *__restrict__ V, int64_t ld, double *__restrict__ w,
+    const double *__restrict__ hsub, int norm, double *part, double *res, unsigned *ticket,
+    const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ av,
+    const double *__restrict__ z, const int *skip) {
+    if (skipping(skip)) return;
+    __shared__ double sh[(kKThreads / 32) * kChunk];
+    __shared__ double hs[64];
+    __shared__ double outs[kChunk];
+    const int stride = gridDim.x * blockDim.x;
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (hsub) {
+        for (int c = threadIdx.x; c < k; c += blockDim.x) hs[c] = __ldcg(hsub + c);
+        __syncthreads();
+    }
+    // rows owned by this thread: i0, i0 + stride, ...  (update in place)
+    if (rp || hsub) {
+        for (int i = i0; i < n; i += stride) {
+            double wi;
+            if (rp) {
+                wi = 0.0;
+                for (int e = rp[i]; e < rp[i + 1]; ++e) wi = fma(av[e], z[ci[e]], wi);
+            } else {
+                wi = w[i];
+            }
+            if (hsub)
+                for (int c = 0; c < k; ++c) wi = fma(-V[(int64_t)c * ld + i], hs[c], wi);
+            w[i] = wi;
+        }
+    }
+    const int nres = norm ? 1 : k;
+    if (norm) {
+        double a[kChunk] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = i0; i < n; i += stride) a[0] = fma(w[i], w[i], a[0]);
+        block_reduce8(a, sh, outs);
+        if (threadIdx.x == 0) part[blockIdx.x] = outs[0];
+    } else {
+        for (int c0 = 0; c0 < k; c0 += kChunk) {
+            double a[kChunk];
+#pragma unroll
+            for (int t = 0; t < kChunk; ++t) a[t] = 0.0;
+            for (int i = i0; i < n; i += stride) {
+                const double wi = w[i];
+#pragma unroll
+                for (int t = 0; t < kChunk; ++t)
+                    if (c0 + t < k) a[t] = fma(V[(int64_t)(c0 + t) * ld + i], wi, a[t]);
+            }
+            block_reduce8(a, sh, outs);
+            if (threadIdx.x < kChunk && c0 + threadIdx.x < k)
+                part[(int64_t)blockIdx.x * nres + c0 + threadIdx.x] = outs[threadIdx.x];
+        }
+    }
+    finish_reduction(part, nres, res, ticket, false);
+}
+
+// One thread: column j of the Hessenberg matrix from h1 + h2 and ||w||^2, and
+// (givens != 0) the FGMRES least-squares update with Givens rotations.
+// H is (ldh x *) column-major; rot = [cs(0:ldh), sn(0:ldh)]; gam (ldh).
+// state: [0] = iterations done in this cycle, [1] = converged/stop flag.
+__global__ void k_hessenberg(int j, const double *h1, const double *h2, const double *wn2, double *H,
+                             int ldh, double *hn_out, int givens, double *rot, double *gam,
+                             double tol_abs, int *state, int *skip) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (skipping(skip)) return;
+    double *col = H + (int64_t)j * ldh;
+    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+    const double hn = sqrt(*wn2);
+    col[j + 1] = hn;
+    *hn_out = hn;
+    state[0] = j + 1;
+    if (!givens) return;
+    double *cs = rot, *sn = rot + ldh;
+    for (int i = 0; i < j; ++i) {
+        const double a = col[i], b = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * b;
+        col[i + 1] = -sn[i] * a + cs[i] * b;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double den = sqrt(a * a + b * b);
+    cs[j] = den > 0.0 ? a / den : 1.0;
+    sn[j] = den > 0.0 ? b / den : 0.0;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    gam[j + 1] = -sn[j] * gam[j];
+    gam[j] = cs[j] * gam[j];
+    if (fabs(gam[j + 1]) <= tol_abs || hn == 0.0 || !(den == den)) {
+        state[1] = 1;
+        if (skip) *skip = 1;
+    }
+}
+
+// v = w / *hn  (hn == 0 leaves v = 0).
+__global__ void k_normalize(int n, const double *w, double *v, const double *hn, const int *skip) {
+    if (skipping(skip)) return;
+    const double h = *hn;
+    const double s = h > 0.0 ? 1.0 / h : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        v[i] = w[i] * s;
+}
+
+// x += Z(:, 0:k) y  (y on the device).
+__global__ void k_gemv_add(int n, int k, const double *Z, int64_t ld, const double *y, double *x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double a = x[i];
+        for (int c = 0; c < k; ++c) a = fma(Z[(int64_t)c * ld + i], y[c], a);
+        x[i] = a;
+    }
+}
+
+// r = b - A x (CSR).  (A x with b == nullptr: r = A x.)
+__global__ void k_residual(int n, const int32_t *rp, const int32_t *ci, const double *av,
+                           const double *x, const double *b, double *r) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) a = fma(av[e], x[ci[e]], a);
+        r[i] = b ? b[i] - a : a;
+    }
+}
+
+// Precision conversions for the FP32 preconditioner inside FP64 FGMRES.
+__global__ void k_d2f(int n, const double *a, float *b, const int *skip) {
+    if (skipping(skip)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+__global__ void k_f2d(int n, const float *a, double *b, const int *skip) {
+    if (skipping(skip)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014), output j of the generator seeded with
+// seed, mapped to [-1, 1) from its top 53 bits: the Arnoldi start vector.
+__global__ void k_splitmix(int n, uint64_t seed, uint64_t j0, double *v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint64_t x = seed + (j0 + (uint64_t)i + 1ull) * 0x9E3779B97F4A7C15ull;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        x = x ^ (x >> 31);
+        v[i] = (double)(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+int krylov_blocks(int n) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int want = (n + kKThreads * 4 - 1) / (kKThreads * 4);
+    int cap = 2 * nsm;
+    if (want > cap) want = cap;
+    return want < 1 ? 1 : want;
+}
+
+void launch_cgs_pass(int n, int k, const double *V, int64_t ld, double *w, const double *hsub,
+                     int norm, double *part, double *res, unsigned *ticket, const int32_t *rp,
+                     const int32_t *ci, const double *av, const double *z, const int *skip,
+                     cudaStream_t st) {
+    k_cgs_pass<<<krylov_blocks(n), kKThreads, 0, st>>>(n, k, V, ld, w, hsub, norm, part, res, ticket,
+                                                       rp, ci, av, z, skip);
+}
+
+void launch_hessenberg(int j, const double *h1, const double *h2, const double *wn2, double *H,
+                       int ldh, double *hn, int givens, double *rot, double *gam, double tol_abs,
+                       int *state, int *skip, cudaStream_t st) {
+    k_hessenberg<<<1, 32, 0, st>>>(j, h1, h2, wn2, H, ldh, hn, givens, rot, gam, tol_abs, state, skip);
+}
+
+void launch_normalize(int n, const double *w, double *v, const double *hn, const int *skip,
+                      cudaStream_t st) {
+    k_normalize<<<krylov_blocks(n), kKThreads, 0, st>>>(n, w, v, hn, skip);
+}
+
+void launch_gemv_add(int n, int k, const double *Z, int64_t ld, const double *y, double *x,
+                     cudaStream_t st) {
+    k_gemv_add<<<krylov_blocks(n), kKThreads, 0, st>>>(n, k, Z, ld, y, x);
+}
+
+void launch_residual(int n, const int32_t *rp, const int32_t *ci, const double *av, const double *x,
+                     const double *b, double *r, cudaStream_t st) {
+    k_residual<<<krylov_blocks(n), kKThreads, 0, st>>>(n, rp, ci, av, x, b, r);
+}
+
+void launch_d2f(int n, const double *a, float *b, const int *skip, cudaStream_t st) {
+    k_d2f<<<krylov_blocks(n), kKThreads, 0, st>>>(n, a, b, skip);
+}
+
+void launch_f2d(int n, const float *a, double *b, const int *skip, cudaStream_t st) {
+    k_f2d<<<krylov_blocks(n), kKThreads, 0, st>>>(n, a, b, skip);
+}
+
+void launch_splitmix(int n, uint64_t seed, uint64_t j0, double *v, cudaStream_t st) {
+    k_splitmix<<<krylov_blocks(n), kKThreads, 0, st>>>(n, seed, j0, v);
+}
+
+}  // namespace pslr

@@ -1,0 +1,282 @@
+"""Thin Python binding of libpslr (include/pslr.h): argument marshalling only.
+
+Every step of the preconditioner and of the solver runs in the library's CUDA
+kernels; this module turns torch tensors into device pointers and the current
+torch stream into a cudaStream_t.  There is no CPU fallback: when libpslr.so
+cannot be loaded, every call raises.
+
+The function names mirror the C ABI (``pslr_setup``, ``pslr_apply``, ...).  The
+class :class:`Pslr` owns one context.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpslr.so")
+
+PSLR_OK = 0
+PSLR_ERR_ARG = 1
+PSLR_ERR_CUDA = 2
+PSLR_ERR_ZERO_PIVOT = 3
+PSLR_ERR_BREAKDOWN = 4
+PSLR_ERR_SINGULAR_IMH = 5
+PSLR_ERR_NOT_CONVERGED = 6
+PSLR_ERR_NAN = 7
+PSLR_ERR_TIMEOUT = 8
+PSLR_ERR_STATE = 9
+PSLR_ERR_TOO_LARGE = 10
+PSLR_FP64 = 0
+PSLR_FP32 = 1
+
+
+class pslr_opts(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("splits", C.c_int32 * 3), ("part", C.c_void_p),
+                ("factor", C.c_int32), ("seed", C.c_uint64)]
+
+
+class pslr_info(C.Structure):
+    _fields_ = [("n", C.c_int32), ("s", C.c_int32), ("p", C.c_int32), ("q", C.c_int32),
+                ("m", C.c_int32), ("rank", C.c_int32), ("nnz_A", C.c_int64), ("nnz_ilu", C.c_int64),
+                ("nnz_lr", C.c_int64), ("fill_ilu", C.c_double), ("fill_lr", C.c_double),
+                ("fill_total", C.c_double), ("max_interior", C.c_int32),
+                ("max_interface", C.c_int32), ("levels_B", C.c_int32), ("levels_C0", C.c_int32),
+                ("apply_bytes_fp64", C.c_int64), ("apply_bytes_fp32", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P, _I32, _I64, _D, _U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint64
+SIGNATURES = {
+    "pslr_setup": (_I32, [_I32, _P, _P, _P, C.POINTER(pslr_opts), _P, C.POINTER(_P)]),
+    "pslr_plan": (_I32, [_I32, _P, _P, _P, C.POINTER(pslr_opts), _I32, _I32, C.POINTER(pslr_info),
+                         _P, _P, _P]),
+    "pslr_build_lowrank": (_I32, [_P, _I32, _I32, _I32, _P]),
+    "pslr_set_lowrank": (_I32, [_P, _I32, _I32, _P, _P, _P]),
+    "pslr_apply": (_I32, [_P, _P, _P, _I32, _I32, _P]),
+    "pslr_apply_T": (_I32, [_P, _P, _P, _I32, _I32, _P]),
+    "pslr_apply_host": (_I32, [_P, _P, _P, _I32, _I32, _I32, _P]),
+    "pslr_solve": (_I32, [_P, _P, _P, _D, _I32, _I32, _I32, _I32, C.POINTER(_I32),
+                          C.POINTER(_D), _P]),
+    "pslr_matvec": (_I32, [_P, _P, _P, _I32, _P]),
+    "pslr_get_maps": (_I32, [_P, _P, _P, _P]),
+    "pslr_get_lowrank": (_I32, [_P, _P, _P, _P]),
+    "pslr_get_info": (_I32, [_P, C.POINTER(pslr_info)]),
+    "pslr_sync": (_I32, [_P, _P]),
+    "pslr_set_wait_limit": (_I64, [_P, _I64]),
+    "pslr_last_error": (C.c_char_p, [_P]),
+    "pslr_status_string": (C.c_char_p, [_I32]),
+    "pslr_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libpslr.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2002_00917_gb300.build.build() "
+                               "(the PSLR path has no CPU fallback)")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class PslrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Pslr:
+    """One PSLR context on the current CUDA device.
+
+    ``A`` is host CSR (``rowptr``, ``col``, ``val`` numpy arrays, or any object
+    with those attributes and ``n``).  ``dims``/``splits`` select the geometric
+    split; ``part`` (length n) overrides it.  ``factor``: 0 ILU(0), 1 exact LU.
+    """
+
+    def __init__(self, A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, seed=0,
+                 stream=None):
+        lib = load()
+        self.lib = lib
+        self.n = int(A.n)
+        self._rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+        self._ci = np.ascontiguousarray(A.col, dtype=np.int32)
+        self._av = np.ascontiguousarray(A.val, dtype=np.float64)
+        o = pslr_opts()
+        for d in range(3):
+            o.dims[d] = int(dims[d])
+            o.splits[d] = int(splits[d])
+        self._part = None if part is None else np.ascontiguousarray(part, dtype=np.int32)
+        o.part = None if self._part is None else self._part.ctypes.data
+        o.factor = int(factor)
+        o.seed = int(seed)
+        h = C.c_void_p()
+        st = lib.pslr_setup(self.n, self._rp.ctypes.data, self._ci.ctypes.data, self._av.ctypes.data,
+                            C.byref(o), _stream(stream), C.byref(h))
+        if st != PSLR_OK:
+            raise PslrError(st, f"pslr_setup: {lib.pslr_status_string(st).decode()}")
+        self.h = h
+        self.info = self.get_info()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pslr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what, ok=(PSLR_OK,)):
+        if st not in ok:
+            msg = self.lib.pslr_last_error(self.h).decode()
+            raise PslrError(st, f"{what}: {msg}")
+        return st
+
+    # -- set-up products
+    def get_info(self):
+        info = pslr_info()
+        self._check(self.lib.pslr_get_info(self.h, C.byref(info)), "pslr_get_info")
+        return info.as_dict()
+
+    def get_maps(self):
+        part = np.empty(self.n, np.int32)
+        iface = np.empty(self.n, np.int32)
+        perm = np.empty(self.n, np.int32)
+        self._check(self.lib.pslr_get_maps(self.h, part.ctypes.data, iface.ctypes.data,
+                                           perm.ctypes.data), "pslr_get_maps")
+        return part, iface, perm
+
+    # -- low-rank term (Algorithm 1, steps 6-8)
+    def build_lowrank(self, m, rank, full_rank=False, stream=None):
+        st = self.lib.pslr_build_lowrank(self.h, int(m), int(rank), int(bool(full_rank)),
+                                         _stream(stream))
+        self._check(st, "pslr_build_lowrank", ok=(PSLR_OK, PSLR_ERR_BREAKDOWN))
+        self.info = self.get_info()
+        return self.info["rank"], st
+
+    def set_lowrank(self, m, V=None, G=None, stream=None):
+        r = 0 if V is None else V.shape[1]
+        Vc = np.asfortranarray(V, dtype=np.float64) if r else None
+        Gc = np.asfortranarray(G, dtype=np.float64) if r else None
+        st = self.lib.pslr_set_lowrank(self.h, int(m), r, None if Vc is None else Vc.ctypes.data,
+                                       None if Gc is None else Gc.ctypes.data, _stream(stream))
+        self._check(st, "pslr_set_lowrank")
+        self.info = self.get_info()
+
+    def get_lowrank(self):
+        q, r = self.info["q"], self.info["rank"]
+        V = np.zeros((q, r), order="F")
+        H = np.zeros((r, r), order="F")
+        G = np.zeros((r, r), order="F")
+        self._check(self.lib.pslr_get_lowrank(self.h, V.ctypes.data if r else None,
+                                              H.ctypes.data if r else None,
+                                              G.ctypes.data if r else None), "pslr_get_lowrank")
+        return V, H, G
+
+    # -- Algorithm 3 and its transpose
+    def apply(self, b, z, transpose=False, stream=None):
+        """z = M^{-1} b (or M^{-T} b) on device tensors, float64 or float32,
+        shape (n,) or (n, nrhs) column-major."""
+        prec = PSLR_FP64 if b.dtype.itemsize == 8 else PSLR_FP32
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+        if b.dim() == 2 and nrhs > 1 and b.stride(0) != 1:
+            raise ValueError("multi-rhs tensors must be column-major (stride(0) == 1)")
+        f = self.lib.pslr_apply_T if transpose else self.lib.pslr_apply
+        return self._check(f(self.h, _ptr(b), _ptr(z), nrhs, prec, _stream(stream)), "pslr_apply")
+
+    def apply_host(self, b, z, transpose=False, stream=None):
+        """End-to-end apply on host numpy arrays (copies in, applies, copies out)."""
+        prec = PSLR_FP64 if b.dtype.itemsize == 8 else PSLR_FP32
+        nrhs = 1 if b.ndim == 1 else b.shape[1]
+        return self._check(self.lib.pslr_apply_host(self.h, C.c_void_p(b.ctypes.data),
+                                                    C.c_void_p(z.ctypes.data), nrhs, prec,
+                                                    int(bool(transpose)), _stream(stream)),
+                           "pslr_apply_host")
+
+    def solve(self, b, x, rtol=1e-8, restart=40, maxit=500, prec=PSLR_FP64, transpose=False,
+              stream=None, check=True):
+        its = C.c_int32(0)
+        rel = C.c_double(0.0)
+        st = self.lib.pslr_solve(self.h, _ptr(b), _ptr(x), float(rtol), int(restart), int(maxit),
+                                 int(prec), int(bool(transpose)), C.byref(its), C.byref(rel),
+                                 _stream(stream))
+        if check:
+            self._check(st, "pslr_solve", ok=(PSLR_OK, PSLR_ERR_NOT_CONVERGED))
+        return its.value, rel.value, st
+
+    def matvec(self, x, y, transpose=False, stream=None):
+        return self._check(self.lib.pslr_matvec(self.h, _ptr(x), _ptr(y), int(bool(transpose)),
+                                                _stream(stream)), "pslr_matvec")
+
+    def sync(self, stream=None, check=True):
+        st = self.lib.pslr_sync(self.h, _stream(stream))
+        if check:
+            self._check(st, "pslr_sync")
+        return st
+
+    def set_wait_limit(self, polls):
+        return self.lib.pslr_set_wait_limit(self.h, int(polls))
+
+
+def _opts(dims, splits, part, factor, seed):
+    o = pslr_opts()
+    for d in range(3):
+        o.dims[d] = int(dims[d])
+        o.splits[d] = int(splits[d])
+    o.part = None if part is None else part.ctypes.data
+    o.factor = int(factor)
+    o.seed = int(seed)
+    return o
+
+
+def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0):
+    """Host-only dry run of the set-up (no GPU needed): returns (info dict,
+    part, is_interface, perm) exactly as a device context would report them."""
+    lib = load()
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.col, dtype=np.int32)
+    av = np.ascontiguousarray(A.val, dtype=np.float64)
+    pa = None if part is None else np.ascontiguousarray(part, dtype=np.int32)
+    o = _opts(dims, splits, pa, factor, 0)
+    info = pslr_info()
+    n = int(A.n)
+    mp = [np.empty(n, np.int32) for _ in range(3)]
+    st = lib.pslr_plan(n, rp.ctypes.data, ci.ctypes.data, av.ctypes.data, C.byref(o), int(m), int(rank),
+                       C.byref(info), *[a.ctypes.data for a in mp])
+    if st != PSLR_OK:
+        raise PslrError(st, f"pslr_plan: {lib.pslr_status_string(st).decode()}")
+    return (info.as_dict(), *mp)
+
+
+def from_workload(w, seed=0, stream=None):
+    """Context for a workload dict of ``pslr_inputs.configs``."""
+    return Pslr(w["A"], dims=w["dims"], splits=w["splits"], factor=w["factor"], seed=seed,
+                stream=stream)

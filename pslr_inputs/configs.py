@@ -96,9 +96,7 @@ def small_problem(kind, dims, splits, factor=FACTOR_ILU0, m=3, rank=4, K=2, seed
     if kind == "lap":
         A, sig, k = _lap(dims, K)
     elif kind == "cd":
-        N = dims[0]
-        a = 50.0 / (N + 1.0)
-        sig, k = G.sigma_for_negative_count([G.convdiff_1d_eigs(N, a)] * nd, K)
+        sig, k = G.sigma_for_negative_count([G.convdiff_1d_eigs(N, 50.0 / (N + 1.0)) for N in dims], K)
         A = G.convection_diffusion(dims, 50.0, sig)
     elif kind == "kappa":
         sig, k = G.sigma_for_negative_count([G.laplacian_1d_eigs(d) for d in dims], K)

@@ -154,21 +154,19 @@ def shifted_laplacian(dims, sigma):
 def convection_diffusion(dims, peclet, sigma):
     """Upwinded -Lap u + w.grad u - sigma u, w = Pe*(1,..,1), scaled by h^2.
 
-    With h = 1/(N+1) and a = Pe*h, row i carries ``2d + d*a - sigma`` on the
-    diagonal, ``-1-a`` on each upwind (minus-side) neighbour and ``-1`` on each
-    downwind neighbour.  The grid must be a cube (one h for all directions).
+    Direction d has h_d = 1/(N_d+1) and a_d = Pe*h_d; its 1D operator is
+    tridiag(-1-a_d, 2+a_d, -1) (upwind neighbour on the minus side), and the
+    matrix is the sum of the 1D operators over the directions minus sigma*I.
+    On a cube (one h) this is the h^2-scaled upwind discretisation.
     """
-    if len(set(dims)) != 1:
-        raise ValueError("convection_diffusion expects equal sides")
-    N = dims[0]
-    a = peclet / (N + 1.0)
     n, idx, coords, strides = _grid(dims)
     nd = len(dims)
+    a = [peclet / (N + 1.0) for N in dims]
     rows = [idx]
     cols = [idx]
-    vals = [np.full(n, 2.0 * nd + nd * a - sigma)]
+    vals = [np.full(n, 2.0 * nd + sum(a) - sigma)]
     for d in range(nd):
-        for sgn, w in ((-1, -1.0 - a), (1, -1.0)):
+        for sgn, w in ((-1, -1.0 - a[d]), (1, -1.0)):
             c = coords[d] + sgn
             m = (c >= 0) & (c < dims[d])
             rows.append(idx[m])

@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars: integer maps bit-exact; FP64 applies within 1e-12 relative difference
+(2-norm, and every element within 1e-12 of the max-norm); FP32 applies within
+1e-5; FGMRES iteration counts within +-1 of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from pslr_inputs import configs as C
+from pslr_inputs import generators as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_00917_gb300 import build
+
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _pair(w, seed=0):
+    from paper_2002_00917_gb300 import pslr
+
+    return pslr.from_workload(w, seed=seed), O.from_workload(w)
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb, np.abs(a - b).max() / np.abs(b).max()
+
+
+def _bf16(x):
+    """Round to bfloat16 (IEEE round to nearest even on the float32 bits)."""
+    f = np.asarray(x, dtype=np.float32).copy()
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+CASES = [
+    # (kind, dims, splits, factor, m, r): several tiles per level, ragged subdomains
+    ("lap", (32, 32), (2, 2), 1, 3, 8),
+    ("lap", (13, 11, 9), (3, 2, 2), 0, 3, 6),
+    ("cd", (12, 10, 8), (3, 2, 2), 0, 2, 5),
+    ("kappa", (10, 9, 11), (2, 3, 2), 0, 4, 7),
+    ("lap", (40, 33), (3, 4), 0, 0, 0),
+    ("lap", (24, 20, 16), (2, 2, 2), 0, 5, 16),
+    ("cd", (9, 9, 9), (1, 1, 1), 0, 3, 0),      # one subdomain: no interface at all
+    ("lap", (7, 6, 5), (7, 6, 5), 0, 2, 3),     # every node its own part: B empty
+]
+
+
+def _setup(case):
+    kind, dims, splits, factor, m, r = case
+    w = C.small_problem(kind, dims, splits, factor=factor, m=m, rank=r, K=3)
+    ctx, orc = _pair(w)
+    if r and orc.q:
+        orc.build_lowrank(m, r, seed=0)
+        V, H, Gm = orc.lowrank()
+        ctx.set_lowrank(m, V, Gm)
+    else:
+        orc.set_lowrank(m, None, None)
+        ctx.set_lowrank(m)
+    return w, ctx, orc
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}{'x'.join(map(str, c[1]))}_f{c[3]}_m{c[4]}_r{c[5]}" for c in CASES])
+def test_maps_bit_exact(dev, case):
+    kind, dims, splits, factor, m, r = case
+    w = C.small_problem(kind, dims, splits, factor=factor, K=3)
+    ctx, orc = _pair(w)
+    for a, b in zip(ctx.get_maps(), orc.maps()):
+        np.testing.assert_array_equal(a, b)
+    info = ctx.info
+    assert (info["s"], info["p"], info["q"]) == (orc.s, orc.p, orc.q)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}{'x'.join(map(str, c[1]))}_f{c[3]}_m{c[4]}_r{c[5]}" for c in CASES])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_apply_fp64(dev, case, transpose):
+    w, ctx, orc = _setup(case)
+    rng = np.random.default_rng(3)
+    b = np.asfortranarray(rng.uniform(-1, 1, (w["A"].n, 2)))
+    bd = torch.tensor(b.T.copy(), device=dev).T  # column-major (n, 2)
+    zd = torch.zeros_like(bd)
+    ctx.apply(bd, zd, transpose=transpose)
+    ctx.sync()
+    z = zd.cpu().numpy()
+    for j in range(2):
+        zo = orc.apply_T(b[:, j]) if transpose else orc.apply(b[:, j])
+        r2, rinf = _rel(z[:, j], zo)
+        assert r2 <= TOL64 and rinf <= TOL64, (r2, rinf)
+
+
+@pytest.mark.parametrize("case", CASES[:6], ids=[f"{c[0]}{'x'.join(map(str, c[1]))}" for c in CASES[:6]])
+def test_apply_fp32(dev, case):
+    """FP32 apply with BF16 V: compared with the oracle run on the same BF16 V
+    (the stored low-rank factor) and the same G."""
+    kind, dims, splits, factor, m, r = case
+    w = C.small_problem(kind, dims, splits, factor=factor, m=m, rank=r, K=3)
+    ctx, orc = _pair(w)
+    if r:
+        orc.build_lowrank(m, r, seed=0)
+        V, H, Gm = orc.lowrank()
+        ctx.set_lowrank(m, V, Gm)
+        orc.set_lowrank(m, _bf16(V), Gm.astype(np.float32).astype(np.float64))
+    else:
+        ctx.set_lowrank(m)
+        orc.set_lowrank(m, None, None)
+    b = np.random.default_rng(4).uniform(-1, 1, w["A"].n)
+    bd = torch.tensor(b, device=dev, dtype=torch.float32)
+    for transpose in (False, True):
+        zd = torch.zeros_like(bd)
+        ctx.apply(bd, zd, transpose=transpose)
+        ctx.sync()
+        zo = (orc.apply_T if transpose else orc.apply)(bd.cpu().double().numpy())
+        r2, rinf = _rel(zd.cpu().double().numpy(), zo)
+        assert r2 <= TOL32 and rinf <= TOL32, (transpose, r2, rinf)
+
+
+def test_apply_host_matches_device(dev):
+    w, ctx, orc = _setup(CASES[1])
+    b = np.random.default_rng(5).uniform(-1, 1, w["A"].n)
+    z = np.empty_like(b)
+    ctx.apply_host(b, z)
+    np.testing.assert_allclose(z, orc.apply(b), rtol=0, atol=TOL64 * np.abs(z).max())
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[5]], ids=["lap3d", "cd3d", "lap3d_r16"])
+def test_build_lowrank_matches_oracle(dev, case):
+    """Device Arnoldi (Algorithm 1, steps 6-8) against the oracle's from the same
+    SplitMix64 start vector: same V, H and G up to rounding growth."""
+    kind, dims, splits, factor, m, r = case
+    w = C.small_problem(kind, dims, splits, factor=factor, m=m, rank=r, K=3)
+    ctx, orc = _pair(w)
+    k, st = ctx.build_lowrank(m, r)
+    ko, sto = orc.build_lowrank(m, r, seed=0)
+    assert k == ko
+    V, H, Gm = ctx.get_lowrank()
+    Vo, Ho, Go = orc.lowrank()
+    np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(H, Ho, atol=1e-9 * max(1, np.abs(Ho).max()))
+    np.testing.assert_allclose(V, Vo, atol=1e-8)
+    np.testing.assert_allclose(Gm, Go, atol=1e-8 * max(1, np.abs(Go).max()))
+
+
+def test_full_rank_exact_factors_one_iteration(dev):
+    """Exact local LU and r = q: the preconditioned system is the identity and
+    FGMRES stops after one iteration (on the GPU as in the oracle)."""
+    w = C.lap2d_32_2x2_exact()
+    ctx, orc = _pair(w)
+    k, st = ctx.build_lowrank(w["m"], ctx.info["q"], full_rank=True)
+    assert k == ctx.info["q"]
+    b, xs = G.uniform_rhs(w["A"], 0)
+    bd = torch.tensor(b, device=dev)
+    x = torch.empty_like(bd)
+    its, rel, st = ctx.solve(bd, x, rtol=1e-8)
+    assert st == 0 and its == 1 and rel <= 1e-8
+    np.testing.assert_allclose(x.cpu().numpy(), xs, atol=1e-8)
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[2], CASES[3]],
+                         ids=["lap2d_exact", "lap3d", "cd3d", "kappa3d"])
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_solve_iterations_match_oracle(dev, case, prec):
+    w, ctx, orc = _setup(case)
+    b, xs = G.uniform_rhs(w["A"], 0)
+    bd = torch.tensor(b, device=dev)
+    x = torch.empty_like(bd)
+    its, rel, st = ctx.solve(bd, x, rtol=1e-8, restart=40, maxit=500, prec=prec)
+    xo, its_o, rel_o, st_o = orc.fgmres(b, rtol=1e-8, restart=40, maxit=500)
+    assert st == 0 and rel <= 1e-8
+    # the true FP64 residual of the returned x
+    A = G.dense_from_csr(w["A"]) if w["A"].n <= 4096 else None
+    if A is not None:
+        xr = x.cpu().numpy()
+        assert np.linalg.norm(b - A @ xr) <= 1.0001e-8 * np.linalg.norm(b)
+    if prec == 0:
+        assert abs(its - its_o) <= 1, (its, its_o)
+
+
+def test_transposed_solve(dev):
+    w, ctx, orc = _setup(CASES[2])
+    b, _ = G.uniform_rhs(w["A"], 1)
+    bd = torch.tensor(b, device=dev)
+    x = torch.empty_like(bd)
+    its, rel, st = ctx.solve(bd, x, rtol=1e-10, transpose=True)
+    xo, its_o, rel_o, st_o = orc.fgmres(b, rtol=1e-10, transpose=True)
+    assert st == 0 and rel <= 1e-10 and abs(its - its_o) <= 1
+    At = G.dense_from_csr(w["A"]).T
+    assert np.linalg.norm(b - At @ x.cpu().numpy()) <= 1.0001e-10 * np.linalg.norm(b)
+
+
+def test_matvec(dev):
+    w, ctx, orc = _setup(CASES[2])
+    x = np.random.default_rng(6).uniform(-1, 1, w["A"].n)
+    D = G.dense_from_csr(w["A"])
+    xd = torch.tensor(x, device=dev)
+    y = torch.empty_like(xd)
+    for tr in (False, True):
+        ctx.matvec(xd, y, transpose=tr)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(y.cpu().numpy(), (D.T if tr else D) @ x, atol=1e-13)
+
+
+def test_timeout_path_reports_and_recovers(dev):
+    """A grid-barrier wait whose limit is 0 gives up at once: the kernel
+    returns, the context reports PSLR_ERR_TIMEOUT, and after the report the
+    next apply is correct again.  No GPU fault is involved."""
+    from paper_2002_00917_gb300 import pslr
+
+    w, ctx, orc = _setup(CASES[1])
+    b = np.random.default_rng(7).uniform(-1, 1, w["A"].n)
+    bd = torch.tensor(b, device=dev)
+    zd = torch.zeros_like(bd)
+    old = ctx.set_wait_limit(0)
+    ctx.apply(bd, zd)
+    st = ctx.sync(check=False)
+    assert st == pslr.PSLR_ERR_TIMEOUT
+    ctx.set_wait_limit(old)
+    ctx.apply(bd, zd)
+    ctx.sync()
+    r2, _ = _rel(zd.cpu().numpy(), orc.apply(b))
+    assert r2 <= TOL64
+
+
+def test_bad_arguments_are_rejected(dev):
+    from paper_2002_00917_gb300 import pslr
+
+    A = G.shifted_laplacian((6, 5), 0.1)
+    with pytest.raises(pslr.PslrError) as e:
+        pslr.Pslr(A, dims=(6, 4, 1), splits=(2, 2, 1))
+    assert e.value.status == pslr.PSLR_ERR_ARG
+    bad = G.CSR(A.n, A.rowptr, A.col.copy(), A.val)
+    bad.col[3] = 10 ** 6
+    with pytest.raises(pslr.PslrError):
+        pslr.Pslr(bad, dims=(6, 5, 1), splits=(2, 2, 1))
+    zp = G.CSR(A.n, A.rowptr, A.col, A.val.copy())
+    zp.val[zp.rowptr[0]] = 0.0
+    with pytest.raises(pslr.PslrError) as e:
+        pslr.Pslr(zp, dims=(6, 5, 1), splits=(2, 1, 1))
+    assert e.value.status == pslr.PSLR_ERR_ZERO_PIVOT

@@ -23,12 +23,11 @@ def test_closed_form_spectrum_matches_brute_force(dims):
     np.testing.assert_allclose(np.sort(ev), lam, atol=1e-12)
 
 
-def test_convdiff_closed_form_spectrum():
-    N = 6
-    a = 50.0 / (N + 1)
-    A = G.convection_diffusion((N, N, N), 50.0, 0.0)
+@pytest.mark.parametrize("dims", [(6, 6, 6), (5, 4, 3)])
+def test_convdiff_closed_form_spectrum(dims):
+    A = G.convection_diffusion(dims, 50.0, 0.0)
     ev = np.sort(np.linalg.eigvals(G.dense_from_csr(A)).real)
-    lam = G._sum_spectrum([G.convdiff_1d_eigs(N, a)] * 3)
+    lam = G._sum_spectrum([G.convdiff_1d_eigs(N, 50.0 / (N + 1)) for N in dims])
     np.testing.assert_allclose(ev, lam, atol=1e-9)
 
 
