@@ -4,29 +4,38 @@
 // operator set, its exact transpose - in ONE cooperative launch.  One CTA owns
 // one subdomain at a time (looping when there are more subdomains than
 // resident CTAs); the subdomain's interior and interface vectors live in
-// shared memory, and every sparse operand (the level segments of the local
-// factors, E_i, F_i, C_g,i) is streamed into a shared-memory ring by TMA bulk
-// copies issued a few segments ahead of use.  The only cross-subdomain
-// couplings in the method are C_g (once per series term, Eq. 3.1) and the
-// reduction V^T t of the low-rank term (Eq. 3.18); they are the only grid
-// barriers, split into arrive/wait so local work overlaps the wait.
+// shared memory.  The CTA is warp-specialised:
+//   * warp 8 (producer) walks the CTA's segment stream and copies every
+//     segment (a level of a local factor, or a slice of E_i, F_i, C_g,i) into
+//     a shared-memory ring with cp.async.bulk as soon as a slot is free
+//     (full/empty mbarrier pair per slot).  It runs ahead of the consumers,
+//     also across grid barriers.
+//   * warps 0-7 (consumers) take the segments in order and do the arithmetic;
+//     they synchronise with a named barrier that the producer never joins.
+// The only cross-subdomain couplings in the method are C_g (once per series
+// term, Eq. 3.1) and the reduction V^T t of the low-rank term (Eq. 3.18); they
+// are the only grid barriers, split into arrive/wait so local work overlaps
+// the wait.
 //
 // pslr_err_kernel computes E_rr(m) v = (E_s C0^{-1})^{m+1} v (Eq. 3.19) for the
 // Arnoldi process with the same machinery (m+1 grid barriers).
 //
-// Every wait (grid barrier, TMA completion) is bounded: when it gives up it
-// latches PSLR_ERR_TIMEOUT, drains the copies it issued and returns.
+// Every wait is bounded.  A grid-barrier wait that gives up latches
+// PSLR_ERR_TIMEOUT; the consumers then stop the producer, wait (bounded) for
+// the copies it issued, and the kernel returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "pslr_internal.h"
 
 namespace pslr {
 
-constexpr int kErrTimeout = 8;          // PSLR_ERR_TIMEOUT
-constexpr long long kTmaWaitLimit = 1ll << 24;
+constexpr int kErrTimeout = 8;  // PSLR_ERR_TIMEOUT
+constexpr long long kTmaWaitLimit = 1ll << 26;
+constexpr int kProducerWarp = kConsumers / 32;
 
 // ------------------------------------------------------------------ PTX helpers
 
@@ -68,12 +77,13 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uin
         : "memory");
 }
 
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Barrier among the consumer warps only (named barrier 1).
+__device__ __forceinline__ void csync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
 }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
@@ -94,128 +104,150 @@ __device__ __forceinline__ float load_v(const __nv_bfloat16 *V, int64_t i) {
     return __bfloat162float(V[i]);
 }
 
-// ----------------------------------------------------- per-CTA shared state
+// ----------------------------------------------------------- shared state
+
+// Control words in shared memory.
+struct Ctl {
+    int abort;          // consumers ask the producer to stop
+    int prod_done;      // producer has stopped issuing
+    unsigned issued;    // segments the producer issued
+    int ok;             // broadcast of a grid-wait result
+};
+
+// Consumer-side ring cursor (every consumer thread keeps an identical copy).
+struct Ring {
+    char *base;
+    uint32_t full_s, empty_s;
+    int slots, slot_bytes;
+    int slot;
+    uint32_t phase;
+    unsigned consumed;
+};
 
 template <class T>
 struct Cta {
-    char *ring;           // kRing slots
-    uint32_t ring_s;      // shared address of slot 0
-    uint32_t mbar_s;      // shared address of mbarrier 0
-    SegDesc *desc;        // descriptor table of the current subdomain
-    T *xi, *wi, *si, *tmp;
-    T *red;               // reduction scratch
-    int slot_bytes;
-    const char *segbase;
-    int cur_sub;          // subdomain whose descriptors are cached
-    // segment program (thread 0 drives the producer side)
-    int prog_b[8], prog_n[8], nprog, total;
-    unsigned seq_base;    // ring sequence number of program segment 0
-    int issued;           // program segments issued so far
-    unsigned seq_issued;  // ring sequence numbers issued in total
-    unsigned seq_done;    // ring sequence numbers consumed in total
-    int failed;           // a wait gave up
-    unsigned bar_gen;     // thread 0: generation seen at the last grid arrive
+    T *xi, *wi, *si, *tmp, *red;
+    Ctl *ctl;
+    Ring ring;
+    unsigned bar_gen;  // consumer thread 0: generation seen at the last grid arrive
 };
 
-// Map program position k to its descriptor index in the cached table.
-template <class T>
-__device__ __forceinline__ int prog_desc(const Cta<T> &c, int k) {
-    for (int i = 0; i < c.nprog; ++i) {
-        if (k < c.prog_n[i]) return c.prog_b[i] + k;
-        k -= c.prog_n[i];
-    }
-    return -1;
-}
-
-// Thread 0: issue program segment k into its ring slot.
-template <class T>
-__device__ __forceinline__ void issue_segment(Cta<T> &c, int k) {
-    unsigned seq = c.seq_base + k;
-    int slot = seq % kRing;
-    uint32_t bar = c.mbar_s + 8 * slot;
-    const SegDesc &d = c.desc[prog_desc(c, k)];
-    if (d.bytes > 0) {
-        fence_proxy_async();
-        mbar_arrive_expect_tx(bar, d.bytes);
-        bulk_copy_g2s(c.ring_s + slot * c.slot_bytes, c.segbase + d.off, d.bytes, bar);
-    } else {
-        mbar_arrive(bar);
-    }
-    c.seq_issued = seq + 1;
-}
-
-// Start a program of descriptor ranges (all threads call; thread 0 issues).
-template <class T>
-__device__ void prog_start(Cta<T> &c, int nr, const int *b, const int *n) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        c.nprog = nr;
-        c.total = 0;
-        for (int i = 0; i < nr; ++i) {
-            c.prog_b[i] = b[i];
-            c.prog_n[i] = n[i];
-            c.total += n[i];
-        }
-        c.seq_base = c.seq_issued;
-        c.issued = 0;
-        while (c.issued < c.total && c.issued < kRing) issue_segment(c, c.issued++);
-    }
-    __syncthreads();
-}
-
-// Wait until program segment k has landed; returns its shared-memory copy.
-template <class T>
-__device__ char *seg_acquire(Cta<T> &c, int k, int *err) {
-    unsigned seq = c.seq_base + k;
-    int slot = seq % kRing;
-    uint32_t bar = c.mbar_s + 8 * slot;
-    uint32_t parity = (seq / kRing) & 1u;
-    long long it = 0;
-    while (!mbar_try_wait(bar, parity)) {
-        if (++it > kTmaWaitLimit) {
-            atomicCAS(err, 0, kErrTimeout);
-            break;
-        }
-    }
-    return c.ring + slot * c.slot_bytes;
-}
-
-// Segment k fully consumed by every thread (caller synchronised): recycle slot.
-template <class T>
-__device__ __forceinline__ void seg_release(Cta<T> &c, int k) {
-    if (threadIdx.x == 0) {
-        c.seq_done = c.seq_base + k + 1;
-        if (c.issued < c.total) issue_segment(c, c.issued++);
-    }
-}
-
-// Before leaving the kernel: wait (bounded) for every copy still in flight.
-template <class T>
-__device__ void drain_ring(Cta<T> &c) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (unsigned seq = c.seq_done; seq < c.seq_issued; ++seq) {
-            uint32_t bar = c.mbar_s + 8 * (seq % kRing);
-            long long it = 0;
-            while (!mbar_try_wait(bar, (seq / kRing) & 1u) && ++it < kTmaWaitLimit) {
+// Wait until the next segment has landed; returns its shared-memory copy.
+__device__ __forceinline__ const char *seg_next(Ring &R, int *err) {
+    const uint32_t bar = R.full_s + 8 * R.slot;
+    if (!mbar_try_wait(bar, R.phase)) {
+        long long it = 0;
+        while (!mbar_try_wait(bar, R.phase)) {
+            if (++it > kTmaWaitLimit) {
+                atomicCAS(err, 0, kErrTimeout);
+                break;
             }
         }
-        c.seq_done = c.seq_issued;
     }
-    __syncthreads();
+    return R.base + (size_t)R.slot * R.slot_bytes;
+}
+
+// The segment is consumed by every consumer (caller synchronised): free it.
+__device__ __forceinline__ void seg_done(Ring &R) {
+    if (threadIdx.x == 0) mbar_arrive(R.empty_s + 8 * R.slot);
+    ++R.consumed;
+    if (++R.slot == R.slots) {
+        R.slot = 0;
+        R.phase ^= 1u;
+    }
+}
+
+// Producer warp: copy the CTA's stream into the ring.
+__device__ void producer(const StreamEnt *stream, int64_t b, int64_t e, const char *segbase,
+                         char *ring, int slots, int slot_bytes, uint32_t full_s, uint32_t empty_s,
+                         Ctl *ctl) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t ring_s = smem_addr(ring);
+    int slot = 0;
+    uint32_t phase = 0;
+    unsigned issued = 0;
+    bool stop = false;
+    StreamEnt nxt;
+    nxt.off = 0;
+    nxt.bytes = 0;
+    if (b + lane < e) nxt = stream[b + lane];
+    for (int64_t base = b; base < e && !stop; base += 32) {
+        const StreamEnt cur = nxt;
+        if (base + 32 + lane < e) nxt = stream[base + 32 + lane];  // prefetch the next chunk
+        const int cnt = (int)((e - base) < 32 ? (e - base) : 32);
+        for (int t = 0; t < cnt; ++t) {
+            const long long off = __shfl_sync(0xffffffffu, (long long)cur.off, t);
+            const int bytes = __shfl_sync(0xffffffffu, cur.bytes, t);
+            if (lane == 0) {
+                // slot free?  (the first pass over the ring finds every slot free)
+                const uint32_t ebar = empty_s + 8 * slot;
+                long long it = 0;
+                while (!mbar_try_wait(ebar, phase ^ 1u)) {
+                    if (ld_volatile(&ctl->abort) || ++it > kTmaWaitLimit) {
+                        stop = true;
+                        break;
+                    }
+                }
+                if (!stop) {
+                    const uint32_t fbar = full_s + 8 * slot;
+                    mbar_arrive_expect_tx(fbar, (uint32_t)bytes);
+                    bulk_copy_g2s(ring_s + slot * slot_bytes, segbase + off, (uint32_t)bytes, fbar);
+                    ++issued;
+                }
+            }
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            if (stop) break;
+            if (++slot == slots) {
+                slot = 0;
+                phase ^= 1u;
+            }
+        }
+    }
+    if (lane == 0) {
+        *(volatile unsigned *)&ctl->issued = issued;
+        __threadfence_block();
+        *(volatile int *)&ctl->prod_done = 1;
+    }
+}
+
+// Consumers, on the way out after an abort: stop the producer, wait
+// (bounded) for it, then for the copies it issued that nobody consumed.
+template <class T>
+__device__ void consumers_abort_drain(Cta<T> &c) {
+    csync();
+    if (threadIdx.x == 0) {
+        *(volatile int *)&c.ctl->abort = 1;
+        long long it = 0;
+        while (!ld_volatile(&c.ctl->prod_done) && ++it < kTmaWaitLimit) {
+        }
+        const unsigned issued = *(volatile unsigned *)&c.ctl->issued;
+        Ring R = c.ring;
+        for (unsigned s = R.consumed; s < issued; ++s) {
+            const uint32_t bar = R.full_s + 8 * R.slot;
+            long long w = 0;
+            while (!mbar_try_wait(bar, R.phase) && ++w < kTmaWaitLimit) {
+            }
+            if (++R.slot == R.slots) {
+                R.slot = 0;
+                R.phase ^= 1u;
+            }
+        }
+    }
+    csync();
 }
 
 // ----------------------------------------------------------------- grid barrier
 
-// Sense-reversing barrier over all CTAs of the cooperative grid.  arrive()
-// publishes this CTA's writes; wait() returns once every CTA has arrived.
+// Sense-reversing barrier over all CTAs of the cooperative grid (consumers
+// only).  arrive() publishes this CTA's writes; wait() returns once every CTA
+// has arrived, or gives up (bounded) and latches PSLR_ERR_TIMEOUT.
 template <class T>
 __device__ void grid_arrive(Cta<T> &c, unsigned *bar, int grid) {
-    __syncthreads();
+    csync();
     if (threadIdx.x == 0) {
         c.bar_gen = ld_acquire(bar + 1);
         __threadfence();
-        unsigned old = atomicAdd(bar, 1u);
+        const unsigned old = atomicAdd(bar, 1u);
         if (old == (unsigned)grid - 1) {
             atomicExch(bar, 0u);
             __threadfence();
@@ -226,9 +258,8 @@ __device__ void grid_arrive(Cta<T> &c, unsigned *bar, int grid) {
 
 template <class T>
 __device__ bool grid_wait(Cta<T> &c, unsigned *bar, int *err, long long limit) {
-    __shared__ int ok;
     if (threadIdx.x == 0) {
-        ok = 1;
+        int ok = 1;
         long long it = 0;
         while (ld_acquire(bar + 1) == c.bar_gen) {
             if (limit <= 0 || ++it > limit || ld_volatile(err) != 0) {
@@ -236,89 +267,343 @@ __device__ bool grid_wait(Cta<T> &c, unsigned *bar, int *err, long long limit) {
                 ok = 0;
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
         }
         __threadfence();
+        c.ctl->ok = ok;
     }
-    __syncthreads();
-    return ok != 0;
+    csync();
+    return c.ctl->ok != 0;
 }
 
 // -------------------------------------------------------------- local operators
 
-// Segment field pointers.
 template <class T, class IDX>
-struct SegView {
+struct Tile {
     const T *vals, *dinv;
     const IDX *cols;
     const uint16_t *rows;
     int n, w, np;
+    bool diag;
 };
 
 template <class T, class IDX>
-__device__ __forceinline__ SegView<T, IDX> seg_view(const char *seg, const SegDesc &d) {
-    SegView<T, IDX> v;
-    v.n = d.n;
-    v.w = d.w;
-    v.np = seg_npad(d.n);
-    v.vals = reinterpret_cast<const T *>(seg);
-    const char *p = seg + (size_t)v.np * v.w * sizeof(T);
-    v.dinv = reinterpret_cast<const T *>(p);
-    if (d.flags & kSegDiag) p += (size_t)v.np * sizeof(T);
-    v.cols = reinterpret_cast<const IDX *>(p);
-    p += (size_t)v.np * v.w * sizeof(IDX);
-    v.rows = reinterpret_cast<const uint16_t *>(p);
-    return v;
+__device__ __forceinline__ Tile<T, IDX> tile_of(const char *seg) {
+    const SegHdr h = *reinterpret_cast<const SegHdr *>(seg);
+    Tile<T, IDX> t;
+    t.n = h.n;
+    t.w = h.w;
+    t.np = h.np;
+    t.diag = (h.flags & kSegDiag) != 0;
+    const char *p = seg + sizeof(SegHdr);
+    t.vals = reinterpret_cast<const T *>(p);
+    p += (size_t)t.np * t.w * sizeof(T);
+    t.dinv = reinterpret_cast<const T *>(p);
+    if (t.diag) p += (size_t)t.np * sizeof(T);
+    t.cols = reinterpret_cast<const IDX *>(p);
+    p += (size_t)t.np * t.w * sizeof(IDX);
+    t.rows = reinterpret_cast<const uint16_t *>(p);
+    return t;
 }
 
-// One triangular sweep over `nlev` level segments starting at program
-// position k0: x[r] = (x[r] - sum_k T_rk x[c_k]) (* dinv[r]), in place.
+// Everything one thread needs of its row of a segment, read ahead of use:
+// the row index, the K column indices and values and the reciprocal diagonal
+// (record encodings), or a pointer for the rare wide tile.  None of it
+// depends on the vector being solved for, so it is loaded while the previous
+// level is still computing.
+template <class T, class IDX>
+struct RowPre {
+    const char *seg;
+    int n, np, fmt;
+    bool diag;
+    int r;
+    IDX c[3];
+    T v[3];
+    T dv;
+};
+
+// The 7-entry record of row j, read when it is used.
+template <class T, class IDX>
+struct Rec7 {
+    int r;
+    IDX c[7];
+    T v[7];
+    T dv;
+};
+
+// Vector loads of one record (K+1 indices, K+1 values), unpacked into the
+// named register fields of q.
+template <class IDX>
+struct IdxLoad;
+
+template <>
+struct IdxLoad<uint16_t> {
+    template <class Q>
+    __device__ __forceinline__ static void rec3(Q &q, const char *p) {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p);
+        q.r = (int)(u.x & 0xffffu);
+        q.c[0] = (uint16_t)(u.x >> 16);
+        q.c[1] = (uint16_t)(u.y & 0xffffu);
+        q.c[2] = (uint16_t)(u.y >> 16);
+    }
+    template <class Q>
+    __device__ __forceinline__ static void rec7(Q &q, const char *p) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(p);
+        q.r = (int)(u.x & 0xffffu);
+        q.c[0] = (uint16_t)(u.x >> 16);
+        q.c[1] = (uint16_t)(u.y & 0xffffu);
+        q.c[2] = (uint16_t)(u.y >> 16);
+        q.c[3] = (uint16_t)(u.z & 0xffffu);
+        q.c[4] = (uint16_t)(u.z >> 16);
+        q.c[5] = (uint16_t)(u.w & 0xffffu);
+        q.c[6] = (uint16_t)(u.w >> 16);
+    }
+};
+
+template <>
+struct IdxLoad<int32_t> {
+    template <class Q>
+    __device__ __forceinline__ static void rec3(Q &q, const char *p) {
+        const int4 u = *reinterpret_cast<const int4 *>(p);
+        q.r = u.x;
+        q.c[0] = u.y;
+        q.c[1] = u.z;
+        q.c[2] = u.w;
+    }
+    template <class Q>
+    __device__ __forceinline__ static void rec7(Q &q, const char *p) {
+        const int4 u = reinterpret_cast<const int4 *>(p)[0];
+        const int4 v = reinterpret_cast<const int4 *>(p)[1];
+        q.r = u.x;
+        q.c[0] = u.y;
+        q.c[1] = u.z;
+        q.c[2] = u.w;
+        q.c[3] = v.x;
+        q.c[4] = v.y;
+        q.c[5] = v.z;
+        q.c[6] = v.w;
+    }
+};
+
 template <class T>
-__device__ void tri_sweep(Cta<T> &c, T *x, int k0, int nlev, int *err) {
-    for (int L = 0; L < nlev; ++L) {
-        const SegDesc &d = c.desc[prog_desc(c, k0 + L)];
-        const char *seg = seg_acquire(c, k0 + L, err);
-        SegView<T, uint16_t> v = seg_view<T, uint16_t>(seg, d);
-        const bool diag = (d.flags & kSegDiag) != 0;
-        for (int j = threadIdx.x; j < v.n; j += blockDim.x) {
-            int r = v.rows[j];
-            T a = x[r];
-            for (int k = 0; k < v.w; ++k) a = fma_t(-v.vals[k * v.np + j], x[v.cols[k * v.np + j]], a);
-            if (diag) a *= v.dinv[j];
-            x[r] = a;
+struct ValLoad;
+
+template <>
+struct ValLoad<float> {
+    template <class Q>
+    __device__ __forceinline__ static void rec3(Q &q, const char *p) {
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        q.v[0] = a.x;
+        q.v[1] = a.y;
+        q.v[2] = a.z;
+        q.dv = a.w;
+    }
+    template <class Q>
+    __device__ __forceinline__ static void rec7(Q &q, const char *p) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[0];
+        const float4 b = reinterpret_cast<const float4 *>(p)[1];
+        q.v[0] = a.x;
+        q.v[1] = a.y;
+        q.v[2] = a.z;
+        q.v[3] = a.w;
+        q.v[4] = b.x;
+        q.v[5] = b.y;
+        q.v[6] = b.z;
+        q.dv = b.w;
+    }
+};
+
+template <>
+struct ValLoad<double> {
+    template <class Q>
+    __device__ __forceinline__ static void rec3(Q &q, const char *p) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0];
+        const double2 b = reinterpret_cast<const double2 *>(p)[1];
+        q.v[0] = a.x;
+        q.v[1] = a.y;
+        q.v[2] = b.x;
+        q.dv = b.y;
+    }
+    template <class Q>
+    __device__ __forceinline__ static void rec7(Q &q, const char *p) {
+        const double2 *d = reinterpret_cast<const double2 *>(p);
+        const double2 a = d[0], b = d[1], c = d[2], e = d[3];
+        q.v[0] = a.x;
+        q.v[1] = a.y;
+        q.v[2] = b.x;
+        q.v[3] = b.y;
+        q.v[4] = c.x;
+        q.v[5] = c.y;
+        q.v[6] = e.x;
+        q.dv = e.y;
+    }
+};
+
+template <class T, class IDX>
+__device__ __forceinline__ void load_rec3(RowPre<T, IDX> &q, const char *seg, int np, int j) {
+    const char *ib = seg + sizeof(SegHdr);
+    const char *vb = ib + (size_t)np * 4 * sizeof(IDX);
+    IdxLoad<IDX>::rec3(q, ib + (size_t)j * 4 * sizeof(IDX));
+    ValLoad<T>::rec3(q, vb + (size_t)j * 4 * sizeof(T));
+}
+
+template <class T, class IDX>
+__device__ __forceinline__ Rec7<T, IDX> load_rec7(const char *seg, int np, int j) {
+    Rec7<T, IDX> q;
+    const char *ib = seg + sizeof(SegHdr);
+    const char *vb = ib + (size_t)np * 8 * sizeof(IDX);
+    IdxLoad<IDX>::rec7(q, ib + (size_t)j * 8 * sizeof(IDX));
+    ValLoad<T>::rec7(q, vb + (size_t)j * 8 * sizeof(T));
+    return q;
+}
+
+template <class T, class IDX>
+__device__ __forceinline__ RowPre<T, IDX> row_pre(const char *seg, int j) {
+    RowPre<T, IDX> q;
+    const SegHdr h = *reinterpret_cast<const SegHdr *>(seg);
+    q.seg = seg;
+    q.n = h.n;
+    q.np = h.np;
+    q.fmt = h.fmt;
+    q.diag = (h.flags & kSegDiag) != 0;
+    q.r = 0;
+    q.dv = T(1);
+    if (j < h.n) {
+        if (h.fmt == kRec3) {
+            load_rec3(q, seg, h.np, j);
+        } else if (h.fmt == kRec7) {
+            const char *ib = seg + sizeof(SegHdr);
+            q.r = (int)reinterpret_cast<const IDX *>(ib)[(size_t)j * 8];
+        } else {
+            const Tile<T, IDX> t = tile_of<T, IDX>(seg);
+            q.r = t.rows[j];
+            if (t.diag) q.dv = t.dinv[j];
         }
-        __syncthreads();
-        seg_release(c, k0 + L);
+    }
+    return q;
+}
+
+// a - sum_k v_k src(c_k) for the thread's row.  Record rows run exactly K
+// fused multiply-adds (padding entries multiply the zero slot by 0); wide
+// tiles read their entries straight from the segment.
+template <class T, class IDX, class SRC>
+__device__ __forceinline__ T row_sub(RowPre<T, IDX> &q, int j, T a, SRC src) {
+    if (q.fmt == kRec3) {
+        T x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[k] = src(q.c[k]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a = fma_t(-q.v[k], x[k], a);
+    } else if (q.fmt == kRec7) {
+        const Rec7<T, IDX> e = load_rec7<T, IDX>(q.seg, q.np, j);
+        q.dv = e.dv;
+        T x[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) x[k] = src(e.c[k]);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) a = fma_t(-e.v[k], x[k], a);
+    } else {
+        const Tile<T, IDX> t = tile_of<T, IDX>(q.seg);
+        for (int k = 0; k < t.w; ++k) a = fma_t(-t.vals[k * t.np + j], src(t.cols[k * t.np + j]), a);
+    }
+    return a;
+}
+
+// The 3-entry record of row j of a kRec3 segment with local columns.
+template <class T>
+struct Rec3 {
+    int r, c0, c1, c2;
+    T v0, v1, v2, d;
+};
+
+template <class T>
+__device__ __forceinline__ Rec3<T> rec3_local(const char *seg, int np, int j) {
+    Rec3<T> e;
+    const uint2 id = reinterpret_cast<const uint2 *>(seg + sizeof(SegHdr))[j];
+    e.r = (int)(id.x & 0xffffu);
+    e.c0 = (int)(id.x >> 16);
+    e.c1 = (int)(id.y & 0xffffu);
+    e.c2 = (int)(id.y >> 16);
+    const char *vp = seg + sizeof(SegHdr) + (size_t)np * 8 + (size_t)j * 4 * sizeof(T);
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(vp);
+        e.v0 = v.x;
+        e.v1 = v.y;
+        e.v2 = v.z;
+        e.d = v.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2 *>(vp)[0];
+        const double2 b = reinterpret_cast<const double2 *>(vp)[1];
+        e.v0 = a.x;
+        e.v1 = a.y;
+        e.v2 = b.x;
+        e.d = b.y;
+    }
+    return e;
+}
+
+// One triangular sweep over `nseg` level segments, in place:
+// x[r] = (x[r] - sum_k T_rk x[c_k]) * dinv[r].  Levels in the 3-entry record
+// encoding (every level of a 7-point ILU(0) factor) take a short fixed path:
+// header, two record loads, four gathers, three FMAs, one multiply, a store.
+template <class T>
+__device__ void tri_sweep(Cta<T> &c, T *x, int nseg, int *err) {
+    const int j = threadIdx.x;
+    for (int L = 0; L < nseg; ++L) {
+        const char *seg = seg_next(c.ring, err);
+        const uint2 h = *reinterpret_cast<const uint2 *>(seg);
+        const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu), fmt = (int)((h.y >> 16) & 0xffu);
+        if (fmt == kRec3) {
+            if (j < n) {
+                const Rec3<T> e = rec3_local<T>(seg, np, j);
+                T a = x[e.r];
+                a = fma_t(-e.v0, x[e.c0], a);
+                a = fma_t(-e.v1, x[e.c1], a);
+                a = fma_t(-e.v2, x[e.c2], a);
+                x[e.r] = a * e.d;
+            }
+        } else {
+            RowPre<T, uint16_t> q = row_pre<T, uint16_t>(seg, j);
+            if (j < q.n) {
+                T a = row_sub(q, j, x[q.r], [&](int col) { return x[col]; });
+                if (q.diag) a *= q.dv;
+                x[q.r] = a;
+            }
+        }
+        csync();
+        seg_done(c.ring);
     }
 }
 
-// ELL product over nseg program segments from k0: out[row] = sum (assign) or
-// out[row] -= sum (subtract), src in shared (local columns) or global memory.
+// ELL product over nseg segments: out[row] = sum (assign) or out[row] -= sum
+// (subtract); src in shared memory (local columns) or global memory.
 template <class T, bool GLOBAL>
-__device__ void ell_op(Cta<T> &c, T *out, const T *src, bool subtract, int k0, int nseg, int *err) {
-    for (int k = k0; k < k0 + nseg; ++k) {
-        const SegDesc &d = c.desc[prog_desc(c, k)];
-        const char *seg = seg_acquire(c, k, err);
-        if (GLOBAL) {
-            SegView<T, int32_t> v = seg_view<T, int32_t>(seg, d);
-            for (int j = threadIdx.x; j < v.n; j += blockDim.x) {
-                T a = T(0);
-                for (int kk = 0; kk < v.w; ++kk)
-                    a = fma_t(v.vals[kk * v.np + j], __ldcg(src + v.cols[kk * v.np + j]), a);
-                int r = v.rows[j];
-                out[r] = subtract ? out[r] - a : a;
+__device__ void ell_op(Cta<T> &c, T *out, const T *src, bool subtract, int nseg, int *err) {
+    const int j = threadIdx.x;
+    using IDX = typename std::conditional<GLOBAL, int32_t, uint16_t>::type;
+    for (int k = 0; k < nseg; ++k) {
+        const char *seg = seg_next(c.ring, err);
+        const uint2 h = *reinterpret_cast<const uint2 *>(seg);
+        const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu), fmt = (int)((h.y >> 16) & 0xffu);
+        if (!GLOBAL && fmt == kRec3) {
+            if (j < n) {
+                const Rec3<T> e = rec3_local<T>(seg, np, j);
+                T a = e.v0 * src[e.c0];
+                a = fma_t(e.v1, src[e.c1], a);
+                a = fma_t(e.v2, src[e.c2], a);
+                out[e.r] = subtract ? out[e.r] - a : a;
             }
         } else {
-            SegView<T, uint16_t> v = seg_view<T, uint16_t>(seg, d);
-            for (int j = threadIdx.x; j < v.n; j += blockDim.x) {
-                T a = T(0);
-                for (int kk = 0; kk < v.w; ++kk) a = fma_t(v.vals[kk * v.np + j], src[v.cols[kk * v.np + j]], a);
-                int r = v.rows[j];
-                out[r] = subtract ? out[r] - a : a;
+            RowPre<T, IDX> q = row_pre<T, IDX>(seg, j);
+            if (j < q.n) {
+                T a;
+                if (GLOBAL) a = -row_sub(q, j, T(0), [&](int col) { return __ldcg(src + col); });
+                else a = -row_sub(q, j, T(0), [&](int col) { return src[col]; });
+                out[q.r] = subtract ? out[q.r] - a : a;
             }
         }
-        __syncthreads();
-        seg_release(c, k);
+        csync();
+        seg_done(c.ring);
     }
 }
 
@@ -326,73 +611,40 @@ __device__ void ell_op(Cta<T> &c, T *out, const T *src, bool subtract, int k0, i
 // x <- P^T x (scatter, after the transposed sweeps), via tmp.
 template <class T>
 __device__ void permute(T *x, T *tmp, const uint16_t *piv, int n, bool scatter) {
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) tmp[j] = x[j];
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    csync();
+    for (int j = threadIdx.x; j < n; j += kConsumers) tmp[j] = x[j];
+    csync();
+    for (int j = threadIdx.x; j < n; j += kConsumers) {
         if (scatter) x[piv[j]] = tmp[j];
         else x[j] = tmp[piv[j]];
     }
-    __syncthreads();
+    csync();
 }
 
-// Local solve x <- B_i~^{-1} x (or its transpose) with the sweeps at k0.
+// Local solve x <- B_i~^{-1} x (or C0_i~^{-1}, or a transpose): two sweeps.
 template <class T>
-__device__ void solve_local(Cta<T> &c, T *x, int n, const uint16_t *piv, int pivot_post, int k0,
-                            int n1, int n2, int *err) {
+__device__ void solve_local(Cta<T> &c, T *x, int n, const uint16_t *piv, int pivot_post, int n1,
+                            int n2, int *err) {
     if (piv && !pivot_post) permute(x, c.tmp, piv, n, false);
-    tri_sweep(c, x, k0, n1, err);
-    tri_sweep(c, x, k0 + n1, n2, err);
+    tri_sweep(c, x, n1, err);
+    tri_sweep(c, x, n2, err);
     if (piv && pivot_post) permute(x, c.tmp, piv, n, true);
 }
 
-// Segment counts of subdomain i and their positions in its descriptor table.
-struct SubOps {
-    int n[kNCnt], pos[kNCnt], total;
+template <class T>
+__device__ __forceinline__ void fill(T *x, int n, T v) {
+    for (int j = threadIdx.x; j < n; j += kConsumers) x[j] = v;
+}
+
+struct Counts {
+    int n[kNCnt];
 };
 
-__device__ __forceinline__ SubOps sub_ops(const OpSetDev &ops, int i) {
-    SubOps o;
-    int acc = 0;
+__device__ __forceinline__ Counts counts_of(const int32_t *cnt, int i) {
+    Counts k;
 #pragma unroll
-    for (int t = 0; t < kNCnt; ++t) {
-        o.n[t] = ops.cnt[kNCnt * i + t];
-        o.pos[t] = acc;
-        acc += o.n[t];
-    }
-    o.total = acc;
-    return o;
-}
-
-// A program under construction: ranges of the descriptor table, in order.
-struct ProgBuild {
-    int b[8], n[8], k = 0, total = 0;
-    __device__ int add(int pos, int cnt) {
-        b[k] = pos;
-        n[k] = cnt;
-        ++k;
-        int at = total;
-        total += cnt;
-        return at;
-    }
-};
-
-// Cache subdomain i's descriptor table in shared memory.
-template <class T>
-__device__ void load_desc(Cta<T> &c, const OpSetDev &ops, int i, int nd) {
-    if (c.cur_sub == i) return;
-    __syncthreads();
-    const int4 *src = reinterpret_cast<const int4 *>(ops.desc + ops.sub_desc[i]);
-    int4 *dst = reinterpret_cast<int4 *>(c.desc);
-    for (int j = threadIdx.x; j < nd; j += blockDim.x) dst[j] = src[j];
-    __syncthreads();
-    if (threadIdx.x == 0) c.cur_sub = i;
-    __syncthreads();
-}
-
-template <class T>
-__device__ void fill(T *x, int n, T v) {
-    for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = v;
+    for (int t = 0; t < kNCnt; ++t) k.n[t] = __ldg(cnt + kNCnt * i + t);
+    return k;
 }
 
 // Partial dots part[i*r + c] = sum_j V[go + j, c] * y[j] over this subdomain,
@@ -400,12 +652,12 @@ __device__ void fill(T *x, int n, T v) {
 template <class T, class VT>
 __device__ void lowrank_partial(Cta<T> &c, const VT *V, int q, int r, int go, int nq, const T *y,
                                 T *part_i) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int c0 = 0; c0 < r; c0 += 8) {
         T a[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) a[k] = T(0);
-        for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+        for (int j = threadIdx.x; j < nq; j += kConsumers) {
             const T yj = y[j];
 #pragma unroll
             for (int k = 0; k < 8; ++k)
@@ -418,13 +670,13 @@ __device__ void lowrank_partial(Cta<T> &c, const VT *V, int q, int r, int go, in
             if (lane == 0 && c0 + k < r) c.red[warp * kMaxRank + c0 + k] = v;
         }
     }
-    __syncthreads();
-    for (int col = threadIdx.x; col < r; col += blockDim.x) {
+    csync();
+    for (int col = threadIdx.x; col < r; col += kConsumers) {
         T a = T(0);
-        for (int w = 0; w < nw; ++w) a += c.red[w * kMaxRank + col];
+        for (int w = 0; w < kConsumers / 32; ++w) a += c.red[w * kMaxRank + col];
         part_i[col] = a;
     }
-    __syncthreads();
+    csync();
 }
 
 // d = G u with u = sum over subdomains of the partials, into the tail of
@@ -432,9 +684,9 @@ __device__ void lowrank_partial(Cta<T> &c, const VT *V, int q, int r, int go, in
 // combined in a fixed order, so every CTA computes the same d.
 template <class T>
 __device__ void lowrank_coeffs(Cta<T> &c, const T *part, const T *G, int s, int r) {
-    T *u = c.red + (kThreads / 32) * kMaxRank;
+    T *u = c.red + (kConsumers / 32) * kMaxRank;
     T *d = u + kMaxRank;
-    const int tpc = blockDim.x / r;  // groups per column (r <= kMaxRank <= blockDim)
+    const int tpc = kConsumers / r;  // groups per column (r <= kMaxRank <= kConsumers)
     const int col = threadIdx.x % r, grp = threadIdx.x / r;
     if (grp < tpc) {
         T a = T(0);
@@ -442,57 +694,70 @@ __device__ void lowrank_coeffs(Cta<T> &c, const T *part, const T *G, int s, int 
         for (int i = grp; i < s; i += tpc) a += __ldcg(part + (int64_t)i * r + col);
         c.red[grp * r + col] = a;
     }
-    __syncthreads();
+    csync();
     if (threadIdx.x < r) {
         T a = T(0);
         for (int g = 0; g < tpc; ++g) a += c.red[g * r + threadIdx.x];
         u[threadIdx.x] = a;
     }
-    __syncthreads();
-    for (int row = threadIdx.x; row < r; row += blockDim.x) {
+    csync();
+    for (int row = threadIdx.x; row < r; row += kConsumers) {
         T a = T(0);
         for (int k = 0; k < r; ++k) a = fma_t(G[k * r + row], u[k], a);
         d[row] = a;
     }
-    __syncthreads();
+    csync();
 }
 
 // y[j] += sum_c V[go + j, c] d[c]
 template <class T, class VT>
 __device__ void lowrank_update(Cta<T> &c, const VT *V, int q, int r, int go, int nq, T *y) {
-    const T *d = c.red + (kThreads / 32) * kMaxRank + kMaxRank;
-    for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+    const T *d = c.red + (kConsumers / 32) * kMaxRank + kMaxRank;
+    for (int j = threadIdx.x; j < nq; j += kConsumers) {
         T a = y[j];
         for (int col = 0; col < r; ++col) a = fma_t(T(load_v(V, (int64_t)col * q + go + j)), d[col], a);
         y[j] = a;
     }
-    __syncthreads();
+    csync();
 }
 
+// Set up the CTA; returns true in the consumer threads.  The producer warp
+// runs its stream inside and returns false.
 template <class T>
-__device__ void cta_init(Cta<T> &c, char *smem, const SmemLayout &L, int slot_bytes,
-                         const char *segbase) {
-    c.ring = smem + L.ring;
-    c.ring_s = smem_addr(c.ring);
-    c.mbar_s = smem_addr(smem + L.mbar);
-    c.desc = reinterpret_cast<SegDesc *>(smem + L.desc);
+__device__ bool cta_start(Cta<T> &c, char *smem, const SmemLayout &L, int ring, int slot_bytes,
+                          const StreamEnt *stream, const int64_t *stream_off, const char *segbase) {
     c.xi = reinterpret_cast<T *>(smem + L.xi);
     c.wi = reinterpret_cast<T *>(smem + L.wi);
     c.si = reinterpret_cast<T *>(smem + L.si);
     c.tmp = reinterpret_cast<T *>(smem + L.tmp);
     c.red = reinterpret_cast<T *>(smem + L.red);
-    c.slot_bytes = slot_bytes;
-    c.segbase = segbase;
-    __syncthreads();
+    c.ctl = reinterpret_cast<Ctl *>(smem + L.ctl);
+    c.ring.base = smem + L.ring;
+    c.ring.full_s = smem_addr(smem + L.full);
+    c.ring.empty_s = smem_addr(smem + L.empty);
+    c.ring.slots = ring;
+    c.ring.slot_bytes = slot_bytes;
+    c.ring.slot = 0;
+    c.ring.phase = 0;
+    c.ring.consumed = 0;
     if (threadIdx.x == 0) {
-        c.cur_sub = -1;
-        c.seq_issued = 0;
-        c.seq_done = 0;
-        c.failed = 0;
-        for (int i = 0; i < kRing; ++i) mbar_init(c.mbar_s + 8 * i, 1);
+        c.ctl->abort = 0;
+        c.ctl->prod_done = 0;
+        c.ctl->issued = 0;
+        c.ctl->ok = 1;
+        for (int i = 0; i < ring; ++i) {
+            mbar_init(c.ring.full_s + 8 * i, 1);
+            mbar_init(c.ring.empty_s + 8 * i, 1);
+        }
         fence_mbar_init();
     }
     __syncthreads();
+    if (threadIdx.x / 32 == kProducerWarp) {
+        producer(stream, stream_off[blockIdx.x], stream_off[blockIdx.x + 1], segbase, c.ring.base, ring,
+                 slot_bytes, c.ring.full_s, c.ring.empty_s, c.ctl);
+        return false;
+    }
+    return true;
 }
 
 // ------------------------------------------------------------------ the apply
@@ -500,55 +765,47 @@ __device__ void cta_init(Cta<T> &c, char *smem, const SmemLayout &L, int slot_by
 template <class T, class VT>
 __global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyParams<T> P) {
     extern __shared__ __align__(128) char smem[];
-    __shared__ Cta<T> c;
     if (P.skip != nullptr && ld_volatile(P.skip) != 0) return;
-    const bool pivots = P.bpiv != nullptr;
-    const SmemLayout L = smem_layout(P.slot_bytes, P.max_desc, P.max_p, P.max_q, sizeof(T), pivots);
-    cta_init(c, smem, L, P.slot_bytes, P.ops.segbase);
     if (ld_volatile(P.err) != 0) return;
+    const bool pivots = P.bpiv != nullptr;
+    const SmemLayout L = smem_layout(P.slot_bytes, P.ring, P.max_p, P.max_q, sizeof(T), pivots);
+    Cta<T> c;
+    if (!cta_start(c, smem, L, P.ring, P.slot_bytes, P.stream, P.stream_off, P.segbase)) return;
 
-    const OpSetDev &ops = P.ops;
     const VT *V = reinterpret_cast<const VT *>(P.V);
     const int q = P.q, p = P.p, r = P.r, m = P.m;
-    const bool lr_before = r > 0 && !ops.lowrank_after;
-    const bool lr_after = r > 0 && ops.lowrank_after;
-    const T *w_cur;
+    const bool lr_before = r > 0 && !P.lowrank_after;
+    const bool lr_after = r > 0 && P.lowrank_after;
+    const int tid = threadIdx.x;
     bool ok = true;
 
     // ---- phase 0: u = B^{-1} f, t = g - F u (Algorithm 3, step 2); without a
     // low-rank term before the series also w_0 = C0^{-1} t.
     for (int i = blockIdx.x; i < P.s; i += gridDim.x) {
-        const SubOps so = sub_ops(ops, i);
-        load_desc(c, ops, i, so.total);
+        const Counts k = counts_of(P.cnt, i);
         const int io = P.ioff[i], np_ = P.ioff[i + 1] - io;
         const int go = P.goff[i], nq = P.goff[i + 1] - go;
-        ProgBuild pb;
-        const int kB = pb.add(so.pos[kB1], so.n[kB1] + so.n[kB2]);
-        const int kF_ = pb.add(so.pos[kF], so.n[kF]);
-        const int kC = lr_before ? 0 : pb.add(so.pos[kC1], so.n[kC1] + so.n[kC2]);
-        prog_start(c, pb.k, pb.b, pb.n);
-        for (int j = threadIdx.x; j < np_; j += blockDim.x) c.xi[j] = P.b[P.perm[io + j]];
-        if (threadIdx.x == 0) c.xi[np_] = T(0);
-        for (int j = threadIdx.x; j < nq; j += blockDim.x) c.si[j] = P.b[P.perm[p + go + j]];
-        __syncthreads();
-        solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, ops.pivot_post, kB, so.n[kB1],
-                    so.n[kB2], P.err);
-        ell_op<T, false>(c, c.si, c.xi, true, kF_, so.n[kF], P.err);
+        for (int j = tid; j < np_; j += kConsumers) c.xi[j] = P.b[P.perm[io + j]];
+        if (tid == 0) c.xi[np_] = T(0);
+        for (int j = tid; j < nq; j += kConsumers) c.si[j] = P.b[P.perm[p + go + j]];
+        csync();
+        solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2], P.err);
+        ell_op<T, false>(c, c.si, c.xi, true, k.n[kF], P.err);
         if (lr_before) {
             lowrank_partial(c, V, q, r, go, nq, c.si, P.part + (int64_t)i * r);
-            for (int j = threadIdx.x; j < nq; j += blockDim.x) P.acc[go + j] = c.si[j];
+            for (int j = tid; j < nq; j += kConsumers) P.acc[go + j] = c.si[j];
         } else {
-            if (threadIdx.x == 0) c.si[nq] = T(0);
-            solve_local(c, c.si, nq, pivots ? P.cpiv + go : nullptr, ops.pivot_post, kC, so.n[kC1],
-                        so.n[kC2], P.err);
-            for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+            if (tid == 0) c.si[nq] = T(0);
+            csync();
+            solve_local(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1], k.n[kC2], P.err);
+            for (int j = tid; j < nq; j += kConsumers) {
                 P.wbuf[go + j] = c.si[j];
                 P.acc[go + j] = c.si[j];
             }
         }
-        __syncthreads();
+        csync();
     }
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (tid == 0 && blockIdx.x == 0) {
         P.wbuf[q] = T(0);
         P.wbuf[(q + 1) + q] = T(0);
     }
@@ -557,74 +814,61 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyPara
     if (lr_before) {
         grid_arrive(c, P.bar, P.grid);
         ok = grid_wait(c, P.bar, P.err, P.wait_limit);
-        if (!ok) goto out;
+        if (!ok) goto abort;
         lowrank_coeffs(c, P.part, P.G, P.s, r);
         for (int i = blockIdx.x; i < P.s; i += gridDim.x) {
-            const SubOps so = sub_ops(ops, i);
-            load_desc(c, ops, i, so.total);
+            const Counts k = counts_of(P.cnt, i);
             const int go = P.goff[i], nq = P.goff[i + 1] - go;
-            ProgBuild pb;
-            const int kC = pb.add(so.pos[kC1], so.n[kC1] + so.n[kC2]);
-            prog_start(c, pb.k, pb.b, pb.n);
-            for (int j = threadIdx.x; j < nq; j += blockDim.x) c.si[j] = __ldcg(P.acc + go + j);
-            if (threadIdx.x == 0) c.si[nq] = T(0);
-            __syncthreads();
+            for (int j = tid; j < nq; j += kConsumers) c.si[j] = __ldcg(P.acc + go + j);
+            if (tid == 0) c.si[nq] = T(0);
+            csync();
             lowrank_update(c, V, q, r, go, nq, c.si);
-            solve_local(c, c.si, nq, pivots ? P.cpiv + go : nullptr, ops.pivot_post, kC, so.n[kC1],
-                        so.n[kC2], P.err);
-            for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+            solve_local(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1], k.n[kC2], P.err);
+            for (int j = tid; j < nq; j += kConsumers) {
                 P.wbuf[go + j] = c.si[j];
                 P.acc[go + j] = c.si[j];
             }
-            __syncthreads();
+            csync();
         }
     }
 
     // ---- series terms w_k = C0^{-1}(F B^{-1} E w_{k-1} - C_g w_{k-1}), acc += w_k (Eq. 3.3)
-    for (int k = 1; k <= m; ++k) {
-        const T *wprev = P.wbuf + ((k - 1) & 1) * (q + 1);
-        T *wnext = P.wbuf + (k & 1) * (q + 1);
+    for (int kk = 1; kk <= m; ++kk) {
+        const T *wprev = P.wbuf + ((kk - 1) & 1) * (q + 1);
+        T *wnext = P.wbuf + (kk & 1) * (q + 1);
         grid_arrive(c, P.bar, P.grid);
         bool waited = false;
         for (int i = blockIdx.x; i < P.s; i += gridDim.x) {
-            const SubOps so = sub_ops(ops, i);
-            load_desc(c, ops, i, so.total);
+            const Counts k = counts_of(P.cnt, i);
             const int io = P.ioff[i], np_ = P.ioff[i + 1] - io;
             const int go = P.goff[i], nq = P.goff[i + 1] - go;
-            ProgBuild pb;
-            const int kE_ = pb.add(so.pos[kE], so.n[kE]);
-            const int kB = pb.add(so.pos[kB1], so.n[kB1] + so.n[kB2]);
-            const int kF_ = pb.add(so.pos[kF], so.n[kF]);
-            const int kG = pb.add(so.pos[kCg], so.n[kCg]);
-            const int kC = pb.add(so.pos[kC1], so.n[kC1] + so.n[kC2]);
-            prog_start(c, pb.k, pb.b, pb.n);
-            for (int j = threadIdx.x; j < nq; j += blockDim.x) c.wi[j] = __ldcg(wprev + go + j);
-            if (threadIdx.x == 0) c.wi[nq] = T(0);
+            for (int j = tid; j < nq; j += kConsumers) c.wi[j] = __ldcg(wprev + go + j);
+            if (tid == 0) c.wi[nq] = T(0);
             fill(c.xi, np_ + 1, T(0));
-            __syncthreads();
-            ell_op<T, false>(c, c.xi, c.wi, false, kE_, so.n[kE], P.err);             // E w
-            solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, ops.pivot_post, kB, so.n[kB1],
-                        so.n[kB2], P.err);                                            // B^{-1}
+            csync();
+            ell_op<T, false>(c, c.xi, c.wi, false, k.n[kE], P.err);                      // E w
+            solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2],
+                        P.err);                                                         // B^{-1}
             fill(c.si, nq + 1, T(0));
-            __syncthreads();
-            ell_op<T, false>(c, c.si, c.xi, false, kF_, so.n[kF], P.err);             // F
+            csync();
+            ell_op<T, false>(c, c.si, c.xi, false, k.n[kF], P.err);                      // F
             if (!waited) {
                 ok = grid_wait(c, P.bar, P.err, P.wait_limit);
                 waited = true;
-                if (!ok) goto out;
+                if (!ok) goto abort;
             }
-            ell_op<T, true>(c, c.si, wprev, true, kG, so.n[kCg], P.err);              // - C_g w
-            solve_local(c, c.si, nq, pivots ? P.cpiv + go : nullptr, ops.pivot_post, kC, so.n[kC1],
-                        so.n[kC2], P.err);                                            // C0^{-1}
-            for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+            ell_op<T, true>(c, c.si, wprev, true, k.n[kCg], P.err);                      // - C_g w
+            solve_local(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1], k.n[kC2],
+                        P.err);                                                         // C0^{-1}
+            for (int j = tid; j < nq; j += kConsumers) {
                 wnext[go + j] = c.si[j];
                 P.acc[go + j] = __ldcg(P.acc + go + j) + c.si[j];
             }
-            __syncthreads();
+            csync();
         }
         if (!waited) {  // a CTA without subdomains still takes part in the barrier
             ok = grid_wait(c, P.bar, P.err, P.wait_limit);
-            if (!ok) goto out;
+            if (!ok) goto abort;
         }
     }
 
@@ -632,42 +876,36 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyPara
     if (lr_after) {
         for (int i = blockIdx.x; i < P.s; i += gridDim.x) {
             const int go = P.goff[i], nq = P.goff[i + 1] - go;
-            for (int j = threadIdx.x; j < nq; j += blockDim.x) c.si[j] = __ldcg(P.acc + go + j);
-            __syncthreads();
+            for (int j = tid; j < nq; j += kConsumers) c.si[j] = __ldcg(P.acc + go + j);
+            csync();
             lowrank_partial(c, V, q, r, go, nq, c.si, P.part + (int64_t)i * r);
         }
         grid_arrive(c, P.bar, P.grid);
         ok = grid_wait(c, P.bar, P.err, P.wait_limit);
-        if (!ok) goto out;
+        if (!ok) goto abort;
         lowrank_coeffs(c, P.part, P.G, P.s, r);
     }
 
     // ---- y = acc; x = B^{-1}(f - E y); scatter (steps 5-6)
-    w_cur = P.acc;
     for (int i = blockIdx.x; i < P.s; i += gridDim.x) {
-        const SubOps so = sub_ops(ops, i);
-        load_desc(c, ops, i, so.total);
+        const Counts k = counts_of(P.cnt, i);
         const int io = P.ioff[i], np_ = P.ioff[i + 1] - io;
         const int go = P.goff[i], nq = P.goff[i + 1] - go;
-        ProgBuild pb;
-        const int kE_ = pb.add(so.pos[kE], so.n[kE]);
-        const int kB = pb.add(so.pos[kB1], so.n[kB1] + so.n[kB2]);
-        prog_start(c, pb.k, pb.b, pb.n);
-        for (int j = threadIdx.x; j < nq; j += blockDim.x) c.wi[j] = __ldcg(w_cur + go + j);
-        if (threadIdx.x == 0) c.wi[nq] = T(0);
-        for (int j = threadIdx.x; j < np_; j += blockDim.x) c.xi[j] = P.b[P.perm[io + j]];
-        if (threadIdx.x == 0) c.xi[np_] = T(0);
-        __syncthreads();
+        for (int j = tid; j < nq; j += kConsumers) c.wi[j] = __ldcg(P.acc + go + j);
+        if (tid == 0) c.wi[nq] = T(0);
+        for (int j = tid; j < np_; j += kConsumers) c.xi[j] = P.b[P.perm[io + j]];
+        if (tid == 0) c.xi[np_] = T(0);
+        csync();
         if (lr_after) lowrank_update(c, V, q, r, go, nq, c.wi);
-        ell_op<T, false>(c, c.xi, c.wi, true, kE_, so.n[kE], P.err);
-        solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, ops.pivot_post, kB, so.n[kB1],
-                    so.n[kB2], P.err);
-        for (int j = threadIdx.x; j < np_; j += blockDim.x) P.z[P.perm[io + j]] = c.xi[j];
-        for (int j = threadIdx.x; j < nq; j += blockDim.x) P.z[P.perm[p + go + j]] = c.wi[j];
-        __syncthreads();
+        ell_op<T, false>(c, c.xi, c.wi, true, k.n[kE], P.err);
+        solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2], P.err);
+        for (int j = tid; j < np_; j += kConsumers) P.z[P.perm[io + j]] = c.xi[j];
+        for (int j = tid; j < nq; j += kConsumers) P.z[P.perm[p + go + j]] = c.wi[j];
+        csync();
     }
-out:
-    drain_ring(c);
+    return;
+abort:
+    consumers_abort_drain(c);
 }
 
 // ------------------------------------------------------------ E_rr(m) matvec
@@ -675,15 +913,14 @@ out:
 template <class T>
 __global__ void __launch_bounds__(kThreads, 1) pslr_err_kernel(const ErrParams<T> P) {
     extern __shared__ __align__(128) char smem[];
-    __shared__ Cta<T> c;
-    const bool pivots = P.bpiv != nullptr;
-    const SmemLayout L = smem_layout(P.slot_bytes, P.max_desc, P.max_p, P.max_q, sizeof(T), pivots);
-    cta_init(c, smem, L, P.slot_bytes, P.ops.segbase);
     if (ld_volatile(P.err) != 0) return;
-    const OpSetDev &ops = P.ops;
-    const int q = P.q;
+    const bool pivots = P.bpiv != nullptr;
+    const SmemLayout L = smem_layout(P.slot_bytes, P.ring, P.max_p, P.max_q, sizeof(T), pivots);
+    Cta<T> c;
+    if (!cta_start(c, smem, L, P.ring, P.slot_bytes, P.stream, P.stream_off, P.segbase)) return;
+    const int q = P.q, tid = threadIdx.x;
     bool ok = true;
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (tid == 0 && blockIdx.x == 0) {
         P.abuf[q] = T(0);
         P.abuf[(q + 1) + q] = T(0);
     }
@@ -692,110 +929,91 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_err_kernel(const ErrParams<T
         const T *vsrc = rep == 0 ? P.vin : P.vout;
         // a_i = C0_i^{-1} v_i  (local)
         for (int i = blockIdx.x; i < P.s; i += gridDim.x) {
-            const SubOps so = sub_ops(ops, i);
-            load_desc(c, ops, i, so.total);
+            const Counts k = counts_of(P.cnt, i);
             const int go = P.goff[i], nq = P.goff[i + 1] - go;
-            ProgBuild pb;
-            const int kC = pb.add(so.pos[kC1], so.n[kC1] + so.n[kC2]);
-            prog_start(c, pb.k, pb.b, pb.n);
-            for (int j = threadIdx.x; j < nq; j += blockDim.x) c.si[j] = __ldcg(vsrc + go + j);
-            if (threadIdx.x == 0) c.si[nq] = T(0);
-            __syncthreads();
-            solve_local(c, c.si, nq, pivots ? P.cpiv + go : nullptr, ops.pivot_post, kC, so.n[kC1],
-                        so.n[kC2], P.err);
-            for (int j = threadIdx.x; j < nq; j += blockDim.x) a[go + j] = c.si[j];
-            __syncthreads();
+            for (int j = tid; j < nq; j += kConsumers) c.si[j] = __ldcg(vsrc + go + j);
+            if (tid == 0) c.si[nq] = T(0);
+            csync();
+            solve_local(c, c.si, nq, pivots ? P.cpiv + go : nullptr, 0, k.n[kC1], k.n[kC2], P.err);
+            for (int j = tid; j < nq; j += kConsumers) a[go + j] = c.si[j];
+            csync();
         }
         grid_arrive(c, P.bar, P.grid);
         bool waited = false;
         // v_i = F_i B_i^{-1} E_i a_i - (C_g a)_i
         for (int i = blockIdx.x; i < P.s; i += gridDim.x) {
-            const SubOps so = sub_ops(ops, i);
-            load_desc(c, ops, i, so.total);
+            const Counts k = counts_of(P.cnt, i);
             const int io = P.ioff[i], np_ = P.ioff[i + 1] - io;
             const int go = P.goff[i], nq = P.goff[i + 1] - go;
-            ProgBuild pb;
-            const int kE_ = pb.add(so.pos[kE], so.n[kE]);
-            const int kB = pb.add(so.pos[kB1], so.n[kB1] + so.n[kB2]);
-            const int kF_ = pb.add(so.pos[kF], so.n[kF]);
-            const int kG = pb.add(so.pos[kCg], so.n[kCg]);
-            prog_start(c, pb.k, pb.b, pb.n);
-            for (int j = threadIdx.x; j < nq; j += blockDim.x) c.wi[j] = __ldcg(a + go + j);
-            if (threadIdx.x == 0) c.wi[nq] = T(0);
+            for (int j = tid; j < nq; j += kConsumers) c.wi[j] = __ldcg(a + go + j);
+            if (tid == 0) c.wi[nq] = T(0);
             fill(c.xi, np_ + 1, T(0));
-            __syncthreads();
-            ell_op<T, false>(c, c.xi, c.wi, false, kE_, so.n[kE], P.err);
-            solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, ops.pivot_post, kB, so.n[kB1],
-                        so.n[kB2], P.err);
+            csync();
+            ell_op<T, false>(c, c.xi, c.wi, false, k.n[kE], P.err);
+            solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, 0, k.n[kB1], k.n[kB2], P.err);
             fill(c.si, nq + 1, T(0));
-            __syncthreads();
-            ell_op<T, false>(c, c.si, c.xi, false, kF_, so.n[kF], P.err);
+            csync();
+            ell_op<T, false>(c, c.si, c.xi, false, k.n[kF], P.err);
             if (!waited) {
                 ok = grid_wait(c, P.bar, P.err, P.wait_limit);
                 waited = true;
-                if (!ok) goto out;
+                if (!ok) goto abort;
             }
-            ell_op<T, true>(c, c.si, a, true, kG, so.n[kCg], P.err);
-            for (int j = threadIdx.x; j < nq; j += blockDim.x) P.vout[go + j] = c.si[j];
-            __syncthreads();
+            ell_op<T, true>(c, c.si, a, true, k.n[kCg], P.err);
+            for (int j = tid; j < nq; j += kConsumers) P.vout[go + j] = c.si[j];
+            csync();
         }
         if (!waited) {
             ok = grid_wait(c, P.bar, P.err, P.wait_limit);
-            if (!ok) goto out;
+            if (!ok) goto abort;
         }
     }
-out:
-    drain_ring(c);
+    return;
+abort:
+    consumers_abort_drain(c);
 }
 
 // ------------------------------------------------------------- host launchers
 
-template <class T, class VT>
-cudaError_t launch_apply_t(const ApplyParams<T> &P, int smem_bytes, cudaStream_t st) {
-    auto kern = pslr_apply_kernel<T, VT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+template <class K, class Prm>
+static cudaError_t launch_coop(K kern, const Prm &P, int grid, int smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    void *args[] = {const_cast<ApplyParams<T> *>(&P)};
-    return cudaLaunchCooperativeKernel((const void *)kern, dim3(P.grid), dim3(kThreads), args,
-                                       smem_bytes, st);
+    void *args[] = {const_cast<Prm *>(&P)};
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kThreads), args, smem, st);
 }
 
 cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, cudaStream_t st) {
-    return launch_apply_t<double, double>(P, smem, st);
+    return launch_coop(pslr_apply_kernel<double, double>, P, P.grid, smem, st);
 }
 cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, cudaStream_t st) {
-    return launch_apply_t<float, __nv_bfloat16>(P, smem, st);
+    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16>, P, P.grid, smem, st);
 }
-
 cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, cudaStream_t st) {
-    auto kern = pslr_err_kernel<double>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    void *args[] = {const_cast<ErrParams<double> *>(&P)};
-    return cudaLaunchCooperativeKernel((const void *)kern, dim3(P.grid), dim3(kThreads), args, smem, st);
+    return launch_coop(pslr_err_kernel<double>, P, P.grid, smem, st);
 }
 
-// Largest cooperative grid of the persistent kernels for a dynamic smem size.
+// Largest cooperative grid of the persistent kernels for a dynamic smem size
+// (the smaller of the apply and E_rr kernels' occupancies).
 int max_coresident_apply(int smem, bool fp32) {
-    int dev = 0, nsm = 0, per = 0;
+    int dev = 0, nsm = 0, per = 0, per2 = 1 << 30;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e;
     if (fp32) {
-        e = cudaFuncSetAttribute(pslr_apply_kernel<float, __nv_bfloat16>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pslr_apply_kernel<float, __nv_bfloat16>,
-                                                              kThreads, smem);
+        auto k = pslr_apply_kernel<float, __nv_bfloat16>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreads, smem);
     } else {
-        e = cudaFuncSetAttribute(pslr_apply_kernel<double, double>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pslr_apply_kernel<double, double>,
-                                                              kThreads, smem);
+        auto k = pslr_apply_kernel<double, double>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreads, smem);
+        auto k2 = pslr_err_kernel<double>;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k2, kThreads, smem);
     }
     if (e != cudaSuccess) return 0;
-    return per * nsm;
+    return (per < per2 ? per : per2) * nsm;
 }
 
 }  // namespace pslr

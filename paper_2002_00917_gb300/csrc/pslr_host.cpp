@@ -15,11 +15,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
 
-#include "../../include/pslr.h"
+#include "pslr.h"
 #include "pslr_internal.h"
 
 namespace pslr {
@@ -73,6 +74,12 @@ uint16_t f32_to_bf16(float f) {  // round to nearest even
     return (uint16_t)(u >> 16);
 }
 
+// Host record of one packed segment.
+struct SegDesc {
+    int64_t off;
+    int32_t bytes;
+};
+
 // Segments of one direction and one precision, accumulated on the host.
 struct SegStore {
     std::vector<char> bytes;
@@ -88,30 +95,57 @@ void pack_segment(SegStore &S, const std::vector<Row> &rows, size_t b, size_t e,
     const int64_t nbytes = seg_bytes<T, IDX>(n, w, diag);
     SegDesc d;
     d.off = (int64_t)S.bytes.size();
-    d.bytes = n > 0 ? (int32_t)nbytes : 0;
-    d.n = (uint16_t)n;
-    d.w = (uint8_t)w;
-    d.flags = (uint8_t)((diag ? (unsigned)kSegDiag : 0u) | (sizeof(IDX) == 4 ? (unsigned)kSegGlobalCols : 0u));
-    if (n > 0) {
-        S.bytes.resize(S.bytes.size() + nbytes, 0);
-        char *base = S.bytes.data() + d.off;
-        T *vals = reinterpret_cast<T *>(base);
-        T *dinv = reinterpret_cast<T *>(base + (size_t)np * w * sizeof(T));
-        IDX *cols = reinterpret_cast<IDX *>(base + (size_t)np * w * sizeof(T) + (diag ? np * sizeof(T) : 0));
-        uint16_t *rws = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(cols) + (size_t)np * w * sizeof(IDX));
+    d.bytes = (int32_t)nbytes;
+    S.bytes.resize(S.bytes.size() + nbytes, 0);
+    char *base = S.bytes.data() + d.off;
+    SegHdr h;
+    std::memset(&h, 0, sizeof(h));
+    h.n = (uint16_t)n;
+    h.w = (uint8_t)w;
+    h.flags = (uint8_t)((diag ? (unsigned)kSegDiag : 0u) | (sizeof(IDX) == 4 ? (unsigned)kSegGlobalCols : 0u));
+    h.np = (uint16_t)np;
+    const int fmt = seg_fmt_for(w);
+    h.fmt = (uint8_t)fmt;
+    if (fmt != kTile) h.w = (uint8_t)fmt;
+    std::memcpy(base, &h, sizeof(h));
+    base += sizeof(SegHdr);
+    if (fmt != kTile) {
+        const int K = fmt;
+        IDX *idx = reinterpret_cast<IDX *>(base);
+        T *val = reinterpret_cast<T *>(base + (size_t)np * rec_idx_bytes<IDX>(K));
         for (int j = 0; j < np; ++j) {
             const bool real = j < n;
             const Row *R = real ? &rows[b + j] : nullptr;
-            for (int k = 0; k < w; ++k) {
+            IDX *ir = idx + (size_t)j * (K + 1);
+            T *vr = val + (size_t)j * (K + 1);
+            ir[0] = real ? (IDX)R->row : (IDX)0;
+            for (int k = 0; k < K; ++k) {
                 const bool has = real && k < (int)R->e.size();
-                vals[(size_t)k * np + j] = has ? (T)R->e[k].second : T(0);
-                cols[(size_t)k * np + j] = has ? (IDX)R->e[k].first : (IDX)zero_col;
+                ir[1 + k] = has ? (IDX)R->e[k].first : (IDX)zero_col;
+                vr[k] = has ? (T)R->e[k].second : T(0);
             }
-            if (diag) dinv[j] = real ? (T)(1.0 / R->diag) : T(0);
-            rws[j] = real ? (uint16_t)R->row : (uint16_t)0;
+            vr[K] = (real && diag) ? (T)(1.0 / R->diag) : T(1);  // rows without a diagonal scale by 1
         }
         S.max_bytes = std::max<int>(S.max_bytes, (int)nbytes);
+        S.desc.push_back(d);
+        return;
     }
+    T *vals = reinterpret_cast<T *>(base);
+    T *dinv = reinterpret_cast<T *>(base + (size_t)np * w * sizeof(T));
+    IDX *cols = reinterpret_cast<IDX *>(base + (size_t)np * w * sizeof(T) + (diag ? np * sizeof(T) : 0));
+    uint16_t *rws = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(cols) + (size_t)np * w * sizeof(IDX));
+    for (int j = 0; j < np; ++j) {
+        const bool real = j < n;
+        const Row *R = real ? &rows[b + j] : nullptr;
+        for (int k = 0; k < w; ++k) {
+            const bool has = real && k < (int)R->e.size();
+            vals[(size_t)k * np + j] = has ? (T)R->e[k].second : T(0);
+            cols[(size_t)k * np + j] = has ? (IDX)R->e[k].first : (IDX)zero_col;
+        }
+        if (diag) dinv[j] = real ? (T)(1.0 / R->diag) : T(0);
+        rws[j] = real ? (uint16_t)R->row : (uint16_t)0;
+    }
+    S.max_bytes = std::max<int>(S.max_bytes, (int)nbytes);
     S.desc.push_back(d);
 }
 
@@ -328,18 +362,24 @@ cudaError_t upload(X **dst, const std::vector<X> &src) {
 
 // ------------------------------------------------------------------ context
 
+// A CTA-ordered segment stream on the device (see pslr_internal.h).
+struct StreamDev {
+    StreamEnt *ent = nullptr;
+    int64_t *off = nullptr;
+};
+
 struct OpSetHost {
-    char *seg = nullptr;
-    SegDesc *desc = nullptr;
-    int32_t *sub_desc = nullptr;
-    int32_t *cnt = nullptr;
+    char *seg = nullptr;                 // device: all segments
+    int32_t *cnt = nullptr;              // device: kNCnt*s segment counts
+    std::vector<SegDesc> hdesc;          // host: segment offsets/sizes
+    std::vector<int32_t> hsub, hcnt;     // host: first descriptor and counts per subdomain
     int slot_bytes = 0;
-    int max_desc = 0;
+    int ring = 0;
     int64_t seg_total = 0;
     int64_t cat_bytes[kNCnt] = {0, 0, 0, 0, 0, 0, 0};  // segment bytes per category, all subdomains
-    int64_t nnz_cg = 0;
     int smem = 0;
     int grid = 0;
+    std::map<std::string, StreamDev> streams;  // keyed by launch shape
 };
 
 struct pslr_ctx {
@@ -408,9 +448,11 @@ void cfree(void *p) {
 
 void free_opset(OpSetHost &o) {
     cfree(o.seg);
-    cfree(o.desc);
-    cfree(o.sub_desc);
     cfree(o.cnt);
+    for (auto &kv : o.streams) {
+        cfree(kv.second.ent);
+        cfree(kv.second.off);
+    }
     o = OpSetHost();
 }
 
@@ -516,36 +558,33 @@ template <class T>
 static pslr_status finish_opset(pslr_ctx *c, OpSetHost &o, SegStore &S, const std::vector<int32_t> &sub_desc,
                                 const std::vector<int32_t> &cnt, bool fp32, bool plan_only) {
     o.slot_bytes = align_up(std::max(S.max_bytes, 128), 128);
-    o.max_desc = 0;
-    for (int i = 0; i < c->s; ++i) {
-        int t = 0;
-        for (int k = 0; k < kNCnt; ++k) t += cnt[(size_t)kNCnt * i + k];
-        o.max_desc = std::max(o.max_desc, t);
-    }
     o.seg_total = (int64_t)S.bytes.size();
     for (int i = 0; i < c->s; ++i) {
         int d = sub_desc[i];
         for (int k = 0; k < kNCnt; ++k)
             for (int t = 0; t < cnt[(size_t)kNCnt * i + k]; ++t) o.cat_bytes[k] += S.desc[d++].bytes;
     }
+    o.hdesc = S.desc;
+    o.hsub = sub_desc;
+    o.hcnt = cnt;
     if (S.bytes.empty()) S.bytes.resize(16, 0);
     const bool piv = c->factor == 1;
-    SmemLayout L = smem_layout(o.slot_bytes, o.max_desc, c->max_p, c->max_q, fp32 ? 4 : 8, piv);
-    o.smem = L.total;
     int optin = 227 * 1024;  // sm_100-class opt-in limit; queried from the device when there is one
     if (!plan_only) {
         CK(upload(&o.seg, S.bytes));
-        CK(upload(&o.desc, S.desc));
-        CK(upload(&o.sub_desc, sub_desc));
         CK(upload(&o.cnt, cnt));
         int dev = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     }
-    if (o.smem + 1024 > optin)
+    // ring depth: as many slots as fit next to the vectors, 2 .. kMaxRing
+    const int avail = optin - 1024 - smem_fixed(c->max_p, c->max_q, fp32 ? 4 : 8, piv);
+    o.ring = std::min(kMaxRing, avail / o.slot_bytes);
+    if (o.ring < 2)
         return fail(c, PSLR_ERR_TOO_LARGE,
-                    "a subdomain needs %d bytes of shared memory (limit %d): use more subdomains",
-                    o.smem, optin - 1024);
+                    "a subdomain needs more shared memory than one CTA has (%d interior, %d interface "
+                    "unknowns): use more subdomains", c->max_p, c->max_q);
+    o.smem = smem_layout(o.slot_bytes, o.ring, c->max_p, c->max_q, fp32 ? 4 : 8, piv).total;
     o.grid = 0;
     return PSLR_OK;
 }
@@ -865,15 +904,74 @@ pslr_status pslr_setup(int32_t n, const int32_t *rowptr, const int32_t *colind, 
 
 // ----------------------------------------------------------------- applies
 
+// The per-CTA segment stream of one launch shape, built on first use: for
+// CTA b and its subdomains b, b+grid, ..., the segments in exactly the order
+// the kernel's consumers take them.  kind 0: apply (forward or transposed,
+// with the low-rank term before the series when lr_before); kind 1: E_rr(m).
+static pslr_status get_stream(pslr_ctx *c, OpSetHost &o, int kind, int m, bool lr_before,
+                              const StreamDev **out) {
+    char key[64];
+    snprintf(key, sizeof(key), "%d/%d/%d", kind, m, (int)lr_before);
+    auto it = o.streams.find(key);
+    if (it != o.streams.end()) {
+        *out = &it->second;
+        return PSLR_OK;
+    }
+    const int s = c->s, G = o.grid;
+    std::vector<StreamEnt> ent;
+    std::vector<int64_t> off(G + 1, 0);
+    auto add = [&](int i, std::initializer_list<int> cats) {
+        for (int cat : cats) {
+            int d = o.hsub[i];
+            for (int k = 0; k < cat; ++k) d += o.hcnt[(size_t)kNCnt * i + k];
+            for (int t = 0; t < o.hcnt[(size_t)kNCnt * i + cat]; ++t) {
+                StreamEnt e;
+                e.off = o.hdesc[d + t].off;
+                e.bytes = o.hdesc[d + t].bytes;
+                e.pad = 0;
+                ent.push_back(e);
+            }
+        }
+    };
+    for (int b = 0; b < G; ++b) {
+        off[b] = (int64_t)ent.size();
+        if (kind == 0) {
+            for (int i = b; i < s; i += G) {
+                add(i, {kB1, kB2, kF});
+                if (!lr_before) add(i, {kC1, kC2});
+            }
+            if (lr_before)
+                for (int i = b; i < s; i += G) add(i, {kC1, kC2});
+            for (int k = 1; k <= m; ++k)
+                for (int i = b; i < s; i += G) add(i, {kE, kB1, kB2, kF, kCg, kC1, kC2});
+            for (int i = b; i < s; i += G) add(i, {kE, kB1, kB2});
+        } else {
+            for (int rep = 0; rep <= m; ++rep) {
+                for (int i = b; i < s; i += G) add(i, {kC1, kC2});
+                for (int i = b; i < s; i += G) add(i, {kE, kB1, kB2, kF, kCg});
+            }
+        }
+    }
+    off[G] = (int64_t)ent.size();
+    StreamDev sd;
+    CK(upload(&sd.ent, ent));
+    CK(upload(&sd.off, off));
+    o.streams[key] = sd;
+    *out = &o.streams[key];
+    return PSLR_OK;
+}
+
 template <class T>
-static void fill_params(pslr_ctx *c, ApplyParams<T> &P, int dir, int prec) {
+static void fill_params(pslr_ctx *c, ApplyParams<T> &P, int dir, int prec, const StreamDev *sd) {
     const OpSetHost &o = c->ops[dir][prec];
-    P.ops.segbase = o.seg;
-    P.ops.desc = o.desc;
-    P.ops.sub_desc = o.sub_desc;
-    P.ops.cnt = o.cnt;
-    P.ops.pivot_post = dir;
-    P.ops.lowrank_after = dir;
+    P.segbase = o.seg;
+    P.stream = sd->ent;
+    P.stream_off = sd->off;
+    P.cnt = o.cnt;
+    P.ring = o.ring;
+    P.slot_bytes = o.slot_bytes;
+    P.pivot_post = dir;
+    P.lowrank_after = dir;
     P.s = c->s;
     P.p = c->p;
     P.q = c->q;
@@ -882,8 +980,6 @@ static void fill_params(pslr_ctx *c, ApplyParams<T> &P, int dir, int prec) {
     P.grid = o.grid;
     P.max_p = c->max_p;
     P.max_q = c->max_q;
-    P.max_desc = o.max_desc;
-    P.slot_bytes = o.slot_bytes;
     P.ioff = c->d_ioff;
     P.goff = c->d_goff;
     P.perm = c->d_perm;
@@ -900,11 +996,14 @@ static void fill_params(pslr_ctx *c, ApplyParams<T> &P, int dir, int prec) {
 
 static pslr_status apply_one(pslr_ctx *c, const void *b, void *z, int prec, int dir, const int *skip,
                              cudaStream_t st) {
-    const OpSetHost &o = c->ops[dir][prec];
+    OpSetHost &o = c->ops[dir][prec];
+    const StreamDev *sd = nullptr;
+    pslr_status ss = get_stream(c, o, 0, c->m, c->r > 0 && dir == 0, &sd);
+    if (ss != PSLR_OK) return ss;
     cudaError_t e;
     if (prec == PSLR_FP64) {
         ApplyParams<double> P;
-        fill_params(c, P, dir, prec);
+        fill_params(c, P, dir, prec, sd);
         P.V = c->d_V;
         P.G = dir ? c->d_GT : c->d_G;
         P.b = static_cast<const double *>(b);
@@ -913,7 +1012,7 @@ static pslr_status apply_one(pslr_ctx *c, const void *b, void *z, int prec, int 
         e = launch_apply_fp64(P, o.smem, st);
     } else {
         ApplyParams<float> P;
-        fill_params(c, P, dir, prec);
+        fill_params(c, P, dir, prec, sd);
         P.V = c->d_Vb;
         P.G = dir ? c->d_GTf : c->d_Gf;
         P.b = static_cast<const float *>(b);
@@ -1224,14 +1323,17 @@ static void cgs2(KWork &W, int len, int k, const double *V, int64_t ld, double *
 }
 
 static pslr_status launch_err(pslr_ctx *c, const double *vin, double *vout, int m, cudaStream_t st) {
-    const OpSetHost &o = c->ops[0][0];
+    OpSetHost &o = c->ops[0][0];
+    const StreamDev *sd = nullptr;
+    pslr_status ss = get_stream(c, o, 1, m, false, &sd);
+    if (ss != PSLR_OK) return ss;
     ErrParams<double> P;
-    P.ops.segbase = o.seg;
-    P.ops.desc = o.desc;
-    P.ops.sub_desc = o.sub_desc;
-    P.ops.cnt = o.cnt;
-    P.ops.pivot_post = 0;
-    P.ops.lowrank_after = 0;
+    P.segbase = o.seg;
+    P.stream = sd->ent;
+    P.stream_off = sd->off;
+    P.cnt = o.cnt;
+    P.ring = o.ring;
+    P.slot_bytes = o.slot_bytes;
     P.s = c->s;
     P.p = c->p;
     P.q = c->q;
@@ -1239,8 +1341,6 @@ static pslr_status launch_err(pslr_ctx *c, const double *vin, double *vout, int 
     P.grid = o.grid;
     P.max_p = c->max_p;
     P.max_q = c->max_q;
-    P.max_desc = o.max_desc;
-    P.slot_bytes = o.slot_bytes;
     P.ioff = c->d_ioff;
     P.goff = c->d_goff;
     P.bpiv = c->d_bpiv;

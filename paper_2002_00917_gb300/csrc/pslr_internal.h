@@ -1,18 +1,28 @@
 // Internal layout shared by the host set-up (pslr_host.cpp) and the kernels.
 //
 // Device data layout.  Every sparse piece the apply touches - one level of a
-// triangular factor, or the E_i / F_i / C_g,i block of one subdomain - is a
-// "segment": a contiguous, 16-byte aligned byte range holding an ELL tile
-// (rows padded to npad = round_up(n, 8), entries slot-major):
+// triangular factor, or a slice of the E_i / F_i / C_g,i block of one
+// subdomain - is a "segment": a contiguous, 16-byte aligned byte range of
+// at most kSegMaxRows rows (one consumer thread per row) that starts with a
+// 16-byte SegHdr.  Rows are padded to np = round_up(n, 8).  Two encodings:
 //
-//     val_t vals[w][npad];   val_t dinv[npad] (only with a diagonal);
-//     idx_t cols[w][npad];   uint16 rows[npad];
+//   record (fmt kRec3 / kRec7, rows with at most 3 / 7 entries): per row one
+//     index record and one value record, so a thread fetches its row with one
+//     or two vector loads at j * size and no address arithmetic:
+//       idx[np]:  {row, c_0 .. c_{K-1}}   (uint16, or int32 for global columns)
+//       val[np]:  {v_0 .. v_{K-1}, dinv}  (value type; dinv = 1/diagonal, or 1)
+//     with K = 3 or 7 entries; unused entries point at the zero slot with
+//     value 0, so every row runs the same K fused multiply-adds.
+//   tile (fmt kTile, wider rows): ELL slot-major,
+//       vals[w][np], dinv[np] (with a diagonal), cols[w][np], rows[np].
 //
-// idx_t is uint16 for subdomain-local columns and int32 for the global
-// interface columns of C_g.  Padded entries point at a zero slot (local index
-// n_local, or q for the global interface vector) with value 0.  Segments are
-// staged into shared memory by TMA bulk copies (cp.async.bulk) a few ahead of
-// their use, so the dependent chain of a triangular solve never waits on L2.
+// The zero slot is index n_local of the shared-memory vector (or q for the
+// global interface vector), which always holds 0.
+//
+// For every launch the host lays out, per CTA, the exact sequence of segments
+// its consumers will use (the "stream").  A producer warp walks the stream and
+// copies each segment into a shared-memory ring with a TMA bulk copy as soon
+// as a slot frees up; consumers take segments from the ring in the same order.
 #pragma once
 #include <cstdint>
 
@@ -24,60 +34,80 @@
 
 namespace pslr {
 
-constexpr int kThreads = 256;      // threads per CTA of the persistent kernels
-constexpr int kRing = 4;           // segments in flight per CTA
-constexpr int kMaxRank = 64;       // largest low-rank term
+constexpr int kConsumers = 256;             // consumer threads (8 warps)
+constexpr int kThreads = kConsumers + 32;   // + one producer warp
+constexpr int kSegMaxRows = kConsumers;     // rows per segment
+constexpr int kSegBudget = 12 * 1024;       // bytes per segment (one ring slot at most)
+constexpr int kMaxRing = 32;                // ring slots at most
+constexpr int kMaxRank = 128;               // largest low-rank term
 
 enum SegFlags : uint32_t { kSegDiag = 1u, kSegGlobalCols = 2u };
+enum SegFmt : uint8_t { kTile = 0, kRec3 = 3, kRec7 = 7 };
 
-struct SegDesc {
-    int64_t off;     // byte offset from the segment base (multiple of 16)
-    int32_t bytes;   // byte size (multiple of 16); 0 = empty segment
+struct SegHdr {
     uint16_t n;      // rows
-    uint8_t w;       // entries per row after padding
+    uint8_t w;       // entries per row (tile: padded width; record: K)
     uint8_t flags;   // SegFlags
+    uint16_t np;     // padded rows
+    uint8_t fmt;     // SegFmt
+    uint8_t pad0;
+    uint32_t pad1, pad2;
 };
-static_assert(sizeof(SegDesc) == 16, "SegDesc is 16 bytes");
+static_assert(sizeof(SegHdr) == 16, "SegHdr is 16 bytes");
+
+// One entry of a CTA's segment stream.
+struct StreamEnt {
+    int64_t off;     // byte offset of the segment from the segment base
+    int32_t bytes;   // byte size (multiple of 16)
+    int32_t pad;
+};
+static_assert(sizeof(StreamEnt) == 16, "StreamEnt is 16 bytes");
 
 PSLR_HD inline int seg_npad(int n) { return (n + 7) & ~7; }
 
+// Record sizes of the kRec3 / kRec7 encodings.
+template <class IDX>
+PSLR_HD inline int rec_idx_bytes(int K) {
+    return (K + 1) * (int)sizeof(IDX);
+}
+template <class T>
+PSLR_HD inline int rec_val_bytes(int K) {
+    return (K + 1) * (int)sizeof(T);
+}
+
+// Bytes of a segment of n rows and width w (fmt chosen from w).
+PSLR_HD inline int seg_fmt_for(int w) { return w <= 3 ? kRec3 : (w <= 7 ? kRec7 : kTile); }
+
 template <class T, class IDX>
 PSLR_HD inline int64_t seg_bytes(int n, int w, bool diag) {
-    int64_t np = seg_npad(n);
-    return np * w * (int64_t)sizeof(T) + (diag ? np * (int64_t)sizeof(T) : 0) +
+    const int64_t np = seg_npad(n);
+    const int fmt = seg_fmt_for(w);
+    if (fmt != kTile) return 16 + np * (rec_idx_bytes<IDX>(fmt) + rec_val_bytes<T>(fmt));
+    return 16 + np * w * (int64_t)sizeof(T) + (diag ? np * (int64_t)sizeof(T) : 0) +
            np * w * (int64_t)sizeof(IDX) + np * 2;
 }
 
-// Per-subdomain descriptor table, in this order: the segments of E, of F, of
-// C_g, of sweep 1 of the B solve, of sweep 2 of the B solve, of sweep 1 of
-// the C0 solve and of sweep 2 of the C0 solve (cnt[7] per subdomain gives the
-// number of each).  A level or block larger than kSegBudget bytes is split
-// into several segments.  In the forward direction the B solve is L then U
+// Segment counts of one subdomain, in stream order of its descriptor table:
+// E, F, C_g, sweep 1 of the B solve, sweep 2 of the B solve, sweep 1 and
+// sweep 2 of the C0 solve.  In the forward direction the B solve is L then U
 // and E, F, C_g are E_i, F_i and the rows of C_g of subdomain i; in the
 // transposed direction the solve is U^T then L^T and the slots hold F_i^T,
 // E_i^T and the rows of C_g^T of subdomain i.
 enum { kE = 0, kF = 1, kCg = 2, kB1 = 3, kB2 = 4, kC1 = 5, kC2 = 6, kNCnt = 7 };
-constexpr int kSegBudget = 12 * 1024;  // bytes per segment (one ring slot)
-constexpr int kSegMaxRows = 256;       // rows per segment (one per thread)
-
-// Everything one direction (forward or transposed) of one precision needs.
-struct OpSetDev {
-    const char *segbase;       // all segments of this direction and precision
-    const SegDesc *desc;       // descriptor tables of all subdomains
-    const int32_t *sub_desc;   // s: first descriptor of subdomain i
-    const int32_t *cnt;        // kNCnt*s: segment counts of E, F, Cg, B1, B2, C1, C2
-    int pivot_post;            // exact LU: 0 gather rhs before the B/C0 sweeps, 1 scatter after
-    int lowrank_after;         // 0: t <- t + V G V^T t before the series (Algorithm 3)
-                               // 1: w <- w + V G^T V^T w after it (transpose)
-};
 
 // Parameters of one launch of the persistent apply kernel.
 template <class T>
 struct ApplyParams {
-    OpSetDev ops;
+    const char *segbase;         // segments of this direction and precision
+    const StreamEnt *stream;     // all CTAs' streams
+    const int64_t *stream_off;   // grid+1: CTA b uses stream[stream_off[b] .. stream_off[b+1])
+    const int32_t *cnt;          // kNCnt*s segment counts
+    int ring, slot_bytes;        // ring slots and slot size
+    int pivot_post;              // exact LU: 0 gather rhs before the sweeps, 1 scatter after
+    int lowrank_after;           // 0: t <- t + V G V^T t before the series (Algorithm 3)
+                                 // 1: w <- w + V G^T V^T w after it (transpose)
     int s, p, q, r, m, grid;
-    int max_p, max_q, max_desc;  // shared-memory sizing
-    int slot_bytes;              // ring slot size
+    int max_p, max_q;            // shared-memory sizing
     const int32_t *ioff, *goff;  // s+1 interior / interface offsets
     const int32_t *perm;         // n: reordered index -> original index
     const uint16_t *bpiv;        // p: exact-LU row permutation of B (local), or nullptr
@@ -92,15 +122,19 @@ struct ApplyParams {
     unsigned *bar;               // [0] arrivals, [1] generation
     int *err;                    // latched error (pslr_status)
     const int *skip;             // when *skip != 0 the launch does nothing (converged FGMRES cycle)
-    long long wait_limit;        // polls before a wait gives up
+    long long wait_limit;        // polls before a grid-barrier wait gives up
 };
 
 // E_rr(m) v for the Arnoldi process (Eq. 3.19): v <- (E_s C0^{-1})^{m+1} v.
 template <class T>
 struct ErrParams {
-    OpSetDev ops;                // forward direction
+    const char *segbase;
+    const StreamEnt *stream;
+    const int64_t *stream_off;
+    const int32_t *cnt;
+    int ring, slot_bytes;
     int s, p, q, m, grid;
-    int max_p, max_q, max_desc, slot_bytes;
+    int max_p, max_q;
     const int32_t *ioff, *goff;
     const uint16_t *bpiv, *cpiv;
     const T *vin;                // q (interface numbering)
@@ -113,23 +147,36 @@ struct ErrParams {
 
 // Shared-memory layout of the persistent kernels (host and device agree on it).
 struct SmemLayout {
-    int ring, mbar, desc, xi, wi, si, tmp, red, total;
+    int ring, full, empty, ctl, xi, wi, si, tmp, red, total;
 };
 
 PSLR_HD inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-PSLR_HD inline SmemLayout smem_layout(int slot_bytes, int max_desc, int max_p,
-                                                  int max_q, int tsize, bool pivots) {
+// Bytes of everything but the ring.
+PSLR_HD inline int smem_fixed(int max_p, int max_q, int tsize, bool pivots) {
+    int o = 2 * align_up(kMaxRing * 8, 16) + 128;
+    o = align_up(o, 128);
+    o += align_up((max_p + 1) * tsize, 128);
+    o += 2 * align_up((max_q + 1) * tsize, 128);
+    o += pivots ? align_up(((max_p > max_q ? max_p : max_q) + 1) * tsize, 128) : 0;
+    o += align_up((kConsumers / 32 + 2) * kMaxRank * 8, 128);
+    return o;
+}
+
+PSLR_HD inline SmemLayout smem_layout(int slot_bytes, int ring, int max_p, int max_q, int tsize,
+                                      bool pivots) {
     SmemLayout L;
     int o = 0;
-    L.ring = o;  o += kRing * slot_bytes;
-    L.mbar = o;  o += align_up(kRing * 8, 128);
-    L.desc = o;  o += align_up(max_desc * 16, 128);
+    L.ring = o;  o += ring * slot_bytes;
+    L.full = o;  o += align_up(kMaxRing * 8, 16);
+    L.empty = o; o += align_up(kMaxRing * 8, 16);
+    L.ctl = o;   o += 128;
+    o = align_up(o, 128);
     L.xi = o;    o += align_up((max_p + 1) * tsize, 128);
     L.wi = o;    o += align_up((max_q + 1) * tsize, 128);
     L.si = o;    o += align_up((max_q + 1) * tsize, 128);
     L.tmp = o;   o += pivots ? align_up(((max_p > max_q ? max_p : max_q) + 1) * tsize, 128) : 0;
-    L.red = o;   o += align_up((kThreads / 32 + 2) * kMaxRank * 8, 128);
+    L.red = o;   o += align_up((kConsumers / 32 + 2) * kMaxRank * 8, 128);
     L.total = o;
     return L;
 }

@@ -20,6 +20,7 @@ namespace pslr {
 
 constexpr int kKThreads = 256;
 constexpr int kChunk = 8;  // basis columns per register chunk
+constexpr int kMaxK = 128; // basis columns of one CGS pass (Arnoldi rank, FGMRES restart + 1)
 
 __device__ __forceinline__ bool skipping(const int *skip) {
     return skip != nullptr && *(volatile const int *)skip != 0;
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(kKThreads) k_cgs_pass(
     const double *__restrict__ z, const int *skip) {
     if (skipping(skip)) return;
     __shared__ double sh[(kKThreads / 32) * kChunk];
-    __shared__ double hs[64];
+    __shared__ double hs[kMaxK];
     __shared__ double outs[kChunk];
     const int stride = gridDim.x * blockDim.x;
     const int i0 = blockIdx.x * blockDim.x + threadIdx.x;

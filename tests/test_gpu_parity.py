@@ -194,11 +194,11 @@ def test_transposed_solve(dev):
     b, _ = G.uniform_rhs(w["A"], 1)
     bd = torch.tensor(b, device=dev)
     x = torch.empty_like(bd)
-    its, rel, st = ctx.solve(bd, x, rtol=1e-10, transpose=True)
-    xo, its_o, rel_o, st_o = orc.fgmres(b, rtol=1e-10, transpose=True)
-    assert st == 0 and rel <= 1e-10 and abs(its - its_o) <= 1
+    its, rel, st = ctx.solve(bd, x, rtol=1e-8, transpose=True)
+    xo, its_o, rel_o, st_o = orc.fgmres(b, rtol=1e-8, transpose=True)
+    assert st_o == 0 and st == 0 and rel <= 1e-8 and abs(its - its_o) <= 1, (its, its_o, rel)
     At = G.dense_from_csr(w["A"]).T
-    assert np.linalg.norm(b - At @ x.cpu().numpy()) <= 1.0001e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(b - At @ x.cpu().numpy()) <= 1.0001e-8 * np.linalg.norm(b)
 
 
 def test_matvec(dev):
