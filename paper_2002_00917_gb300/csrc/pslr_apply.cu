@@ -81,6 +81,42 @@ __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Explicit shared-memory accesses on 32-bit shared addresses (the hot loops
+// reach their vectors through struct members, where generic addressing
+// would otherwise be used).  volatile keeps them in program order with the
+// barriers and with each other.
+__device__ __forceinline__ float lds(uint32_t a, float) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ double lds(uint32_t a, double) {
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts(uint32_t a, float v) {
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void sts(uint32_t a, double v) {
+    asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ uint2 lds_u2(uint32_t a) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float4 lds_f4(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ double2 lds_d2(uint32_t a) {
+    double2 v;
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
+    return v;
+}
+
 // Barrier among the consumer warps only (named barrier 1).
 __device__ __forceinline__ void csync() {
     asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
@@ -182,11 +218,14 @@ __device__ void producer(const StreamEnt *stream, int64_t b, int64_t e, const ch
                 // slot free?  (the first pass over the ring finds every slot free)
                 const uint32_t ebar = empty_s + 8 * slot;
                 long long it = 0;
+                // the ring is normally full here: back off instead of polling,
+                // so this warp does not take issue slots from the consumers
                 while (!mbar_try_wait(ebar, phase ^ 1u)) {
                     if (ld_volatile(&ctl->abort) || ++it > kTmaWaitLimit) {
                         stop = true;
                         break;
                     }
+                    __nanosleep(128);
                 }
                 if (!stop) {
                     const uint32_t fbar = full_s + 8 * slot;
@@ -542,36 +581,154 @@ __device__ __forceinline__ Rec3<T> rec3_local(const char *seg, int np, int j) {
     return e;
 }
 
+// Header fields and, for a 3-entry record level, the thread's row: all read
+// ahead of use (nothing here depends on the vector being solved for).
+template <class T>
+struct LevelPre {
+    const char *seg;
+    int n, np, fmt;
+    Rec3<T> e;
+};
+
+template <class T>
+__device__ __forceinline__ LevelPre<T> level_pre(const char *seg, int j) {
+    LevelPre<T> q;
+    q.seg = seg;
+    const uint2 h = *reinterpret_cast<const uint2 *>(seg);
+    q.n = (int)(h.x & 0xffffu);
+    q.np = (int)(h.y & 0xffffu);
+    q.fmt = (int)((h.y >> 16) & 0xffu);
+    if (q.fmt == kRec3 && j < q.n) q.e = rec3_local<T>(seg, q.np, j);
+    return q;
+}
+
+// Rows of a level in the 7-entry record or tile encodings (exact local LU,
+// irregular matrices): out of line, so the common path stays small.
+template <class T>
+__device__ __noinline__ void level_row_general(const char *seg, T *x, int j) {
+    RowPre<T, uint16_t> g = row_pre<T, uint16_t>(seg, j);
+    if (j < g.n) {
+        T a = row_sub(g, j, x[g.r], [&](int col) { return x[col]; });
+        if (g.diag) a *= g.dv;
+        x[g.r] = a;
+    }
+}
+
+// x[r] = (x[r] - sum_k T_rk x[c_k]) * dinv[r] for the thread's row of one level.
+template <class T>
+__device__ __forceinline__ void level_row(const LevelPre<T> &q, T *x, int j) {
+    if (q.fmt == kRec3) {
+        if (j < q.n) {
+            T a = x[q.e.r];
+            a = fma_t(-q.e.v0, x[q.e.c0], a);
+            a = fma_t(-q.e.v1, x[q.e.c1], a);
+            a = fma_t(-q.e.v2, x[q.e.c2], a);
+            x[q.e.r] = a * q.e.d;
+        }
+    } else {
+        level_row_general(q.seg, x, j);
+    }
+}
+
+// Slow path of a segment wait (the producer is normally far ahead).
+__device__ __noinline__ void wait_full_slow(uint32_t bar, uint32_t phase, int *err) {
+    long long it = 0;
+    while (!mbar_try_wait(bar, phase)) {
+        if (++it > kTmaWaitLimit) {
+            atomicCAS(err, 0, kErrTimeout);
+            return;
+        }
+    }
+}
+
+// The 3-entry record of row j of the kRec3 segment at shared address seg.
+template <class T>
+__device__ __forceinline__ Rec3<T> rec3_shared(uint32_t seg, int np, int j) {
+    Rec3<T> e;
+    const uint2 id = lds_u2(seg + (uint32_t)sizeof(SegHdr) + 8u * j);
+    e.r = (int)(id.x & 0xffffu);
+    e.c0 = (int)(id.x >> 16);
+    e.c1 = (int)(id.y & 0xffffu);
+    e.c2 = (int)(id.y >> 16);
+    const uint32_t vp = seg + (uint32_t)sizeof(SegHdr) + 8u * np + (uint32_t)(4 * sizeof(T)) * j;
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = lds_f4(vp);
+        e.v0 = v.x;
+        e.v1 = v.y;
+        e.v2 = v.z;
+        e.d = v.w;
+    } else {
+        const double2 a = lds_d2(vp), b = lds_d2(vp + 16);
+        e.v0 = a.x;
+        e.v1 = a.y;
+        e.v2 = b.x;
+        e.d = b.y;
+    }
+    return e;
+}
+
 // One triangular sweep over `nseg` level segments, in place:
-// x[r] = (x[r] - sum_k T_rk x[c_k]) * dinv[r].  Levels in the 3-entry record
-// encoding (every level of a 7-point ILU(0) factor) take a short fixed path:
-// header, two record loads, four gathers, three FMAs, one multiply, a store.
+// x[r] = (x[r] - sum_k T_rk x[c_k]) (* dinv[r]).  The loop is kept to a few
+// instructions per level (the level chain is latency-bound with two warps per
+// scheduler, so every instruction costs): ring cursor in registers advanced
+// incrementally, one wait, one header load, the 3-entry record path inline and
+// everything else out of line.
 template <class T>
 __device__ void tri_sweep(Cta<T> &c, T *x, int nseg, int *err) {
+    Ring &R = c.ring;
+    int slot = R.slot;
+    uint32_t phase = R.phase;
+    uint32_t fbar = R.full_s + 8 * slot;
+    const uint32_t edelta = R.empty_s - R.full_s;
+    const uint32_t base_s = smem_addr(R.base);
+    uint32_t ptr_s = base_s + (uint32_t)(slot * R.slot_bytes);
+    const uint32_t xs = smem_addr(x);
     const int j = threadIdx.x;
+    constexpr uint32_t ts = sizeof(T);
     for (int L = 0; L < nseg; ++L) {
-        const char *seg = seg_next(c.ring, err);
-        const uint2 h = *reinterpret_cast<const uint2 *>(seg);
-        const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu), fmt = (int)((h.y >> 16) & 0xffu);
-        if (fmt == kRec3) {
-            if (j < n) {
-                const Rec3<T> e = rec3_local<T>(seg, np, j);
-                T a = x[e.r];
-                a = fma_t(-e.v0, x[e.c0], a);
-                a = fma_t(-e.v1, x[e.c1], a);
-                a = fma_t(-e.v2, x[e.c2], a);
-                x[e.r] = a * e.d;
+        if (!mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
+        const uint2 h = lds_u2(ptr_s);
+        if (((h.y >> 16) & 0xffu) == kRec3) {
+            if (j < (int)(h.x & 0xffffu)) {
+                const Rec3<T> e = rec3_shared<T>(ptr_s, (int)(h.y & 0xffffu), j);
+                const T x0 = lds(xs + ts * e.c0, T()), x1 = lds(xs + ts * e.c1, T());
+                const T x2 = lds(xs + ts * e.c2, T()), xr = lds(xs + ts * e.r, T());
+                T a = fma_t(-e.v0, x0, xr);
+                a = fma_t(-e.v1, x1, a);
+                a = fma_t(-e.v2, x2, a);
+                if ((h.x >> 24) & kSegDiag) a *= e.d;
+                sts(xs + ts * e.r, a);
             }
         } else {
-            RowPre<T, uint16_t> q = row_pre<T, uint16_t>(seg, j);
-            if (j < q.n) {
-                T a = row_sub(q, j, x[q.r], [&](int col) { return x[col]; });
-                if (q.diag) a *= q.dv;
-                x[q.r] = a;
-            }
+            level_row_general(R.base + (ptr_s - base_s), x, j);
         }
         csync();
-        seg_done(c.ring);
+        if (j == 0) mbar_arrive(fbar + edelta);
+        ++slot;
+        fbar += 8;
+        ptr_s += R.slot_bytes;
+        if (slot == R.slots) {
+            slot = 0;
+            phase ^= 1u;
+            fbar = R.full_s;
+            ptr_s = base_s;
+        }
+    }
+    R.slot = slot;
+    R.phase = phase;
+    R.consumed += nseg;
+}
+
+// Rows of an ELL segment in the general encodings (out of line).
+template <class T, bool GLOBAL>
+__device__ __noinline__ void ell_row_general(const char *seg, T *out, const T *src, bool subtract, int j) {
+    using IDX = typename std::conditional<GLOBAL, int32_t, uint16_t>::type;
+    RowPre<T, IDX> q = row_pre<T, IDX>(seg, j);
+    if (j < q.n) {
+        T a;
+        if (GLOBAL) a = -row_sub(q, j, T(0), [&](int col) { return __ldcg(src + col); });
+        else a = -row_sub(q, j, T(0), [&](int col) { return src[col]; });
+        out[q.r] = subtract ? out[q.r] - a : a;
     }
 }
 
@@ -579,32 +736,48 @@ __device__ void tri_sweep(Cta<T> &c, T *x, int nseg, int *err) {
 // (subtract); src in shared memory (local columns) or global memory.
 template <class T, bool GLOBAL>
 __device__ void ell_op(Cta<T> &c, T *out, const T *src, bool subtract, int nseg, int *err) {
+    Ring &R = c.ring;
+    int slot = R.slot;
+    uint32_t phase = R.phase;
+    uint32_t fbar = R.full_s + 8 * slot;
+    const uint32_t edelta = R.empty_s - R.full_s;
+    const uint32_t base_s = smem_addr(R.base);
+    uint32_t ptr_s = base_s + (uint32_t)(slot * R.slot_bytes);
+    const uint32_t os = smem_addr(out);
     const int j = threadIdx.x;
-    using IDX = typename std::conditional<GLOBAL, int32_t, uint16_t>::type;
+    constexpr uint32_t ts = sizeof(T);
     for (int k = 0; k < nseg; ++k) {
-        const char *seg = seg_next(c.ring, err);
-        const uint2 h = *reinterpret_cast<const uint2 *>(seg);
-        const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu), fmt = (int)((h.y >> 16) & 0xffu);
-        if (!GLOBAL && fmt == kRec3) {
-            if (j < n) {
-                const Rec3<T> e = rec3_local<T>(seg, np, j);
-                T a = e.v0 * src[e.c0];
-                a = fma_t(e.v1, src[e.c1], a);
-                a = fma_t(e.v2, src[e.c2], a);
-                out[e.r] = subtract ? out[e.r] - a : a;
+        if (!mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
+        const uint2 h = lds_u2(ptr_s);
+        if (!GLOBAL && ((h.y >> 16) & 0xffu) == kRec3) {
+            if (j < (int)(h.x & 0xffffu)) {
+                const uint32_t ss = smem_addr(src);
+                const Rec3<T> e = rec3_shared<T>(ptr_s, (int)(h.y & 0xffffu), j);
+                const T s0 = lds(ss + ts * e.c0, T()), s1 = lds(ss + ts * e.c1, T()), s2 = lds(ss + ts * e.c2, T());
+                T a = e.v0 * s0;
+                a = fma_t(e.v1, s1, a);
+                a = fma_t(e.v2, s2, a);
+                if (subtract) a = lds(os + ts * e.r, T()) - a;
+                sts(os + ts * e.r, a);
             }
         } else {
-            RowPre<T, IDX> q = row_pre<T, IDX>(seg, j);
-            if (j < q.n) {
-                T a;
-                if (GLOBAL) a = -row_sub(q, j, T(0), [&](int col) { return __ldcg(src + col); });
-                else a = -row_sub(q, j, T(0), [&](int col) { return src[col]; });
-                out[q.r] = subtract ? out[q.r] - a : a;
-            }
+            ell_row_general<T, GLOBAL>(R.base + (ptr_s - base_s), out, src, subtract, j);
         }
         csync();
-        seg_done(c.ring);
+        if (j == 0) mbar_arrive(fbar + edelta);
+        ++slot;
+        fbar += 8;
+        ptr_s += R.slot_bytes;
+        if (slot == R.slots) {
+            slot = 0;
+            phase ^= 1u;
+            fbar = R.full_s;
+            ptr_s = base_s;
+        }
     }
+    R.slot = slot;
+    R.phase = phase;
+    R.consumed += nseg;
 }
 
 // Exact-LU row permutation: x <- P x (gather, before the sweeps) or
