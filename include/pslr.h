@@ -190,6 +190,33 @@ pslr_status pslr_get_lowrank(const pslr_ctx *c, double *V, double *H, double *G)
 
 pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info);
 
+/*
+ * pslr_apply (or, with transpose != 0, pslr_apply_T) for callers that cannot
+ * allocate device memory when they apply the preconditioner - for instance
+ * code whose device memory all belongs to its own pool allocator, which
+ * forbids cudaMalloc, cudaFree and allocating library calls outside it.  The
+ * paper has no counterpart: this is an interface convenience.
+ *
+ * The call allocates nothing.  Its scratch (series iterates, accumulator,
+ * partial sums, barrier and error words) is a 16 MiB array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits; it fits interface sizes up to q ~ 690,000 in FP64 (3*(q+1) + s*rank
+ * values plus 256 bytes).  Larger contexts are rejected with
+ * PSLR_ERR_TOO_LARGE and a message.  The context, built by pslr_setup and
+ * pslr_build_lowrank / pslr_set_lowrank beforehand, keeps everything else.
+ * b_dev, z_dev: device vectors of n elements (double for PSLR_FP64, float for
+ * PSLR_FP32), original ordering, one right-hand side.
+ *
+ * All calls share the one array and it keeps the previous call's contents;
+ * the call clears the words that must start at zero.  Calls that overlap on
+ * the GPU (different streams, or different contexts on concurrent streams)
+ * race on the array: issue them in one stream or order them.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ */
+pslr_status pslr_apply_noalloc(pslr_ctx *c, const void *b_dev, void *z_dev, pslr_prec prec,
+                               int32_t transpose, void *stream);
+
 /* Synchronise `stream` and report any latched asynchronous error. */
 pslr_status pslr_sync(pslr_ctx *c, void *stream);
 

@@ -1,6 +1,6 @@
 """Compile libpslr.so in-tree for sm_103a (GB300).
 
-Three translation units are compiled in parallel with nvcc (one -gencode,
+The translation units are compiled in parallel with nvcc (one -gencode,
 compute_103a -> sm_103a, -lineinfo) and linked into
 ``paper_2002_00917_gb300/libpslr.so``; objects go to ``_build/`` next to this
 file.  No CMake, no host-specific flags, so the same command works on x86 and
@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpslr.so")
-SOURCES = ["pslr_apply.cu", "pslr_krylov.cu", "pslr_host.cpp"]
+SOURCES = ["pslr_apply.cu", "pslr_krylov.cu", "pslr_host.cpp", "pslr_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "pslr_internal.h"), os.path.join(ROOT, "include", "pslr.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -628,6 +628,8 @@ void pslr_destroy(pslr_ctx *c) {
 
 }  // extern "C"
 
+static pslr_status prebuild_streams(pslr_ctx *c);
+
 // Everything pslr_setup does; with plan_only the device is never touched (no
 // uploads, no allocations), which pslr_plan uses.
 static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, const int32_t *colind,
@@ -878,7 +880,7 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
     CK(cudaMalloc(&c->d_err, sizeof(int)));
     CK(cudaMemset(c->d_err, 0, sizeof(int)));
     CK(cudaDeviceSynchronize());
-    return PSLR_OK;
+    return prebuild_streams(c);
 }
 
 extern "C" {
@@ -994,12 +996,32 @@ static void fill_params(pslr_ctx *c, ApplyParams<T> &P, int dir, int prec, const
     P.wait_limit = c->wait_limit;
 }
 
-static pslr_status apply_one(pslr_ctx *c, const void *b, void *z, int prec, int dir, const int *skip,
-                             cudaStream_t st) {
+// Scratch of one apply launch: series iterates (2(q+1)), accumulator (q+1),
+// per-subdomain partials (s*r), grid-barrier words (2) and the error word.
+struct ApplyScratch {
+    void *wbuf, *acc, *part;
+    unsigned *bar;
+    int *err;
+};
+
+static const StreamDev *find_stream(const OpSetHost &o, int kind, int m, bool lr_before) {
+    char key[64];
+    snprintf(key, sizeof(key), "%d/%d/%d", kind, m, (int)lr_before);
+    auto it = o.streams.find(key);
+    return it == o.streams.end() ? nullptr : &it->second;
+}
+
+static pslr_status apply_launch(pslr_ctx *c, const void *b, void *z, int prec, int dir, const int *skip,
+                                cudaStream_t st, const ApplyScratch *scr, bool may_allocate) {
     OpSetHost &o = c->ops[dir][prec];
-    const StreamDev *sd = nullptr;
-    pslr_status ss = get_stream(c, o, 0, c->m, c->r > 0 && dir == 0, &sd);
-    if (ss != PSLR_OK) return ss;
+    const bool lr_before = c->r > 0 && dir == 0;
+    const StreamDev *sd = find_stream(o, 0, c->m, lr_before);
+    if (!sd) {
+        if (!may_allocate)
+            return fail(c, PSLR_ERR_STATE, "the segment stream of this launch shape is not built");
+        pslr_status ss = get_stream(c, o, 0, c->m, lr_before, &sd);
+        if (ss != PSLR_OK) return ss;
+    }
     cudaError_t e;
     if (prec == PSLR_FP64) {
         ApplyParams<double> P;
@@ -1009,6 +1031,13 @@ static pslr_status apply_one(pslr_ctx *c, const void *b, void *z, int prec, int 
         P.b = static_cast<const double *>(b);
         P.z = static_cast<double *>(z);
         P.skip = skip;
+        if (scr) {
+            P.wbuf = static_cast<double *>(scr->wbuf);
+            P.acc = static_cast<double *>(scr->acc);
+            P.part = static_cast<double *>(scr->part);
+            P.bar = scr->bar;
+            P.err = scr->err;
+        }
         e = launch_apply_fp64(P, o.smem, st);
     } else {
         ApplyParams<float> P;
@@ -1018,11 +1047,67 @@ static pslr_status apply_one(pslr_ctx *c, const void *b, void *z, int prec, int 
         P.b = static_cast<const float *>(b);
         P.z = static_cast<float *>(z);
         P.skip = skip;
+        if (scr) {
+            P.wbuf = static_cast<float *>(scr->wbuf);
+            P.acc = static_cast<float *>(scr->acc);
+            P.part = static_cast<float *>(scr->part);
+            P.bar = scr->bar;
+            P.err = scr->err;
+        }
         e = launch_apply_fp32(P, o.smem, st);
     }
     if (e != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "apply launch: %s", cudaGetErrorString(e));
     return PSLR_OK;
 }
+
+static pslr_status apply_one(pslr_ctx *c, const void *b, void *z, int prec, int dir, const int *skip,
+                             cudaStream_t st) {
+    return apply_launch(c, b, z, prec, dir, skip, st, nullptr, true);
+}
+
+// Build the apply streams of the current (m, r) for both directions and
+// precisions, so that no later apply has to allocate.
+static pslr_status prebuild_streams(pslr_ctx *c) {
+    for (int dir = 0; dir < 2; ++dir)
+        for (int prec = 0; prec < 2; ++prec) {
+            const StreamDev *sd = nullptr;
+            pslr_status st = get_stream(c, c->ops[dir][prec], 0, c->m, c->r > 0 && dir == 0, &sd);
+            if (st != PSLR_OK) return st;
+        }
+    return PSLR_OK;
+}
+
+namespace pslr {
+// Record an error on a context from another translation unit.
+pslr_status report(pslr_ctx *c, pslr_status st, const char *msg) { return fail(c, st, "%s", msg); }
+
+// Apply with caller-provided scratch and no allocation (used by the
+// no-allocation entry point).  Returns PSLR_ERR_TOO_LARGE when the scratch
+// does not hold this context's vectors.
+pslr_status apply_with_scratch(pslr_ctx *c, const void *b, void *z, int prec, int dir, cudaStream_t st,
+                               void *scratch, size_t scratch_bytes) {
+    if (!c || !b || !z || !scratch || (prec != PSLR_FP64 && prec != PSLR_FP32))
+        return fail(c, PSLR_ERR_ARG, "apply (no allocation): bad argument");
+    const size_t head = 256;  // barrier and error words
+    const size_t need = head + sizeof(double) * ((size_t)3 * (c->q + 1) + (size_t)c->s * c->r);
+    if (need > scratch_bytes)
+        return fail(c, PSLR_ERR_TOO_LARGE,
+                    "apply (no allocation): needs %zu bytes of scratch for q = %d, s = %d, r = %d; "
+                    "the static scratch holds %zu",
+                    need, c->q, c->s, c->r, scratch_bytes);
+    char *p = static_cast<char *>(scratch);
+    ApplyScratch scr;
+    scr.bar = reinterpret_cast<unsigned *>(p);
+    scr.err = reinterpret_cast<int *>(p + 16);
+    scr.wbuf = p + head;
+    scr.acc = p + head + sizeof(double) * 2 * (c->q + 1);
+    scr.part = p + head + sizeof(double) * 3 * (c->q + 1);
+    // the shared array keeps the previous call's words: barrier and error start at zero
+    cudaError_t e = cudaMemsetAsync(p, 0, 32, st);
+    if (e != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    return apply_launch(c, b, z, prec, dir, nullptr, st, &scr, false);
+}
+}  // namespace pslr
 
 static pslr_status apply_dir(pslr_ctx *c, const void *b, void *z, int32_t nrhs, pslr_prec prec, int dir,
                              void *stream) {
@@ -1233,7 +1318,7 @@ static pslr_status install_lowrank(pslr_ctx *c, int m, int r, const std::vector<
     cudaFree(c->d_Vb); cudaFree(c->d_G); cudaFree(c->d_GT); cudaFree(c->d_Gf); cudaFree(c->d_GTf);
     cudaFree(c->d_part);
     c->d_Vb = nullptr; c->d_G = c->d_GT = nullptr; c->d_Gf = c->d_GTf = nullptr; c->d_part = nullptr;
-    if (r == 0) return PSLR_OK;
+    if (r == 0) return prebuild_streams(c);
     c->V.resize((size_t)q * r);
     CK(cudaMemcpy(c->V.data(), c->d_V, sizeof(double) * (size_t)q * r, cudaMemcpyDeviceToHost));
     std::vector<uint16_t> vb((size_t)q * r);
@@ -1252,7 +1337,7 @@ static pslr_status install_lowrank(pslr_ctx *c, int m, int r, const std::vector<
     CK(upload(&c->d_Gf, Gf));
     CK(upload(&c->d_GTf, GTf));
     CK(cudaMalloc(&c->d_part, sizeof(double) * (size_t)c->s * r + 16));
-    return PSLR_OK;
+    return prebuild_streams(c);
 }
 
 extern "C" {

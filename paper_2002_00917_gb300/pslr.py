@@ -60,6 +60,7 @@ SIGNATURES = {
     "pslr_apply": (_I32, [_P, _P, _P, _I32, _I32, _P]),
     "pslr_apply_T": (_I32, [_P, _P, _P, _I32, _I32, _P]),
     "pslr_apply_host": (_I32, [_P, _P, _P, _I32, _I32, _I32, _P]),
+    "pslr_apply_noalloc": (_I32, [_P, _P, _P, _I32, _I32, _P]),
     "pslr_solve": (_I32, [_P, _P, _P, _D, _I32, _I32, _I32, _I32, C.POINTER(_I32),
                           C.POINTER(_D), _P]),
     "pslr_matvec": (_I32, [_P, _P, _P, _I32, _P]),
