@@ -166,7 +166,7 @@ pslr_status pslr_apply_host(pslr_ctx *c, const void *b_host, void *z_host, int32
  * refines an FP32 preconditioner to FP64 accuracy.  b_dev, x_dev: device
  * double arrays of length n (nrhs = 1 per call).  *iters (cumulative over
  * restarts) and *relres (true residual ||b - A x||/||b|| in FP64) are written
- * on return.  Synchronises `stream` once per restart cycle.
+ * on return.  restart is 1..127.  Synchronises `stream` once per restart cycle.
  * Returns PSLR_OK or PSLR_ERR_NOT_CONVERGED (x holds the last iterate).
  */
 pslr_status pslr_solve(pslr_ctx *c, const double *b_dev, double *x_dev, double rtol,

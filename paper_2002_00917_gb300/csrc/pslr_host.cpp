@@ -1577,9 +1577,9 @@ extern "C" {
 pslr_status pslr_solve(pslr_ctx *c, const double *b_dev, double *x_dev, double rtol, int32_t restart,
                        int32_t maxit, pslr_prec prec, int32_t transpose, int32_t *iters, double *relres,
                        void *stream) {
-    if (!c || !b_dev || !x_dev || restart < 1 || restart > 63 || maxit < 0 || !(rtol > 0.0) ||
+    if (!c || !b_dev || !x_dev || restart < 1 || restart > 127 || maxit < 0 || !(rtol > 0.0) ||
         (prec != PSLR_FP64 && prec != PSLR_FP32))
-        return fail(c, PSLR_ERR_ARG, "solve: bad argument (restart must be 1..63)");
+        return fail(c, PSLR_ERR_ARG, "solve: bad argument (restart must be 1..127)");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     pslr_status as = krylov_alloc(c, restart);
     if (as != PSLR_OK) return as;

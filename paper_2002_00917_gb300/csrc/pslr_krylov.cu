@@ -20,7 +20,7 @@ namespace pslr {
 
 constexpr int kKThreads = 256;
 constexpr int kChunk = 8;  // basis columns per register chunk
-constexpr int kMaxK = 128; // basis columns of one CGS pass (Arnoldi rank, FGMRES restart + 1)
+constexpr int kMaxK = 128; // basis columns of one CGS pass (Arnoldi rank <= 128, FGMRES restart + 1 <= 128)
 
 __device__ __forceinline__ bool skipping(const int *skip) {
     return skip != nullptr && *(volatile const int *)skip != 0;
