@@ -178,6 +178,17 @@ pslr_status pslr_solve(pslr_ctx *c, const double *b_dev, double *x_dev, double r
 pslr_status pslr_matvec(pslr_ctx *c, const double *x_dev, double *y_dev, int32_t transpose,
                         void *stream);
 
+/*
+ * Adjoint of the solve (used for differentiation, not a step of the paper):
+ * for A u = b and a loss L(u), with lambda = A^{-T} dL/du (pslr_solve with
+ * transpose != 0), dL/db = lambda and dL/da_ij = -lambda_i u_j for every
+ * stored entry of A.  Writes grad_dev[k] for the k-th stored value of the CSR
+ * given to pslr_setup (device doubles, length nnz).  Vectors: device doubles
+ * of length n, original ordering.  Enqueued on `stream`.
+ */
+pslr_status pslr_grad_values(pslr_ctx *c, const double *lambda_dev, const double *u_dev,
+                             double *grad_dev, void *stream);
+
 /* Copy the reordering of Section 2 to host arrays of length n (any may be
  * NULL): part[v] subdomain of unknown v, is_interface[v] 0/1, perm[t] = the
  * original index of reordered unknown t (interiors by subdomain, then

@@ -45,6 +45,8 @@ void launch_residual(int n, const int32_t *rp, const int32_t *ci, const double *
 void launch_d2f(int n, const double *a, float *b, const int *skip, cudaStream_t st);
 void launch_f2d(int n, const float *a, double *b, const int *skip, cudaStream_t st);
 void launch_splitmix(int n, uint64_t seed, uint64_t j0, double *v, cudaStream_t st);
+void launch_grad_values(int n, const int32_t *rp, const int32_t *ci, const double *lambda, const double *u,
+                        double *g, cudaStream_t st);
 }  // namespace pslr
 
 using namespace pslr;
@@ -1249,6 +1251,14 @@ pslr_status pslr_plan(int32_t n, const int32_t *rowptr, const int32_t *colind, c
     }
     pslr_destroy(c);
     return st;
+}
+
+pslr_status pslr_grad_values(pslr_ctx *c, const double *lambda_dev, const double *u_dev, double *grad_dev,
+                             void *stream) {
+    if (!c || !lambda_dev || !u_dev || !grad_dev) return fail(c, PSLR_ERR_ARG, "grad_values: bad argument");
+    launch_grad_values(c->n, c->d_rp, c->d_ci, lambda_dev, u_dev, grad_dev, static_cast<cudaStream_t>(stream));
+    CK(cudaGetLastError());
+    return PSLR_OK;
 }
 
 pslr_status pslr_matvec(pslr_ctx *c, const double *x_dev, double *y_dev, int32_t transpose, void *stream) {

@@ -212,6 +212,16 @@ __global__ void k_splitmix(int n, uint64_t seed, uint64_t j0, double *v) {
     }
 }
 
+// Gradient of a loss with respect to the stored values of A for A u = b:
+// dL/da_ij = -lambda_i u_j on A's pattern (lambda = A^{-T} dL/du).
+__global__ void k_grad_values(int n, const int32_t *rp, const int32_t *ci, const double *lambda,
+                              const double *u, double *g) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double li = lambda[i];
+        for (int e = rp[i]; e < rp[i + 1]; ++e) g[e] = -li * u[ci[e]];
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 
 int krylov_blocks(int n) {
@@ -259,6 +269,11 @@ void launch_d2f(int n, const double *a, float *b, const int *skip, cudaStream_t 
 
 void launch_f2d(int n, const float *a, double *b, const int *skip, cudaStream_t st) {
     k_f2d<<<krylov_blocks(n), kKThreads, 0, st>>>(n, a, b, skip);
+}
+
+void launch_grad_values(int n, const int32_t *rp, const int32_t *ci, const double *lambda, const double *u,
+                        double *g, cudaStream_t st) {
+    k_grad_values<<<krylov_blocks(n), kKThreads, 0, st>>>(n, rp, ci, lambda, u, g);
 }
 
 void launch_splitmix(int n, uint64_t seed, uint64_t j0, double *v, cudaStream_t st) {

@@ -64,6 +64,7 @@ SIGNATURES = {
     "pslr_solve": (_I32, [_P, _P, _P, _D, _I32, _I32, _I32, _I32, C.POINTER(_I32),
                           C.POINTER(_D), _P]),
     "pslr_matvec": (_I32, [_P, _P, _P, _I32, _P]),
+    "pslr_grad_values": (_I32, [_P, _P, _P, _P, _P]),
     "pslr_get_maps": (_I32, [_P, _P, _P, _P]),
     "pslr_get_lowrank": (_I32, [_P, _P, _P, _P]),
     "pslr_get_info": (_I32, [_P, C.POINTER(pslr_info)]),
@@ -232,6 +233,11 @@ class Pslr:
         if check:
             self._check(st, "pslr_solve", ok=(PSLR_OK, PSLR_ERR_NOT_CONVERGED))
         return its.value, rel.value, st
+
+    def grad_values(self, lam, u, grad, stream=None):
+        """grad[k] = -lam[row_k] * u[col_k] over the stored entries of A."""
+        return self._check(self.lib.pslr_grad_values(self.h, _ptr(lam), _ptr(u), _ptr(grad),
+                                                     _stream(stream)), "pslr_grad_values")
 
     def matvec(self, x, y, transpose=False, stream=None):
         return self._check(self.lib.pslr_matvec(self.h, _ptr(x), _ptr(y), int(bool(transpose)),
