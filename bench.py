@@ -51,7 +51,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("pslr_apply.cu", "pslr_internal.h"):  # the kernel and its data layout
+    for f in ("pslr_apply.cu", "pslr_device.cuh", "pslr_internal.h"):  # the kernel, its device code, its data layout
         with open(os.path.join(ROOT, "paper_2002_00917_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -20,7 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpslr.so")
 SOURCES = ["pslr_apply.cu", "pslr_krylov.cu", "pslr_host.cpp", "pslr_noalloc.cu"]
-HEADERS = [os.path.join(CSRC, "pslr_internal.h"), os.path.join(ROOT, "include", "pslr.h")]
+HEADERS = [os.path.join(CSRC, "pslr_internal.h"), os.path.join(CSRC, "pslr_device.cuh"),
+           os.path.join(ROOT, "include", "pslr.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
