@@ -240,6 +240,83 @@ const char *pslr_last_error(const pslr_ctx *c);
 const char *pslr_status_string(pslr_status s);
 void pslr_destroy(pslr_ctx *c);
 
+/* ------------------------------------------------------------------ batch
+ *
+ * Many independent systems A_k z_k = b_k, each with nrhs right-hand sides,
+ * preconditioned and solved together: one launch applies Algorithm 3 to
+ * every system and right-hand side, and one FGMRES (Section 4) per (system,
+ * right-hand side) pair - a "problem" - advances in lockstep with the others,
+ * each with its own basis, Hessenberg matrix and stopping test.  The paper
+ * treats one system at a time; each problem of a batch follows the same
+ * algorithm as the per-system calls (pslr_apply, pslr_solve), and the results
+ * agree with theirs up to the order of rounding in the reductions.
+ *
+ * Batched vector layout: the systems one after the other in the order given
+ * to pslr_batch_create, each as an n_k x nrhs column-major block in the
+ * original ordering of A_k (problem (k, j) starts at offset
+ * nrhs * (n_0 + ... + n_{k-1}) + j * n_k).  pslr_batch_info.n_total is the
+ * length.
+ */
+typedef struct pslr_batch pslr_batch;
+
+typedef struct {
+    int32_t nsys, nrhs, nprob;      /* systems, right-hand sides each, problems      */
+    int64_t n_total;                /* length of a batched vector                    */
+    int32_t items;                  /* (system, subdomain) work items                */
+    int32_t grid;                   /* CTAs of the batched apply launch              */
+    int32_t ring[2];                /* ring slots of the apply, [FP64, FP32]         */
+    int32_t max_m, max_p, max_q;
+    int64_t apply_bytes_fp64;       /* algorithmic bytes of one batched apply        */
+    int64_t apply_bytes_fp32;
+    int32_t graph;                  /* 1: the last solve replayed its cycles as CUDA graphs */
+} pslr_batch_info;
+
+/*
+ * Build a batch over nsys contexts that pslr_setup made and whose low-rank
+ * term is built (pslr_build_lowrank / pslr_set_lowrank; rank 0 is allowed).
+ * nrhs: 1..4 right-hand sides per system.  The batch reads the contexts'
+ * device state and does not own them: keep every context alive, and leave its
+ * low-rank term unchanged, while the batch exists (a batch call on a context
+ * whose low-rank term was replaced returns PSLR_ERR_STATE).  Systems with
+ * exact LU factors (factor 1) are rejected with PSLR_ERR_ARG.  *out is NULL
+ * on failure, and pslr_batch_last_error(NULL) gives the message of the last
+ * failed pslr_batch_create of the calling thread.
+ */
+pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nrhs, pslr_batch **out);
+
+/* z = M_k^{-1} b for every system k and right-hand side (Algorithm 3), one
+ * launch.  b_dev, z_dev: batched device vectors of n_total doubles
+ * (PSLR_FP64) or floats (PSLR_FP32, V in BF16).  Enqueued on `stream`;
+ * asynchronous errors are reported by pslr_batch_sync. */
+pslr_status pslr_batch_apply(pslr_batch *bt, const void *b_dev, void *z_dev, pslr_prec prec, void *stream);
+
+/*
+ * FGMRES(restart) on every problem with x0 = 0, preconditioned by the
+ * batched apply in precision prec (FP64 Krylov vectors, Gram-Schmidt and
+ * least squares in either case).  A problem stops when ||b - A x|| <=
+ * rtol ||b|| (true residual, checked at the end of each cycle, or earlier by
+ * the estimate), after maxit iterations, or on a non-finite value.  b_dev,
+ * x_dev: batched device vectors of doubles.  iters (int32, nprob) and relres
+ * (double, nprob) are optional host arrays, problem order.  Each restart
+ * cycle is captured once as a CUDA graph and replayed; if capture is not
+ * available the same launches are issued directly (pslr_batch_info.graph
+ * says which).  Synchronises `stream` once per cycle.  Returns PSLR_OK when
+ * every problem converged, PSLR_ERR_NAN if one went non-finite, else
+ * PSLR_ERR_NOT_CONVERGED.  restart: 1..127.
+ */
+pslr_status pslr_batch_solve(pslr_batch *bt, const double *b_dev, double *x_dev, double rtol, int32_t restart,
+                             int32_t maxit, pslr_prec prec, int32_t *iters, double *relres, void *stream);
+
+pslr_status pslr_batch_get_info(const pslr_batch *bt, pslr_batch_info *info);
+
+/* Synchronise `stream` and report a latched asynchronous error of the batch. */
+pslr_status pslr_batch_sync(pslr_batch *bt, void *stream);
+
+int64_t pslr_batch_set_wait_limit(pslr_batch *bt, int64_t polls);
+const char *pslr_batch_last_error(const pslr_batch *bt);
+void pslr_batch_destroy(pslr_batch *bt);
+
+
 #ifdef __cplusplus
 }
 #endif

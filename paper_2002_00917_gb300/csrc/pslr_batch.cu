@@ -1,0 +1,380 @@
+// Batched PSLR apply for sm_103a: many independent systems of uneven sizes,
+// each with up to kMaxBatchRhs right-hand sides, in ONE cooperative launch
+// (Algorithm 3, Eq. 3.24, applied to every system and right-hand side).
+//
+// Work items are (system, subdomain) pairs.  The host assigns them to the
+// CTAs of one co-resident grid (longest first, onto the least-loaded CTA) and
+// lays out each CTA's segment stream; the segments stay where each system's
+// set-up put them.  Within every phase a CTA takes its items one after the
+// other.  For an item it holds all right-hand sides of the subdomain in
+// shared memory (vector k at offset k * stride) and sweeps every level once
+// for all of them: a thread reads its row's record once, issues the loads of
+// all right-hand sides, then their stores, so the right-hand sides give the
+// level step independent work instead of each paying the level latency.
+//
+// The phases and grid barriers are those of the single-system kernel
+// (pslr_apply.cu); systems with fewer series terms (smaller m) sit out the
+// later terms, and the low-rank coefficients d = G V^T t of each (system,
+// right-hand side) pair are formed once, by the CTA that owns the pair,
+// between two grid barriers.  Local exact-LU factors (row pivoting) are not
+// supported here; the host rejects such systems.
+#include "pslr_device.cuh"
+
+namespace pslr {
+
+// ---------------------------------------------------- multi-rhs local ops
+
+// One level sweep per segment for nr vectors x + k*xs (k < nr <= kMaxBatchRhs):
+// x_k[r] = (x_k[r] - sum_e T_re x_k[c_e]) (* dinv[r]).
+template <class T>
+__device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int xs, int nr, int nseg, int *err) {
+    Ring &R = c.ring;
+    int slot = R.slot;
+    uint32_t phase = R.phase;
+    uint32_t fbar = R.full_s + 8 * slot;
+    const uint32_t edelta = R.empty_s - R.full_s;
+    const uint32_t base_s = smem_addr(R.base);
+    uint32_t ptr_s = base_s + (uint32_t)(slot * R.slot_bytes);
+    const uint32_t x0s = smem_addr(x);
+    constexpr uint32_t ts = sizeof(T);
+    const uint32_t kstep = ts * (uint32_t)xs;
+    const int j = threadIdx.x;
+    for (int L = 0; L < nseg; ++L) {
+        if (!mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
+        const uint2 h = lds_u2(ptr_s);
+        if (((h.y >> 16) & 0xffu) == kRec3) {
+            if (j < (int)(h.x & 0xffffu)) {
+                const Rec3<T> e = rec3_shared<T>(ptr_s, (int)(h.y & 0xffffu), j);
+                const bool diag = (h.x >> 24) & kSegDiag;
+                T a0[kMaxBatchRhs], a1[kMaxBatchRhs], a2[kMaxBatchRhs], ar[kMaxBatchRhs];
+#pragma unroll
+                for (int k = 0; k < kMaxBatchRhs; ++k)
+                    if (k < nr) {
+                        const uint32_t b = x0s + kstep * k;
+                        a0[k] = lds(b + ts * e.c0, T());
+                        a1[k] = lds(b + ts * e.c1, T());
+                        a2[k] = lds(b + ts * e.c2, T());
+                        ar[k] = lds(b + ts * e.r, T());
+                    }
+#pragma unroll
+                for (int k = 0; k < kMaxBatchRhs; ++k)
+                    if (k < nr) {
+                        T a = fma_t(-e.v0, a0[k], ar[k]);
+                        a = fma_t(-e.v1, a1[k], a);
+                        a = fma_t(-e.v2, a2[k], a);
+                        if (diag) a *= e.d;
+                        sts(x0s + kstep * k + ts * e.r, a);
+                    }
+            }
+        } else {
+            const char *seg = R.base + (ptr_s - base_s);
+            for (int k = 0; k < nr; ++k) level_row_general(seg, x + (size_t)k * xs, j);
+        }
+        csync();
+        if (j == 0) mbar_arrive(fbar + edelta);
+        ++slot;
+        fbar += 8;
+        ptr_s += R.slot_bytes;
+        if (slot == R.slots) {
+            slot = 0;
+            phase ^= 1u;
+            fbar = R.full_s;
+            ptr_s = base_s;
+        }
+    }
+    R.slot = slot;
+    R.phase = phase;
+    R.consumed += nseg;
+}
+
+// ELL product of nseg segments for nr vectors: out_k[row] = sum (assign) or
+// out_k[row] -= sum (subtract), sum = sum_e v_e src_k[c_e]; src in shared
+// memory (local columns) or global memory (GLOBAL, the C_g rows).
+template <class T, bool GLOBAL>
+__device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, int os, const T *src, int ss, int nr, bool subtract,
+                             int nseg, int *err) {
+    Ring &R = c.ring;
+    int slot = R.slot;
+    uint32_t phase = R.phase;
+    uint32_t fbar = R.full_s + 8 * slot;
+    const uint32_t edelta = R.empty_s - R.full_s;
+    const uint32_t base_s = smem_addr(R.base);
+    uint32_t ptr_s = base_s + (uint32_t)(slot * R.slot_bytes);
+    constexpr uint32_t ts = sizeof(T);
+    const int j = threadIdx.x;
+    for (int kseg = 0; kseg < nseg; ++kseg) {
+        if (!mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
+        const uint2 h = lds_u2(ptr_s);
+        if (!GLOBAL && ((h.y >> 16) & 0xffu) == kRec3) {
+            if (j < (int)(h.x & 0xffffu)) {
+                const uint32_t o0 = smem_addr(out), s0 = smem_addr(src);
+                const Rec3<T> e = rec3_shared<T>(ptr_s, (int)(h.y & 0xffffu), j);
+                T b0[kMaxBatchRhs], b1[kMaxBatchRhs], b2[kMaxBatchRhs], br[kMaxBatchRhs];
+#pragma unroll
+                for (int k = 0; k < kMaxBatchRhs; ++k)
+                    if (k < nr) {
+                        const uint32_t sb = s0 + ts * (uint32_t)(k * ss);
+                        b0[k] = lds(sb + ts * e.c0, T());
+                        b1[k] = lds(sb + ts * e.c1, T());
+                        b2[k] = lds(sb + ts * e.c2, T());
+                        br[k] = subtract ? lds(o0 + ts * (uint32_t)(k * os + e.r), T()) : T(0);
+                    }
+#pragma unroll
+                for (int k = 0; k < kMaxBatchRhs; ++k)
+                    if (k < nr) {
+                        T a = e.v0 * b0[k];
+                        a = fma_t(e.v1, b1[k], a);
+                        a = fma_t(e.v2, b2[k], a);
+                        if (subtract) a = br[k] - a;
+                        sts(o0 + ts * (uint32_t)(k * os + e.r), a);
+                    }
+            }
+        } else {
+            const char *seg = R.base + (ptr_s - base_s);
+            for (int k = 0; k < nr; ++k)
+                ell_row_general<T, GLOBAL>(seg, out + (size_t)k * os, src + (size_t)k * ss, subtract, j);
+        }
+        csync();
+        if (j == 0) mbar_arrive(fbar + edelta);
+        ++slot;
+        fbar += 8;
+        ptr_s += R.slot_bytes;
+        if (slot == R.slots) {
+            slot = 0;
+            phase ^= 1u;
+            fbar = R.full_s;
+            ptr_s = base_s;
+        }
+    }
+    R.slot = slot;
+    R.phase = phase;
+    R.consumed += nseg;
+}
+
+// ------------------------------------------------------------------ kernel
+
+template <class T, class VT, class IO>
+__global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const BatchParams<T, IO> P) {
+    extern __shared__ __align__(128) char smem[];
+    if (P.skip != nullptr && ld_volatile(P.skip) != 0) return;
+    if (ld_volatile(P.err) != 0) return;
+    const int nr = P.nrhs;
+    const int xs = P.max_p + 1, gs = P.max_q + 1;  // per-rhs strides of the local vectors
+    const SmemLayout L = smem_layout(P.slot_bytes, P.ring, nr * xs - 1, nr * gs - 1, sizeof(T), false);
+    Cta<T> c;
+    if (!cta_start(c, smem, L, P.ring, P.slot_bytes, P.stream, P.stream_off, P.segbase)) return;
+    const int tid = threadIdx.x;
+    const int ib = P.item_off[blockIdx.x], ie = P.item_off[blockIdx.x + 1];
+    T *const dsh = c.red + (kConsumers / 32) * kMaxRank + kMaxRank;  // where lowrank_coeffs leaves d
+    bool ok = true;
+
+    // ---- phase 0: u = B^{-1} f, t = g - F u (Algorithm 3, step 2); a system
+    // without a low-rank term also takes w_0 = C0^{-1} t here.
+    for (int it = ib; it < ie; ++it) {
+        const BatchSys<T> &S = P.sys[P.items[2 * it]];
+        const int i = P.items[2 * it + 1];
+        const Counts k = counts_of(S.cnt, i);
+        const int io = S.ioff[i], np_ = S.ioff[i + 1] - io;
+        const int go = S.goff[i], nq = S.goff[i + 1] - go;
+        const IO *bs = P.b + S.voff;
+        for (int kr = 0; kr < nr; ++kr) {
+            const IO *bk = bs + (int64_t)kr * S.n;
+            for (int j = tid; j < np_; j += kConsumers) c.xi[kr * xs + j] = T(bk[S.perm[io + j]]);
+            for (int j = tid; j < nq; j += kConsumers) c.si[kr * gs + j] = T(bk[S.perm[S.p + go + j]]);
+            if (tid == 0) {
+                c.xi[kr * xs + np_] = T(0);
+                c.si[kr * gs + nq] = T(0);
+            }
+        }
+        csync();
+        tri_sweep_multi(c, c.xi, xs, nr, k.n[kB1], P.err);
+        tri_sweep_multi(c, c.xi, xs, nr, k.n[kB2], P.err);
+        ell_op_multi<T, false>(c, c.si, gs, c.xi, xs, nr, true, k.n[kF], P.err);
+        if (S.r > 0) {
+            const VT *V = reinterpret_cast<const VT *>(S.V);
+            for (int kr = 0; kr < nr; ++kr) {
+                lowrank_partial(c, V, S.q, S.r, go, nq, c.si + kr * gs,
+                                S.part + ((int64_t)kr * S.s + i) * S.r);
+                for (int j = tid; j < nq; j += kConsumers) S.acc[(int64_t)kr * (S.q + 1) + go + j] = c.si[kr * gs + j];
+            }
+        } else {
+            tri_sweep_multi(c, c.si, gs, nr, k.n[kC1], P.err);
+            tri_sweep_multi(c, c.si, gs, nr, k.n[kC2], P.err);
+            for (int kr = 0; kr < nr; ++kr)
+                for (int j = tid; j < nq; j += kConsumers) {
+                    S.wbuf[(int64_t)kr * 2 * (S.q + 1) + go + j] = c.si[kr * gs + j];
+                    S.acc[(int64_t)kr * (S.q + 1) + go + j] = c.si[kr * gs + j];
+                }
+        }
+        csync();
+        if (i == 0 && tid == 0)  // zero slots of the system's series iterates
+            for (int kr = 0; kr < nr; ++kr) {
+                S.wbuf[(int64_t)kr * 2 * (S.q + 1) + S.q] = T(0);
+                S.wbuf[(int64_t)kr * 2 * (S.q + 1) + (S.q + 1) + S.q] = T(0);
+            }
+    }
+
+    // ---- phase 1: d = G V^T t per (system, rhs); t <- t + V d; w_0 = C0^{-1} t (steps 3-4)
+    if (P.any_lr) {
+        grid_arrive(c, P.bar, P.grid);
+        ok = grid_wait(c, P.bar, P.err, P.wait_limit);
+        if (!ok) goto abort;
+        for (int pi = P.pair_off[blockIdx.x]; pi < P.pair_off[blockIdx.x + 1]; ++pi) {
+            const BatchSys<T> &S = P.sys[P.pairs[2 * pi]];
+            const int kr = P.pairs[2 * pi + 1];
+            lowrank_coeffs(c, S.part + (int64_t)kr * S.s * S.r, S.G, S.s, S.r);
+            for (int j = tid; j < S.r; j += kConsumers) S.dco[(int64_t)kr * S.r + j] = dsh[j];
+            csync();
+        }
+        grid_arrive(c, P.bar, P.grid);
+        ok = grid_wait(c, P.bar, P.err, P.wait_limit);
+        if (!ok) goto abort;
+        for (int it = ib; it < ie; ++it) {
+            const BatchSys<T> &S = P.sys[P.items[2 * it]];
+            if (S.r == 0) continue;
+            const int i = P.items[2 * it + 1];
+            const Counts k = counts_of(S.cnt, i);
+            const int go = S.goff[i], nq = S.goff[i + 1] - go;
+            const VT *V = reinterpret_cast<const VT *>(S.V);
+            for (int kr = 0; kr < nr; ++kr) {
+                for (int j = tid; j < nq; j += kConsumers) c.si[kr * gs + j] = __ldcg(S.acc + (int64_t)kr * (S.q + 1) + go + j);
+                for (int j = tid; j < S.r; j += kConsumers) dsh[j] = __ldcg(S.dco + (int64_t)kr * S.r + j);
+                if (tid == 0) c.si[kr * gs + nq] = T(0);
+                csync();
+                lowrank_update(c, V, S.q, S.r, go, nq, c.si + kr * gs);
+            }
+            tri_sweep_multi(c, c.si, gs, nr, k.n[kC1], P.err);
+            tri_sweep_multi(c, c.si, gs, nr, k.n[kC2], P.err);
+            for (int kr = 0; kr < nr; ++kr)
+                for (int j = tid; j < nq; j += kConsumers) {
+                    S.wbuf[(int64_t)kr * 2 * (S.q + 1) + go + j] = c.si[kr * gs + j];
+                    S.acc[(int64_t)kr * (S.q + 1) + go + j] = c.si[kr * gs + j];
+                }
+            csync();
+        }
+    }
+
+    // ---- series terms w_k = C0^{-1}(F B^{-1} E w_{k-1} - C_g w_{k-1}), acc += w_k (Eq. 3.3),
+    // for the systems with m >= k
+    for (int kk = 1; kk <= P.max_m; ++kk) {
+        grid_arrive(c, P.bar, P.grid);
+        bool waited = false;
+        for (int it = ib; it < ie; ++it) {
+            const BatchSys<T> &S = P.sys[P.items[2 * it]];
+            if (S.m < kk) continue;
+            const int i = P.items[2 * it + 1];
+            const Counts k = counts_of(S.cnt, i);
+            const int np_ = S.ioff[i + 1] - S.ioff[i];
+            const int go = S.goff[i], nq = S.goff[i + 1] - go;
+            const int64_t wst = 2 * (int64_t)(S.q + 1);
+            const T *wprev = S.wbuf + ((kk - 1) & 1) * (S.q + 1);
+            T *wnext = S.wbuf + (kk & 1) * (S.q + 1);
+            for (int kr = 0; kr < nr; ++kr) {
+                for (int j = tid; j < nq; j += kConsumers) c.wi[kr * gs + j] = __ldcg(wprev + kr * wst + go + j);
+                if (tid == 0) c.wi[kr * gs + nq] = T(0);
+                fill(c.xi + kr * xs, np_ + 1, T(0));
+                fill(c.si + kr * gs, nq + 1, T(0));
+            }
+            csync();
+            ell_op_multi<T, false>(c, c.xi, xs, c.wi, gs, nr, false, k.n[kE], P.err);   // E w
+            tri_sweep_multi(c, c.xi, xs, nr, k.n[kB1], P.err);                         // B^{-1}
+            tri_sweep_multi(c, c.xi, xs, nr, k.n[kB2], P.err);
+            ell_op_multi<T, false>(c, c.si, gs, c.xi, xs, nr, false, k.n[kF], P.err);   // F
+            if (!waited) {
+                ok = grid_wait(c, P.bar, P.err, P.wait_limit);
+                waited = true;
+                if (!ok) goto abort;
+            }
+            ell_op_multi<T, true>(c, c.si, gs, wprev, (int)wst, nr, true, k.n[kCg], P.err);  // - C_g w
+            tri_sweep_multi(c, c.si, gs, nr, k.n[kC1], P.err);                               // C0^{-1}
+            tri_sweep_multi(c, c.si, gs, nr, k.n[kC2], P.err);
+            for (int kr = 0; kr < nr; ++kr)
+                for (int j = tid; j < nq; j += kConsumers) {
+                    const int64_t a = (int64_t)kr * (S.q + 1) + go + j;
+                    wnext[kr * wst + go + j] = c.si[kr * gs + j];
+                    S.acc[a] = __ldcg(S.acc + a) + c.si[kr * gs + j];
+                }
+            csync();
+        }
+        if (!waited) {  // a CTA with no work in this term still takes part in the barrier
+            ok = grid_wait(c, P.bar, P.err, P.wait_limit);
+            if (!ok) goto abort;
+        }
+    }
+
+    // ---- y = acc; x = B^{-1}(f - E y); scatter (steps 5-6)
+    for (int it = ib; it < ie; ++it) {
+        const BatchSys<T> &S = P.sys[P.items[2 * it]];
+        const int i = P.items[2 * it + 1];
+        const Counts k = counts_of(S.cnt, i);
+        const int io = S.ioff[i], np_ = S.ioff[i + 1] - io;
+        const int go = S.goff[i], nq = S.goff[i + 1] - go;
+        const IO *bs = P.b + S.voff;
+        for (int kr = 0; kr < nr; ++kr) {
+            const IO *bk = bs + (int64_t)kr * S.n;
+            for (int j = tid; j < nq; j += kConsumers) c.wi[kr * gs + j] = __ldcg(S.acc + (int64_t)kr * (S.q + 1) + go + j);
+            for (int j = tid; j < np_; j += kConsumers) c.xi[kr * xs + j] = T(bk[S.perm[io + j]]);
+            if (tid == 0) {
+                c.wi[kr * gs + nq] = T(0);
+                c.xi[kr * xs + np_] = T(0);
+            }
+        }
+        csync();
+        ell_op_multi<T, false>(c, c.xi, xs, c.wi, gs, nr, true, k.n[kE], P.err);
+        tri_sweep_multi(c, c.xi, xs, nr, k.n[kB1], P.err);
+        tri_sweep_multi(c, c.xi, xs, nr, k.n[kB2], P.err);
+        IO *zs = P.z + S.voff;
+        for (int kr = 0; kr < nr; ++kr) {
+            IO *zk = zs + (int64_t)kr * S.n;
+            for (int j = tid; j < np_; j += kConsumers) zk[S.perm[io + j]] = IO(c.xi[kr * xs + j]);
+            for (int j = tid; j < nq; j += kConsumers) zk[S.perm[S.p + go + j]] = IO(c.wi[kr * gs + j]);
+        }
+        csync();
+    }
+    return;
+abort:
+    consumers_abort_drain(c);
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <class T, class VT, class IO>
+static cudaError_t launch_batch_t(const void *prm, int smem, cudaStream_t st) {
+    const BatchParams<T, IO> &P = *static_cast<const BatchParams<T, IO> *>(prm);
+    auto kern = pslr_batch_apply_kernel<T, VT, IO>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {const_cast<BatchParams<T, IO> *>(&P)};
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(P.grid), dim3(kThreads), args, smem, st);
+}
+
+// form 0: FP64 in and out; 1: FP32 in and out (BF16 V); 2: FP32 arithmetic on FP64 in and out.
+cudaError_t launch_batch(int form, const void *params, int smem, cudaStream_t st) {
+    switch (form) {
+    case 0: return launch_batch_t<double, double, double>(params, smem, st);
+    case 1: return launch_batch_t<float, __nv_bfloat16, float>(params, smem, st);
+    case 2: return launch_batch_t<float, __nv_bfloat16, double>(params, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class K>
+static int coresident(K kern, int smem) {
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem) != cudaSuccess) return 0;
+    return per * nsm;
+}
+
+// Largest cooperative grid of the batched kernel at this shared-memory size
+// (the smaller over the forms that share the layout).
+int max_coresident_batch(int smem, bool fp32) {
+    if (!fp32) return coresident(pslr_batch_apply_kernel<double, double, double>, smem);
+    const int a = coresident(pslr_batch_apply_kernel<float, __nv_bfloat16, float>, smem);
+    const int b = coresident(pslr_batch_apply_kernel<float, __nv_bfloat16, double>, smem);
+    return a < b ? a : b;
+}
+
+}  // namespace pslr

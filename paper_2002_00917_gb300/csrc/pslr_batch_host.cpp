@@ -1,0 +1,721 @@
+// Host side of the batched entry points (include/pslr.h, "batch"): work-item
+// assignment and segment streams of the batched apply (pslr_batch.cu), and
+// the batched FGMRES driver over the kernels of pslr_bkrylov.cu, with each
+// restart cycle captured once as a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <type_traits>
+#include <vector>
+
+#include "pslr.h"
+#include "pslr_internal.h"
+#include "pslr_sys.h"
+
+namespace pslr {
+cudaError_t launch_batch(int form, const void *params, int smem, cudaStream_t st);
+int max_coresident_batch(int smem, bool fp32);
+void bk_spmv_dots(int nchunk, int j, const BkChunk *ch, const BkProb *pr, const BkSys *sys, const double *z,
+                  double *w, const double *V, int64_t ld, const BkState &S, cudaStream_t st);
+void bk_update(int nchunk, int j, const BkChunk *ch, const BkProb *pr, double *w, const double *V, int64_t ld,
+               const double *pin, double *pout, double *hout, int last, const BkState &S, cudaStream_t st);
+void bk_hessenberg(int j, int nprob, const BkProb *pr, const BkState &S, cudaStream_t st);
+void bk_normalize(int nchunk, const BkChunk *ch, const double *w, double *v, const BkState &S, cudaStream_t st);
+void bk_lsq(int nprob, const BkState &S, cudaStream_t st);
+void bk_gemv_add(int nchunk, const BkChunk *ch, const double *Z, int64_t ld, double *x, const BkState &S,
+                 cudaStream_t st);
+void bk_residual(int nchunk, const BkChunk *ch, const BkProb *pr, const BkSys *sys, const double *x,
+                 const double *b, double *r, const BkState &S, cudaStream_t st);
+void bk_restart(int first, int nprob, const BkProb *pr, const BkState &S, cudaStream_t st);
+void bk_start(int nchunk, const BkChunk *ch, const double *r, double *v, const BkState &S, cudaStream_t st);
+}  // namespace pslr
+
+using namespace pslr;
+
+namespace {
+thread_local std::string g_create_error;  // message of the last failed pslr_batch_create
+}
+
+struct pslr_batch {
+    int nsys = 0, nrhs = 0, nprob = 0;
+    int64_t n_total = 0;
+    std::vector<pslr_ctx *> ctx;
+    std::vector<SysExport> sx;
+    std::vector<int64_t> voff;
+    int max_p = 0, max_q = 0, max_m = 0, any_lr = 0, items = 0, grid = 0;
+    const char *segbase[2] = {nullptr, nullptr};
+    int ring[2] = {0, 0}, slot_bytes[2] = {0, 0}, smem[2] = {0, 0};
+    int64_t apply_bytes[2] = {0, 0};
+    // device: assignment, streams, per-system parameters and scratch
+    int32_t *d_items = nullptr, *d_item_off = nullptr, *d_pairs = nullptr, *d_pair_off = nullptr;
+    StreamEnt *d_stream[2] = {nullptr, nullptr};
+    int64_t *d_stream_off[2] = {nullptr, nullptr};
+    void *d_sys[2] = {nullptr, nullptr};  // BatchSys<double>[nsys], BatchSys<float>[nsys]
+    void *d_scratch = nullptr;
+    unsigned *d_bar = nullptr;
+    int *d_err = nullptr;
+    long long wait_limit = 1ll << 22;
+    // batched FGMRES
+    int nchunk = 0;
+    BkChunk *d_chunks = nullptr;
+    BkProb *d_probs = nullptr;
+    BkSys *d_bsys = nullptr;
+    int kK = 0;  // restart length the workspace is sized for
+    double *d_V = nullptr, *d_Z = nullptr, *d_w = nullptr, *d_r = nullptr, *d_b = nullptr, *d_x = nullptr;
+    void *d_state = nullptr;
+    BkState S{};
+    cudaStream_t cap = nullptr;
+    std::map<std::tuple<int, int, double, int, long long>, cudaGraphExec_t> graphs;
+    int graph_used = 0;
+    std::string err;
+};
+
+namespace {
+
+pslr_status bfail(pslr_batch *b, pslr_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+#define BCK(call)                                                                                   \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return bfail(bt, PSLR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class X>
+cudaError_t upload(X **dst, const std::vector<X> &src) {
+    const size_t bytes = sizeof(X) * std::max<size_t>(src.size(), 1);
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) return e;
+    if (src.empty()) return cudaMemset(*dst, 0, bytes);
+    return cudaMemcpy(*dst, src.data(), sizeof(X) * src.size(), cudaMemcpyHostToDevice);
+}
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+void free_krylov(pslr_batch *bt) {
+    for (auto &kv : bt->graphs) cudaGraphExecDestroy(kv.second);
+    bt->graphs.clear();
+    dfree(bt->d_V); dfree(bt->d_Z); dfree(bt->d_w); dfree(bt->d_r); dfree(bt->d_b); dfree(bt->d_x);
+    dfree(bt->d_state);
+    bt->d_V = bt->d_Z = bt->d_w = bt->d_r = bt->d_b = bt->d_x = nullptr;
+    bt->d_state = nullptr;
+    bt->kK = 0;
+}
+
+void free_batch(pslr_batch *bt) {
+    free_krylov(bt);
+    dfree(bt->d_items); dfree(bt->d_item_off); dfree(bt->d_pairs); dfree(bt->d_pair_off);
+    for (int p = 0; p < 2; ++p) {
+        dfree(bt->d_stream[p]);
+        dfree(bt->d_stream_off[p]);
+        dfree(bt->d_sys[p]);
+    }
+    dfree(bt->d_scratch); dfree(bt->d_bar); dfree(bt->d_err);
+    dfree(bt->d_chunks); dfree(bt->d_probs); dfree(bt->d_bsys);
+    if (bt->cap) cudaStreamDestroy(bt->cap);
+}
+
+// Segments of one category of one item.
+int nseg(const pslr_batch *bt, int k, int i, int cat, int prec) {
+    std::vector<StreamEnt> tmp;
+    sys_segments(bt->ctx[k], prec, i, cat, 0, tmp);
+    return (int)tmp.size();
+}
+
+// Phase costs of an item, in level steps (one segment = one step) plus a
+// fixed charge for its gathers, scatters and low-rank reductions.  Phases:
+// 0, 1 (low rank), the series terms 1..max_m, final.
+std::vector<double> item_cost(const pslr_batch *bt, int k, int i) {
+    const SysExport &e = bt->sx[k];
+    const int nph = 3 + bt->max_m;
+    std::vector<double> c(nph, 0.0);
+    int n[kNCnt];
+    for (int t = 0; t < kNCnt; ++t) n[t] = nseg(bt, k, i, t, 1);
+    const double nr = bt->nrhs;
+    c[0] = n[kB1] + n[kB2] + n[kF] + 8 + (e.r > 0 ? nr * (2 + e.r / 8.0) : n[kC1] + n[kC2]);
+    if (e.r > 0) c[1] = n[kC1] + n[kC2] + nr * (2 + e.r / 8.0);
+    for (int kk = 1; kk <= e.m; ++kk) c[1 + kk] = n[kE] + n[kB1] + n[kB2] + n[kF] + n[kCg] + n[kC1] + n[kC2] + 4;
+    c[nph - 1] = n[kE] + n[kB1] + n[kB2] + 8;
+    return c;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ create
+
+static pslr_status batch_build(pslr_batch *bt) {
+    const int nsys = bt->nsys, nr = bt->nrhs;
+    // sizes and offsets
+    bt->voff.resize(nsys);
+    int64_t off = 0;
+    for (int k = 0; k < nsys; ++k) {
+        const SysExport &e = bt->sx[k];
+        bt->voff[k] = off;
+        off += (int64_t)e.n * nr;
+        bt->max_p = std::max(bt->max_p, e.max_p);
+        bt->max_q = std::max(bt->max_q, e.max_q);
+        bt->max_m = std::max(bt->max_m, e.m);
+        bt->any_lr |= e.r > 0;
+        bt->items += e.s;
+    }
+    bt->n_total = off;
+    bt->nprob = nsys * nr;
+    // shared memory, ring depth and grid per precision (same layout rule as the kernel)
+    int dev = 0, optin = 227 * 1024;
+    BCK(cudaGetDevice(&dev));
+    BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int xs = bt->max_p + 1, gs = bt->max_q + 1;
+    int grid = 1 << 30;
+    for (int prec = 0; prec < 2; ++prec) {
+        const int ts = prec == 0 ? 8 : 4;
+        int sb = 128;
+        for (int k = 0; k < nsys; ++k) sb = std::max(sb, bt->sx[k].slot_bytes[prec]);
+        bt->slot_bytes[prec] = sb;
+        const int avail = optin - 1024 - smem_fixed(nr * xs - 1, nr * gs - 1, ts, false);
+        bt->ring[prec] = std::min(kMaxRing, avail / sb);
+        if (bt->ring[prec] < 2)
+            return bfail(bt, PSLR_ERR_TOO_LARGE,
+                         "batch: %d right-hand sides of the largest subdomain (%d interior, %d interface "
+                         "unknowns) do not fit one CTA's shared memory",
+                         nr, bt->max_p, bt->max_q);
+        bt->smem[prec] = smem_layout(sb, bt->ring[prec], nr * xs - 1, nr * gs - 1, ts, false).total;
+        const int g = max_coresident_batch(bt->smem[prec], prec == 1);
+        if (g < 1) return bfail(bt, PSLR_ERR_CUDA, "batch: the apply kernel cannot be made resident");
+        grid = std::min(grid, g);
+    }
+    grid = std::min(grid, bt->items);
+    bt->grid = grid;
+
+    // item assignment: longest first onto the CTA that raises the sum of the
+    // per-phase maxima least (phases are separated by grid barriers)
+    struct Item {
+        int k, i;
+        std::vector<double> c;
+        double tot;
+    };
+    std::vector<Item> items;
+    for (int k = 0; k < nsys; ++k)
+        for (int i = 0; i < bt->sx[k].s; ++i) {
+            Item it{k, i, item_cost(bt, k, i), 0.0};
+            for (double v : it.c) it.tot += v;
+            items.push_back(std::move(it));
+        }
+    std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.tot > b.tot; });
+    const int nph = 3 + bt->max_m;
+    std::vector<std::vector<double>> load(grid, std::vector<double>(nph, 0.0));
+    std::vector<double> tot(grid, 0.0), mx(nph, 0.0);
+    std::vector<std::vector<std::pair<int, int>>> own(grid);
+    for (const Item &it : items) {
+        int best = 0;
+        double bd = 1e300, bt_ = 1e300;
+        for (int b = 0; b < grid; ++b) {
+            double d = 0.0;
+            for (int ph = 0; ph < nph; ++ph) d += std::max(0.0, load[b][ph] + it.c[ph] - mx[ph]);
+            if (d < bd || (d == bd && tot[b] < bt_)) {
+                bd = d;
+                bt_ = tot[b];
+                best = b;
+            }
+        }
+        for (int ph = 0; ph < nph; ++ph) {
+            load[best][ph] += it.c[ph];
+            mx[ph] = std::max(mx[ph], load[best][ph]);
+        }
+        tot[best] += it.tot;
+        own[best].push_back({it.k, it.i});
+    }
+    std::vector<int32_t> hitems, hoff(grid + 1, 0), hpairs, hpoff(grid + 1, 0);
+    for (int b = 0; b < grid; ++b) {
+        hoff[b] = (int32_t)(hitems.size() / 2);
+        for (auto &ki : own[b]) {
+            hitems.push_back(ki.first);
+            hitems.push_back(ki.second);
+        }
+    }
+    hoff[grid] = (int32_t)(hitems.size() / 2);
+    {   // low-rank (system, rhs) pairs, dealt round robin
+        std::vector<std::vector<int32_t>> pb(grid);
+        int t = 0;
+        for (int k = 0; k < nsys; ++k)
+            if (bt->sx[k].r > 0)
+                for (int j = 0; j < nr; ++j, ++t) {
+                    pb[t % grid].push_back(k);
+                    pb[t % grid].push_back(j);
+                }
+        for (int b = 0; b < grid; ++b) {
+            hpoff[b] = (int32_t)(hpairs.size() / 2);
+            hpairs.insert(hpairs.end(), pb[b].begin(), pb[b].end());
+        }
+        hpoff[grid] = (int32_t)(hpairs.size() / 2);
+    }
+    BCK(upload(&bt->d_items, hitems));
+    BCK(upload(&bt->d_item_off, hoff));
+    BCK(upload(&bt->d_pairs, hpairs));
+    BCK(upload(&bt->d_pair_off, hpoff));
+
+    // segment streams, in exactly the order the kernel's consumers take them
+    for (int prec = 0; prec < 2; ++prec) {
+        const char *base = bt->sx[0].seg[prec];
+        for (int k = 1; k < nsys; ++k) base = std::min(base, bt->sx[k].seg[prec]);
+        bt->segbase[prec] = base;
+        std::vector<StreamEnt> ent;
+        std::vector<int64_t> soff(grid + 1, 0);
+        auto add = [&](int k, int i, std::initializer_list<int> cats) {
+            const int64_t shift = bt->sx[k].seg[prec] - base;
+            for (int cat : cats) sys_segments(bt->ctx[k], prec, i, cat, shift, ent);
+        };
+        for (int b = 0; b < grid; ++b) {
+            soff[b] = (int64_t)ent.size();
+            for (auto &ki : own[b]) {
+                add(ki.first, ki.second, {kB1, kB2, kF});
+                if (bt->sx[ki.first].r == 0) add(ki.first, ki.second, {kC1, kC2});
+            }
+            if (bt->any_lr)
+                for (auto &ki : own[b])
+                    if (bt->sx[ki.first].r > 0) add(ki.first, ki.second, {kC1, kC2});
+            for (int kk = 1; kk <= bt->max_m; ++kk)
+                for (auto &ki : own[b])
+                    if (bt->sx[ki.first].m >= kk) add(ki.first, ki.second, {kE, kB1, kB2, kF, kCg, kC1, kC2});
+            for (auto &ki : own[b]) add(ki.first, ki.second, {kE, kB1, kB2});
+        }
+        soff[grid] = (int64_t)ent.size();
+        int64_t seg_bytes = 0;
+        for (const StreamEnt &e : ent) seg_bytes += e.bytes;
+        // algorithmic bytes: every segment once, V once per pass, and per
+        // right-hand side the vectors of the single-system count
+        const int64_t vs = prec == 0 ? 8 : 4, vb = prec == 0 ? 8 : 2;
+        int64_t bytes = seg_bytes;
+        for (int k = 0; k < nsys; ++k) {
+            const SysExport &e = bt->sx[k];
+            const int64_t m = e.m, r = e.r, q = e.q;
+            bytes += 2 * q * r * vb;
+            int64_t vec = 2 * (int64_t)e.p + q + e.n;
+            vec += (r > 0 ? 2 * q : 0) + 2 * q;
+            vec += m * (q + q + 2 * q);
+            bytes += vec * vs * nr;
+        }
+        bt->apply_bytes[prec] = bytes;
+        BCK(upload(&bt->d_stream[prec], ent));
+        BCK(upload(&bt->d_stream_off[prec], soff));
+    }
+
+    // per-system scratch (sized in doubles; the FP32 form uses the front of each piece)
+    std::vector<int64_t> so(nsys + 1, 0);
+    auto al = [](int64_t x) { return (x + 31) / 32 * 32; };  // 256-byte pieces
+    for (int k = 0; k < nsys; ++k) {
+        const SysExport &e = bt->sx[k];
+        so[k + 1] = so[k] + al((int64_t)nr * 2 * (e.q + 1)) + al((int64_t)nr * (e.q + 1)) +
+                    al((int64_t)nr * e.s * std::max(e.r, 1)) + al((int64_t)nr * std::max(e.r, 1));
+    }
+    BCK(cudaMalloc(&bt->d_scratch, sizeof(double) * std::max<int64_t>(so[nsys], 1)));
+    BCK(cudaMemset(bt->d_scratch, 0, sizeof(double) * std::max<int64_t>(so[nsys], 1)));
+    std::vector<BatchSys<double>> s64(nsys);
+    std::vector<BatchSys<float>> s32(nsys);
+    double *sc = static_cast<double *>(bt->d_scratch);
+    for (int k = 0; k < nsys; ++k) {
+        const SysExport &e = bt->sx[k];
+        double *w = sc + so[k];
+        double *a = w + al((int64_t)nr * 2 * (e.q + 1));
+        double *pt = a + al((int64_t)nr * (e.q + 1));
+        double *d = pt + al((int64_t)nr * e.s * std::max(e.r, 1));
+        auto fillsys = [&](auto &B, int prec, auto *tp) {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            B.cnt = e.cnt[prec];
+            B.ioff = e.ioff;
+            B.goff = e.goff;
+            B.perm = e.perm;
+            B.V = prec == 0 ? (const void *)e.V : (const void *)e.Vb;
+            B.G = reinterpret_cast<const T *>(prec == 0 ? (const void *)e.G : (const void *)e.Gf);
+            B.wbuf = reinterpret_cast<T *>(w);
+            B.acc = reinterpret_cast<T *>(a);
+            B.part = reinterpret_cast<T *>(pt);
+            B.dco = reinterpret_cast<T *>(d);
+            B.voff = bt->voff[k];
+            B.n = e.n;
+            B.s = e.s;
+            B.p = e.p;
+            B.q = e.q;
+            B.r = e.r;
+            B.m = e.m;
+        };
+        fillsys(s64[k], 0, (double *)nullptr);
+        fillsys(s32[k], 1, (float *)nullptr);
+    }
+    {
+        BatchSys<double> *p64 = nullptr;
+        BatchSys<float> *p32 = nullptr;
+        BCK(upload(&p64, s64));
+        bt->d_sys[0] = p64;
+        BCK(upload(&p32, s32));
+        bt->d_sys[1] = p32;
+    }
+    BCK(cudaMalloc(&bt->d_bar, 16));
+    BCK(cudaMemset(bt->d_bar, 0, 16));
+    BCK(cudaMalloc(&bt->d_err, sizeof(int) * 2));
+    BCK(cudaMemset(bt->d_err, 0, sizeof(int) * 2));
+
+    // problems and chunks of the batched Krylov kernels
+    std::vector<BkProb> probs;
+    std::vector<BkChunk> chunks;
+    for (int k = 0; k < nsys; ++k)
+        for (int j = 0; j < nr; ++j) {
+            BkProb p;
+            p.off = bt->voff[k] + (int64_t)j * bt->sx[k].n;
+            p.n = bt->sx[k].n;
+            p.sys = k;
+            p.nc = std::max(1, (p.n + kBkChunk - 1) / kBkChunk);
+            p.c0 = (int32_t)chunks.size();
+            for (int c = 0; c < p.nc; ++c) {
+                BkChunk ch;
+                ch.b = p.off + (int64_t)p.n * c / p.nc;
+                ch.e = p.off + (int64_t)p.n * (c + 1) / p.nc;
+                ch.prob = (int32_t)probs.size();
+                ch.pad = 0;
+                chunks.push_back(ch);
+            }
+            probs.push_back(p);
+        }
+    std::vector<BkSys> bs(nsys);
+    for (int k = 0; k < nsys; ++k) {
+        bs[k].rp = bt->sx[k].rp;
+        bs[k].ci = bt->sx[k].ci;
+        bs[k].av = bt->sx[k].av;
+    }
+    bt->nchunk = (int)chunks.size();
+    BCK(upload(&bt->d_chunks, chunks));
+    BCK(upload(&bt->d_probs, probs));
+    BCK(upload(&bt->d_bsys, bs));
+    BCK(cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking));
+    return PSLR_OK;
+}
+
+// ------------------------------------------------------------------ apply
+
+static pslr_status batch_check(pslr_batch *bt) {
+    for (int k = 0; k < bt->nsys; ++k)
+        if (sys_lr_gen(bt->ctx[k]) != bt->sx[k].lr_gen)
+            return bfail(bt, PSLR_ERR_STATE,
+                         "batch: the low-rank term of system %d was replaced after pslr_batch_create; "
+                         "create the batch again", k);
+    return PSLR_OK;
+}
+
+// form 0: FP64; 1: FP32 in and out; 2: FP32 arithmetic, FP64 in and out.
+static pslr_status batch_launch(pslr_batch *bt, int form, const void *b, void *z, const int *skip,
+                                cudaStream_t st) {
+    const int prec = form == 0 ? 0 : 1;
+    auto fill = [&](auto &P) {
+        P.segbase = bt->segbase[prec];
+        P.items = bt->d_items;
+        P.item_off = bt->d_item_off;
+        P.pairs = bt->d_pairs;
+        P.pair_off = bt->d_pair_off;
+        P.stream = bt->d_stream[prec];
+        P.stream_off = bt->d_stream_off[prec];
+        P.ring = bt->ring[prec];
+        P.slot_bytes = bt->slot_bytes[prec];
+        P.max_p = bt->max_p;
+        P.max_q = bt->max_q;
+        P.max_m = bt->max_m;
+        P.nrhs = bt->nrhs;
+        P.grid = bt->grid;
+        P.any_lr = bt->any_lr;
+        P.bar = bt->d_bar;
+        P.err = bt->d_err;
+        P.skip = skip;
+        P.wait_limit = bt->wait_limit;
+    };
+    cudaError_t e;
+    if (form == 0) {
+        BatchParams<double, double> P;
+        fill(P);
+        P.sys = static_cast<const BatchSys<double> *>(bt->d_sys[0]);
+        P.b = static_cast<const double *>(b);
+        P.z = static_cast<double *>(z);
+        e = launch_batch(0, &P, bt->smem[0], st);
+    } else if (form == 1) {
+        BatchParams<float, float> P;
+        fill(P);
+        P.sys = static_cast<const BatchSys<float> *>(bt->d_sys[1]);
+        P.b = static_cast<const float *>(b);
+        P.z = static_cast<float *>(z);
+        e = launch_batch(1, &P, bt->smem[1], st);
+    } else {
+        BatchParams<float, double> P;
+        fill(P);
+        P.sys = static_cast<const BatchSys<float> *>(bt->d_sys[1]);
+        P.b = static_cast<const double *>(b);
+        P.z = static_cast<double *>(z);
+        e = launch_batch(2, &P, bt->smem[1], st);
+    }
+    if (e != cudaSuccess) return bfail(bt, PSLR_ERR_CUDA, "batched apply launch: %s", cudaGetErrorString(e));
+    return PSLR_OK;
+}
+
+// ------------------------------------------------------------------ FGMRES
+
+static pslr_status krylov_ensure(pslr_batch *bt, int K) {
+    if (bt->kK == K) return PSLR_OK;
+    free_krylov(bt);
+    const int64_t N = bt->n_total;
+    const int P = bt->nprob, ldp = K + 1;
+    BCK(cudaMalloc(&bt->d_V, sizeof(double) * (size_t)N * (K + 1)));
+    BCK(cudaMalloc(&bt->d_Z, sizeof(double) * (size_t)N * K));
+    BCK(cudaMemset(bt->d_V, 0, sizeof(double) * (size_t)N * (K + 1)));
+    BCK(cudaMemset(bt->d_Z, 0, sizeof(double) * (size_t)N * K));
+    BCK(cudaMalloc(&bt->d_w, sizeof(double) * (size_t)N));
+    BCK(cudaMalloc(&bt->d_r, sizeof(double) * (size_t)N));
+    BCK(cudaMalloc(&bt->d_b, sizeof(double) * (size_t)N));
+    BCK(cudaMalloc(&bt->d_x, sizeof(double) * (size_t)N));
+    // state: doubles first, then ints
+    const size_t nd = (size_t)P * 4                          // bn, rn, hn, relres
+                      + (size_t)P * ldp * K                  // H
+                      + (size_t)P * 2 * K                    // rot
+                      + (size_t)P * ldp * 3                  // gam, h1, h2
+                      + (size_t)P * K                        // y
+                      + (size_t)bt->nchunk * ldp * 2;        // pa, pb
+    const size_t ni = (size_t)P * 4 + 2;
+    BCK(cudaMalloc(&bt->d_state, sizeof(double) * nd + sizeof(int) * ni));
+    BCK(cudaMemset(bt->d_state, 0, sizeof(double) * nd + sizeof(int) * ni));
+    double *d = static_cast<double *>(bt->d_state);
+    BkState &S = bt->S;
+    S.bn = d; d += P;
+    S.rn = d; d += P;
+    S.hn = d; d += P;
+    S.relres = d; d += P;
+    S.H = d; d += (size_t)P * ldp * K;
+    S.rot = d; d += (size_t)P * 2 * K;
+    S.gam = d; d += (size_t)P * ldp;
+    S.h1 = d; d += (size_t)P * ldp;
+    S.h2 = d; d += (size_t)P * ldp;
+    S.y = d; d += (size_t)P * K;
+    S.pa = d; d += (size_t)bt->nchunk * ldp;
+    S.pb = d; d += (size_t)bt->nchunk * ldp;
+    int *ip = reinterpret_cast<int *>(d);
+    S.stop = ip; ip += P;
+    S.jd = ip; ip += P;
+    S.conv = ip; ip += P;
+    S.its = ip; ip += P;
+    S.remaining = ip; ip += 1;
+    S.skip = ip;
+    S.K = K;
+    bt->kK = K;
+    return PSLR_OK;
+}
+
+// One restart cycle: K Arnoldi steps (apply, CGS2, Givens, normalise), then
+// least squares, x += Z y, the true residual and the restart decision.
+static pslr_status enqueue_cycle(pslr_batch *bt, int form, cudaStream_t st) {
+    const BkState &S = bt->S;
+    const int K = S.K, nc = bt->nchunk, P = bt->nprob;
+    const int64_t N = bt->n_total;
+    for (int j = 0; j < K; ++j) {
+        const double *vj = bt->d_V + (size_t)j * N;
+        double *zj = bt->d_Z + (size_t)j * N;
+        pslr_status a = batch_launch(bt, form, vj, zj, S.skip, st);
+        if (a != PSLR_OK) return a;
+        bk_spmv_dots(nc, j, bt->d_chunks, bt->d_probs, bt->d_bsys, zj, bt->d_w, bt->d_V, N, S, st);
+        bk_update(nc, j, bt->d_chunks, bt->d_probs, bt->d_w, bt->d_V, N, S.pa, S.pb, S.h1, 0, S, st);
+        bk_update(nc, j, bt->d_chunks, bt->d_probs, bt->d_w, bt->d_V, N, S.pb, S.pa, S.h2, 1, S, st);
+        bk_hessenberg(j, P, bt->d_probs, S, st);
+        bk_normalize(nc, bt->d_chunks, bt->d_w, bt->d_V + (size_t)(j + 1) * N, S, st);
+    }
+    bk_lsq(P, S, st);
+    bk_gemv_add(nc, bt->d_chunks, bt->d_Z, N, bt->d_x, S, st);
+    bk_residual(nc, bt->d_chunks, bt->d_probs, bt->d_bsys, bt->d_x, bt->d_b, bt->d_r, S, st);
+    bk_restart(0, P, bt->d_probs, S, st);
+    bk_start(nc, bt->d_chunks, bt->d_r, bt->d_V, S, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(bt, PSLR_ERR_CUDA, "batched FGMRES launch: %s", cudaGetErrorString(e));
+    return PSLR_OK;
+}
+
+// The cycle as a CUDA graph (captured on the batch's own stream), or nullptr
+// when capture or instantiation is not available.
+static cudaGraphExec_t cycle_graph(pslr_batch *bt, int form) {
+    const auto key = std::make_tuple(form, bt->S.K, bt->S.rtol, bt->S.maxit, bt->wait_limit);
+    auto it = bt->graphs.find(key);
+    if (it != bt->graphs.end()) return it->second;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    if (cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const pslr_status st = enqueue_cycle(bt, form, bt->cap);
+    const cudaError_t e = cudaStreamEndCapture(bt->cap, &g);
+    if (st != PSLR_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) x = nullptr;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (x) bt->graphs[key] = x;
+    return x;
+}
+
+extern "C" {
+
+pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nrhs, pslr_batch **out) {
+    pslr_batch *bt = nullptr;
+    if (out) *out = nullptr;
+    if (!out || nsys < 1 || !systems || nrhs < 1 || nrhs > kMaxBatchRhs)
+        return bfail(nullptr, PSLR_ERR_ARG, "batch_create: bad argument (nsys >= 1, nrhs 1..%d)", kMaxBatchRhs);
+    std::vector<SysExport> sx(nsys);
+    for (int k = 0; k < nsys; ++k) {
+        if (!systems[k] || !sys_export(systems[k], &sx[k]))
+            return bfail(nullptr, PSLR_ERR_ARG, "batch_create: system %d is not set up", k);
+        if (sx[k].factor != 0)
+            return bfail(nullptr, PSLR_ERR_ARG,
+                         "batch_create: system %d uses exact LU factors; the batch takes ILU(0) systems", k);
+        if (sx[k].r > 0 && (!sx[k].V || !sx[k].Vb || !sx[k].G || !sx[k].Gf))
+            return bfail(nullptr, PSLR_ERR_STATE, "batch_create: system %d has no low-rank term on the device", k);
+    }
+    bt = new pslr_batch();
+    bt->nsys = nsys;
+    bt->nrhs = nrhs;
+    bt->ctx.assign(systems, systems + nsys);
+    bt->sx = sx;
+    pslr_status st = batch_build(bt);
+    if (st != PSLR_OK) {
+        g_create_error = bt->err;
+        free_batch(bt);
+        delete bt;
+        return st;
+    }
+    *out = bt;
+    return PSLR_OK;
+}
+
+pslr_status pslr_batch_apply(pslr_batch *bt, const void *b_dev, void *z_dev, pslr_prec prec, void *stream) {
+    if (!bt || !b_dev || !z_dev || (prec != PSLR_FP64 && prec != PSLR_FP32))
+        return bfail(bt, PSLR_ERR_ARG, "batch_apply: bad argument");
+    pslr_status st = batch_check(bt);
+    if (st != PSLR_OK) return st;
+    return batch_launch(bt, prec == PSLR_FP64 ? 0 : 1, b_dev, z_dev, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+pslr_status pslr_batch_sync(pslr_batch *bt, void *stream) {
+    if (!bt) return PSLR_ERR_ARG;
+    BCK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int err = 0;
+    BCK(cudaMemcpy(&err, bt->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err != 0) {
+        BCK(cudaMemset(bt->d_err, 0, sizeof(int) * 2));
+        BCK(cudaMemset(bt->d_bar, 0, 16));
+        return bfail(bt, (pslr_status)err, "batch: a device-side wait gave up (status %d)", err);
+    }
+    return PSLR_OK;
+}
+
+pslr_status pslr_batch_solve(pslr_batch *bt, const double *b_dev, double *x_dev, double rtol, int32_t restart,
+                             int32_t maxit, pslr_prec prec, int32_t *iters, double *relres, void *stream) {
+    if (!bt || !b_dev || !x_dev || restart < 1 || restart > 127 || maxit < 0 || !(rtol > 0.0) ||
+        (prec != PSLR_FP64 && prec != PSLR_FP32))
+        return bfail(bt, PSLR_ERR_ARG, "batch_solve: bad argument (restart must be 1..127)");
+    pslr_status st = batch_check(bt);
+    if (st != PSLR_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = krylov_ensure(bt, restart);
+    if (st != PSLR_OK) return st;
+    bt->S.rtol = rtol;
+    bt->S.maxit = maxit;
+    const BkState &S = bt->S;
+    const int P = bt->nprob, nc = bt->nchunk;
+    const int64_t N = bt->n_total;
+    const int form = prec == PSLR_FP64 ? 0 : 2;
+    BCK(cudaMemcpyAsync(bt->d_b, b_dev, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    BCK(cudaMemsetAsync(bt->d_x, 0, sizeof(double) * N, s));
+    BCK(cudaMemsetAsync(S.conv, 0, sizeof(int) * P, s));
+    bk_residual(nc, bt->d_chunks, bt->d_probs, bt->d_bsys, nullptr, bt->d_b, bt->d_r, S, s);
+    bk_restart(1, P, bt->d_probs, S, s);
+    bk_start(nc, bt->d_chunks, bt->d_r, bt->d_V, S, s);
+    int remaining = 0;
+    BCK(cudaMemcpyAsync(&remaining, S.remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    cudaGraphExec_t g = remaining > 0 ? cycle_graph(bt, form) : nullptr;
+    bt->graph_used = g != nullptr;
+    for (int cyc = 0; remaining > 0 && cyc <= maxit; ++cyc) {
+        if (g) {
+            BCK(cudaGraphLaunch(g, s));
+        } else {
+            st = enqueue_cycle(bt, form, s);
+            if (st != PSLR_OK) return st;
+        }
+        BCK(cudaMemcpyAsync(&remaining, S.remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
+        st = pslr_batch_sync(bt, stream);
+        if (st != PSLR_OK) return st;
+    }
+    BCK(cudaMemcpyAsync(x_dev, bt->d_x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    std::vector<int> conv(P), its(P);
+    std::vector<double> rel(P);
+    BCK(cudaMemcpyAsync(conv.data(), S.conv, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(its.data(), S.its, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(rel.data(), S.relres, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    if (iters) std::copy(its.begin(), its.end(), iters);
+    if (relres) std::copy(rel.begin(), rel.end(), relres);
+    int nan = 0, nconv = 0;
+    for (int p = 0; p < P; ++p) {
+        nan += conv[p] == 3;
+        nconv += conv[p] == 1;
+    }
+    if (nan) return bfail(bt, PSLR_ERR_NAN, "batch_solve: %d problem(s) went non-finite", nan);
+    if (nconv < P)
+        return bfail(bt, PSLR_ERR_NOT_CONVERGED, "batch_solve: %d of %d problems reached maxit = %d", P - nconv, P,
+                     maxit);
+    return PSLR_OK;
+}
+
+pslr_status pslr_batch_get_info(const pslr_batch *bt, pslr_batch_info *info) {
+    if (!bt || !info) return PSLR_ERR_ARG;
+    info->nsys = bt->nsys;
+    info->nrhs = bt->nrhs;
+    info->nprob = bt->nprob;
+    info->n_total = bt->n_total;
+    info->items = bt->items;
+    info->grid = bt->grid;
+    info->ring[0] = bt->ring[0];
+    info->ring[1] = bt->ring[1];
+    info->max_m = bt->max_m;
+    info->max_p = bt->max_p;
+    info->max_q = bt->max_q;
+    info->apply_bytes_fp64 = bt->apply_bytes[0];
+    info->apply_bytes_fp32 = bt->apply_bytes[1];
+    info->graph = bt->graph_used;
+    return PSLR_OK;
+}
+
+int64_t pslr_batch_set_wait_limit(pslr_batch *bt, int64_t polls) {
+    if (!bt) return -1;
+    const int64_t old = bt->wait_limit;
+    bt->wait_limit = polls;
+    return old;
+}
+
+const char *pslr_batch_last_error(const pslr_batch *bt) {
+    return bt ? bt->err.c_str() : g_create_error.c_str();
+}
+
+void pslr_batch_destroy(pslr_batch *bt) {
+    if (!bt) return;
+    cudaDeviceSynchronize();
+    free_batch(bt);
+    delete bt;
+}
+
+}  // extern "C"

@@ -176,7 +176,7 @@ __device__ __forceinline__ void seg_done(Ring &R) {
 }
 
 // Producer warp: copy the CTA's stream into the ring.
-__device__ void producer(const StreamEnt *stream, int64_t b, int64_t e, const char *segbase,
+static __device__ void producer(const StreamEnt *stream, int64_t b, int64_t e, const char *segbase,
                          char *ring, int slots, int slot_bytes, uint32_t full_s, uint32_t empty_s,
                          Ctl *ctl) {
     const int lane = threadIdx.x & 31;
@@ -613,7 +613,7 @@ __device__ __forceinline__ void level_row(const LevelPre<T> &q, T *x, int j) {
 }
 
 // Slow path of a segment wait (the producer is normally far ahead).
-__device__ __noinline__ void wait_full_slow(uint32_t bar, uint32_t phase, int *err) {
+static __device__ __noinline__ void wait_full_slow(uint32_t bar, uint32_t phase, int *err) {
     long long it = 0;
     while (!mbar_try_wait(bar, phase)) {
         if (++it > kTmaWaitLimit) {

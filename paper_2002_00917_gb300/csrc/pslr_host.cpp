@@ -22,6 +22,7 @@
 
 #include "pslr.h"
 #include "pslr_internal.h"
+#include "pslr_sys.h"
 
 namespace pslr {
 // kernels (pslr_apply.cu, pslr_krylov.cu)
@@ -400,6 +401,7 @@ struct pslr_ctx {
     double *d_av = nullptr, *d_avT = nullptr;
     // low-rank term
     int m = 0, r = 0;
+    uint64_t lr_gen = 0;         // incremented whenever the low-rank term is replaced
     std::vector<double> V, H, G;
     double *d_V = nullptr;       // q x r FP64 (leading dimension q)
     uint16_t *d_Vb = nullptr;    // q x r BF16
@@ -478,6 +480,7 @@ void free_lowrank(pslr_ctx *c) {
     c->d_V = nullptr; c->d_Vb = nullptr; c->d_G = c->d_GT = nullptr; c->d_Gf = c->d_GTf = nullptr;
     c->d_part = nullptr;
     c->r = 0;
+    ++c->lr_gen;
     c->V.clear(); c->H.clear(); c->G.clear();
 }
 
@@ -1322,6 +1325,7 @@ static bool compute_G(int r, const std::vector<double> &H, std::vector<double> &
 // Install V (device FP64 q x r, already in c->d_V) plus host G: derived copies.
 static pslr_status install_lowrank(pslr_ctx *c, int m, int r, const std::vector<double> &G) {
     const int q = c->q;
+    ++c->lr_gen;
     c->m = m;
     c->r = r;
     c->G = G;
@@ -1684,3 +1688,55 @@ pslr_status pslr_solve(pslr_ctx *c, const double *b_dev, double *x_dev, double r
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ view for the batch
+
+namespace pslr {
+
+bool sys_export(const pslr_ctx *c, SysExport *e) {
+    if (!c || !c->ops[0][0].seg || !c->ops[0][1].seg) return false;
+    e->n = c->n;
+    e->s = c->s;
+    e->p = c->p;
+    e->q = c->q;
+    e->m = c->m;
+    e->r = c->r;
+    e->factor = c->factor;
+    e->max_p = c->max_p;
+    e->max_q = c->max_q;
+    e->ioff = c->d_ioff;
+    e->goff = c->d_goff;
+    e->perm = c->d_perm;
+    e->rp = c->d_rp;
+    e->ci = c->d_ci;
+    e->av = c->d_av;
+    e->V = c->d_V;
+    e->Vb = c->d_Vb;
+    e->G = c->d_G;
+    e->Gf = c->d_Gf;
+    for (int prec = 0; prec < 2; ++prec) {
+        e->seg[prec] = c->ops[0][prec].seg;
+        e->cnt[prec] = c->ops[0][prec].cnt;
+        e->slot_bytes[prec] = c->ops[0][prec].slot_bytes;
+        e->seg_bytes[prec] = c->ops[0][prec].seg_total;
+    }
+    e->lr_gen = c->lr_gen;
+    return true;
+}
+
+void sys_segments(const pslr_ctx *c, int prec, int i, int cat, int64_t shift, std::vector<StreamEnt> &out) {
+    const OpSetHost &o = c->ops[0][prec];
+    int d = o.hsub[i];
+    for (int k = 0; k < cat; ++k) d += o.hcnt[(size_t)kNCnt * i + k];
+    for (int t = 0; t < o.hcnt[(size_t)kNCnt * i + cat]; ++t) {
+        StreamEnt e;
+        e.off = o.hdesc[d + t].off + shift;
+        e.bytes = o.hdesc[d + t].bytes;
+        e.pad = 0;
+        out.push_back(e);
+    }
+}
+
+uint64_t sys_lr_gen(const pslr_ctx *c) { return c ? c->lr_gen : 0; }
+
+}  // namespace pslr

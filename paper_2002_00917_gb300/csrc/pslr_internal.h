@@ -145,6 +145,84 @@ struct ErrParams {
     long long wait_limit;
 };
 
+// Batched apply (pslr_batch.cu): per-system parameters and launch parameters.
+constexpr int kMaxBatchRhs = 4;             // right-hand sides per system in one batched launch
+
+template <class T>
+struct BatchSys {
+    const int32_t *cnt;         // kNCnt*s segment counts (this precision)
+    const int32_t *ioff, *goff, *perm;
+    const void *V;              // q x r: double (FP64) or bf16 (FP32)
+    const T *G;                 // r x r column-major
+    T *wbuf;                    // nrhs blocks of 2(q+1): series iterates (ping-pong, slot q = 0)
+    T *acc;                     // nrhs blocks of q+1: accumulator
+    T *part;                    // nrhs blocks of s*r: per-subdomain partials of V^T t
+    T *dco;                     // nrhs blocks of r: low-rank coefficients d = G V^T t
+    int64_t voff;               // start of the system's n x nrhs block in b and z
+    int n, s, p, q, r, m;
+};
+
+template <class T, class IO>
+struct BatchParams {
+    const BatchSys<T> *sys;
+    const char *segbase;        // every stream offset is relative to this address
+    const int32_t *items;       // (system, subdomain) pairs, grouped by CTA
+    const int32_t *item_off;    // grid+1
+    const int32_t *pairs;       // (system, rhs) pairs of systems with r > 0, grouped by CTA
+    const int32_t *pair_off;    // grid+1
+    const StreamEnt *stream;
+    const int64_t *stream_off;  // grid+1
+    const IO *b;                // batched input (system-major, n_k x nrhs column-major per system)
+    IO *z;                      // batched output, same layout
+    int ring, slot_bytes, max_p, max_q, max_m, nrhs, grid, any_lr;
+    unsigned *bar;
+    int *err;
+    const int *skip;            // when *skip != 0 the launch does nothing
+    long long wait_limit;
+};
+
+// Batched FGMRES (pslr_bkrylov.cu).  A "problem" is one (system, right-hand
+// side) pair: a contiguous range of the batched vector.  Each problem is cut
+// into chunks of at most kBkChunk rows; one CTA handles one chunk, and every
+// per-problem reduction adds its chunks' partials in chunk order.
+constexpr int kBkChunk = 4096;
+
+struct BkProb {
+    int64_t off;        // first element of the problem in the batched vector
+    int32_t n, sys;     // length, system
+    int32_t c0, nc;     // its chunks
+};
+
+struct BkChunk {
+    int64_t b, e;       // element range in the batched vector
+    int32_t prob, pad;
+};
+
+struct BkSys {          // the system's matrix A (CSR, original ordering)
+    const int32_t *rp, *ci;
+    const double *av;
+};
+
+// Per-problem FGMRES state (device arrays of length nprob unless noted).
+struct BkState {
+    int *stop;          // no further Arnoldi steps in this cycle
+    int *jd;            // Arnoldi steps done in this cycle
+    int *conv;          // 0 running, 1 converged, 2 stopped (maxit), 3 not finite
+    int *its;           // iterations so far
+    double *bn, *rn, *hn, *relres;
+    double *H;          // nprob x (K+1) x K, column-major per problem
+    double *rot;        // nprob x 2K: cosines then sines
+    double *gam;        // nprob x (K+1)
+    double *h1, *h2;    // nprob x (K+1): the two CGS coefficient vectors of this step
+    double *y;          // nprob x K: least-squares solution of the cycle
+    double *pa, *pb;    // nchunk x (K+1): per-chunk partials (ping-pong)
+    int *remaining;     // [1] problems still running
+    int *skip;          // [1] no problem running: later launches of the cycle return at once
+    double rtol;
+    int maxit;
+    int K;              // restart length
+};
+
 // Shared-memory layout of the persistent kernels (host and device agree on it).
 struct SmemLayout {
     int ring, full, empty, ctl, xi, wi, si, tmp, red, total;

@@ -50,6 +50,18 @@ class pslr_info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pslr_batch_info(C.Structure):
+    _fields_ = [("nsys", C.c_int32), ("nrhs", C.c_int32), ("nprob", C.c_int32), ("n_total", C.c_int64),
+                ("items", C.c_int32), ("grid", C.c_int32), ("ring", C.c_int32 * 2), ("max_m", C.c_int32),
+                ("max_p", C.c_int32), ("max_q", C.c_int32), ("apply_bytes_fp64", C.c_int64),
+                ("apply_bytes_fp32", C.c_int64), ("graph", C.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["ring"] = list(self.ring)
+        return d
+
+
 _P, _I32, _I64, _D, _U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint64
 SIGNATURES = {
     "pslr_setup": (_I32, [_I32, _P, _P, _P, C.POINTER(pslr_opts), _P, C.POINTER(_P)]),
@@ -73,6 +85,14 @@ SIGNATURES = {
     "pslr_last_error": (C.c_char_p, [_P]),
     "pslr_status_string": (C.c_char_p, [_I32]),
     "pslr_destroy": (None, [_P]),
+    "pslr_batch_create": (_I32, [_I32, _P, _I32, C.POINTER(_P)]),
+    "pslr_batch_apply": (_I32, [_P, _P, _P, _I32, _P]),
+    "pslr_batch_solve": (_I32, [_P, _P, _P, _D, _I32, _I32, _I32, _P, _P, _P]),
+    "pslr_batch_get_info": (_I32, [_P, C.POINTER(pslr_batch_info)]),
+    "pslr_batch_sync": (_I32, [_P, _P]),
+    "pslr_batch_set_wait_limit": (_I64, [_P, _I64]),
+    "pslr_batch_last_error": (C.c_char_p, [_P]),
+    "pslr_batch_destroy": (None, [_P]),
 }
 
 _lib = None
@@ -251,6 +271,88 @@ class Pslr:
 
     def set_wait_limit(self, polls):
         return self.lib.pslr_set_wait_limit(self.h, int(polls))
+
+
+class Batch:
+    """Many set-up contexts (:class:`Pslr`, low-rank term built) applied and
+    solved together, ``nrhs`` right-hand sides each (pslr_batch_*).
+
+    Batched vectors are 1-D device tensors of ``info["n_total"]`` elements:
+    the systems in order, each an n_k x nrhs column-major block;
+    :meth:`offsets` gives the blocks' starts.  The contexts must outlive the
+    batch; the batch keeps references to them."""
+
+    def __init__(self, systems, nrhs):
+        lib = load()
+        self.lib = lib
+        self.systems = list(systems)
+        self.nrhs = int(nrhs)
+        arr = (C.c_void_p * len(self.systems))(*[p.h for p in self.systems])
+        h = C.c_void_p()
+        st = lib.pslr_batch_create(len(self.systems), arr, self.nrhs, C.byref(h))
+        if st != PSLR_OK:
+            raise PslrError(st, f"pslr_batch_create: {lib.pslr_batch_last_error(None).decode()}")
+        self.h = h
+        self.info = self.get_info()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pslr_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what, ok=(PSLR_OK,)):
+        if st not in ok:
+            msg = self.lib.pslr_batch_last_error(self.h).decode()
+            raise PslrError(st, f"{what}: {msg}")
+        return st
+
+    def get_info(self):
+        info = pslr_batch_info()
+        self._check(self.lib.pslr_batch_get_info(self.h, C.byref(info)), "pslr_batch_get_info")
+        return info.as_dict()
+
+    def offsets(self):
+        """Start of each system's n_k x nrhs block in a batched vector."""
+        out, o = [], 0
+        for p in self.systems:
+            out.append(o)
+            o += p.n * self.nrhs
+        return out
+
+    def apply(self, b, z, stream=None):
+        """z = M_k^{-1} b for every system and right-hand side, one launch;
+        float64 (FP64 form) or float32 (FP32 form, BF16 V) batched vectors."""
+        prec = PSLR_FP64 if b.dtype.itemsize == 8 else PSLR_FP32
+        return self._check(self.lib.pslr_batch_apply(self.h, _ptr(b), _ptr(z), prec, _stream(stream)),
+                           "pslr_batch_apply")
+
+    def solve(self, b, x, rtol=1e-8, restart=40, maxit=500, prec=PSLR_FP64, stream=None, check=True):
+        """Batched FGMRES; returns (iters, relres, status), per problem
+        ((system, rhs) pairs in system-major order)."""
+        P = self.info["nprob"]
+        its = np.zeros(P, np.int32)
+        rel = np.zeros(P, np.float64)
+        st = self.lib.pslr_batch_solve(self.h, _ptr(b), _ptr(x), float(rtol), int(restart), int(maxit),
+                                       int(prec), its.ctypes.data, rel.ctypes.data, _stream(stream))
+        if check:
+            self._check(st, "pslr_batch_solve", ok=(PSLR_OK, PSLR_ERR_NOT_CONVERGED))
+        self.info = self.get_info()
+        return its, rel, st
+
+    def sync(self, stream=None, check=True):
+        st = self.lib.pslr_batch_sync(self.h, _stream(stream))
+        if check:
+            self._check(st, "pslr_batch_sync")
+        return st
+
+    def set_wait_limit(self, polls):
+        return self.lib.pslr_batch_set_wait_limit(self.h, int(polls))
 
 
 def _opts(dims, splits, part, factor, seed):

@@ -1,0 +1,258 @@
+"""GPU parity of the batched form: many uneven systems, several right-hand
+sides each, in one launch per apply and one FGMRES per (system, rhs) pair.
+
+The oracle has no batched form: a batch is a set of independent systems, so
+the reference for problem (k, j) is the oracle's apply / FGMRES on system k
+and right-hand side j.  Bars as for the single-system path: FP64 applies
+within 1e-12, FP32 applies within 1e-5 (against the oracle on the same BF16
+V), FGMRES iteration counts within +-1 of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from pslr_inputs import configs as C
+from pslr_inputs import generators as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+# (kind, dims, splits, m, r): uneven sizes, 2D and 3D, degenerate m = 0 / r = 0
+SYSTEMS = [
+    ("lap", (20, 17), (3, 2), 3, 6),
+    ("lap", (33, 30), (4, 4), 2, 8),
+    ("cd", (9, 8, 7), (2, 2, 2), 4, 5),
+    ("lap", (12, 12), (2, 2), 0, 0),
+    ("kappa", (8, 9, 7), (2, 2, 1), 1, 0),
+    ("lap", (26, 19), (4, 3), 5, 12),
+]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_00917_gb300 import build
+
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _bf16(x):
+    f = np.asarray(x, dtype=np.float32).copy()
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb, np.abs(a - b).max() / np.abs(b).max()
+
+
+def _system(spec, bf16_oracle=False):
+    """A context and an oracle with the same low-rank term (the oracle's)."""
+    from paper_2002_00917_gb300 import pslr
+
+    kind, dims, splits, m, r = spec
+    w = C.small_problem(kind, dims, splits, m=m, rank=r, K=3)
+    ctx = pslr.from_workload(w)
+    orc = O.from_workload(w)
+    if r:
+        orc.build_lowrank(m, r, seed=0)
+        V, H, Gm = orc.lowrank()
+        ctx.set_lowrank(m, V, Gm)
+        if bf16_oracle:
+            orc.set_lowrank(m, _bf16(V), Gm.astype(np.float32).astype(np.float64))
+    else:
+        ctx.set_lowrank(m)
+        orc.set_lowrank(m, None, None)
+    return w, ctx, orc
+
+
+def _systems(specs, bf16_oracle=False):
+    return [_system(s, bf16_oracle) for s in specs]
+
+
+def _split(bt, v):
+    """Batched vector -> list over systems of (n_k, nrhs) arrays."""
+    out = []
+    for p, o in zip(bt.systems, bt.offsets()):
+        out.append(v[o:o + p.n * bt.nrhs].reshape(bt.nrhs, p.n).T)
+    return out
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 4])
+def test_batch_apply_fp64_matches_oracle(dev, nrhs):
+    from paper_2002_00917_gb300 import pslr
+
+    sy = _systems(SYSTEMS)
+    bt = pslr.Batch([c for _, c, _ in sy], nrhs)
+    N = bt.info["n_total"]
+    assert N == sum(w["A"].n for w, _, _ in sy) * nrhs
+    b = np.random.default_rng(11).uniform(-1, 1, N)
+    bd = torch.tensor(b, device=dev)
+    zd = torch.full_like(bd, np.nan)
+    bt.apply(bd, zd)
+    bt.sync()
+    z = zd.cpu().numpy()
+    for (w, ctx, orc), bk, zk in zip(sy, _split(bt, b), _split(bt, z)):
+        for j in range(nrhs):
+            r2, rinf = _rel(zk[:, j], orc.apply(np.ascontiguousarray(bk[:, j])))
+            assert r2 <= TOL64 and rinf <= TOL64, (w["A"].n, j, r2, rinf)
+
+
+def test_batch_apply_equals_single_system_apply(dev):
+    """The batched launch and the per-system launches run the same arithmetic
+    per row; only the order of the low-rank partial sums can differ."""
+    from paper_2002_00917_gb300 import pslr
+
+    sy = _systems(SYSTEMS)
+    bt = pslr.Batch([c for _, c, _ in sy], 2)
+    b = torch.tensor(np.random.default_rng(12).uniform(-1, 1, bt.info["n_total"]), device=dev)
+    z = torch.zeros_like(b)
+    bt.apply(b, z)
+    bt.sync()
+    for (w, ctx, _), o in zip(sy, bt.offsets()):
+        n = w["A"].n
+        bk = b[o:o + 2 * n].reshape(2, n).T  # column-major (n, 2) view
+        zk = torch.zeros_like(bk)
+        ctx.apply(bk, zk)
+        ctx.sync()
+        r2, rinf = _rel(z[o:o + 2 * n].reshape(2, n).T.cpu().numpy(), zk.cpu().numpy())
+        assert r2 <= 1e-14 and rinf <= 1e-14, (n, r2, rinf)
+
+
+def test_batch_apply_fp32_matches_oracle(dev):
+    from paper_2002_00917_gb300 import pslr
+
+    sy = _systems(SYSTEMS, bf16_oracle=True)
+    bt = pslr.Batch([c for _, c, _ in sy], 4)
+    b = np.random.default_rng(13).uniform(-1, 1, bt.info["n_total"]).astype(np.float32)
+    bd = torch.tensor(b, device=dev)
+    zd = torch.zeros_like(bd)
+    bt.apply(bd, zd)
+    bt.sync()
+    z = zd.cpu().double().numpy()
+    for (w, ctx, orc), bk, zk in zip(sy, _split(bt, b.astype(np.float64)), _split(bt, z)):
+        for j in range(4):
+            r2, rinf = _rel(zk[:, j], orc.apply(np.ascontiguousarray(bk[:, j])))
+            assert r2 <= TOL32 and rinf <= TOL32, (w["A"].n, j, r2, rinf)
+
+
+def test_batch_more_items_than_ctas(dev):
+    """40 systems of 16 subdomains: several items per CTA in every phase, with
+    m and r varying across systems."""
+    from paper_2002_00917_gb300 import pslr
+
+    specs = [("lap", (16 + (k % 7), 16 + (k % 5)), (4, 4), k % 4, (0, 4, 8)[k % 3]) for k in range(40)]
+    sy = _systems(specs)
+    bt = pslr.Batch([c for _, c, _ in sy], 2)
+    assert bt.info["items"] == 640 and bt.info["items"] > bt.info["grid"]
+    b = np.random.default_rng(14).uniform(-1, 1, bt.info["n_total"])
+    bd = torch.tensor(b, device=dev)
+    zd = torch.zeros_like(bd)
+    bt.apply(bd, zd)
+    bt.sync()
+    for (w, ctx, orc), bk, zk in zip(sy, _split(bt, b), _split(bt, zd.cpu().numpy())):
+        for j in range(2):
+            r2, rinf = _rel(zk[:, j], orc.apply(np.ascontiguousarray(bk[:, j])))
+            assert r2 <= TOL64 and rinf <= TOL64
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_batch_solve(dev, prec):
+    """Every (system, rhs) problem converges to 1e-8 in its true residual; in
+    FP64 its iteration count is within +-1 of the oracle's FGMRES."""
+    from paper_2002_00917_gb300 import pslr
+
+    sy = _systems(SYSTEMS)
+    nrhs = 3
+    bt = pslr.Batch([c for _, c, _ in sy], nrhs)
+    rng = np.random.default_rng(15)
+    bs = []
+    for w, _, _ in sy:
+        cols = [G.csr_matvec(w["A"], rng.uniform(-1, 1, w["A"].n)) for _ in range(nrhs)]
+        bs.append(np.concatenate(cols))
+    b = np.concatenate(bs)
+    bd = torch.tensor(b, device=dev)
+    x = torch.zeros_like(bd)
+    its, rel, st = bt.solve(bd, x, rtol=1e-8, restart=20, maxit=400, prec=prec)
+    assert st == pslr.PSLR_OK, (its, rel)
+    assert bt.info["graph"] == 1
+    xs = _split(bt, x.cpu().numpy())
+    for k, ((w, ctx, orc), bk) in enumerate(zip(sy, _split(bt, b))):
+        A = G.dense_from_csr(w["A"])
+        for j in range(nrhs):
+            p = k * nrhs + j
+            assert rel[p] <= 1e-8
+            assert np.linalg.norm(bk[:, j] - A @ xs[k][:, j]) <= 1.0001e-8 * np.linalg.norm(bk[:, j])
+            if prec == 0:
+                _, its_o, _, st_o = orc.fgmres(np.ascontiguousarray(bk[:, j]), rtol=1e-8, restart=20, maxit=400)
+                assert st_o == 0 and abs(int(its[p]) - its_o) <= 1, (k, j, its[p], its_o)
+
+
+def test_batch_solve_maxit_and_zero_rhs(dev):
+    """A zero right-hand side is solved by x = 0 in 0 iterations; the others
+    stop at maxit and the call reports PSLR_ERR_NOT_CONVERGED."""
+    from paper_2002_00917_gb300 import pslr
+
+    sy = _systems(SYSTEMS[:3])
+    bt = pslr.Batch([c for _, c, _ in sy], 2)
+    b = np.random.default_rng(16).uniform(-1, 1, bt.info["n_total"])
+    o = bt.offsets()
+    n1 = sy[1][0]["A"].n
+    b[o[1]:o[1] + n1] = 0.0  # system 1, rhs 0
+    bd = torch.tensor(b, device=dev)
+    x = torch.zeros_like(bd)
+    its, rel, st = bt.solve(bd, x, rtol=1e-14, restart=2, maxit=3)
+    assert st == pslr.PSLR_ERR_NOT_CONVERGED
+    assert its[2] == 0 and rel[2] == 0.0
+    assert np.all(x[o[1]:o[1] + n1].cpu().numpy() == 0.0)
+    assert all(its[p] == 3 for p in range(6) if p != 2)
+
+
+def test_batch_rejects_stale_lowrank_and_bad_arguments(dev):
+    from paper_2002_00917_gb300 import pslr
+
+    sy = _systems(SYSTEMS[:2])
+    bt = pslr.Batch([c for _, c, _ in sy], 1)
+    b = torch.zeros(bt.info["n_total"], device=dev, dtype=torch.float64)
+    z = torch.zeros_like(b)
+    sy[0][1].set_lowrank(1)  # replaces system 0's low-rank term
+    with pytest.raises(pslr.PslrError) as e:
+        bt.apply(b, z)
+    assert e.value.status == pslr.PSLR_ERR_STATE
+    with pytest.raises(pslr.PslrError) as e:
+        pslr.Batch([c for _, c, _ in sy], 5)
+    assert e.value.status == pslr.PSLR_ERR_ARG
+    w = C.small_problem("lap", (10, 10), (2, 2), factor=1, K=3)
+    exact = pslr.from_workload(w)
+    exact.set_lowrank(1)
+    with pytest.raises(pslr.PslrError) as e:
+        pslr.Batch([exact], 1)
+    assert e.value.status == pslr.PSLR_ERR_ARG
+
+
+def test_batch_timeout_path_reports_and_recovers(dev):
+    """A grid-barrier wait with limit 0 gives up at once; the batch reports
+    PSLR_ERR_TIMEOUT and the next apply is correct.  No GPU fault is involved."""
+    from paper_2002_00917_gb300 import pslr
+
+    sy = _systems(SYSTEMS[:3])
+    bt = pslr.Batch([c for _, c, _ in sy], 2)
+    b = np.random.default_rng(17).uniform(-1, 1, bt.info["n_total"])
+    bd = torch.tensor(b, device=dev)
+    zd = torch.zeros_like(bd)
+    old = bt.set_wait_limit(0)
+    bt.apply(bd, zd)
+    assert bt.sync(check=False) == pslr.PSLR_ERR_TIMEOUT
+    bt.set_wait_limit(old)
+    bt.apply(bd, zd)
+    bt.sync()
+    for (w, ctx, orc), bk, zk in zip(sy, _split(bt, b), _split(bt, zd.cpu().numpy())):
+        r2, _ = _rel(zk[:, 1], orc.apply(np.ascontiguousarray(bk[:, 1])))
+        assert r2 <= TOL64
