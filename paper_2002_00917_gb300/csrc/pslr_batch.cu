@@ -16,8 +16,11 @@
 // (pslr_apply.cu); systems with fewer series terms (smaller m) sit out the
 // later terms, and the low-rank coefficients d = G V^T t of each (system,
 // right-hand side) pair are formed once, by the CTA that owns the pair,
-// between two grid barriers.  Local exact-LU factors (row pivoting) are not
-// supported here; the host rejects such systems.
+// between two grid barriers.  Inside the batched FGMRES a system whose
+// problems have all converged drops out: the producer skips its segments and
+// the consumers its items (per-system flags, fixed for the launch).  Local
+// exact-LU factors (row pivoting) are not supported here; the host rejects
+// such systems.
 #include "pslr_device.cuh"
 
 namespace pslr {
@@ -153,6 +156,13 @@ __device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, int os, const T *sr
 
 // ------------------------------------------------------------------ kernel
 
+// Does system k take part in this launch?  (The producer skips the same
+// systems' segments: both read the flags, which no launch changes while it runs.)
+template <class T, class IO>
+__device__ __forceinline__ bool on(const BatchParams<T, IO> &P, int k) {
+    return P.active == nullptr || __ldg(P.active + k) != 0;
+}
+
 template <class T, class VT, class IO>
 __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const BatchParams<T, IO> P) {
     extern __shared__ __align__(128) char smem[];
@@ -162,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
     const int xs = P.max_p + 1, gs = P.max_q + 1;  // per-rhs strides of the local vectors
     const SmemLayout L = smem_layout(P.slot_bytes, P.ring, nr * xs - 1, nr * gs - 1, sizeof(T), false);
     Cta<T> c;
-    if (!cta_start(c, smem, L, P.ring, P.slot_bytes, P.stream, P.stream_off, P.segbase)) return;
+    if (!cta_start(c, smem, L, P.ring, P.slot_bytes, P.stream, P.stream_off, P.segbase, P.active)) return;
     const int tid = threadIdx.x;
     const int ib = P.item_off[blockIdx.x], ie = P.item_off[blockIdx.x + 1];
     T *const dsh = c.red + (kConsumers / 32) * kMaxRank + kMaxRank;  // where lowrank_coeffs leaves d
@@ -171,6 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
     // ---- phase 0: u = B^{-1} f, t = g - F u (Algorithm 3, step 2); a system
     // without a low-rank term also takes w_0 = C0^{-1} t here.
     for (int it = ib; it < ie; ++it) {
+        if (!on(P, P.items[2 * it])) continue;
         const BatchSys<T> &S = P.sys[P.items[2 * it]];
         const int i = P.items[2 * it + 1];
         const Counts k = counts_of(S.cnt, i);
@@ -220,6 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
         ok = grid_wait(c, P.bar, P.err, P.wait_limit);
         if (!ok) goto abort;
         for (int pi = P.pair_off[blockIdx.x]; pi < P.pair_off[blockIdx.x + 1]; ++pi) {
+            if (!on(P, P.pairs[2 * pi])) continue;
             const BatchSys<T> &S = P.sys[P.pairs[2 * pi]];
             const int kr = P.pairs[2 * pi + 1];
             lowrank_coeffs(c, S.part + (int64_t)kr * S.s * S.r, S.G, S.s, S.r);
@@ -230,6 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
         ok = grid_wait(c, P.bar, P.err, P.wait_limit);
         if (!ok) goto abort;
         for (int it = ib; it < ie; ++it) {
+            if (!on(P, P.items[2 * it])) continue;
             const BatchSys<T> &S = P.sys[P.items[2 * it]];
             if (S.r == 0) continue;
             const int i = P.items[2 * it + 1];
@@ -260,6 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
         grid_arrive(c, P.bar, P.grid);
         bool waited = false;
         for (int it = ib; it < ie; ++it) {
+            if (!on(P, P.items[2 * it])) continue;
             const BatchSys<T> &S = P.sys[P.items[2 * it]];
             if (S.m < kk) continue;
             const int i = P.items[2 * it + 1];
@@ -304,6 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
 
     // ---- y = acc; x = B^{-1}(f - E y); scatter (steps 5-6)
     for (int it = ib; it < ie; ++it) {
+        if (!on(P, P.items[2 * it])) continue;
         const BatchSys<T> &S = P.sys[P.items[2 * it]];
         const int i = P.items[2 * it + 1];
         const Counts k = counts_of(S.cnt, i);

@@ -279,7 +279,9 @@ static pslr_status batch_build(pslr_batch *bt) {
         std::vector<int64_t> soff(grid + 1, 0);
         auto add = [&](int k, int i, std::initializer_list<int> cats) {
             const int64_t shift = bt->sx[k].seg[prec] - base;
+            const size_t first = ent.size();
             for (int cat : cats) sys_segments(bt->ctx[k], prec, i, cat, shift, ent);
+            for (size_t t = first; t < ent.size(); ++t) ent[t].pad = k;  // the producer skips by system
         };
         for (int b = 0; b < grid; ++b) {
             soff[b] = (int64_t)ent.size();
@@ -419,7 +421,7 @@ static pslr_status batch_check(pslr_batch *bt) {
 
 // form 0: FP64; 1: FP32 in and out; 2: FP32 arithmetic, FP64 in and out.
 static pslr_status batch_launch(pslr_batch *bt, int form, const void *b, void *z, const int *skip,
-                                cudaStream_t st) {
+                                const int *active, cudaStream_t st) {
     const int prec = form == 0 ? 0 : 1;
     auto fill = [&](auto &P) {
         P.segbase = bt->segbase[prec];
@@ -440,6 +442,7 @@ static pslr_status batch_launch(pslr_batch *bt, int form, const void *b, void *z
         P.bar = bt->d_bar;
         P.err = bt->d_err;
         P.skip = skip;
+        P.active = active;
         P.wait_limit = bt->wait_limit;
     };
     cudaError_t e;
@@ -491,7 +494,7 @@ static pslr_status krylov_ensure(pslr_batch *bt, int K) {
                       + (size_t)P * ldp * 3                  // gam, h1, h2
                       + (size_t)P * K                        // y
                       + (size_t)bt->nchunk * ldp * 2;        // pa, pb
-    const size_t ni = (size_t)P * 4 + 2;
+    const size_t ni = (size_t)P * 4 + 2 + (size_t)bt->nsys;
     BCK(cudaMalloc(&bt->d_state, sizeof(double) * nd + sizeof(int) * ni));
     BCK(cudaMemset(bt->d_state, 0, sizeof(double) * nd + sizeof(int) * ni));
     double *d = static_cast<double *>(bt->d_state);
@@ -514,7 +517,10 @@ static pslr_status krylov_ensure(pslr_batch *bt, int K) {
     S.conv = ip; ip += P;
     S.its = ip; ip += P;
     S.remaining = ip; ip += 1;
-    S.skip = ip;
+    S.skip = ip; ip += 1;
+    S.sys_active = ip;
+    S.nsys = bt->nsys;
+    S.nrhs = bt->nrhs;
     S.K = K;
     bt->kK = K;
     return PSLR_OK;
@@ -529,7 +535,7 @@ static pslr_status enqueue_cycle(pslr_batch *bt, int form, cudaStream_t st) {
     for (int j = 0; j < K; ++j) {
         const double *vj = bt->d_V + (size_t)j * N;
         double *zj = bt->d_Z + (size_t)j * N;
-        pslr_status a = batch_launch(bt, form, vj, zj, S.skip, st);
+        pslr_status a = batch_launch(bt, form, vj, zj, S.skip, S.sys_active, st);
         if (a != PSLR_OK) return a;
         bk_spmv_dots(nc, j, bt->d_chunks, bt->d_probs, bt->d_bsys, zj, bt->d_w, bt->d_V, N, S, st);
         bk_update(nc, j, bt->d_chunks, bt->d_probs, bt->d_w, bt->d_V, N, S.pa, S.pb, S.h1, 0, S, st);
@@ -606,7 +612,8 @@ pslr_status pslr_batch_apply(pslr_batch *bt, const void *b_dev, void *z_dev, psl
         return bfail(bt, PSLR_ERR_ARG, "batch_apply: bad argument");
     pslr_status st = batch_check(bt);
     if (st != PSLR_OK) return st;
-    return batch_launch(bt, prec == PSLR_FP64 ? 0 : 1, b_dev, z_dev, nullptr, static_cast<cudaStream_t>(stream));
+    return batch_launch(bt, prec == PSLR_FP64 ? 0 : 1, b_dev, z_dev, nullptr, nullptr,
+                        static_cast<cudaStream_t>(stream));
 }
 
 pslr_status pslr_batch_sync(pslr_batch *bt, void *stream) {

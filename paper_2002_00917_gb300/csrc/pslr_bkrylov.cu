@@ -14,7 +14,8 @@
 // The cycle end (least squares, x += Z y, true residual, restart) is also on
 // the device, so one restart cycle needs no host round trip and can be
 // replayed as one CUDA graph.  A problem that has stopped makes every later
-// launch of the cycle return at once for its chunks.
+// launch of the cycle return at once for its chunks, and a system whose
+// problems have all stopped drops out of the batched apply (sys_active).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -127,6 +128,16 @@ __global__ void __launch_bounds__(kBkThreads) kb_update(int j, const BkChunk *__
     else bk_dots(k, V, ld, w, ch.b, ch.e, pout, ldp);
 }
 
+// sys_active[k] = some problem of system k still runs (after stop[] changed;
+// one block, called after a __syncthreads).
+__device__ void bk_sys_active(const BkState &S) {
+    for (int k = threadIdx.x; k < S.nsys; k += blockDim.x) {
+        int a = 0;
+        for (int j = 0; j < S.nrhs; ++j) a |= S.stop[k * S.nrhs + j] == 0;
+        S.sys_active[k] = a;
+    }
+}
+
 // One thread per problem: Hessenberg column j = h1 + h2 with h_{j+1,j} = ||w||,
 // the Givens rotations of the least-squares problem, and the stopping test
 // (estimated residual |gamma_{j+1}| <= rtol ||b||, breakdown, iteration
@@ -171,6 +182,7 @@ __global__ void kb_hessenberg(int j, int nprob, const BkProb *__restrict__ probs
     if (mine) atomicAdd(&active, mine);
     __syncthreads();
     if (threadIdx.x == 0) *S.skip = active == 0;
+    bk_sys_active(S);
 }
 
 // v_{j+1} = w / h_{j+1,j} for the problems still running.
@@ -285,6 +297,7 @@ __global__ void kb_restart(int first, int nprob, const BkProb *__restrict__ prob
         *S.remaining = running;
         *S.skip = running == 0;
     }
+    bk_sys_active(S);
 }
 
 // v_0 = r / ||r|| for the problems still running.

@@ -176,9 +176,12 @@ __device__ __forceinline__ void seg_done(Ring &R) {
 }
 
 // Producer warp: copy the CTA's stream into the ring.
+// With active != nullptr an entry is skipped when active[entry.pad] == 0
+// (the batched kernel tags each entry with its system; the consumers skip the
+// same systems, from the same flags, which no launch changes while it runs).
 static __device__ void producer(const StreamEnt *stream, int64_t b, int64_t e, const char *segbase,
                          char *ring, int slots, int slot_bytes, uint32_t full_s, uint32_t empty_s,
-                         Ctl *ctl) {
+                         Ctl *ctl, const int *active) {
     const int lane = threadIdx.x & 31;
     const uint32_t ring_s = smem_addr(ring);
     int slot = 0;
@@ -196,6 +199,7 @@ static __device__ void producer(const StreamEnt *stream, int64_t b, int64_t e, c
         for (int t = 0; t < cnt; ++t) {
             const long long off = __shfl_sync(0xffffffffu, (long long)cur.off, t);
             const int bytes = __shfl_sync(0xffffffffu, cur.bytes, t);
+            if (active != nullptr && __ldg(active + __shfl_sync(0xffffffffu, cur.pad, t)) == 0) continue;
             if (lane == 0) {
                 // slot free?  (the first pass over the ring finds every slot free)
                 const uint32_t ebar = empty_s + 8 * slot;
@@ -880,7 +884,8 @@ __device__ void lowrank_update(Cta<T> &c, const VT *V, int q, int r, int go, int
 // runs its stream inside and returns false.
 template <class T>
 __device__ bool cta_start(Cta<T> &c, char *smem, const SmemLayout &L, int ring, int slot_bytes,
-                          const StreamEnt *stream, const int64_t *stream_off, const char *segbase) {
+                          const StreamEnt *stream, const int64_t *stream_off, const char *segbase,
+                          const int *active = nullptr) {
     c.xi = reinterpret_cast<T *>(smem + L.xi);
     c.wi = reinterpret_cast<T *>(smem + L.wi);
     c.si = reinterpret_cast<T *>(smem + L.si);
@@ -909,7 +914,7 @@ __device__ bool cta_start(Cta<T> &c, char *smem, const SmemLayout &L, int ring, 
     __syncthreads();
     if (threadIdx.x / 32 == kProducerWarp) {
         producer(stream, stream_off[blockIdx.x], stream_off[blockIdx.x + 1], segbase, c.ring.base, ring,
-                 slot_bytes, c.ring.full_s, c.ring.empty_s, c.ctl);
+                 slot_bytes, c.ring.full_s, c.ring.empty_s, c.ctl, active);
         return false;
     }
     return true;

@@ -178,6 +178,7 @@ struct BatchParams {
     unsigned *bar;
     int *err;
     const int *skip;            // when *skip != 0 the launch does nothing
+    const int *active;          // nsys flags, or nullptr: systems with active[k] == 0 are skipped
     long long wait_limit;
 };
 
@@ -218,6 +219,8 @@ struct BkState {
     double *pa, *pb;    // nchunk x (K+1): per-chunk partials (ping-pong)
     int *remaining;     // [1] problems still running
     int *skip;          // [1] no problem running: later launches of the cycle return at once
+    int *sys_active;    // nsys: some problem of the system still runs (the apply skips the others)
+    int nsys, nrhs;     // problem p belongs to system p / nrhs
     double rtol;
     int maxit;
     int K;              // restart length
