@@ -12,6 +12,13 @@ uniform[-1,1] right-hand side.  Its operator (~28 MB) fits in L2, so L2 is
 flushed (a 512 MB write) between timed applies and only the apply itself is
 inside each CUDA-event pair.
 
+The line's "batch" object covers the batched form on its own workload (64
+uneven 2D shifted Laplacians, sides 64..256, 4 right-hand sides each): the
+bandwidth of one batched apply launch, batched FGMRES(127) to 1e-8 with the
+FP32 and with the FP64 preconditioner (cycles replayed as CUDA graphs), and
+the plain FP64 form - one pslr_solve per (system, rhs) - timed on a stated
+sample of the problems and scaled to all of them (--batch-seq-stride).
+
     python bench.py [--gpus N --steps K --warmup W --workload NAME --impl ours|reference]
 
 With N > 1 (torchrun) every rank runs an independent replica of the workload
@@ -49,22 +56,26 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+APPLY_SOURCES = ("pslr_apply.cu", "pslr_device.cuh", "pslr_internal.h")  # the kernel, its device code, its layout
+BATCH_SOURCES = ("pslr_batch.cu", "pslr_device.cuh", "pslr_internal.h")
+
+
+def kernel_source_hash(files=APPLY_SOURCES):
     h = hashlib.sha256()
-    for f in ("pslr_apply.cu", "pslr_device.cuh", "pslr_internal.h"):  # the kernel, its device code, its data layout
+    for f in files:
         with open(os.path.join(ROOT, "paper_2002_00917_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def committed_traffic(workload, prec):
-    """DRAM bytes per apply launch from the committed ncu summary, if it was
-    taken on the current kernel sources; else None."""
+def committed_traffic(workload, prec, files=APPLY_SOURCES):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
         e = d.get(f"{workload}/{prec}")
-        if e and e.get("source_hash") == kernel_source_hash():
+        if e and e.get("source_hash") == kernel_source_hash(files):
             return int(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -208,6 +219,108 @@ def reference_apply_bytes(w, rank):
     return info["apply_bytes_fp64"]
 
 
+def run_batch(dev, flush, stream, steps, warmup, seq_stride, solve=True):
+    """The batched workload (64 uneven 2D shifted Laplacians x 4 rhs): batched
+    apply bandwidth (one launch for all systems and rhs), batched FGMRES to
+    1e-8 with the FP32 and the FP64 preconditioner, and the plain FP64 form -
+    per-system pslr_solve, one problem at a time - on every seq_stride-th
+    system's problems."""
+    import torch
+
+    from paper_2002_00917_gb300 import pslr
+    from pslr_inputs import configs as Cfg
+    from pslr_inputs import generators as Gen
+
+    w = Cfg.batch2d_64sys()
+    nr = w["nrhs"]
+    t0 = time.perf_counter()
+    ctxs = []
+    for s in w["systems"]:
+        c = pslr.Pslr(s["A"], dims=s["dims"], splits=s["splits"], factor=s["factor"])
+        c.build_lowrank(s["m"], s["rank"])
+        ctxs.append(c)
+    bt = pslr.Batch(ctxs, nr)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = bt.info
+    rng = np.random.default_rng(0)
+    bs, xs = [], []
+    for s in w["systems"]:
+        for _ in range(nr):
+            x = rng.uniform(-1, 1, s["A"].n)
+            xs.append(x)
+            bs.append(Gen.csr_matvec(s["A"], x))
+    xs = np.concatenate(xs)
+    b = torch.tensor(np.concatenate(bs), device=dev)
+
+    def timed(bin_, zout):
+        for _ in range(warmup):
+            bt.apply(bin_, zout)
+        bt.sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
+            flush.fill_(1.0)
+            e0.record(stream)
+            bt.apply(bin_, zout)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        bt.sync()
+        return sum(e0.elapsed_time(e1) for e0, e1 in evs) / steps
+
+    peak, _ = measured_peaks()
+    out = {"workload": w["name"], "nsys": info["nsys"], "nrhs": nr, "problems": info["nprob"],
+           "n_total": info["n_total"], "work_items": info["items"], "grid": info["grid"],
+           "setup_s": setup_s}
+    for name, bin_ in (("apply_fp64", b), ("apply_fp32", b.float())):
+        ms = timed(bin_, torch.empty_like(bin_))
+        nb = info["apply_bytes_fp64" if name == "apply_fp64" else "apply_bytes_fp32"]
+        out[name] = {"ms": ms, "GB/s": nb / ms / 1e6, "frac": nb / ms / 1e6 / peak, "bytes_per_launch": nb,
+                     "traffic": committed_traffic(w["name"], "fp64", BATCH_SOURCES) if name == "apply_fp64" else None}
+    if not solve:
+        bt.close()
+        for c in ctxs:
+            c.close()
+        return out
+    restart, maxit = 127, 2000
+    for name, prec in (("fgmres_fp32", pslr.PSLR_FP32), ("fgmres_fp64", pslr.PSLR_FP64)):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        its, rel, st = bt.solve(b, x, rtol=1e-8, restart=restart, maxit=maxit, prec=prec)
+        torch.cuda.synchronize()
+        out[name] = {"ms": 1e3 * (time.perf_counter() - c0), "restart": restart, "iters_max": int(its.max()),
+                     "iters_mean": float(its.mean()), "converged": int((rel <= 1e-8).sum()),
+                     "relres_max": float(rel.max()), "graph": bt.info["graph"],
+                     "rel_err_vs_xstar": float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))}
+    # the plain FP64 GPU form: one pslr_solve per (system, rhs), on a sample
+    t_seq, n_seq, its_seq, conv_seq = 0.0, 0, 0, 0
+    for k, (c, o) in enumerate(zip(ctxs, bt.offsets())):
+        if k % seq_stride:
+            continue
+        for j in range(nr):
+            bk = b[o + j * c.n:o + (j + 1) * c.n].contiguous()
+            xk = torch.zeros_like(bk)
+            torch.cuda.synchronize()
+            c0 = time.perf_counter()
+            it1, rel1, st1 = c.solve(bk, xk, rtol=1e-8, restart=restart, maxit=maxit)
+            torch.cuda.synchronize()
+            t_seq += time.perf_counter() - c0
+            n_seq += 1
+            its_seq += it1
+            conv_seq += st1 == 0
+    est_all = 1e3 * t_seq * info["nprob"] / n_seq
+    out["sequential_fp64"] = {
+        "sample": f"every {seq_stride}th system's {nr} problems ({n_seq} of {info['nprob']}), one pslr_solve each",
+        "ms_sample": 1e3 * t_seq, "iters_mean": its_seq / n_seq, "converged": conv_seq,
+        "ms_all_estimated": est_all}
+    out["speedup_vs_sequential_fp64"] = {"fgmres_fp32": est_all / out["fgmres_fp32"]["ms"],
+                                         "fgmres_fp64": est_all / out["fgmres_fp64"]["ms"]}
+    bt.close()
+    for c in ctxs:
+        c.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,6 +330,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fgmres", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-seq-stride", type=int, default=8)
+    ap.add_argument("--no-batch-solve", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -339,6 +455,11 @@ def main():
                     "converged": st == 0, "status": "ok" if st == 0 else "F",
                     "rel_err_vs_xstar": err}
 
+    batch = None
+    if not args.no_batch and rank == 0:
+        batch = run_batch(dev, flush, stream, min(args.steps, 20), args.warmup, args.batch_seq_stride,
+                          solve=not args.no_batch_solve)
+
     res = None
     if rank == 0:
         V, H, G = ctx.get_lowrank()
@@ -361,6 +482,7 @@ def main():
                            "bytes_per_launch": bytes32, "launch_us": 1e6 * t32 / args.steps,
                            "dtype": "f32 (BF16 V)"},
             "fgmres": fg,
+            "batch": batch,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w["A"].n,
                     "d2h_bytes_per_step": 8 * w["A"].n},
             "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
