@@ -265,6 +265,8 @@ typedef struct {
     int32_t items;                  /* (system, subdomain) work items                */
     int32_t grid;                   /* CTAs of the batched apply launch              */
     int32_t ring[2];                /* ring slots of the apply, [FP64, FP32]         */
+    int32_t group[2];               /* subdomains swept in lockstep per CTA, [FP64, FP32] */
+    int32_t groups[2];              /* groups of the launch, [FP64, FP32]            */
     int32_t max_m, max_p, max_q;
     int64_t apply_bytes_fp64;       /* algorithmic bytes of one batched apply        */
     int64_t apply_bytes_fp32;
@@ -274,7 +276,10 @@ typedef struct {
 /*
  * Build a batch over nsys contexts that pslr_setup made and whose low-rank
  * term is built (pslr_build_lowrank / pslr_set_lowrank; rank 0 is allowed).
- * nrhs: 1..4 right-hand sides per system.  The batch reads the contexts'
+ * nrhs: 1..4 right-hand sides per system.  group: how many subdomains of one
+ * system a CTA sweeps in lockstep (their levels merged, so one level step
+ * serves all of them): 1..8, or 0 for the largest that fits shared memory;
+ * a request that does not fit is reduced.  It changes speed, not results.  The batch reads the contexts'
  * device state and does not own them: keep every context alive, and leave its
  * low-rank term unchanged, while the batch exists (a batch call on a context
  * whose low-rank term was replaced returns PSLR_ERR_STATE).  Systems with
@@ -282,7 +287,8 @@ typedef struct {
  * on failure, and pslr_batch_last_error(NULL) gives the message of the last
  * failed pslr_batch_create of the calling thread.
  */
-pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nrhs, pslr_batch **out);
+pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nrhs, int32_t group,
+                              pslr_batch **out);
 
 /* z = M_k^{-1} b for every system k and right-hand side (Algorithm 3), one
  * launch.  b_dev, z_dev: batched device vectors of n_total doubles

@@ -163,66 +163,89 @@ __device__ __forceinline__ bool on(const BatchParams<T, IO> &P, int k) {
     return P.active == nullptr || __ldg(P.active + k) != 0;
 }
 
+// One item of a group: its subdomain's ranges in the system and in the
+// group's shared-memory vectors.
+struct ItemRange {
+    int i, io, np, go, nq, xo, lo;  // subdomain; interior start/length; interface start/length; group offsets
+};
+
+template <class T>
+__device__ __forceinline__ ItemRange item_range(const BatchSys<T> &S, const BatchGroup &g, int t) {
+    ItemRange it;
+    it.i = g.sub[t];
+    it.io = S.ioff[it.i];
+    it.np = S.ioff[it.i + 1] - it.io;
+    it.go = S.goff[it.i];
+    it.nq = S.goff[it.i + 1] - it.go;
+    it.xo = g.xo[t];
+    it.lo = g.go[t];
+    return it;
+}
+
 template <class T, class VT, class IO>
 __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const BatchParams<T, IO> P) {
     extern __shared__ __align__(128) char smem[];
     if (P.skip != nullptr && ld_volatile(P.skip) != 0) return;
     if (ld_volatile(P.err) != 0) return;
     const int nr = P.nrhs;
-    const int xs = P.max_p + 1, gs = P.max_q + 1;  // per-rhs strides of the local vectors
+    const int xs = P.xs, gs = P.gs;  // per-rhs strides of the group vectors
     const SmemLayout L = smem_layout(P.slot_bytes, P.ring, nr * xs - 1, nr * gs - 1, sizeof(T), false);
     Cta<T> c;
     if (!cta_start(c, smem, L, P.ring, P.slot_bytes, P.stream, P.stream_off, P.segbase, P.active)) return;
     const int tid = threadIdx.x;
-    const int ib = P.item_off[blockIdx.x], ie = P.item_off[blockIdx.x + 1];
+    const int gb = P.group_off[blockIdx.x], ge = P.group_off[blockIdx.x + 1];
     T *const dsh = c.red + (kConsumers / 32) * kMaxRank + kMaxRank;  // where lowrank_coeffs leaves d
     bool ok = true;
 
     // ---- phase 0: u = B^{-1} f, t = g - F u (Algorithm 3, step 2); a system
     // without a low-rank term also takes w_0 = C0^{-1} t here.
-    for (int it = ib; it < ie; ++it) {
-        if (!on(P, P.items[2 * it])) continue;
-        const BatchSys<T> &S = P.sys[P.items[2 * it]];
-        const int i = P.items[2 * it + 1];
-        const Counts k = counts_of(S.cnt, i);
-        const int io = S.ioff[i], np_ = S.ioff[i + 1] - io;
-        const int go = S.goff[i], nq = S.goff[i + 1] - go;
+    for (int gi = gb; gi < ge; ++gi) {
+        const BatchGroup &g = P.groups[gi];
+        if (!on(P, g.sys)) continue;
+        const BatchSys<T> &S = P.sys[g.sys];
         const IO *bs = P.b + S.voff;
-        for (int kr = 0; kr < nr; ++kr) {
-            const IO *bk = bs + (int64_t)kr * S.n;
-            for (int j = tid; j < np_; j += kConsumers) c.xi[kr * xs + j] = T(bk[S.perm[io + j]]);
-            for (int j = tid; j < nq; j += kConsumers) c.si[kr * gs + j] = T(bk[S.perm[S.p + go + j]]);
-            if (tid == 0) {
-                c.xi[kr * xs + np_] = T(0);
-                c.si[kr * gs + nq] = T(0);
+        for (int t = 0; t < g.n; ++t) {
+            const ItemRange it = item_range(S, g, t);
+            for (int kr = 0; kr < nr; ++kr) {
+                const IO *bk = bs + (int64_t)kr * S.n;
+                T *x = c.xi + kr * xs + it.xo, *y = c.si + kr * gs + it.lo;
+                for (int j = tid; j < it.np; j += kConsumers) x[j] = T(bk[S.perm[it.io + j]]);
+                for (int j = tid; j < it.nq; j += kConsumers) y[j] = T(bk[S.perm[S.p + it.go + j]]);
+                if (tid == 0) {
+                    x[it.np] = T(0);
+                    y[it.nq] = T(0);
+                }
             }
         }
         csync();
-        tri_sweep_multi(c, c.xi, xs, nr, k.n[kB1], P.err);
-        tri_sweep_multi(c, c.xi, xs, nr, k.n[kB2], P.err);
-        ell_op_multi<T, false>(c, c.si, gs, c.xi, xs, nr, true, k.n[kF], P.err);
-        if (S.r > 0) {
-            const VT *V = reinterpret_cast<const VT *>(S.V);
+        tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB1], P.err);
+        tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB2], P.err);
+        ell_op_multi<T, false>(c, c.si, gs, c.xi, xs, nr, true, g.cnt[kF], P.err);
+        if (S.r == 0) {
+            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC1], P.err);
+            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC2], P.err);
+        }
+        const VT *V = reinterpret_cast<const VT *>(S.V);
+        for (int t = 0; t < g.n; ++t) {
+            const ItemRange it = item_range(S, g, t);
             for (int kr = 0; kr < nr; ++kr) {
-                lowrank_partial(c, V, S.q, S.r, go, nq, c.si + kr * gs,
-                                S.part + ((int64_t)kr * S.s + i) * S.r);
-                for (int j = tid; j < nq; j += kConsumers) S.acc[(int64_t)kr * (S.q + 1) + go + j] = c.si[kr * gs + j];
+                const T *y = c.si + kr * gs + it.lo;
+                if (S.r > 0)
+                    lowrank_partial(c, V, S.q, S.r, it.go, it.nq, y, S.part + ((int64_t)kr * S.s + it.i) * S.r);
+                T *acc = S.acc + (int64_t)kr * (S.q + 1) + it.go;
+                T *w0 = S.wbuf + (int64_t)kr * 2 * (S.q + 1) + it.go;
+                for (int j = tid; j < it.nq; j += kConsumers) {
+                    acc[j] = y[j];
+                    if (S.r == 0) w0[j] = y[j];
+                }
             }
-        } else {
-            tri_sweep_multi(c, c.si, gs, nr, k.n[kC1], P.err);
-            tri_sweep_multi(c, c.si, gs, nr, k.n[kC2], P.err);
-            for (int kr = 0; kr < nr; ++kr)
-                for (int j = tid; j < nq; j += kConsumers) {
-                    S.wbuf[(int64_t)kr * 2 * (S.q + 1) + go + j] = c.si[kr * gs + j];
-                    S.acc[(int64_t)kr * (S.q + 1) + go + j] = c.si[kr * gs + j];
+            if (it.i == 0 && tid == 0)  // zero slots of the system's series iterates
+                for (int kr = 0; kr < nr; ++kr) {
+                    S.wbuf[(int64_t)kr * 2 * (S.q + 1) + S.q] = T(0);
+                    S.wbuf[(int64_t)kr * 2 * (S.q + 1) + (S.q + 1) + S.q] = T(0);
                 }
         }
         csync();
-        if (i == 0 && tid == 0)  // zero slots of the system's series iterates
-            for (int kr = 0; kr < nr; ++kr) {
-                S.wbuf[(int64_t)kr * 2 * (S.q + 1) + S.q] = T(0);
-                S.wbuf[(int64_t)kr * 2 * (S.q + 1) + (S.q + 1) + S.q] = T(0);
-            }
     }
 
     // ---- phase 1: d = G V^T t per (system, rhs); t <- t + V d; w_0 = C0^{-1} t (steps 3-4)
@@ -241,28 +264,38 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
         grid_arrive(c, P.bar, P.grid);
         ok = grid_wait(c, P.bar, P.err, P.wait_limit);
         if (!ok) goto abort;
-        for (int it = ib; it < ie; ++it) {
-            if (!on(P, P.items[2 * it])) continue;
-            const BatchSys<T> &S = P.sys[P.items[2 * it]];
+        for (int gi = gb; gi < ge; ++gi) {
+            const BatchGroup &g = P.groups[gi];
+            if (!on(P, g.sys)) continue;
+            const BatchSys<T> &S = P.sys[g.sys];
             if (S.r == 0) continue;
-            const int i = P.items[2 * it + 1];
-            const Counts k = counts_of(S.cnt, i);
-            const int go = S.goff[i], nq = S.goff[i + 1] - go;
             const VT *V = reinterpret_cast<const VT *>(S.V);
             for (int kr = 0; kr < nr; ++kr) {
-                for (int j = tid; j < nq; j += kConsumers) c.si[kr * gs + j] = __ldcg(S.acc + (int64_t)kr * (S.q + 1) + go + j);
                 for (int j = tid; j < S.r; j += kConsumers) dsh[j] = __ldcg(S.dco + (int64_t)kr * S.r + j);
-                if (tid == 0) c.si[kr * gs + nq] = T(0);
-                csync();
-                lowrank_update(c, V, S.q, S.r, go, nq, c.si + kr * gs);
-            }
-            tri_sweep_multi(c, c.si, gs, nr, k.n[kC1], P.err);
-            tri_sweep_multi(c, c.si, gs, nr, k.n[kC2], P.err);
-            for (int kr = 0; kr < nr; ++kr)
-                for (int j = tid; j < nq; j += kConsumers) {
-                    S.wbuf[(int64_t)kr * 2 * (S.q + 1) + go + j] = c.si[kr * gs + j];
-                    S.acc[(int64_t)kr * (S.q + 1) + go + j] = c.si[kr * gs + j];
+                for (int t = 0; t < g.n; ++t) {
+                    const ItemRange it = item_range(S, g, t);
+                    T *y = c.si + kr * gs + it.lo;
+                    const T *acc = S.acc + (int64_t)kr * (S.q + 1) + it.go;
+                    for (int j = tid; j < it.nq; j += kConsumers) y[j] = __ldcg(acc + j);
+                    if (tid == 0) y[it.nq] = T(0);
+                    csync();
+                    lowrank_update(c, V, S.q, S.r, it.go, it.nq, y);
                 }
+            }
+            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC1], P.err);
+            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC2], P.err);
+            for (int t = 0; t < g.n; ++t) {
+                const ItemRange it = item_range(S, g, t);
+                for (int kr = 0; kr < nr; ++kr) {
+                    const T *y = c.si + kr * gs + it.lo;
+                    T *acc = S.acc + (int64_t)kr * (S.q + 1) + it.go;
+                    T *w0 = S.wbuf + (int64_t)kr * 2 * (S.q + 1) + it.go;
+                    for (int j = tid; j < it.nq; j += kConsumers) {
+                        w0[j] = y[j];
+                        acc[j] = y[j];
+                    }
+                }
+            }
             csync();
         }
     }
@@ -272,42 +305,51 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
     for (int kk = 1; kk <= P.max_m; ++kk) {
         grid_arrive(c, P.bar, P.grid);
         bool waited = false;
-        for (int it = ib; it < ie; ++it) {
-            if (!on(P, P.items[2 * it])) continue;
-            const BatchSys<T> &S = P.sys[P.items[2 * it]];
+        for (int gi = gb; gi < ge; ++gi) {
+            const BatchGroup &g = P.groups[gi];
+            if (!on(P, g.sys)) continue;
+            const BatchSys<T> &S = P.sys[g.sys];
             if (S.m < kk) continue;
-            const int i = P.items[2 * it + 1];
-            const Counts k = counts_of(S.cnt, i);
-            const int np_ = S.ioff[i + 1] - S.ioff[i];
-            const int go = S.goff[i], nq = S.goff[i + 1] - go;
             const int64_t wst = 2 * (int64_t)(S.q + 1);
             const T *wprev = S.wbuf + ((kk - 1) & 1) * (S.q + 1);
             T *wnext = S.wbuf + (kk & 1) * (S.q + 1);
+            const int nx = g.xo[g.n], ng = g.go[g.n];
             for (int kr = 0; kr < nr; ++kr) {
-                for (int j = tid; j < nq; j += kConsumers) c.wi[kr * gs + j] = __ldcg(wprev + kr * wst + go + j);
-                if (tid == 0) c.wi[kr * gs + nq] = T(0);
-                fill(c.xi + kr * xs, np_ + 1, T(0));
-                fill(c.si + kr * gs, nq + 1, T(0));
+                fill(c.xi + kr * xs, nx, T(0));
+                fill(c.si + kr * gs, ng, T(0));
+                for (int t = 0; t < g.n; ++t) {
+                    const ItemRange it = item_range(S, g, t);
+                    T *w = c.wi + kr * gs + it.lo;
+                    const T *src = wprev + kr * wst + it.go;
+                    for (int j = tid; j < it.nq; j += kConsumers) w[j] = __ldcg(src + j);
+                    if (tid == 0) w[it.nq] = T(0);
+                }
             }
             csync();
-            ell_op_multi<T, false>(c, c.xi, xs, c.wi, gs, nr, false, k.n[kE], P.err);   // E w
-            tri_sweep_multi(c, c.xi, xs, nr, k.n[kB1], P.err);                         // B^{-1}
-            tri_sweep_multi(c, c.xi, xs, nr, k.n[kB2], P.err);
-            ell_op_multi<T, false>(c, c.si, gs, c.xi, xs, nr, false, k.n[kF], P.err);   // F
+            ell_op_multi<T, false>(c, c.xi, xs, c.wi, gs, nr, false, g.cnt[kE], P.err);   // E w
+            tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB1], P.err);                         // B^{-1}
+            tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB2], P.err);
+            ell_op_multi<T, false>(c, c.si, gs, c.xi, xs, nr, false, g.cnt[kF], P.err);   // F
             if (!waited) {
                 ok = grid_wait(c, P.bar, P.err, P.wait_limit);
                 waited = true;
                 if (!ok) goto abort;
             }
-            ell_op_multi<T, true>(c, c.si, gs, wprev, (int)wst, nr, true, k.n[kCg], P.err);  // - C_g w
-            tri_sweep_multi(c, c.si, gs, nr, k.n[kC1], P.err);                               // C0^{-1}
-            tri_sweep_multi(c, c.si, gs, nr, k.n[kC2], P.err);
-            for (int kr = 0; kr < nr; ++kr)
-                for (int j = tid; j < nq; j += kConsumers) {
-                    const int64_t a = (int64_t)kr * (S.q + 1) + go + j;
-                    wnext[kr * wst + go + j] = c.si[kr * gs + j];
-                    S.acc[a] = __ldcg(S.acc + a) + c.si[kr * gs + j];
+            ell_op_multi<T, true>(c, c.si, gs, wprev, (int)wst, nr, true, g.cnt[kCg], P.err);  // - C_g w
+            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC1], P.err);                               // C0^{-1}
+            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC2], P.err);
+            for (int t = 0; t < g.n; ++t) {
+                const ItemRange it = item_range(S, g, t);
+                for (int kr = 0; kr < nr; ++kr) {
+                    const T *y = c.si + kr * gs + it.lo;
+                    T *acc = S.acc + (int64_t)kr * (S.q + 1) + it.go;
+                    T *wn = wnext + kr * wst + it.go;
+                    for (int j = tid; j < it.nq; j += kConsumers) {
+                        wn[j] = y[j];
+                        acc[j] = __ldcg(acc + j) + y[j];
+                    }
                 }
+            }
             csync();
         }
         if (!waited) {  // a CTA with no work in this term still takes part in the barrier
@@ -317,32 +359,38 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
     }
 
     // ---- y = acc; x = B^{-1}(f - E y); scatter (steps 5-6)
-    for (int it = ib; it < ie; ++it) {
-        if (!on(P, P.items[2 * it])) continue;
-        const BatchSys<T> &S = P.sys[P.items[2 * it]];
-        const int i = P.items[2 * it + 1];
-        const Counts k = counts_of(S.cnt, i);
-        const int io = S.ioff[i], np_ = S.ioff[i + 1] - io;
-        const int go = S.goff[i], nq = S.goff[i + 1] - go;
+    for (int gi = gb; gi < ge; ++gi) {
+        const BatchGroup &g = P.groups[gi];
+        if (!on(P, g.sys)) continue;
+        const BatchSys<T> &S = P.sys[g.sys];
         const IO *bs = P.b + S.voff;
-        for (int kr = 0; kr < nr; ++kr) {
-            const IO *bk = bs + (int64_t)kr * S.n;
-            for (int j = tid; j < nq; j += kConsumers) c.wi[kr * gs + j] = __ldcg(S.acc + (int64_t)kr * (S.q + 1) + go + j);
-            for (int j = tid; j < np_; j += kConsumers) c.xi[kr * xs + j] = T(bk[S.perm[io + j]]);
-            if (tid == 0) {
-                c.wi[kr * gs + nq] = T(0);
-                c.xi[kr * xs + np_] = T(0);
+        for (int t = 0; t < g.n; ++t) {
+            const ItemRange it = item_range(S, g, t);
+            for (int kr = 0; kr < nr; ++kr) {
+                const IO *bk = bs + (int64_t)kr * S.n;
+                T *x = c.xi + kr * xs + it.xo, *w = c.wi + kr * gs + it.lo;
+                const T *acc = S.acc + (int64_t)kr * (S.q + 1) + it.go;
+                for (int j = tid; j < it.nq; j += kConsumers) w[j] = __ldcg(acc + j);
+                for (int j = tid; j < it.np; j += kConsumers) x[j] = T(bk[S.perm[it.io + j]]);
+                if (tid == 0) {
+                    w[it.nq] = T(0);
+                    x[it.np] = T(0);
+                }
             }
         }
         csync();
-        ell_op_multi<T, false>(c, c.xi, xs, c.wi, gs, nr, true, k.n[kE], P.err);
-        tri_sweep_multi(c, c.xi, xs, nr, k.n[kB1], P.err);
-        tri_sweep_multi(c, c.xi, xs, nr, k.n[kB2], P.err);
+        ell_op_multi<T, false>(c, c.xi, xs, c.wi, gs, nr, true, g.cnt[kE], P.err);
+        tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB1], P.err);
+        tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB2], P.err);
         IO *zs = P.z + S.voff;
-        for (int kr = 0; kr < nr; ++kr) {
-            IO *zk = zs + (int64_t)kr * S.n;
-            for (int j = tid; j < np_; j += kConsumers) zk[S.perm[io + j]] = IO(c.xi[kr * xs + j]);
-            for (int j = tid; j < nq; j += kConsumers) zk[S.perm[S.p + go + j]] = IO(c.wi[kr * gs + j]);
+        for (int t = 0; t < g.n; ++t) {
+            const ItemRange it = item_range(S, g, t);
+            for (int kr = 0; kr < nr; ++kr) {
+                IO *zk = zs + (int64_t)kr * S.n;
+                const T *x = c.xi + kr * xs + it.xo, *w = c.wi + kr * gs + it.lo;
+                for (int j = tid; j < it.np; j += kConsumers) zk[S.perm[it.io + j]] = IO(x[j]);
+                for (int j = tid; j < it.nq; j += kConsumers) zk[S.perm[S.p + it.go + j]] = IO(w[j]);
+            }
         }
         csync();
     }

@@ -50,11 +50,16 @@ struct pslr_batch {
     std::vector<SysExport> sx;
     std::vector<int64_t> voff;
     int max_p = 0, max_q = 0, max_m = 0, any_lr = 0, items = 0, grid = 0;
-    const char *segbase[2] = {nullptr, nullptr};
+    int group_req = 0;                         // requested items per group (0: largest that fits)
+    int group[2] = {0, 0}, ngroups[2] = {0, 0};  // items per group and groups, [FP64, FP32]
+    int xs[2] = {0, 0}, gs[2] = {0, 0};        // group vector strides
     int ring[2] = {0, 0}, slot_bytes[2] = {0, 0}, smem[2] = {0, 0};
     int64_t apply_bytes[2] = {0, 0};
-    // device: assignment, streams, per-system parameters and scratch
-    int32_t *d_items = nullptr, *d_item_off = nullptr, *d_pairs = nullptr, *d_pair_off = nullptr;
+    // device: merged segments, groups, assignment, streams, per-system parameters and scratch
+    char *d_seg[2] = {nullptr, nullptr};
+    BatchGroup *d_groups[2] = {nullptr, nullptr};
+    int32_t *d_group_off[2] = {nullptr, nullptr};
+    int32_t *d_pairs = nullptr, *d_pair_off = nullptr;
     StreamEnt *d_stream[2] = {nullptr, nullptr};
     int64_t *d_stream_off[2] = {nullptr, nullptr};
     void *d_sys[2] = {nullptr, nullptr};  // BatchSys<double>[nsys], BatchSys<float>[nsys]
@@ -121,8 +126,11 @@ void free_krylov(pslr_batch *bt) {
 
 void free_batch(pslr_batch *bt) {
     free_krylov(bt);
-    dfree(bt->d_items); dfree(bt->d_item_off); dfree(bt->d_pairs); dfree(bt->d_pair_off);
+    dfree(bt->d_pairs); dfree(bt->d_pair_off);
     for (int p = 0; p < 2; ++p) {
+        dfree(bt->d_seg[p]);
+        dfree(bt->d_groups[p]);
+        dfree(bt->d_group_off[p]);
         dfree(bt->d_stream[p]);
         dfree(bt->d_stream_off[p]);
         dfree(bt->d_sys[p]);
@@ -132,33 +140,265 @@ void free_batch(pslr_batch *bt) {
     if (bt->cap) cudaStreamDestroy(bt->cap);
 }
 
-// Segments of one category of one item.
-int nseg(const pslr_batch *bt, int k, int i, int cat, int prec) {
-    std::vector<StreamEnt> tmp;
-    sys_segments(bt->ctx[k], prec, i, cat, 0, tmp);
-    return (int)tmp.size();
+// ------------------------------------------------- merged segments of a group
+
+// Host record of one merged segment.
+struct SegDesc {
+    int64_t off;
+    int32_t bytes;
+};
+
+// One row of a parsed segment: output row, entries (padding included) and
+// the value of the record's last slot (1/diagonal, or 1).
+template <class T>
+struct PRow {
+    int32_t row;
+    int32_t zero;  // the zero slot this row's padding entries point at
+    std::vector<int32_t> col;
+    std::vector<T> val;
+    T dinv;
+};
+
+// Append the rows of one packed segment (layout of pslr_internal.h) to out,
+// with row indices shifted by rs, local column indices by cs (global columns
+// are kept), and padding pointed at zero.
+template <class T, class IDX>
+void parse_segment(const char *seg, int rs, int cs, int zero, std::vector<PRow<T>> &out, bool *diag) {
+    SegHdr h;
+    std::memcpy(&h, seg, sizeof(h));
+    *diag = (h.flags & kSegDiag) != 0;
+    const bool global = (h.flags & kSegGlobalCols) != 0;
+    const int n = h.n, np = h.np;
+    const char *p = seg + sizeof(SegHdr);
+    auto col_of = [&](IDX c) { return global ? (int32_t)c : (int32_t)c + cs; };
+    if (h.fmt != kTile) {
+        const int K = h.fmt;
+        const IDX *idx = reinterpret_cast<const IDX *>(p);
+        const T *val = reinterpret_cast<const T *>(p + (size_t)np * rec_idx_bytes<IDX>(K));
+        for (int j = 0; j < n; ++j) {
+            PRow<T> r;
+            r.row = (int32_t)idx[(size_t)j * (K + 1)] + rs;
+            r.zero = zero;
+            for (int k = 0; k < K; ++k) {
+                r.col.push_back(col_of(idx[(size_t)j * (K + 1) + 1 + k]));
+                r.val.push_back(val[(size_t)j * (K + 1) + k]);
+            }
+            r.dinv = val[(size_t)j * (K + 1) + K];
+            out.push_back(std::move(r));
+        }
+        return;
+    }
+    const int w = h.w;
+    const T *vals = reinterpret_cast<const T *>(p);
+    const T *dinv = reinterpret_cast<const T *>(p + (size_t)np * w * sizeof(T));
+    const IDX *cols = reinterpret_cast<const IDX *>(p + (size_t)np * w * sizeof(T) + (*diag ? np * sizeof(T) : 0));
+    const uint16_t *rws = reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(cols) +
+                                                             (size_t)np * w * sizeof(IDX));
+    for (int j = 0; j < n; ++j) {
+        PRow<T> r;
+        r.row = (int32_t)rws[j] + rs;
+        r.zero = zero;
+        for (int k = 0; k < w; ++k) {
+            r.col.push_back(col_of(cols[(size_t)k * np + j]));
+            r.val.push_back(vals[(size_t)k * np + j]);
+        }
+        r.dinv = *diag ? dinv[j] : T(1);
+        out.push_back(std::move(r));
+    }
 }
 
-// Phase costs of an item, in level steps (one segment = one step) plus a
-// fixed charge for its gathers, scatters and low-rank reductions.  Phases:
-// 0, 1 (low rank), the series terms 1..max_m, final.
-std::vector<double> item_cost(const pslr_batch *bt, int k, int i) {
-    const SysExport &e = bt->sx[k];
+// Pack rows [b, e) as one segment (same encodings as the set-up's packer);
+// values are copied bit for bit.
+template <class T, class IDX>
+void pack_prows(std::vector<char> &bytes, std::vector<SegDesc> &desc, const std::vector<PRow<T>> &rows,
+                size_t b, size_t e, bool diag, bool global) {
+    const int n = (int)(e - b);
+    int w = 0;
+    for (size_t i = b; i < e; ++i) w = std::max<int>(w, (int)rows[i].col.size());
+    const int np = seg_npad(n);
+    const int64_t nbytes = seg_bytes<T, IDX>(n, w, diag);
+    SegDesc d;
+    d.off = (int64_t)bytes.size();
+    d.bytes = (int32_t)nbytes;
+    bytes.resize(bytes.size() + nbytes, 0);
+    char *base = bytes.data() + d.off;
+    SegHdr h;
+    std::memset(&h, 0, sizeof(h));
+    h.n = (uint16_t)n;
+    h.flags = (uint8_t)((diag ? (unsigned)kSegDiag : 0u) | (global ? (unsigned)kSegGlobalCols : 0u));
+    h.np = (uint16_t)np;
+    const int fmt = seg_fmt_for(w);
+    h.fmt = (uint8_t)fmt;
+    h.w = (uint8_t)(fmt != kTile ? fmt : w);
+    std::memcpy(base, &h, sizeof(h));
+    base += sizeof(SegHdr);
+    const int zero0 = rows[b].zero;
+    if (fmt != kTile) {
+        const int K = fmt;
+        IDX *idx = reinterpret_cast<IDX *>(base);
+        T *val = reinterpret_cast<T *>(base + (size_t)np * rec_idx_bytes<IDX>(K));
+        for (int j = 0; j < np; ++j) {
+            const PRow<T> *R = j < n ? &rows[b + j] : nullptr;
+            IDX *ir = idx + (size_t)j * (K + 1);
+            T *vr = val + (size_t)j * (K + 1);
+            ir[0] = R ? (IDX)R->row : (IDX)0;
+            for (int k = 0; k < K; ++k) {
+                const bool has = R && k < (int)R->col.size();
+                ir[1 + k] = has ? (IDX)R->col[k] : (IDX)(R ? R->zero : zero0);
+                vr[k] = has ? R->val[k] : T(0);
+            }
+            vr[K] = R ? R->dinv : T(1);
+        }
+    } else {
+        T *vals = reinterpret_cast<T *>(base);
+        T *dinv = reinterpret_cast<T *>(base + (size_t)np * w * sizeof(T));
+        IDX *cols = reinterpret_cast<IDX *>(base + (size_t)np * w * sizeof(T) + (diag ? np * sizeof(T) : 0));
+        uint16_t *rws = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(cols) + (size_t)np * w * sizeof(IDX));
+        for (int j = 0; j < np; ++j) {
+            const PRow<T> *R = j < n ? &rows[b + j] : nullptr;
+            for (int k = 0; k < w; ++k) {
+                const bool has = R && k < (int)R->col.size();
+                vals[(size_t)k * np + j] = has ? R->val[k] : T(0);
+                cols[(size_t)k * np + j] = has ? (IDX)R->col[k] : (IDX)(R ? R->zero : zero0);
+            }
+            if (diag) dinv[j] = R ? R->dinv : T(0);
+            rws[j] = R ? (uint16_t)R->row : (uint16_t)0;
+        }
+    }
+    desc.push_back(d);
+}
+
+// Rows into segments of at most kSegMaxRows rows and kSegBudget bytes.
+template <class T, class IDX>
+int pack_prow_list(std::vector<char> &bytes, std::vector<SegDesc> &desc, const std::vector<PRow<T>> &rows,
+                   bool diag, bool global) {
+    int cnt = 0;
+    size_t b = 0;
+    while (b < rows.size()) {
+        size_t e = b;
+        int w = 0;
+        while (e < rows.size() && (int)(e - b) < kSegMaxRows) {
+            const int w2 = std::max<int>(w, (int)rows[e].col.size());
+            if (e > b && seg_bytes<T, IDX>((int)(e - b + 1), w2, diag) > kSegBudget) break;
+            w = w2;
+            ++e;
+        }
+        pack_prows<T, IDX>(bytes, desc, rows, b, e, diag, global);
+        ++cnt;
+        b = e;
+    }
+    return cnt;
+}
+
+// Host copies of every system's forward segments of one precision.
+pslr_status download_segments(pslr_batch *bt, int prec, std::vector<std::vector<char>> &host) {
+    host.resize(bt->nsys);
+    for (int k = 0; k < bt->nsys; ++k) {
+        host[k].resize((size_t)bt->sx[k].seg_bytes[prec]);
+        if (!host[k].empty())
+            BCK(cudaMemcpy(host[k].data(), bt->sx[k].seg[prec], host[k].size(), cudaMemcpyDeviceToHost));
+    }
+    return PSLR_OK;
+}
+
+// The merged segments of one group, category by category (kE .. kC2): level
+// j of a sweep holds segment j of every item (items are independent, so any
+// rows of one merged level may run together); the products take all rows of
+// all items.  Returns the merged counts in g.cnt.
+template <class T>
+void merge_group(const pslr_batch *bt, int prec, const std::vector<char> &host, BatchGroup &g,
+                 std::vector<char> &bytes, std::vector<SegDesc> &desc) {
+    const SysExport &e = bt->sx[g.sys];
+    for (int cat = 0; cat < kNCnt; ++cat) {
+        const bool interior_rows = cat == kE || cat == kB1 || cat == kB2;
+        const bool global = cat == kCg;
+        std::vector<std::vector<StreamEnt>> segs(g.n);
+        size_t nmax = 0;
+        for (int t = 0; t < g.n; ++t) {
+            sys_segments(bt->ctx[g.sys], prec, g.sub[t], cat, 0, segs[t]);
+            nmax = std::max(nmax, segs[t].size());
+        }
+        const bool sweep = cat >= kB1;
+        int cnt = 0;
+        std::vector<PRow<T>> rows;
+        bool diag = false;
+        auto flush = [&]() {
+            if (rows.empty()) return;
+            cnt += global ? pack_prow_list<T, int32_t>(bytes, desc, rows, diag, true)
+                          : pack_prow_list<T, uint16_t>(bytes, desc, rows, diag, false);
+            rows.clear();
+        };
+        for (size_t j = 0; j < nmax; ++j) {
+            for (int t = 0; t < g.n; ++t) {
+                if (j >= segs[t].size()) continue;
+                const int i = g.sub[t];
+                const int p = bt->sx[g.sys].ioff_h[i + 1] - bt->sx[g.sys].ioff_h[i];
+                const int q = bt->sx[g.sys].goff_h[i + 1] - bt->sx[g.sys].goff_h[i];
+                // rows: interior (E, B) or interface (F, C_g, C0); columns: interior (B, F),
+                // interface (E, C0) or global (C_g)
+                const int rs = interior_rows ? g.xo[t] : g.go[t];
+                const bool col_interior = cat == kF || cat == kB1 || cat == kB2;
+                const int cs = col_interior ? g.xo[t] : g.go[t];
+                const int zero = global ? e.q : (col_interior ? g.xo[t] + p : g.go[t] + q);
+                const char *seg = host.data() + segs[t][j].off;
+                if (global) parse_segment<T, int32_t>(seg, rs, cs, zero, rows, &diag);
+                else parse_segment<T, uint16_t>(seg, rs, cs, zero, rows, &diag);
+            }
+            if (sweep) flush();  // one merged level per item segment index
+        }
+        flush();
+        g.cnt[cat] = cnt;
+    }
+}
+
+// Phase costs of a group in level steps (one merged segment = one step),
+// plus a charge for gathers, scatters and low-rank reductions per item.
+// Phases: 0, 1 (low rank), the series terms 1..max_m, final.
+std::vector<double> group_cost(const pslr_batch *bt, const BatchGroup &g) {
+    const SysExport &e = bt->sx[g.sys];
     const int nph = 3 + bt->max_m;
     std::vector<double> c(nph, 0.0);
-    int n[kNCnt];
-    for (int t = 0; t < kNCnt; ++t) n[t] = nseg(bt, k, i, t, 1);
-    const double nr = bt->nrhs;
-    c[0] = n[kB1] + n[kB2] + n[kF] + 8 + (e.r > 0 ? nr * (2 + e.r / 8.0) : n[kC1] + n[kC2]);
-    if (e.r > 0) c[1] = n[kC1] + n[kC2] + nr * (2 + e.r / 8.0);
-    for (int kk = 1; kk <= e.m; ++kk) c[1 + kk] = n[kE] + n[kB1] + n[kB2] + n[kF] + n[kCg] + n[kC1] + n[kC2] + 4;
-    c[nph - 1] = n[kE] + n[kB1] + n[kB2] + 8;
+    const int *n = g.cnt;
+    const double nr = bt->nrhs, per = g.n * 2.0;
+    c[0] = n[kB1] + n[kB2] + n[kF] + 4 * per + (e.r > 0 ? per * nr * (1 + e.r / 8.0) : n[kC1] + n[kC2]);
+    if (e.r > 0) c[1] = n[kC1] + n[kC2] + per * nr * (1 + e.r / 16.0);
+    for (int kk = 1; kk <= e.m; ++kk) c[1 + kk] = n[kE] + n[kB1] + n[kB2] + n[kF] + n[kCg] + n[kC1] + n[kC2] + 2 * per;
+    c[nph - 1] = n[kE] + n[kB1] + n[kB2] + 4 * per;
     return c;
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ create
+
+// Groups of up to G consecutive subdomains per system, sizes balanced within
+// the system; returns the largest group vector lengths through xs, gs.
+static std::vector<BatchGroup> form_groups(const pslr_batch *bt, int G, int *xs, int *gs) {
+    std::vector<BatchGroup> out;
+    *xs = *gs = 1;
+    for (int k = 0; k < bt->nsys; ++k) {
+        const SysExport &e = bt->sx[k];
+        const int ng = (e.s + G - 1) / G;
+        for (int a = 0; a < ng; ++a) {
+            const int i0 = (int)((int64_t)e.s * a / ng), i1 = (int)((int64_t)e.s * (a + 1) / ng);
+            BatchGroup g;
+            std::memset(&g, 0, sizeof(g));
+            g.sys = k;
+            g.n = i1 - i0;
+            g.xo[0] = g.go[0] = 0;
+            for (int t = 0; t < g.n; ++t) {
+                const int i = i0 + t;
+                g.sub[t] = i;
+                g.xo[t + 1] = g.xo[t] + (e.ioff_h[i + 1] - e.ioff_h[i]) + 1;
+                g.go[t + 1] = g.go[t] + (e.goff_h[i + 1] - e.goff_h[i]) + 1;
+            }
+            *xs = std::max(*xs, g.xo[g.n]);
+            *gs = std::max(*gs, g.go[g.n]);
+            out.push_back(g);
+        }
+    }
+    return out;
+}
 
 static pslr_status batch_build(pslr_batch *bt) {
     const int nsys = bt->nsys, nr = bt->nrhs;
@@ -177,131 +417,138 @@ static pslr_status batch_build(pslr_batch *bt) {
     }
     bt->n_total = off;
     bt->nprob = nsys * nr;
-    // shared memory, ring depth and grid per precision (same layout rule as the kernel)
     int dev = 0, optin = 227 * 1024;
     BCK(cudaGetDevice(&dev));
     BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const int xs = bt->max_p + 1, gs = bt->max_q + 1;
+
+    // groups, merged segments and shared-memory layout per precision
+    std::vector<std::vector<BatchGroup>> groups(2);
+    std::vector<std::vector<char>> mbytes(2);
+    std::vector<std::vector<SegDesc>> mdesc(2);
+    std::vector<std::vector<int32_t>> gfirst(2);  // first merged descriptor of each group
     int grid = 1 << 30;
     for (int prec = 0; prec < 2; ++prec) {
         const int ts = prec == 0 ? 8 : 4;
-        int sb = 128;
-        for (int k = 0; k < nsys; ++k) sb = std::max(sb, bt->sx[k].slot_bytes[prec]);
-        bt->slot_bytes[prec] = sb;
-        const int avail = optin - 1024 - smem_fixed(nr * xs - 1, nr * gs - 1, ts, false);
-        bt->ring[prec] = std::min(kMaxRing, avail / sb);
-        if (bt->ring[prec] < 2)
+        int item_slot = 128;
+        for (int k = 0; k < nsys; ++k) item_slot = std::max(item_slot, bt->sx[k].slot_bytes[prec]);
+        // largest group size whose vectors and a 4-slot ring of merged segments fit
+        int G = bt->group_req > 0 ? std::min(bt->group_req, kMaxGroup) : kMaxGroup, xs = 1, gs = 1;
+        for (; G >= 1; --G) {
+            groups[prec] = form_groups(bt, G, &xs, &gs);
+            const int slot_est = std::min(kSegBudget, align_up(G * item_slot, 128));
+            const int need = 1024 + smem_fixed(nr * xs - 1, nr * gs - 1, ts, false) + 4 * slot_est;
+            if (need <= optin && xs < 65536 && gs < 65536) break;
+        }
+        if (G < 1)
             return bfail(bt, PSLR_ERR_TOO_LARGE,
                          "batch: %d right-hand sides of the largest subdomain (%d interior, %d interface "
                          "unknowns) do not fit one CTA's shared memory",
                          nr, bt->max_p, bt->max_q);
+        bt->group[prec] = G;
+        bt->xs[prec] = xs;
+        bt->gs[prec] = gs;
+        std::vector<std::vector<char>> host;
+        pslr_status st = download_segments(bt, prec, host);
+        if (st != PSLR_OK) return st;
+        for (BatchGroup &g : groups[prec]) {
+            gfirst[prec].push_back((int32_t)mdesc[prec].size());
+            if (prec == 0) merge_group<double>(bt, prec, host[g.sys], g, mbytes[prec], mdesc[prec]);
+            else merge_group<float>(bt, prec, host[g.sys], g, mbytes[prec], mdesc[prec]);
+        }
+        int sb = 128;
+        for (const SegDesc &d : mdesc[prec]) sb = std::max(sb, (int)d.bytes);
+        sb = align_up(sb, 128);
+        bt->slot_bytes[prec] = sb;
+        const int avail = optin - 1024 - smem_fixed(nr * xs - 1, nr * gs - 1, ts, false);
+        bt->ring[prec] = std::min(kMaxRing, avail / sb);
+        if (bt->ring[prec] < 2)
+            return bfail(bt, PSLR_ERR_TOO_LARGE, "batch: no room for the segment ring (%d-byte slots)", sb);
         bt->smem[prec] = smem_layout(sb, bt->ring[prec], nr * xs - 1, nr * gs - 1, ts, false).total;
         const int g = max_coresident_batch(bt->smem[prec], prec == 1);
         if (g < 1) return bfail(bt, PSLR_ERR_CUDA, "batch: the apply kernel cannot be made resident");
         grid = std::min(grid, g);
+        bt->ngroups[prec] = (int)groups[prec].size();
     }
-    grid = std::min(grid, bt->items);
+    grid = std::min(grid, std::max(bt->ngroups[0], bt->ngroups[1]));
     bt->grid = grid;
 
-    // item assignment: longest first onto the CTA that raises the sum of the
-    // per-phase maxima least (phases are separated by grid barriers)
-    struct Item {
-        int k, i;
-        std::vector<double> c;
-        double tot;
-    };
-    std::vector<Item> items;
-    for (int k = 0; k < nsys; ++k)
-        for (int i = 0; i < bt->sx[k].s; ++i) {
-            Item it{k, i, item_cost(bt, k, i), 0.0};
-            for (double v : it.c) it.tot += v;
-            items.push_back(std::move(it));
-        }
-    std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.tot > b.tot; });
+    // per precision: groups to CTAs (longest first onto the CTA that raises
+    // the sum of the per-phase maxima least: phases are separated by grid
+    // barriers, so each phase is balanced, not only the total), then streams
     const int nph = 3 + bt->max_m;
-    std::vector<std::vector<double>> load(grid, std::vector<double>(nph, 0.0));
-    std::vector<double> tot(grid, 0.0), mx(nph, 0.0);
-    std::vector<std::vector<std::pair<int, int>>> own(grid);
-    for (const Item &it : items) {
-        int best = 0;
-        double bd = 1e300, bt_ = 1e300;
-        for (int b = 0; b < grid; ++b) {
-            double d = 0.0;
-            for (int ph = 0; ph < nph; ++ph) d += std::max(0.0, load[b][ph] + it.c[ph] - mx[ph]);
-            if (d < bd || (d == bd && tot[b] < bt_)) {
-                bd = d;
-                bt_ = tot[b];
-                best = b;
-            }
-        }
-        for (int ph = 0; ph < nph; ++ph) {
-            load[best][ph] += it.c[ph];
-            mx[ph] = std::max(mx[ph], load[best][ph]);
-        }
-        tot[best] += it.tot;
-        own[best].push_back({it.k, it.i});
-    }
-    std::vector<int32_t> hitems, hoff(grid + 1, 0), hpairs, hpoff(grid + 1, 0);
-    for (int b = 0; b < grid; ++b) {
-        hoff[b] = (int32_t)(hitems.size() / 2);
-        for (auto &ki : own[b]) {
-            hitems.push_back(ki.first);
-            hitems.push_back(ki.second);
-        }
-    }
-    hoff[grid] = (int32_t)(hitems.size() / 2);
-    {   // low-rank (system, rhs) pairs, dealt round robin
-        std::vector<std::vector<int32_t>> pb(grid);
-        int t = 0;
-        for (int k = 0; k < nsys; ++k)
-            if (bt->sx[k].r > 0)
-                for (int j = 0; j < nr; ++j, ++t) {
-                    pb[t % grid].push_back(k);
-                    pb[t % grid].push_back(j);
-                }
-        for (int b = 0; b < grid; ++b) {
-            hpoff[b] = (int32_t)(hpairs.size() / 2);
-            hpairs.insert(hpairs.end(), pb[b].begin(), pb[b].end());
-        }
-        hpoff[grid] = (int32_t)(hpairs.size() / 2);
-    }
-    BCK(upload(&bt->d_items, hitems));
-    BCK(upload(&bt->d_item_off, hoff));
-    BCK(upload(&bt->d_pairs, hpairs));
-    BCK(upload(&bt->d_pair_off, hpoff));
-
-    // segment streams, in exactly the order the kernel's consumers take them
     for (int prec = 0; prec < 2; ++prec) {
-        const char *base = bt->sx[0].seg[prec];
-        for (int k = 1; k < nsys; ++k) base = std::min(base, bt->sx[k].seg[prec]);
-        bt->segbase[prec] = base;
+        std::vector<BatchGroup> &gl = groups[prec];
+        std::vector<int> order(gl.size());
+        std::vector<std::vector<double>> cost(gl.size());
+        std::vector<double> tot(gl.size(), 0.0);
+        for (size_t u = 0; u < gl.size(); ++u) {
+            order[u] = (int)u;
+            cost[u] = group_cost(bt, gl[u]);
+            for (double v : cost[u]) tot[u] += v;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tot[a] > tot[b]; });
+        std::vector<std::vector<double>> load(grid, std::vector<double>(nph, 0.0));
+        std::vector<double> ctot(grid, 0.0), mx(nph, 0.0);
+        std::vector<std::vector<int>> own(grid);
+        for (int u : order) {
+            int best = 0;
+            double bd = 1e300, bl = 1e300;
+            for (int b = 0; b < grid; ++b) {
+                double d = 0.0;
+                for (int ph = 0; ph < nph; ++ph) d += std::max(0.0, load[b][ph] + cost[u][ph] - mx[ph]);
+                if (d < bd || (d == bd && ctot[b] < bl)) {
+                    bd = d;
+                    bl = ctot[b];
+                    best = b;
+                }
+            }
+            for (int ph = 0; ph < nph; ++ph) {
+                load[best][ph] += cost[u][ph];
+                mx[ph] = std::max(mx[ph], load[best][ph]);
+            }
+            ctot[best] += tot[u];
+            own[best].push_back(u);
+        }
+        std::vector<BatchGroup> hg;
+        std::vector<int32_t> hoff(grid + 1, 0);
         std::vector<StreamEnt> ent;
         std::vector<int64_t> soff(grid + 1, 0);
-        auto add = [&](int k, int i, std::initializer_list<int> cats) {
-            const int64_t shift = bt->sx[k].seg[prec] - base;
-            const size_t first = ent.size();
-            for (int cat : cats) sys_segments(bt->ctx[k], prec, i, cat, shift, ent);
-            for (size_t t = first; t < ent.size(); ++t) ent[t].pad = k;  // the producer skips by system
+        auto add = [&](int u, std::initializer_list<int> cats) {
+            const BatchGroup &g = gl[u];
+            for (int cat : cats) {
+                int d = gfirst[prec][u];
+                for (int k = 0; k < cat; ++k) d += g.cnt[k];
+                for (int t = 0; t < g.cnt[cat]; ++t) {
+                    StreamEnt e;
+                    e.off = mdesc[prec][d + t].off;
+                    e.bytes = mdesc[prec][d + t].bytes;
+                    e.pad = g.sys;  // the producer skips by system
+                    ent.push_back(e);
+                }
+            }
         };
         for (int b = 0; b < grid; ++b) {
+            hoff[b] = (int32_t)hg.size();
+            for (int u : own[b]) hg.push_back(gl[u]);
             soff[b] = (int64_t)ent.size();
-            for (auto &ki : own[b]) {
-                add(ki.first, ki.second, {kB1, kB2, kF});
-                if (bt->sx[ki.first].r == 0) add(ki.first, ki.second, {kC1, kC2});
+            for (int u : own[b]) {
+                add(u, {kB1, kB2, kF});
+                if (bt->sx[gl[u].sys].r == 0) add(u, {kC1, kC2});
             }
             if (bt->any_lr)
-                for (auto &ki : own[b])
-                    if (bt->sx[ki.first].r > 0) add(ki.first, ki.second, {kC1, kC2});
+                for (int u : own[b])
+                    if (bt->sx[gl[u].sys].r > 0) add(u, {kC1, kC2});
             for (int kk = 1; kk <= bt->max_m; ++kk)
-                for (auto &ki : own[b])
-                    if (bt->sx[ki.first].m >= kk) add(ki.first, ki.second, {kE, kB1, kB2, kF, kCg, kC1, kC2});
-            for (auto &ki : own[b]) add(ki.first, ki.second, {kE, kB1, kB2});
+                for (int u : own[b])
+                    if (bt->sx[gl[u].sys].m >= kk) add(u, {kE, kB1, kB2, kF, kCg, kC1, kC2});
+            for (int u : own[b]) add(u, {kE, kB1, kB2});
         }
+        hoff[grid] = (int32_t)hg.size();
         soff[grid] = (int64_t)ent.size();
         int64_t seg_bytes = 0;
         for (const StreamEnt &e : ent) seg_bytes += e.bytes;
-        // algorithmic bytes: every segment once, V once per pass, and per
-        // right-hand side the vectors of the single-system count
+        // algorithmic bytes: every segment of the stream once, V once per pass,
+        // and per right-hand side the vectors of the single-system count
         const int64_t vs = prec == 0 ? 8 : 4, vb = prec == 0 ? 8 : 2;
         int64_t bytes = seg_bytes;
         for (int k = 0; k < nsys; ++k) {
@@ -314,10 +561,31 @@ static pslr_status batch_build(pslr_batch *bt) {
             bytes += vec * vs * nr;
         }
         bt->apply_bytes[prec] = bytes;
+        if (mbytes[prec].empty()) mbytes[prec].resize(16, 0);
+        BCK(upload(&bt->d_seg[prec], mbytes[prec]));
+        BCK(upload(&bt->d_groups[prec], hg));
+        BCK(upload(&bt->d_group_off[prec], hoff));
         BCK(upload(&bt->d_stream[prec], ent));
         BCK(upload(&bt->d_stream_off[prec], soff));
     }
-
+    {   // low-rank (system, rhs) pairs, dealt round robin
+        std::vector<std::vector<int32_t>> pb(grid);
+        std::vector<int32_t> hpairs, hpoff(grid + 1, 0);
+        int t = 0;
+        for (int k = 0; k < nsys; ++k)
+            if (bt->sx[k].r > 0)
+                for (int j = 0; j < nr; ++j, ++t) {
+                    pb[t % grid].push_back(k);
+                    pb[t % grid].push_back(j);
+                }
+        for (int b = 0; b < grid; ++b) {
+            hpoff[b] = (int32_t)(hpairs.size() / 2);
+            hpairs.insert(hpairs.end(), pb[b].begin(), pb[b].end());
+        }
+        hpoff[grid] = (int32_t)(hpairs.size() / 2);
+        BCK(upload(&bt->d_pairs, hpairs));
+        BCK(upload(&bt->d_pair_off, hpoff));
+    }
     // per-system scratch (sized in doubles; the FP32 form uses the front of each piece)
     std::vector<int64_t> so(nsys + 1, 0);
     auto al = [](int64_t x) { return (x + 31) / 32 * 32; };  // 256-byte pieces
@@ -339,7 +607,6 @@ static pslr_status batch_build(pslr_batch *bt) {
         double *d = pt + al((int64_t)nr * e.s * std::max(e.r, 1));
         auto fillsys = [&](auto &B, int prec, auto *tp) {
             using T = std::remove_pointer_t<decltype(tp)>;
-            B.cnt = e.cnt[prec];
             B.ioff = e.ioff;
             B.goff = e.goff;
             B.perm = e.perm;
@@ -424,17 +691,17 @@ static pslr_status batch_launch(pslr_batch *bt, int form, const void *b, void *z
                                 const int *active, cudaStream_t st) {
     const int prec = form == 0 ? 0 : 1;
     auto fill = [&](auto &P) {
-        P.segbase = bt->segbase[prec];
-        P.items = bt->d_items;
-        P.item_off = bt->d_item_off;
+        P.segbase = bt->d_seg[prec];
+        P.groups = bt->d_groups[prec];
+        P.group_off = bt->d_group_off[prec];
         P.pairs = bt->d_pairs;
         P.pair_off = bt->d_pair_off;
         P.stream = bt->d_stream[prec];
         P.stream_off = bt->d_stream_off[prec];
         P.ring = bt->ring[prec];
         P.slot_bytes = bt->slot_bytes[prec];
-        P.max_p = bt->max_p;
-        P.max_q = bt->max_q;
+        P.xs = bt->xs[prec];
+        P.gs = bt->gs[prec];
         P.max_m = bt->max_m;
         P.nrhs = bt->nrhs;
         P.grid = bt->grid;
@@ -576,11 +843,13 @@ static cudaGraphExec_t cycle_graph(pslr_batch *bt, int form) {
 
 extern "C" {
 
-pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nrhs, pslr_batch **out) {
+pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nrhs, int32_t group,
+                              pslr_batch **out) {
     pslr_batch *bt = nullptr;
     if (out) *out = nullptr;
-    if (!out || nsys < 1 || !systems || nrhs < 1 || nrhs > kMaxBatchRhs)
-        return bfail(nullptr, PSLR_ERR_ARG, "batch_create: bad argument (nsys >= 1, nrhs 1..%d)", kMaxBatchRhs);
+    if (!out || nsys < 1 || !systems || nrhs < 1 || nrhs > kMaxBatchRhs || group < 0 || group > kMaxGroup)
+        return bfail(nullptr, PSLR_ERR_ARG, "batch_create: bad argument (nsys >= 1, nrhs 1..%d, group 0..%d)",
+                     kMaxBatchRhs, kMaxGroup);
     std::vector<SysExport> sx(nsys);
     for (int k = 0; k < nsys; ++k) {
         if (!systems[k] || !sys_export(systems[k], &sx[k]))
@@ -594,6 +863,7 @@ pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nr
     bt = new pslr_batch();
     bt->nsys = nsys;
     bt->nrhs = nrhs;
+    bt->group_req = group;
     bt->ctx.assign(systems, systems + nsys);
     bt->sx = sx;
     pslr_status st = batch_build(bt);
@@ -698,6 +968,10 @@ pslr_status pslr_batch_get_info(const pslr_batch *bt, pslr_batch_info *info) {
     info->grid = bt->grid;
     info->ring[0] = bt->ring[0];
     info->ring[1] = bt->ring[1];
+    info->group[0] = bt->group[0];
+    info->group[1] = bt->group[1];
+    info->groups[0] = bt->ngroups[0];
+    info->groups[1] = bt->ngroups[1];
     info->max_m = bt->max_m;
     info->max_p = bt->max_p;
     info->max_q = bt->max_q;

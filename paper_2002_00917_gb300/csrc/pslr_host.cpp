@@ -1721,6 +1721,8 @@ bool sys_export(const pslr_ctx *c, SysExport *e) {
         e->seg_bytes[prec] = c->ops[0][prec].seg_total;
     }
     e->lr_gen = c->lr_gen;
+    e->ioff_h = c->ioff;
+    e->goff_h = c->goff;
     return true;
 }
 

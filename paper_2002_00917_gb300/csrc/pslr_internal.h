@@ -147,10 +147,23 @@ struct ErrParams {
 
 // Batched apply (pslr_batch.cu): per-system parameters and launch parameters.
 constexpr int kMaxBatchRhs = 4;             // right-hand sides per system in one batched launch
+constexpr int kMaxGroup = 8;                // subdomains of one system swept in lockstep by one CTA
+
+// A group: up to kMaxGroup subdomains of one system that one CTA sweeps in
+// lockstep.  Their local vectors are concatenated in shared memory (item t's
+// interior part at xo[t] .. xo[t] + p_i, its zero slot last; likewise the
+// interface part at go[t]), and the group's merged segments index those
+// concatenated vectors: merged level j holds level j of every item.
+struct BatchGroup {
+    int32_t sys, n;                 // system, items (1..kMaxGroup)
+    int32_t sub[kMaxGroup];         // subdomain of each item
+    int32_t xo[kMaxGroup + 1];      // interior offsets (item t spans p_i + 1 entries)
+    int32_t go[kMaxGroup + 1];      // interface offsets (item t spans q_i + 1 entries)
+    int32_t cnt[kNCnt];             // merged segments per category
+};
 
 template <class T>
 struct BatchSys {
-    const int32_t *cnt;         // kNCnt*s segment counts (this precision)
     const int32_t *ioff, *goff, *perm;
     const void *V;              // q x r: double (FP64) or bf16 (FP32)
     const T *G;                 // r x r column-major
@@ -165,16 +178,18 @@ struct BatchSys {
 template <class T, class IO>
 struct BatchParams {
     const BatchSys<T> *sys;
-    const char *segbase;        // every stream offset is relative to this address
-    const int32_t *items;       // (system, subdomain) pairs, grouped by CTA
-    const int32_t *item_off;    // grid+1
+    const char *segbase;        // the batch's merged segments (stream offsets are relative to it)
+    const BatchGroup *groups;   // grouped by CTA
+    const int32_t *group_off;   // grid+1
     const int32_t *pairs;       // (system, rhs) pairs of systems with r > 0, grouped by CTA
     const int32_t *pair_off;    // grid+1
     const StreamEnt *stream;
     const int64_t *stream_off;  // grid+1
     const IO *b;                // batched input (system-major, n_k x nrhs column-major per system)
     IO *z;                      // batched output, same layout
-    int ring, slot_bytes, max_p, max_q, max_m, nrhs, grid, any_lr;
+    int ring, slot_bytes;
+    int xs, gs;                 // per-rhs strides of a group's interior / interface vectors in shared memory
+    int max_m, nrhs, grid, any_lr;
     unsigned *bar;
     int *err;
     const int *skip;            // when *skip != 0 the launch does nothing

@@ -11,6 +11,9 @@
 //   pass 3  w -= V h2,                        ||w||^2
 // then one thread forms h = h1 + h2, h_{j+1,j} = ||w|| and (FGMRES) applies
 // the Givens rotations, and a last launch writes v_{j+1} = w / h_{j+1,j}.
+// The second pass is not optional here: with a good preconditioner
+// A M^{-1} v_j is close to v_j, so the first projection removes almost all of
+// w and a selective test (norm drop below 1/sqrt(2)) asks for it every step.
 // Every kernel returns at once when *skip is set (the cycle has converged).
 #include <cuda_runtime.h>
 

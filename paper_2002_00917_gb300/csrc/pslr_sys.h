@@ -24,6 +24,7 @@ struct SysExport {
     int slot_bytes[2];
     uint64_t lr_gen;                        // changes whenever the low-rank term is replaced
     int64_t seg_bytes[2];                   // bytes of the forward segments
+    std::vector<int32_t> ioff_h, goff_h;    // host copies of the s+1 interior / interface offsets
 };
 
 // Fill e from a set-up context; false when the context has no device state.

@@ -52,13 +52,15 @@ class pslr_info(C.Structure):
 
 class pslr_batch_info(C.Structure):
     _fields_ = [("nsys", C.c_int32), ("nrhs", C.c_int32), ("nprob", C.c_int32), ("n_total", C.c_int64),
-                ("items", C.c_int32), ("grid", C.c_int32), ("ring", C.c_int32 * 2), ("max_m", C.c_int32),
+                ("items", C.c_int32), ("grid", C.c_int32), ("ring", C.c_int32 * 2),
+                ("group", C.c_int32 * 2), ("groups", C.c_int32 * 2), ("max_m", C.c_int32),
                 ("max_p", C.c_int32), ("max_q", C.c_int32), ("apply_bytes_fp64", C.c_int64),
                 ("apply_bytes_fp32", C.c_int64), ("graph", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
-        d["ring"] = list(self.ring)
+        for k in ("ring", "group", "groups"):
+            d[k] = list(getattr(self, k))
         return d
 
 
@@ -85,7 +87,7 @@ SIGNATURES = {
     "pslr_last_error": (C.c_char_p, [_P]),
     "pslr_status_string": (C.c_char_p, [_I32]),
     "pslr_destroy": (None, [_P]),
-    "pslr_batch_create": (_I32, [_I32, _P, _I32, C.POINTER(_P)]),
+    "pslr_batch_create": (_I32, [_I32, _P, _I32, _I32, C.POINTER(_P)]),
     "pslr_batch_apply": (_I32, [_P, _P, _P, _I32, _P]),
     "pslr_batch_solve": (_I32, [_P, _P, _P, _D, _I32, _I32, _I32, _P, _P, _P]),
     "pslr_batch_get_info": (_I32, [_P, C.POINTER(pslr_batch_info)]),
@@ -282,14 +284,14 @@ class Batch:
     :meth:`offsets` gives the blocks' starts.  The contexts must outlive the
     batch; the batch keeps references to them."""
 
-    def __init__(self, systems, nrhs):
+    def __init__(self, systems, nrhs, group=0):
         lib = load()
         self.lib = lib
         self.systems = list(systems)
         self.nrhs = int(nrhs)
         arr = (C.c_void_p * len(self.systems))(*[p.h for p in self.systems])
         h = C.c_void_p()
-        st = lib.pslr_batch_create(len(self.systems), arr, self.nrhs, C.byref(h))
+        st = lib.pslr_batch_create(len(self.systems), arr, self.nrhs, int(group), C.byref(h))
         if st != PSLR_OK:
             raise PslrError(st, f"pslr_batch_create: {lib.pslr_batch_last_error(None).decode()}")
         self.h = h

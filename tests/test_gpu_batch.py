@@ -105,13 +105,17 @@ def test_batch_apply_fp64_matches_oracle(dev, nrhs):
             assert r2 <= TOL64 and rinf <= TOL64, (w["A"].n, j, r2, rinf)
 
 
-def test_batch_apply_equals_single_system_apply(dev):
+@pytest.mark.parametrize("group", [0, 1, 2, 3, 8])
+def test_batch_apply_equals_single_system_apply(dev, group):
     """The batched launch and the per-system launches run the same arithmetic
-    per row; only the order of the low-rank partial sums can differ."""
+    per row, whatever number of subdomains a CTA sweeps in lockstep (merged
+    levels); only the order of the low-rank partial sums could differ."""
     from paper_2002_00917_gb300 import pslr
 
     sy = _systems(SYSTEMS)
-    bt = pslr.Batch([c for _, c, _ in sy], 2)
+    bt = pslr.Batch([c for _, c, _ in sy], 2, group=group)
+    if group:
+        assert max(bt.info["group"]) <= group
     b = torch.tensor(np.random.default_rng(12).uniform(-1, 1, bt.info["n_total"]), device=dev)
     z = torch.zeros_like(b)
     bt.apply(b, z)
@@ -143,15 +147,18 @@ def test_batch_apply_fp32_matches_oracle(dev):
             assert r2 <= TOL32 and rinf <= TOL32, (w["A"].n, j, r2, rinf)
 
 
-def test_batch_more_items_than_ctas(dev):
-    """40 systems of 16 subdomains: several items per CTA in every phase, with
+@pytest.mark.parametrize("group", [1, 0])
+def test_batch_more_items_than_ctas(dev, group):
+    """40 systems of 16 subdomains: several groups per CTA in every phase, with
     m and r varying across systems."""
     from paper_2002_00917_gb300 import pslr
 
     specs = [("lap", (16 + (k % 7), 16 + (k % 5)), (4, 4), k % 4, (0, 4, 8)[k % 3]) for k in range(40)]
     sy = _systems(specs)
-    bt = pslr.Batch([c for _, c, _ in sy], 2)
-    assert bt.info["items"] == 640 and bt.info["items"] > bt.info["grid"]
+    bt = pslr.Batch([c for _, c, _ in sy], 2, group=group)
+    assert bt.info["items"] == 640
+    if group == 1:
+        assert bt.info["groups"] == [640, 640] and bt.info["grid"] < 640
     b = np.random.default_rng(14).uniform(-1, 1, bt.info["n_total"])
     bd = torch.tensor(b, device=dev)
     zd = torch.zeros_like(bd)
