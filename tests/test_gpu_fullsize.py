@@ -1,0 +1,239 @@
+"""GPU parity at the full sizes of the workloads, in the launch configuration
+bench.py times (one cooperative launch per apply, the grid the library
+picks).  The oracle finishes one apply of the largest problem (128^3,
+n = 2,097,152) in well under a second, so the applies are compared element by
+element; FGMRES, whose oracle run would take minutes at these sizes, is
+checked through properties that hold at any size (the true FP64 residual of
+the returned x; the adjoint relations of the gradient), and against the
+oracle's iteration count where that is cheap (the 32^2 problem).
+
+The low-rank term is built on the GPU (device Arnoldi) and handed to the
+oracle, so the apply comparison isolates Algorithm 3; the device Arnoldi
+itself is compared with the oracle's on the two mid-size problems.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from pslr_inputs import configs as C
+from pslr_inputs import generators as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+FULL = ["lap2d_32_2x2_exact", "lap3d_64_4x4x2_ilu0", "kappa3d_48_3x3x3", "cd3d_128_8x8x4_ilu0"]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_00917_gb300 import build
+
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _bf16(x):
+    f = np.asarray(x, dtype=np.float32).copy()
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b), np.abs(a - b).max() / np.abs(b).max()
+
+
+def _matvec_T(A, x):
+    rows = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.rowptr))
+    return np.bincount(A.col, weights=A.val * x[rows], minlength=A.n)
+
+
+@pytest.fixture(scope="module", params=FULL)
+def full(request, dev):
+    from paper_2002_00917_gb300 import pslr
+
+    w = C.WORKLOADS[request.param]()
+    ctx = pslr.from_workload(w)
+    k, _ = ctx.build_lowrank(w["m"], w["rank"])
+    V, H, Gm = ctx.get_lowrank()
+    orc = O.from_workload(w)
+    orc.set_lowrank(w["m"], V, Gm)
+    return w, ctx, orc, (V, H, Gm)
+
+
+def test_full_maps_bit_exact(full):
+    w, ctx, orc, _ = full
+    for a, b in zip(ctx.get_maps(), orc.maps()):
+        assert np.array_equal(a, b)
+
+
+def test_full_apply_fp64_both_directions(full, dev):
+    w, ctx, orc, _ = full
+    b = np.random.default_rng(21).uniform(-1, 1, w["A"].n)
+    bd = torch.tensor(b, device=dev)
+    for transpose in (False, True):
+        zd = torch.full_like(bd, np.nan)
+        ctx.apply(bd, zd, transpose=transpose)
+        ctx.sync()
+        zo = orc.apply_T(b) if transpose else orc.apply(b)
+        r2, rinf = _rel(zd.cpu().numpy(), zo)
+        assert r2 <= TOL64 and rinf <= TOL64, (w["name"], transpose, r2, rinf)
+
+
+def test_full_apply_fp32(full, dev):
+    """FP32 form (BF16 V, FP32 G) against the oracle run on the same stored
+    low-rank factors."""
+    w, ctx, orc, (V, H, Gm) = full
+    b = np.random.default_rng(22).uniform(-1, 1, w["A"].n).astype(np.float32)
+    bd = torch.tensor(b, device=dev)
+    zd = torch.zeros_like(bd)
+    ctx.apply(bd, zd)
+    ctx.sync()
+    orc.set_lowrank(w["m"], _bf16(V), Gm.astype(np.float32).astype(np.float64))
+    try:
+        zo = orc.apply(b.astype(np.float64))
+    finally:
+        orc.set_lowrank(w["m"], V, Gm)
+    r2, rinf = _rel(zd.cpu().double().numpy(), zo)
+    assert r2 <= TOL32 and rinf <= TOL32, (w["name"], r2, rinf)
+
+
+@pytest.mark.parametrize("name", ["lap3d_64_4x4x2_ilu0", "kappa3d_48_3x3x3"])
+def test_full_device_arnoldi_matches_oracle(dev, name):
+    """Algorithm 1 steps 6-8 at full size: the device Arnoldi (same SplitMix64
+    start vector) against the oracle's V, H and G."""
+    from paper_2002_00917_gb300 import pslr
+
+    w = C.WORKLOADS[name]()
+    ctx = pslr.from_workload(w)
+    k, _ = ctx.build_lowrank(w["m"], w["rank"])
+    orc = O.from_workload(w)
+    ko, _ = orc.build_lowrank(w["m"], w["rank"], seed=0)
+    assert k == ko == w["rank"]
+    V, H, Gm = ctx.get_lowrank()
+    Vo, Ho, Go = orc.lowrank()
+    np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(H, Ho, atol=1e-9 * np.abs(Ho).max())
+    np.testing.assert_allclose(V, Vo, atol=1e-8)
+    np.testing.assert_allclose(Gm, Go, atol=1e-8 * max(1.0, np.abs(Go).max()))
+
+
+@pytest.mark.parametrize("name,restart,maxit", [("lap2d_32_2x2_exact", 40, 500), ("lap3d_64_4x4x2_ilu0", 120, 1500),
+                                                ("kappa3d_48_3x3x3", 120, 1500)])
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_full_fgmres_true_residual(dev, name, restart, maxit, prec):
+    """FGMRES to 1e-8 with either preconditioner form: the returned x meets the
+    tolerance in its true FP64 residual (computed here on the CPU); on the
+    32^2 problem the FP64 iteration count is within +-1 of the oracle's."""
+    from paper_2002_00917_gb300 import pslr
+
+    w = C.WORKLOADS[name]()
+    ctx = pslr.from_workload(w)
+    ctx.build_lowrank(w["m"], w["rank"])
+    b, xs = G.uniform_rhs(w["A"], 0)
+    bd = torch.tensor(b, device=dev)
+    x = torch.empty_like(bd)
+    its, rel, st = ctx.solve(bd, x, rtol=1e-8, restart=restart, maxit=maxit, prec=prec)
+    assert st == pslr.PSLR_OK and rel <= 1e-8, (its, rel)
+    xr = x.cpu().numpy()
+    assert np.linalg.norm(b - G.csr_matvec(w["A"], xr)) <= 1.0001e-8 * np.linalg.norm(b)
+    if name == "lap2d_32_2x2_exact" and prec == 0:
+        orc = O.from_workload(w)
+        V, H, Gm = ctx.get_lowrank()
+        orc.set_lowrank(w["m"], V, Gm)
+        _, its_o, _, st_o = orc.fgmres(b, rtol=1e-8, restart=restart, maxit=maxit)
+        assert st_o == 0 and abs(its - its_o) <= 1, (its, its_o)
+
+
+def test_full_batch_apply(dev):
+    """The 64-system batch at full size, 4 rhs: every (system, rhs) against the
+    oracle of its system, FP64 (1e-12) and FP32 with BF16 V (1e-5)."""
+    from paper_2002_00917_gb300 import pslr
+
+    wb = C.batch2d_64sys()
+    nr = wb["nrhs"]
+    ctxs, orcs, lrs = [], [], []
+    for s in wb["systems"]:
+        c = pslr.Pslr(s["A"], dims=s["dims"], splits=s["splits"], factor=s["factor"])
+        c.build_lowrank(s["m"], s["rank"])
+        V, H, Gm = c.get_lowrank()
+        o = O.Oracle(s["A"], dims=s["dims"], splits=s["splits"], factor=s["factor"])
+        o.set_lowrank(s["m"], V, Gm)
+        ctxs.append(c)
+        orcs.append(o)
+        lrs.append((V, Gm))
+    bt = pslr.Batch(ctxs, nr)
+    N = bt.info["n_total"]
+    b = np.random.default_rng(23).uniform(-1, 1, N)
+    for prec in (0, 1):
+        bd = torch.tensor(b, device=dev, dtype=torch.float64 if prec == 0 else torch.float32)
+        zd = torch.zeros_like(bd)
+        bt.apply(bd, zd)
+        bt.sync()
+        z = zd.cpu().double().numpy()
+        bin_ = bd.cpu().double().numpy()
+        for k, (s, o, off) in enumerate(zip(wb["systems"], orcs, bt.offsets())):
+            n = s["A"].n
+            if prec == 1:
+                V, Gm = lrs[k]
+                o.set_lowrank(s["m"], _bf16(V), Gm.astype(np.float32).astype(np.float64))
+            for j in range(nr):
+                seg = slice(off + j * n, off + (j + 1) * n)
+                r2, rinf = _rel(z[seg], o.apply(bin_[seg]))
+                tol = TOL64 if prec == 0 else TOL32
+                assert r2 <= tol and rinf <= tol, (k, j, prec, r2, rinf)
+
+
+def test_full_gradient_kappa48(dev):
+    """The differentiable 48^3 variable-coefficient problem at full size: the
+    forward solve meets its tolerance in the true residual, the gradient with
+    respect to b is the adjoint lambda with A^T lambda = dL/du (checked by
+    residual), the gradient with respect to kappa equals the chain rule through
+    the assembly from (lambda, u), and a central difference of the loss along a
+    seeded direction agrees with <dL/dkappa, delta>."""
+    from paper_2002_00917_gb300 import autograd as AG
+
+    w = C.kappa3d_48_3x3x3()
+    dims, A, sigma, kap0 = w["dims"], w["A"], w["sigma"], w["kappa"]
+    b0, _ = G.uniform_rhs(A, 0)
+    ut = torch.tensor(np.random.default_rng(1).uniform(-1, 1, A.n), device=dev)
+    opts = dict(dims=dims, splits=w["splits"], m=w["m"], rank=w["rank"], rtol=1e-12, restart=127, maxit=6000)
+
+    def loss_of(kv, grad=False):
+        kappa = torch.tensor(kv, device=dev, requires_grad=grad)
+        b = torch.tensor(b0, device=dev, requires_grad=grad)
+        vals = G.variable_kappa_values(dims, A, kappa, sigma, xp=torch)
+        u = AG.solve(vals, b, A.rowptr, A.col, **opts)
+        L = torch.sum((u - ut) ** 2)
+        if grad:
+            L.backward()
+        return L, u, kappa, b
+
+    L, u, kappa, b = loss_of(kap0, grad=True)
+    un, utn = u.detach().cpu().numpy(), ut.cpu().numpy()
+    Ak = G.variable_kappa(dims, kap0, sigma)
+    assert np.linalg.norm(b0 - G.csr_matvec(Ak, un)) <= 1.0001e-12 * np.linalg.norm(b0)
+    lam = b.grad.cpu().numpy()
+    gu = 2 * (un - utn)
+    assert np.linalg.norm(_matvec_T(Ak, lam) - gu) <= 1.0001e-12 * np.linalg.norm(gu)
+    # chain rule through the assembly, on the CPU, from the same lambda and u
+    kc = torch.tensor(kap0, requires_grad=True)
+    vc = G.variable_kappa_values(dims, Ak, kc, sigma, xp=torch)
+    rows = np.repeat(np.arange(A.n), np.diff(Ak.rowptr))
+    (vc * torch.tensor(-lam[rows] * un[Ak.col])).sum().backward()
+    gk = kappa.grad.cpu().numpy()
+    np.testing.assert_allclose(gk, kc.grad.numpy(), rtol=1e-10, atol=1e-12 * np.abs(gk).max())
+    # central difference along a seeded direction; h = 1e-3 keeps the
+    # difference of two losses well above the solves' 1e-12 tolerance, and
+    # the O(h^2) truncation error below the bar
+    delta = np.random.default_rng(3).uniform(-1, 1, A.n)
+    h = 1e-3
+    Lp = loss_of(kap0 + h * delta)[0].item()
+    Lm = loss_of(kap0 - h * delta)[0].item()
+    fd = (Lp - Lm) / (2 * h)
+    ad = float(gk @ delta)
+    assert abs(fd - ad) <= 1e-4 * abs(ad), (fd, ad)
