@@ -31,6 +31,8 @@ cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, cudaStream_
 cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, cudaStream_t st);
 int max_coresident_apply(int smem, bool fp32);
 int krylov_blocks(int n);
+size_t krylov_part_doubles(int nblk, int nres);
+int krylov_tickets();
 void launch_cgs_pass(int n, int k, const double *V, int64_t ld, double *w, const double *hsub, int norm,
                      double *part, double *res, unsigned *ticket, const int32_t *rp, const int32_t *ci,
                      const double *av, const double *z, const int *skip, cudaStream_t st);
@@ -1391,13 +1393,13 @@ struct KWork {
 
 static pslr_status kwork_alloc(pslr_ctx *c, KWork &W, int len, int kcols) {
     W.nblk = krylov_blocks(len);
-    CK(cudaMalloc(&W.part, sizeof(double) * (size_t)W.nblk * (kcols + 1)));
+    CK(cudaMalloc(&W.part, sizeof(double) * krylov_part_doubles(W.nblk, kcols + 1)));
     CK(cudaMalloc(&W.h1, sizeof(double) * (kcols + 1)));
     CK(cudaMalloc(&W.h2, sizeof(double) * (kcols + 1)));
     CK(cudaMalloc(&W.wn2, sizeof(double) * 2));
     CK(cudaMalloc(&W.hn, sizeof(double) * 2));
-    CK(cudaMalloc(&W.ticket, sizeof(unsigned)));
-    CK(cudaMemset(W.ticket, 0, sizeof(unsigned)));
+    CK(cudaMalloc(&W.ticket, sizeof(unsigned) * krylov_tickets()));
+    CK(cudaMemset(W.ticket, 0, sizeof(unsigned) * krylov_tickets()));
     return PSLR_OK;
 }
 

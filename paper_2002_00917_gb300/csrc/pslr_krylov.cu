@@ -4,8 +4,8 @@
 // Classical Gram-Schmidt applied twice (CGS2) is split into three passes over
 // the rows, each one launch whose blocks stream the basis V column-chunk by
 // column-chunk (coalesced along rows) and leave one partial per block; the
-// last block to finish (atomic ticket) adds the partials in block order, so
-// every reduction is deterministic:
+// partials are added in a fixed two-level order (finish_reduction), so every
+// reduction is deterministic:
 //   pass 1  w = A z (optional, fused CSR SpMV), h1 = V^T w
 //   pass 2  w -= V h1,                        h2 = V^T w
 //   pass 3  w -= V h2,                        ||w||^2
@@ -47,24 +47,47 @@ __device__ __forceinline__ void block_reduce8(double (&a)[kChunk], double *sh, d
     __syncthreads();
 }
 
-// Last block to finish adds the per-block partials (nres values each) in
-// block order into res (res[c] = sum_b part[b*nres + c]; accumulate adds to
-// the existing res).  Returns true in the reducing block.
-__device__ bool finish_reduction(const double *part, int nres, double *res, unsigned *ticket,
-                                 bool accumulate) {
+// Two-level deterministic reduction of the per-block partials (nres values
+// each, part[b*nres + c]) into res: the last block of each group of kRedGroup
+// consecutive blocks adds its group's partials in block order (into the
+// group partials after the block partials), and the last group to finish adds
+// the group partials in group order.  On GB300 a dependent FP64 add costs a
+// full pass through the FP64 pipe, so the short chains (16 + groups instead of
+// one add per block) matter.  ticket[0] counts finished groups, ticket[1 + g]
+// the finished blocks of group g; the finishers reset them.  Returns true in
+// the block that wrote res.
+constexpr int kRedGroup = 16;
+constexpr int kMaxTickets = 64;  // 1 + groups: up to 1008 blocks
+
+__device__ bool finish_reduction(double *part, int nres, double *res, unsigned *ticket, bool accumulate) {
     __shared__ unsigned last;
+    const int nb = gridDim.x, ng = (nb + kRedGroup - 1) / kRedGroup;
+    const int g = blockIdx.x / kRedGroup, gb = g * kRedGroup, ge = min(nb, gb + kRedGroup);
+    double *gpart = part + (int64_t)nb * nres;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) last = atomicAdd(ticket + 1 + g, 1u) == (unsigned)(ge - gb - 1);
     __syncthreads();
     if (!last) return false;
     __threadfence();
     for (int c = threadIdx.x; c < nres; c += blockDim.x) {
         double v = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) v += __ldcg(part + (int64_t)b * nres + c);
+        for (int b = gb; b < ge; ++b) v += __ldcg(part + (int64_t)b * nres + c);
+        gpart[(int64_t)g * nres + c] = v;
+    }
+    if (threadIdx.x == 0) ticket[1 + g] = 0u;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == (unsigned)(ng - 1);
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    for (int c = threadIdx.x; c < nres; c += blockDim.x) {
+        double v = 0.0;
+        for (int q = 0; q < ng; ++q) v += __ldcg(gpart + (int64_t)q * nres + c);
         res[c] = accumulate ? res[c] + v : v;
     }
-    if (threadIdx.x == 0) *ticket = 0u;
+    if (threadIdx.x == 0) ticket[0] = 0u;
     __syncthreads();
     return true;
 }
@@ -227,15 +250,25 @@ __global__ void k_grad_values(int n, const int32_t *rp, const int32_t *ci, const
 
 // ---------------------------------------------------------------- launchers
 
+// Blocks of the row-parallel Krylov kernels: four rows per thread, at most
+// two blocks per SM, and within the reduction's ticket array.  (On the 64^3
+// FGMRES, 256 blocks beat 128, 152 and 512 by 5-10%.)
 int krylov_blocks(int n) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int want = (n + kKThreads * 4 - 1) / (kKThreads * 4);
     int cap = 2 * nsm;
+    if (cap > (kMaxTickets - 1) * kRedGroup) cap = (kMaxTickets - 1) * kRedGroup;
     if (want > cap) want = cap;
     return want < 1 ? 1 : want;
 }
+
+// Sizes of the reduction buffers for up to `nres` results per block.
+size_t krylov_part_doubles(int nblk, int nres) {
+    return (size_t)(nblk + (nblk + kRedGroup - 1) / kRedGroup) * nres;
+}
+int krylov_tickets() { return kMaxTickets; }
 
 void launch_cgs_pass(int n, int k, const double *V, int64_t ld, double *w, const double *hsub,
                      int norm, double *part, double *res, unsigned *ticket, const int32_t *rp,
