@@ -157,33 +157,51 @@ __global__ void __launch_bounds__(kKThreads) k_cgs_pass(
 __global__ void k_hessenberg(int j, const double *h1, const double *h2, const double *wn2, double *H,
                              int ldh, double *hn_out, int givens, double *rot, double *gam,
                              double tol_abs, int *state, int *skip) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    // one warp: the column and the rotations are staged in shared memory, so
+    // the sequential rotation chain runs on shared-memory and register latency
+    __shared__ double c[kMaxK + 2], scs[kMaxK + 1], ssn[kMaxK + 1];
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     if (skipping(skip)) return;
+    const int lane = threadIdx.x;
     double *col = H + (int64_t)j * ldh;
-    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-    const double hn = sqrt(*wn2);
-    col[j + 1] = hn;
-    *hn_out = hn;
-    state[0] = j + 1;
-    if (!givens) return;
     double *cs = rot, *sn = rot + ldh;
-    for (int i = 0; i < j; ++i) {
-        const double a = col[i], b = col[i + 1];
-        col[i] = cs[i] * a + sn[i] * b;
-        col[i + 1] = -sn[i] * a + cs[i] * b;
+    const double hn = sqrt(*wn2);
+    for (int i = lane; i <= j; i += 32) c[i] = h1[i] + h2[i];
+    if (givens)
+        for (int i = lane; i < j; i += 32) {
+            scs[i] = cs[i];
+            ssn[i] = sn[i];
+        }
+    __syncwarp();
+    if (lane == 0) {
+        c[j + 1] = hn;
+        *hn_out = hn;
+        state[0] = j + 1;
+        if (givens) {
+            double carry = c[0];  // entry i after the rotations before i
+            for (int i = 0; i < j; ++i) {
+                const double a = carry, b = c[i + 1], ci = scs[i], si = ssn[i];
+                c[i] = ci * a + si * b;
+                carry = -si * a + ci * b;
+            }
+            const double a = carry, b = c[j + 1];
+            const double den = sqrt(a * a + b * b);
+            const double cj = den > 0.0 ? a / den : 1.0, sj = den > 0.0 ? b / den : 0.0;
+            cs[j] = cj;
+            sn[j] = sj;
+            c[j] = den;
+            c[j + 1] = 0.0;
+            const double g = gam[j];
+            gam[j + 1] = -sj * g;
+            gam[j] = cj * g;
+            if (fabs(gam[j + 1]) <= tol_abs || hn == 0.0 || !(den == den)) {
+                state[1] = 1;
+                if (skip) *skip = 1;
+            }
+        }
     }
-    const double a = col[j], b = col[j + 1];
-    const double den = sqrt(a * a + b * b);
-    cs[j] = den > 0.0 ? a / den : 1.0;
-    sn[j] = den > 0.0 ? b / den : 0.0;
-    col[j] = den;
-    col[j + 1] = 0.0;
-    gam[j + 1] = -sn[j] * gam[j];
-    gam[j] = cs[j] * gam[j];
-    if (fabs(gam[j + 1]) <= tol_abs || hn == 0.0 || !(den == den)) {
-        state[1] = 1;
-        if (skip) *skip = 1;
-    }
+    __syncwarp();
+    for (int i = lane; i <= j + 1; i += 32) col[i] = c[i];
 }
 
 // v = w / *hn  (hn == 0 leaves v = 0).
