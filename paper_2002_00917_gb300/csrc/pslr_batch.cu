@@ -74,7 +74,7 @@ __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int xs, int nr, in
             for (int k = 0; k < nr; ++k) level_row_general(seg, x + (size_t)k * xs, j);
         }
         csync();
-        if (j == 0) mbar_arrive(fbar + edelta);
+        if (j == 0) mbar_arrive_cnt(fbar + edelta, kConsumerWarps);
         ++slot;
         fbar += 8;
         ptr_s += R.slot_bytes;
@@ -92,7 +92,8 @@ __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int xs, int nr, in
 
 // ELL product of nseg segments for nr vectors: out_k[row] = sum (assign) or
 // out_k[row] -= sum (subtract), sum = sum_e v_e src_k[c_e]; src in shared
-// memory (local columns) or global memory (GLOBAL, the C_g rows).
+// memory (local columns) or global memory (GLOBAL, the C_g rows).  Disjoint
+// rows per segment: no CTA barrier between segments, one at the end.
 template <class T, bool GLOBAL>
 __device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, int os, const T *src, int ss, int nr, bool subtract,
                              int nseg, int *err) {
@@ -137,8 +138,8 @@ __device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, int os, const T *sr
             for (int k = 0; k < nr; ++k)
                 ell_row_general<T, GLOBAL>(seg, out + (size_t)k * os, src + (size_t)k * ss, subtract, j);
         }
-        csync();
-        if (j == 0) mbar_arrive(fbar + edelta);
+        __syncwarp();
+        if ((j & 31) == 0) mbar_arrive(fbar + edelta);  // this warp is done with the slot
         ++slot;
         fbar += 8;
         ptr_s += R.slot_bytes;
@@ -152,6 +153,7 @@ __device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, int os, const T *sr
     R.slot = slot;
     R.phase = phase;
     R.consumed += nseg;
+    csync();  // the product is complete before anyone reads it
 }
 
 // ------------------------------------------------------------------ kernel

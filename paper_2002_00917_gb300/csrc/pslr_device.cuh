@@ -18,6 +18,11 @@ namespace pslr {
 constexpr int kErrTimeout = 8;  // PSLR_ERR_TIMEOUT
 constexpr long long kTmaWaitLimit = 1ll << 26;
 constexpr int kProducerWarp = kConsumers / 32;
+// A ring slot is free again once every consumer warp has arrived on its empty
+// barrier: a level sweep (which synchronises the CTA per level anyway) arrives
+// once for all warps; the products E, F, C_g, whose segments write disjoint
+// rows, let every warp arrive on its own and move on without a CTA barrier.
+constexpr uint32_t kConsumerWarps = kConsumers / 32;
 
 // ------------------------------------------------------------------ PTX helpers
 
@@ -36,6 +41,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cnt(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
@@ -149,31 +158,6 @@ struct Cta {
     Ring ring;
     unsigned bar_gen;  // consumer thread 0: generation seen at the last grid arrive
 };
-
-// Wait until the next segment has landed; returns its shared-memory copy.
-__device__ __forceinline__ const char *seg_next(Ring &R, int *err) {
-    const uint32_t bar = R.full_s + 8 * R.slot;
-    if (!mbar_try_wait(bar, R.phase)) {
-        long long it = 0;
-        while (!mbar_try_wait(bar, R.phase)) {
-            if (++it > kTmaWaitLimit) {
-                atomicCAS(err, 0, kErrTimeout);
-                break;
-            }
-        }
-    }
-    return R.base + (size_t)R.slot * R.slot_bytes;
-}
-
-// The segment is consumed by every consumer (caller synchronised): free it.
-__device__ __forceinline__ void seg_done(Ring &R) {
-    if (threadIdx.x == 0) mbar_arrive(R.empty_s + 8 * R.slot);
-    ++R.consumed;
-    if (++R.slot == R.slots) {
-        R.slot = 0;
-        R.phase ^= 1u;
-    }
-}
 
 // Producer warp: copy the CTA's stream into the ring.
 // With active != nullptr an entry is skipped when active[entry.pad] == 0
@@ -534,59 +518,12 @@ __device__ __forceinline__ T row_sub(RowPre<T, IDX> &q, int j, T a, SRC src) {
     return a;
 }
 
-// The 3-entry record of row j of a kRec3 segment with local columns.
+// The 3-entry record of row j of a kRec3 segment.
 template <class T>
 struct Rec3 {
     int r, c0, c1, c2;
     T v0, v1, v2, d;
 };
-
-template <class T>
-__device__ __forceinline__ Rec3<T> rec3_local(const char *seg, int np, int j) {
-    Rec3<T> e;
-    const uint2 id = reinterpret_cast<const uint2 *>(seg + sizeof(SegHdr))[j];
-    e.r = (int)(id.x & 0xffffu);
-    e.c0 = (int)(id.x >> 16);
-    e.c1 = (int)(id.y & 0xffffu);
-    e.c2 = (int)(id.y >> 16);
-    const char *vp = seg + sizeof(SegHdr) + (size_t)np * 8 + (size_t)j * 4 * sizeof(T);
-    if constexpr (sizeof(T) == 4) {
-        const float4 v = *reinterpret_cast<const float4 *>(vp);
-        e.v0 = v.x;
-        e.v1 = v.y;
-        e.v2 = v.z;
-        e.d = v.w;
-    } else {
-        const double2 a = reinterpret_cast<const double2 *>(vp)[0];
-        const double2 b = reinterpret_cast<const double2 *>(vp)[1];
-        e.v0 = a.x;
-        e.v1 = a.y;
-        e.v2 = b.x;
-        e.d = b.y;
-    }
-    return e;
-}
-
-// Header fields and, for a 3-entry record level, the thread's row: all read
-// ahead of use (nothing here depends on the vector being solved for).
-template <class T>
-struct LevelPre {
-    const char *seg;
-    int n, np, fmt;
-    Rec3<T> e;
-};
-
-template <class T>
-__device__ __forceinline__ LevelPre<T> level_pre(const char *seg, int j) {
-    LevelPre<T> q;
-    q.seg = seg;
-    const uint2 h = *reinterpret_cast<const uint2 *>(seg);
-    q.n = (int)(h.x & 0xffffu);
-    q.np = (int)(h.y & 0xffffu);
-    q.fmt = (int)((h.y >> 16) & 0xffu);
-    if (q.fmt == kRec3 && j < q.n) q.e = rec3_local<T>(seg, q.np, j);
-    return q;
-}
 
 // Rows of a level in the 7-entry record or tile encodings (exact local LU,
 // irregular matrices): out of line, so the common path stays small.
@@ -597,22 +534,6 @@ __device__ __noinline__ void level_row_general(const char *seg, T *x, int j) {
         T a = row_sub(g, j, x[g.r], [&](int col) { return x[col]; });
         if (g.diag) a *= g.dv;
         x[g.r] = a;
-    }
-}
-
-// x[r] = (x[r] - sum_k T_rk x[c_k]) * dinv[r] for the thread's row of one level.
-template <class T>
-__device__ __forceinline__ void level_row(const LevelPre<T> &q, T *x, int j) {
-    if (q.fmt == kRec3) {
-        if (j < q.n) {
-            T a = x[q.e.r];
-            a = fma_t(-q.e.v0, x[q.e.c0], a);
-            a = fma_t(-q.e.v1, x[q.e.c1], a);
-            a = fma_t(-q.e.v2, x[q.e.c2], a);
-            x[q.e.r] = a * q.e.d;
-        }
-    } else {
-        level_row_general(q.seg, x, j);
     }
 }
 
@@ -689,7 +610,7 @@ __device__ void tri_sweep(Cta<T> &c, T *x, int nseg, int *err) {
             level_row_general(R.base + (ptr_s - base_s), x, j);
         }
         csync();
-        if (j == 0) mbar_arrive(fbar + edelta);
+        if (j == 0) mbar_arrive_cnt(fbar + edelta, kConsumerWarps);
         ++slot;
         fbar += 8;
         ptr_s += R.slot_bytes;
@@ -719,7 +640,9 @@ __device__ __noinline__ void ell_row_general(const char *seg, T *out, const T *s
 }
 
 // ELL product over nseg segments: out[row] = sum (assign) or out[row] -= sum
-// (subtract); src in shared memory (local columns) or global memory.
+// (subtract); src in shared memory (local columns) or global memory.  The
+// segments write disjoint rows, so the warps go through them without a CTA
+// barrier (each releases a slot on its own); one barrier closes the product.
 template <class T, bool GLOBAL>
 __device__ void ell_op(Cta<T> &c, T *out, const T *src, bool subtract, int nseg, int *err) {
     Ring &R = c.ring;
@@ -749,8 +672,8 @@ __device__ void ell_op(Cta<T> &c, T *out, const T *src, bool subtract, int nseg,
         } else {
             ell_row_general<T, GLOBAL>(R.base + (ptr_s - base_s), out, src, subtract, j);
         }
-        csync();
-        if (j == 0) mbar_arrive(fbar + edelta);
+        __syncwarp();
+        if ((j & 31) == 0) mbar_arrive(fbar + edelta);  // this warp is done with the slot
         ++slot;
         fbar += 8;
         ptr_s += R.slot_bytes;
@@ -764,6 +687,7 @@ __device__ void ell_op(Cta<T> &c, T *out, const T *src, bool subtract, int nseg,
     R.slot = slot;
     R.phase = phase;
     R.consumed += nseg;
+    csync();  // the product is complete before anyone reads it
 }
 
 // Exact-LU row permutation: x <- P x (gather, before the sweeps) or
@@ -907,7 +831,7 @@ __device__ bool cta_start(Cta<T> &c, char *smem, const SmemLayout &L, int ring, 
         c.ctl->ok = 1;
         for (int i = 0; i < ring; ++i) {
             mbar_init(c.ring.full_s + 8 * i, 1);
-            mbar_init(c.ring.empty_s + 8 * i, 1);
+            mbar_init(c.ring.empty_s + 8 * i, kConsumerWarps);
         }
         fence_mbar_init();
     }
