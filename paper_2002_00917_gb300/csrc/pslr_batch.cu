@@ -27,6 +27,31 @@ namespace pslr {
 
 // ---------------------------------------------------- multi-rhs local ops
 
+// Work split of a level among the consumer threads.  FP32 (and one rhs): one
+// thread per row, all right-hand sides (their loads issue back to back).
+// FP64 with several rhs: one thread per (row, rhs) pair, so the rhs spread
+// over more warps - on GB300 a warp-wide FP64 instruction occupies its
+// scheduler's FP64 pipe for many cycles whatever the number of active lanes,
+// and a level has few rows (measured on 64 systems x 4 rhs: 5.96 -> 4.63 ms).
+// Pair u = row * nr + k; thread j takes u = j, j + kConsumers, ...
+struct PairWalk {
+    int row, k, drow, dk, nr;
+    __device__ __forceinline__ PairWalk(int j, int nr_) : nr(nr_) {
+        row = j / nr_;
+        k = j - row * nr_;
+        drow = kConsumers / nr_;
+        dk = kConsumers - drow * nr_;
+    }
+    __device__ __forceinline__ void next() {
+        row += drow;
+        k += dk;
+        if (k >= nr) {
+            k -= nr;
+            ++row;
+        }
+    }
+};
+
 // One level sweep per segment for nr vectors x + k*xs (k < nr <= kMaxBatchRhs):
 // x_k[r] = (x_k[r] - sum_e T_re x_k[c_e]) (* dinv[r]).
 template <class T>
@@ -45,7 +70,21 @@ __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int xs, int nr, in
     for (int L = 0; L < nseg; ++L) {
         if (!mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
         const uint2 h = lds_u2(ptr_s);
-        if (((h.y >> 16) & 0xffu) == kRec3) {
+        if (sizeof(T) == 8 && nr > 1 && ((h.y >> 16) & 0xffu) == kRec3) {
+            const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu);
+            const bool diag = (h.x >> 24) & kSegDiag;
+            for (PairWalk u(j, nr); u.row < n; u.next()) {
+                const Rec3<T> e = rec3_shared<T>(ptr_s, np, u.row);
+                const uint32_t b = x0s + kstep * u.k;
+                const T x0 = lds(b + ts * e.c0, T()), x1 = lds(b + ts * e.c1, T());
+                const T x2 = lds(b + ts * e.c2, T()), xr = lds(b + ts * e.r, T());
+                T a = fma_t(-e.v0, x0, xr);
+                a = fma_t(-e.v1, x1, a);
+                a = fma_t(-e.v2, x2, a);
+                if (diag) a *= e.d;
+                sts(b + ts * e.r, a);
+            }
+        } else if (((h.y >> 16) & 0xffu) == kRec3) {
             if (j < (int)(h.x & 0xffffu)) {
                 const Rec3<T> e = rec3_shared<T>(ptr_s, (int)(h.y & 0xffffu), j);
                 const bool diag = (h.x >> 24) & kSegDiag;
@@ -109,7 +148,19 @@ __device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, int os, const T *sr
     for (int kseg = 0; kseg < nseg; ++kseg) {
         if (!mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
         const uint2 h = lds_u2(ptr_s);
-        if (!GLOBAL && ((h.y >> 16) & 0xffu) == kRec3) {
+        if (!GLOBAL && sizeof(T) == 8 && nr > 1 && ((h.y >> 16) & 0xffu) == kRec3) {
+            const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu);
+            const uint32_t o0 = smem_addr(out), s0 = smem_addr(src);
+            for (PairWalk u(j, nr); u.row < n; u.next()) {
+                const Rec3<T> e = rec3_shared<T>(ptr_s, np, u.row);
+                const uint32_t sb = s0 + ts * (uint32_t)(u.k * ss), ob = o0 + ts * (uint32_t)(u.k * os);
+                T a = e.v0 * lds(sb + ts * e.c0, T());
+                a = fma_t(e.v1, lds(sb + ts * e.c1, T()), a);
+                a = fma_t(e.v2, lds(sb + ts * e.c2, T()), a);
+                if (subtract) a = lds(ob + ts * e.r, T()) - a;
+                sts(ob + ts * e.r, a);
+            }
+        } else if (!GLOBAL && ((h.y >> 16) & 0xffu) == kRec3) {
             if (j < (int)(h.x & 0xffffu)) {
                 const uint32_t o0 = smem_addr(out), s0 = smem_addr(src);
                 const Rec3<T> e = rec3_shared<T>(ptr_s, (int)(h.y & 0xffffu), j);
