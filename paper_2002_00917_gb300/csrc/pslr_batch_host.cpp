@@ -77,7 +77,7 @@ struct pslr_batch {
     void *d_state = nullptr;
     BkState S{};
     cudaStream_t cap = nullptr;
-    std::map<std::tuple<int, int, double, int, long long>, cudaGraphExec_t> graphs;
+    std::map<std::tuple<int, int, long long>, cudaGraphExec_t> graphs;  // (form, restart, wait limit)
     int graph_used = 0;
     std::string err;
 };
@@ -755,17 +755,18 @@ static pslr_status krylov_ensure(pslr_batch *bt, int K) {
     BCK(cudaMalloc(&bt->d_b, sizeof(double) * (size_t)N));
     BCK(cudaMalloc(&bt->d_x, sizeof(double) * (size_t)N));
     // state: doubles first, then ints
-    const size_t nd = (size_t)P * 4                          // bn, rn, hn, relres
+    const size_t nd = 1 + (size_t)P * 4                      // rtol; bn, rn, hn, relres
                       + (size_t)P * ldp * K                  // H
                       + (size_t)P * 2 * K                    // rot
                       + (size_t)P * ldp * 3                  // gam, h1, h2
                       + (size_t)P * K                        // y
                       + (size_t)bt->nchunk * ldp * 2;        // pa, pb
-    const size_t ni = (size_t)P * 4 + 2 + (size_t)bt->nsys;
+    const size_t ni = (size_t)P * 4 + 3 + (size_t)bt->nsys;
     BCK(cudaMalloc(&bt->d_state, sizeof(double) * nd + sizeof(int) * ni));
     BCK(cudaMemset(bt->d_state, 0, sizeof(double) * nd + sizeof(int) * ni));
     double *d = static_cast<double *>(bt->d_state);
     BkState &S = bt->S;
+    S.rtol = d; d += 1;
     S.bn = d; d += P;
     S.rn = d; d += P;
     S.hn = d; d += P;
@@ -785,6 +786,7 @@ static pslr_status krylov_ensure(pslr_batch *bt, int K) {
     S.its = ip; ip += P;
     S.remaining = ip; ip += 1;
     S.skip = ip; ip += 1;
+    S.maxit = ip; ip += 1;
     S.sys_active = ip;
     S.nsys = bt->nsys;
     S.nrhs = bt->nrhs;
@@ -823,7 +825,7 @@ static pslr_status enqueue_cycle(pslr_batch *bt, int form, cudaStream_t st) {
 // The cycle as a CUDA graph (captured on the batch's own stream), or nullptr
 // when capture or instantiation is not available.
 static cudaGraphExec_t cycle_graph(pslr_batch *bt, int form) {
-    const auto key = std::make_tuple(form, bt->S.K, bt->S.rtol, bt->S.maxit, bt->wait_limit);
+    const auto key = std::make_tuple(form, bt->S.K, bt->wait_limit);
     auto it = bt->graphs.find(key);
     if (it != bt->graphs.end()) return it->second;
     cudaGraph_t g = nullptr;
@@ -909,9 +911,9 @@ pslr_status pslr_batch_solve(pslr_batch *bt, const double *b_dev, double *x_dev,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     st = krylov_ensure(bt, restart);
     if (st != PSLR_OK) return st;
-    bt->S.rtol = rtol;
-    bt->S.maxit = maxit;
     const BkState &S = bt->S;
+    BCK(cudaMemcpyAsync(const_cast<double *>(S.rtol), &rtol, sizeof(double), cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(const_cast<int *>(S.maxit), &maxit, sizeof(int), cudaMemcpyHostToDevice, s));
     const int P = bt->nprob, nc = bt->nchunk;
     const int64_t N = bt->n_total;
     const int form = prec == PSLR_FP64 ? 0 : 2;

@@ -174,8 +174,8 @@ __global__ void kb_hessenberg(int j, int nprob, const BkProb *__restrict__ probs
         col[j + 1] = 0.0;
         gam[j + 1] = -sn[j] * gam[j];
         gam[j] = cs[j] * gam[j];
-        const bool stop = fabs(gam[j + 1]) <= S.rtol * S.bn[p] || hn == 0.0 || !(den == den) ||
-                          S.its[p] + j + 1 >= S.maxit || j + 1 == K;
+        const bool stop = fabs(gam[j + 1]) <= *S.rtol * S.bn[p] || hn == 0.0 || !(den == den) ||
+                          S.its[p] + j + 1 >= *S.maxit || j + 1 == K;
         if (stop) S.stop[p] = 1;
         else ++mine;
     }
@@ -279,8 +279,8 @@ __global__ void kb_restart(int first, int nprob, const BkProb *__restrict__ prob
         }
         if (bn == 0.0) cv = 1;
         else if (!finite) cv = 3;
-        else if (rn <= S.rtol * bn) cv = 1;
-        else if (S.its[p] >= S.maxit) cv = 2;
+        else if (rn <= *S.rtol * bn) cv = 1;
+        else if (S.its[p] >= *S.maxit) cv = 2;
         S.conv[p] = cv;
         S.relres[p] = bn > 0.0 ? rn / bn : 0.0;
         S.rn[p] = rn;

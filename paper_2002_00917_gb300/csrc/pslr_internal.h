@@ -236,8 +236,8 @@ struct BkState {
     int *skip;          // [1] no problem running: later launches of the cycle return at once
     int *sys_active;    // nsys: some problem of the system still runs (the apply skips the others)
     int nsys, nrhs;     // problem p belongs to system p / nrhs
-    double rtol;
-    int maxit;
+    const double *rtol;  // [1] device: relative tolerance of this solve
+    const int *maxit;    // [1] device: iteration limit of this solve (both outside the cycle graph)
     int K;              // restart length
 };
 

@@ -193,6 +193,9 @@ def test_batch_solve(dev, prec):
     b = np.concatenate(bs)
     bd = torch.tensor(b, device=dev)
     x = torch.zeros_like(bd)
+    # a first solve with other limits: the cycle graph it captures serves the next one
+    its1, _, st1 = bt.solve(bd, x, rtol=1e-3, restart=20, maxit=1, prec=prec)
+    assert st1 in (pslr.PSLR_OK, pslr.PSLR_ERR_NOT_CONVERGED) and np.all(its1 == 1)
     its, rel, st = bt.solve(bd, x, rtol=1e-8, restart=20, maxit=400, prec=prec)
     assert st == pslr.PSLR_OK, (its, rel)
     assert bt.info["graph"] == 1
