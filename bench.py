@@ -57,7 +57,7 @@ def measured_peaks():
 
 
 APPLY_SOURCES = ("pslr_apply.cu", "pslr_device.cuh", "pslr_internal.h")  # the kernel, its device code, its layout
-BATCH_SOURCES = ("pslr_batch.cu", "pslr_device.cuh", "pslr_internal.h")
+BATCH_SOURCES = ("pslr_batch.cuh", "pslr_device.cuh", "pslr_internal.h")
 
 
 def kernel_source_hash(files=APPLY_SOURCES):
@@ -239,9 +239,14 @@ def run_batch(dev, flush, stream, steps, warmup, seq_stride, solve=True):
         c = pslr.Pslr(s["A"], dims=s["dims"], splits=s["splits"], factor=s["factor"])
         c.build_lowrank(s["m"], s["rank"])
         ctxs.append(c)
-    bt = pslr.Batch(ctxs, nr)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
+    # group size: the autotuner times the FP32 batched apply for a few
+    # requests (0 = the largest group that fits) and keeps the fastest
+    from paper_2002_00917_gb300 import autotune
+
+    group, tune = autotune.tune_group(ctxs, nr, prec=pslr.PSLR_FP32, candidates=(0, 2, 4, 6), steps=3, warmup=2)
+    bt = pslr.Batch(ctxs, nr, group=group)
     info = bt.info
     rng = np.random.default_rng(0)
     bs, xs = [], []
@@ -270,7 +275,8 @@ def run_batch(dev, flush, stream, steps, warmup, seq_stride, solve=True):
     peak, _ = measured_peaks()
     out = {"workload": w["name"], "nsys": info["nsys"], "nrhs": nr, "problems": info["nprob"],
            "n_total": info["n_total"], "work_items": info["items"], "grid": info["grid"],
-           "setup_s": setup_s}
+           "group": info["group"], "groups": info["groups"],
+           "autotune_fp32_ms": {str(k): round(v[1], 3) for k, v in tune.items()}, "setup_s": setup_s}
     for name, bin_ in (("apply_fp64", b), ("apply_fp32", b.float())):
         ms = timed(bin_, torch.empty_like(bin_))
         nb = info["apply_bytes_fp64" if name == "apply_fp64" else "apply_bytes_fp32"]

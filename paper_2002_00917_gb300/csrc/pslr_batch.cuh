@@ -1,4 +1,6 @@
-// Batched PSLR apply for sm_103a: many independent systems of uneven sizes,
+// Batched PSLR apply for sm_103a (device code; pslr_batch_f64.cu,
+// pslr_batch_f32.cu and pslr_batch_f32d.cu instantiate it, one precision form
+// each, for 1..kMaxBatchRhs right-hand sides): many independent systems of uneven sizes,
 // each with up to kMaxBatchRhs right-hand sides, in ONE cooperative launch
 // (Algorithm 3, Eq. 3.24, applied to every system and right-hand side).
 //
@@ -7,7 +9,7 @@
 // lays out each CTA's segment stream; the segments stay where each system's
 // set-up put them.  Within every phase a CTA takes its items one after the
 // other.  For an item it holds all right-hand sides of the subdomain in
-// shared memory (vector k at offset k * stride) and sweeps every level once
+// shared memory (interleaved: entry i of rhs k at i * nrhs + k) and sweeps every level once
 // for all of them: a thread reads its row's record once, issues the loads of
 // all right-hand sides, then their stores, so the right-hand sides give the
 // level step independent work instead of each paying the level latency.
@@ -21,18 +23,78 @@
 // the consumers its items (per-system flags, fixed for the launch).  Local
 // exact-LU factors (row pivoting) are not supported here; the host rejects
 // such systems.
+#pragma once
 #include "pslr_device.cuh"
 
 namespace pslr {
 
 // ---------------------------------------------------- multi-rhs local ops
 
+// The local vectors hold the nr right-hand sides interleaved: entry i of
+// right-hand side k is x[i * nr + k], so the values of one entry for all rhs
+// are adjacent (one vector access for nr = 4 or 2).
+
+template <int NR>
+__device__ __forceinline__ void lds_rhs(uint32_t a, float (&v)[kMaxBatchRhs]) {
+    if constexpr (NR == 4) {
+        const float4 t = lds_f4(a);
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    } else if constexpr (NR == 2) {
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v[0]), "=f"(v[1]) : "r"(a));
+    } else {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) v[k] = lds(a + 4u * k, 0.f);
+    }
+}
+template <int NR>
+__device__ __forceinline__ void sts_rhs(uint32_t a, const float (&v)[kMaxBatchRhs]) {
+    if constexpr (NR == 4) {
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
+                     : "memory");
+    } else if constexpr (NR == 2) {
+        asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v[0]), "f"(v[1]) : "memory");
+    } else {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) sts(a + 4u * k, v[k]);
+    }
+}
+template <int NR>
+__device__ __forceinline__ void lds_rhs(uint32_t a, double (&v)[kMaxBatchRhs]) {
+    if constexpr (NR == 4 || NR == 2) {
+        const double2 t = lds_d2(a);
+        v[0] = t.x;
+        v[1] = t.y;
+        if constexpr (NR == 4) {
+            const double2 u = lds_d2(a + 16u);
+            v[2] = u.x;
+            v[3] = u.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) v[k] = lds(a + 8u * k, 0.0);
+    }
+}
+template <int NR>
+__device__ __forceinline__ void sts_rhs(uint32_t a, const double (&v)[kMaxBatchRhs]) {
+    if constexpr (NR == 4 || NR == 2) {
+        asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v[0]), "d"(v[1]) : "memory");
+        if constexpr (NR == 4)
+            asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a + 16u), "d"(v[2]), "d"(v[3]) : "memory");
+    } else {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) sts(a + 8u * k, v[k]);
+    }
+}
+
 // Work split of a level among the consumer threads.  FP32 (and one rhs): one
-// thread per row, all right-hand sides (their loads issue back to back).
-// FP64 with several rhs: one thread per (row, rhs) pair, so the rhs spread
-// over more warps - on GB300 a warp-wide FP64 instruction occupies its
-// scheduler's FP64 pipe for many cycles whatever the number of active lanes,
-// and a level has few rows (measured on 64 systems x 4 rhs: 5.96 -> 4.63 ms).
+// thread per row, all right-hand sides (one vector load per column).  FP64
+// with several rhs: one thread per (row, rhs) pair, so the rhs spread over
+// more warps - on GB300 a warp-wide FP64 instruction occupies its scheduler's
+// FP64 pipe for many cycles whatever the number of active lanes, and a level
+// has few rows (measured on 64 systems x 4 rhs: 5.96 -> 4.63 ms).
 // Pair u = row * nr + k; thread j takes u = j, j + kConsumers, ...
 struct PairWalk {
     int row, k, drow, dk, nr;
@@ -52,10 +114,39 @@ struct PairWalk {
     }
 };
 
-// One level sweep per segment for nr vectors x + k*xs (k < nr <= kMaxBatchRhs):
-// x_k[r] = (x_k[r] - sum_e T_re x_k[c_e]) (* dinv[r]).
+// Rows of a level in the 7-entry record or tile encodings, one rhs (out of line).
 template <class T>
-__device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int xs, int nr, int nseg, int *err) {
+__device__ __noinline__ void level_row_general_rhs(const char *seg, T *x, int nr, int k, int j) {
+    RowPre<T, uint16_t> g = row_pre<T, uint16_t>(seg, j);
+    if (j < g.n) {
+        T a = row_sub(g, j, x[g.r * nr + k], [&](int col) { return x[col * nr + k]; });
+        if (g.diag) a *= g.dv;
+        x[g.r * nr + k] = a;
+    }
+}
+
+// Rows of a product segment in the general encodings, one rhs (out of line);
+// GLOBAL: src is the system's interface iterate in global memory (rhs k at
+// src + k * ss), else an interleaved shared-memory vector.
+template <class T, bool GLOBAL>
+__device__ __noinline__ void ell_row_general_rhs(const char *seg, T *out, int nr, const T *src, int64_t ss, int k,
+                                                 bool subtract, int j) {
+    using IDX = typename std::conditional<GLOBAL, int32_t, uint16_t>::type;
+    RowPre<T, IDX> q = row_pre<T, IDX>(seg, j);
+    if (j < q.n) {
+        T a;
+        if (GLOBAL) a = -row_sub(q, j, T(0), [&](int col) { return __ldcg(src + k * ss + col); });
+        else a = -row_sub(q, j, T(0), [&](int col) { return src[col * nr + k]; });
+        T &o = out[q.r * nr + k];
+        o = subtract ? o - a : a;
+    }
+}
+
+// One level sweep per segment for the nr interleaved right-hand sides of x:
+// x_k[r] = (x_k[r] - sum_e T_re x_k[c_e]) (* dinv[r]).
+template <class T, int NR>
+__device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int nseg, int *err) {
+    constexpr int nr = NR;
     Ring &R = c.ring;
     int slot = R.slot;
     uint32_t phase = R.phase;
@@ -65,7 +156,7 @@ __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int xs, int nr, in
     uint32_t ptr_s = base_s + (uint32_t)(slot * R.slot_bytes);
     const uint32_t x0s = smem_addr(x);
     constexpr uint32_t ts = sizeof(T);
-    const uint32_t kstep = ts * (uint32_t)xs;
+    const uint32_t es = ts * (uint32_t)nr;  // bytes per entry (all rhs)
     const int j = threadIdx.x;
     for (int L = 0; L < nseg; ++L) {
         if (!mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
@@ -75,42 +166,37 @@ __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int xs, int nr, in
             const bool diag = (h.x >> 24) & kSegDiag;
             for (PairWalk u(j, nr); u.row < n; u.next()) {
                 const Rec3<T> e = rec3_shared<T>(ptr_s, np, u.row);
-                const uint32_t b = x0s + kstep * u.k;
-                const T x0 = lds(b + ts * e.c0, T()), x1 = lds(b + ts * e.c1, T());
-                const T x2 = lds(b + ts * e.c2, T()), xr = lds(b + ts * e.r, T());
+                const uint32_t b = x0s + ts * u.k;
+                const T x0 = lds(b + es * e.c0, T()), x1 = lds(b + es * e.c1, T());
+                const T x2 = lds(b + es * e.c2, T()), xr = lds(b + es * e.r, T());
                 T a = fma_t(-e.v0, x0, xr);
                 a = fma_t(-e.v1, x1, a);
                 a = fma_t(-e.v2, x2, a);
                 if (diag) a *= e.d;
-                sts(b + ts * e.r, a);
+                sts(b + es * e.r, a);
             }
         } else if (((h.y >> 16) & 0xffu) == kRec3) {
             if (j < (int)(h.x & 0xffffu)) {
                 const Rec3<T> e = rec3_shared<T>(ptr_s, (int)(h.y & 0xffffu), j);
                 const bool diag = (h.x >> 24) & kSegDiag;
                 T a0[kMaxBatchRhs], a1[kMaxBatchRhs], a2[kMaxBatchRhs], ar[kMaxBatchRhs];
-#pragma unroll
-                for (int k = 0; k < kMaxBatchRhs; ++k)
-                    if (k < nr) {
-                        const uint32_t b = x0s + kstep * k;
-                        a0[k] = lds(b + ts * e.c0, T());
-                        a1[k] = lds(b + ts * e.c1, T());
-                        a2[k] = lds(b + ts * e.c2, T());
-                        ar[k] = lds(b + ts * e.r, T());
-                    }
+                lds_rhs<NR>(x0s + es * e.c0, a0);
+                lds_rhs<NR>(x0s + es * e.c1, a1);
+                lds_rhs<NR>(x0s + es * e.c2, a2);
+                lds_rhs<NR>(x0s + es * e.r, ar);
 #pragma unroll
                 for (int k = 0; k < kMaxBatchRhs; ++k)
                     if (k < nr) {
                         T a = fma_t(-e.v0, a0[k], ar[k]);
                         a = fma_t(-e.v1, a1[k], a);
                         a = fma_t(-e.v2, a2[k], a);
-                        if (diag) a *= e.d;
-                        sts(x0s + kstep * k + ts * e.r, a);
+                        ar[k] = diag ? a * e.d : a;
                     }
+                sts_rhs<NR>(x0s + es * e.r, ar);
             }
         } else {
             const char *seg = R.base + (ptr_s - base_s);
-            for (int k = 0; k < nr; ++k) level_row_general(seg, x + (size_t)k * xs, j);
+            for (int k = 0; k < nr; ++k) level_row_general_rhs(seg, x, nr, k, j);
         }
         csync();
         if (j == 0) mbar_arrive_cnt(fbar + edelta, kConsumerWarps);
@@ -129,13 +215,15 @@ __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int xs, int nr, in
     R.consumed += nseg;
 }
 
-// ELL product of nseg segments for nr vectors: out_k[row] = sum (assign) or
-// out_k[row] -= sum (subtract), sum = sum_e v_e src_k[c_e]; src in shared
-// memory (local columns) or global memory (GLOBAL, the C_g rows).  Disjoint
-// rows per segment: no CTA barrier between segments, one at the end.
-template <class T, bool GLOBAL>
-__device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, int os, const T *src, int ss, int nr, bool subtract,
-                             int nseg, int *err) {
+// ELL product of nseg segments for the nr interleaved right-hand sides:
+// out_k[row] = sum (assign) or out_k[row] -= sum (subtract), sum = sum_e v_e
+// src_k[c_e]; src interleaved in shared memory (local columns), or global
+// (GLOBAL, the C_g rows: rhs k at src + k * ss).  Disjoint rows per segment:
+// no CTA barrier between segments, one at the end.
+template <class T, bool GLOBAL, int NR>
+__device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, const T *src, int64_t ss, bool subtract, int nseg,
+                                          int *err) {
+    constexpr int nr = NR;
     Ring &R = c.ring;
     int slot = R.slot;
     uint32_t phase = R.phase;
@@ -144,6 +232,7 @@ __device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, int os, const T *sr
     const uint32_t base_s = smem_addr(R.base);
     uint32_t ptr_s = base_s + (uint32_t)(slot * R.slot_bytes);
     constexpr uint32_t ts = sizeof(T);
+    const uint32_t es = ts * (uint32_t)nr;
     const int j = threadIdx.x;
     for (int kseg = 0; kseg < nseg; ++kseg) {
         if (!mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
@@ -153,41 +242,35 @@ __device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, int os, const T *sr
             const uint32_t o0 = smem_addr(out), s0 = smem_addr(src);
             for (PairWalk u(j, nr); u.row < n; u.next()) {
                 const Rec3<T> e = rec3_shared<T>(ptr_s, np, u.row);
-                const uint32_t sb = s0 + ts * (uint32_t)(u.k * ss), ob = o0 + ts * (uint32_t)(u.k * os);
-                T a = e.v0 * lds(sb + ts * e.c0, T());
-                a = fma_t(e.v1, lds(sb + ts * e.c1, T()), a);
-                a = fma_t(e.v2, lds(sb + ts * e.c2, T()), a);
-                if (subtract) a = lds(ob + ts * e.r, T()) - a;
-                sts(ob + ts * e.r, a);
+                const uint32_t sb = s0 + ts * u.k, ob = o0 + ts * u.k;
+                T a = e.v0 * lds(sb + es * e.c0, T());
+                a = fma_t(e.v1, lds(sb + es * e.c1, T()), a);
+                a = fma_t(e.v2, lds(sb + es * e.c2, T()), a);
+                if (subtract) a = lds(ob + es * e.r, T()) - a;
+                sts(ob + es * e.r, a);
             }
         } else if (!GLOBAL && ((h.y >> 16) & 0xffu) == kRec3) {
             if (j < (int)(h.x & 0xffffu)) {
                 const uint32_t o0 = smem_addr(out), s0 = smem_addr(src);
                 const Rec3<T> e = rec3_shared<T>(ptr_s, (int)(h.y & 0xffffu), j);
                 T b0[kMaxBatchRhs], b1[kMaxBatchRhs], b2[kMaxBatchRhs], br[kMaxBatchRhs];
-#pragma unroll
-                for (int k = 0; k < kMaxBatchRhs; ++k)
-                    if (k < nr) {
-                        const uint32_t sb = s0 + ts * (uint32_t)(k * ss);
-                        b0[k] = lds(sb + ts * e.c0, T());
-                        b1[k] = lds(sb + ts * e.c1, T());
-                        b2[k] = lds(sb + ts * e.c2, T());
-                        br[k] = subtract ? lds(o0 + ts * (uint32_t)(k * os + e.r), T()) : T(0);
-                    }
+                lds_rhs<NR>(s0 + es * e.c0, b0);
+                lds_rhs<NR>(s0 + es * e.c1, b1);
+                lds_rhs<NR>(s0 + es * e.c2, b2);
+                if (subtract) lds_rhs<NR>(o0 + es * e.r, br);
 #pragma unroll
                 for (int k = 0; k < kMaxBatchRhs; ++k)
                     if (k < nr) {
                         T a = e.v0 * b0[k];
                         a = fma_t(e.v1, b1[k], a);
                         a = fma_t(e.v2, b2[k], a);
-                        if (subtract) a = br[k] - a;
-                        sts(o0 + ts * (uint32_t)(k * os + e.r), a);
+                        br[k] = subtract ? br[k] - a : a;
                     }
+                sts_rhs<NR>(o0 + es * e.r, br);
             }
         } else {
             const char *seg = R.base + (ptr_s - base_s);
-            for (int k = 0; k < nr; ++k)
-                ell_row_general<T, GLOBAL>(seg, out + (size_t)k * os, src + (size_t)k * ss, subtract, j);
+            for (int k = 0; k < nr; ++k) ell_row_general_rhs<T, GLOBAL>(seg, out, nr, src, ss, k, subtract, j);
         }
         __syncwarp();
         if ((j & 31) == 0) mbar_arrive(fbar + edelta);  // this warp is done with the slot
@@ -235,14 +318,14 @@ __device__ __forceinline__ ItemRange item_range(const BatchSys<T> &S, const Batc
     return it;
 }
 
-template <class T, class VT, class IO>
+template <class T, class VT, class IO, int NR>
 __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const BatchParams<T, IO> P) {
     extern __shared__ __align__(128) char smem[];
     if (P.skip != nullptr && ld_volatile(P.skip) != 0) return;
     if (ld_volatile(P.err) != 0) return;
-    const int nr = P.nrhs;
-    const int xs = P.xs, gs = P.gs;  // per-rhs strides of the group vectors
-    const SmemLayout L = smem_layout(P.slot_bytes, P.ring, nr * xs - 1, nr * gs - 1, sizeof(T), false);
+    constexpr int nr = NR;  // == P.nrhs
+    // group vectors: P.xs interior / P.gs interface entries, nr values each (interleaved)
+    const SmemLayout L = smem_layout(P.slot_bytes, P.ring, nr * P.xs - 1, nr * P.gs - 1, sizeof(T), false);
     Cta<T> c;
     if (!cta_start(c, smem, L, P.ring, P.slot_bytes, P.stream, P.stream_off, P.segbase, P.active)) return;
     const int tid = threadIdx.x;
@@ -259,39 +342,42 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
         const IO *bs = P.b + S.voff;
         for (int t = 0; t < g.n; ++t) {
             const ItemRange it = item_range(S, g, t);
-            for (int kr = 0; kr < nr; ++kr) {
-                const IO *bk = bs + (int64_t)kr * S.n;
-                T *x = c.xi + kr * xs + it.xo, *y = c.si + kr * gs + it.lo;
-                for (int j = tid; j < it.np; j += kConsumers) x[j] = T(bk[S.perm[it.io + j]]);
-                for (int j = tid; j < it.nq; j += kConsumers) y[j] = T(bk[S.perm[S.p + it.go + j]]);
-                if (tid == 0) {
-                    x[it.np] = T(0);
-                    y[it.nq] = T(0);
-                }
+            T *x = c.xi + it.xo * nr, *y = c.si + it.lo * nr;
+            for (int j = tid; j < it.np; j += kConsumers) {
+                const int o = S.perm[it.io + j];
+                for (int kr = 0; kr < nr; ++kr) x[j * nr + kr] = T(bs[(int64_t)kr * S.n + o]);
+            }
+            for (int j = tid; j < it.nq; j += kConsumers) {
+                const int o = S.perm[S.p + it.go + j];
+                for (int kr = 0; kr < nr; ++kr) y[j * nr + kr] = T(bs[(int64_t)kr * S.n + o]);
+            }
+            for (int kr = tid; kr < nr; kr += kConsumers) {
+                x[it.np * nr + kr] = T(0);
+                y[it.nq * nr + kr] = T(0);
             }
         }
         csync();
-        tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB1], P.err);
-        tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB2], P.err);
-        ell_op_multi<T, false>(c, c.si, gs, c.xi, xs, nr, true, g.cnt[kF], P.err);
+        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB1], P.err);
+        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB2], P.err);
+        ell_op_multi<T, false, NR>(c, c.si, c.xi, 0, true, g.cnt[kF], P.err);
         if (S.r == 0) {
-            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC1], P.err);
-            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC2], P.err);
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC1], P.err);
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC2], P.err);
         }
         const VT *V = reinterpret_cast<const VT *>(S.V);
         for (int t = 0; t < g.n; ++t) {
             const ItemRange it = item_range(S, g, t);
-            for (int kr = 0; kr < nr; ++kr) {
-                const T *y = c.si + kr * gs + it.lo;
-                if (S.r > 0)
-                    lowrank_partial(c, V, S.q, S.r, it.go, it.nq, y, S.part + ((int64_t)kr * S.s + it.i) * S.r);
-                T *acc = S.acc + (int64_t)kr * (S.q + 1) + it.go;
-                T *w0 = S.wbuf + (int64_t)kr * 2 * (S.q + 1) + it.go;
-                for (int j = tid; j < it.nq; j += kConsumers) {
-                    acc[j] = y[j];
-                    if (S.r == 0) w0[j] = y[j];
+            const T *y = c.si + it.lo * nr;
+            if (S.r > 0)
+                for (int kr = 0; kr < nr; ++kr)
+                    lowrank_partial(c, V, S.q, S.r, it.go, it.nq, y + kr, S.part + ((int64_t)kr * S.s + it.i) * S.r,
+                                    nr);
+            for (int j = tid; j < it.nq; j += kConsumers)
+                for (int kr = 0; kr < nr; ++kr) {
+                    const T v = y[j * nr + kr];
+                    S.acc[(int64_t)kr * (S.q + 1) + it.go + j] = v;
+                    if (S.r == 0) S.wbuf[(int64_t)kr * 2 * (S.q + 1) + it.go + j] = v;
                 }
-            }
             if (it.i == 0 && tid == 0)  // zero slots of the system's series iterates
                 for (int kr = 0; kr < nr; ++kr) {
                     S.wbuf[(int64_t)kr * 2 * (S.q + 1) + S.q] = T(0);
@@ -323,31 +409,32 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
             const BatchSys<T> &S = P.sys[g.sys];
             if (S.r == 0) continue;
             const VT *V = reinterpret_cast<const VT *>(S.V);
-            for (int kr = 0; kr < nr; ++kr) {
-                for (int j = tid; j < S.r; j += kConsumers) dsh[j] = __ldcg(S.dco + (int64_t)kr * S.r + j);
-                for (int t = 0; t < g.n; ++t) {
-                    const ItemRange it = item_range(S, g, t);
-                    T *y = c.si + kr * gs + it.lo;
-                    const T *acc = S.acc + (int64_t)kr * (S.q + 1) + it.go;
-                    for (int j = tid; j < it.nq; j += kConsumers) y[j] = __ldcg(acc + j);
-                    if (tid == 0) y[it.nq] = T(0);
-                    csync();
-                    lowrank_update(c, V, S.q, S.r, it.go, it.nq, y);
-                }
-            }
-            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC1], P.err);
-            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC2], P.err);
             for (int t = 0; t < g.n; ++t) {
                 const ItemRange it = item_range(S, g, t);
-                for (int kr = 0; kr < nr; ++kr) {
-                    const T *y = c.si + kr * gs + it.lo;
-                    T *acc = S.acc + (int64_t)kr * (S.q + 1) + it.go;
-                    T *w0 = S.wbuf + (int64_t)kr * 2 * (S.q + 1) + it.go;
-                    for (int j = tid; j < it.nq; j += kConsumers) {
-                        w0[j] = y[j];
-                        acc[j] = y[j];
-                    }
+                T *y = c.si + it.lo * nr;
+                for (int j = tid; j < it.nq; j += kConsumers)
+                    for (int kr = 0; kr < nr; ++kr) y[j * nr + kr] = __ldcg(S.acc + (int64_t)kr * (S.q + 1) + it.go + j);
+                for (int kr = tid; kr < nr; kr += kConsumers) y[it.nq * nr + kr] = T(0);
+            }
+            for (int kr = 0; kr < nr; ++kr) {
+                for (int j = tid; j < S.r; j += kConsumers) dsh[j] = __ldcg(S.dco + (int64_t)kr * S.r + j);
+                csync();
+                for (int t = 0; t < g.n; ++t) {
+                    const ItemRange it = item_range(S, g, t);
+                    lowrank_update(c, V, S.q, S.r, it.go, it.nq, c.si + it.lo * nr + kr, nr);
                 }
+            }
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC1], P.err);
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC2], P.err);
+            for (int t = 0; t < g.n; ++t) {
+                const ItemRange it = item_range(S, g, t);
+                const T *y = c.si + it.lo * nr;
+                for (int j = tid; j < it.nq; j += kConsumers)
+                    for (int kr = 0; kr < nr; ++kr) {
+                        const T v = y[j * nr + kr];
+                        S.wbuf[(int64_t)kr * 2 * (S.q + 1) + it.go + j] = v;
+                        S.acc[(int64_t)kr * (S.q + 1) + it.go + j] = v;
+                    }
             }
             csync();
         }
@@ -366,42 +453,38 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
             const int64_t wst = 2 * (int64_t)(S.q + 1);
             const T *wprev = S.wbuf + ((kk - 1) & 1) * (S.q + 1);
             T *wnext = S.wbuf + (kk & 1) * (S.q + 1);
-            const int nx = g.xo[g.n], ng = g.go[g.n];
-            for (int kr = 0; kr < nr; ++kr) {
-                fill(c.xi + kr * xs, nx, T(0));
-                fill(c.si + kr * gs, ng, T(0));
-                for (int t = 0; t < g.n; ++t) {
-                    const ItemRange it = item_range(S, g, t);
-                    T *w = c.wi + kr * gs + it.lo;
-                    const T *src = wprev + kr * wst + it.go;
-                    for (int j = tid; j < it.nq; j += kConsumers) w[j] = __ldcg(src + j);
-                    if (tid == 0) w[it.nq] = T(0);
-                }
+            fill(c.xi, g.xo[g.n] * nr, T(0));
+            fill(c.si, g.go[g.n] * nr, T(0));
+            for (int t = 0; t < g.n; ++t) {
+                const ItemRange it = item_range(S, g, t);
+                T *w = c.wi + it.lo * nr;
+                for (int j = tid; j < it.nq; j += kConsumers)
+                    for (int kr = 0; kr < nr; ++kr) w[j * nr + kr] = __ldcg(wprev + kr * wst + it.go + j);
+                for (int kr = tid; kr < nr; kr += kConsumers) w[it.nq * nr + kr] = T(0);
             }
             csync();
-            ell_op_multi<T, false>(c, c.xi, xs, c.wi, gs, nr, false, g.cnt[kE], P.err);   // E w
-            tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB1], P.err);                         // B^{-1}
-            tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB2], P.err);
-            ell_op_multi<T, false>(c, c.si, gs, c.xi, xs, nr, false, g.cnt[kF], P.err);   // F
+            ell_op_multi<T, false, NR>(c, c.xi, c.wi, 0, false, g.cnt[kE], P.err);   // E w
+            tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB1], P.err);                       // B^{-1}
+            tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB2], P.err);
+            ell_op_multi<T, false, NR>(c, c.si, c.xi, 0, false, g.cnt[kF], P.err);   // F
             if (!waited) {
                 ok = grid_wait(c, P.bar, P.err, P.wait_limit);
                 waited = true;
                 if (!ok) goto abort;
             }
-            ell_op_multi<T, true>(c, c.si, gs, wprev, (int)wst, nr, true, g.cnt[kCg], P.err);  // - C_g w
-            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC1], P.err);                               // C0^{-1}
-            tri_sweep_multi(c, c.si, gs, nr, g.cnt[kC2], P.err);
+            ell_op_multi<T, true, NR>(c, c.si, wprev, wst, true, g.cnt[kCg], P.err);  // - C_g w
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC1], P.err);                       // C0^{-1}
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC2], P.err);
             for (int t = 0; t < g.n; ++t) {
                 const ItemRange it = item_range(S, g, t);
-                for (int kr = 0; kr < nr; ++kr) {
-                    const T *y = c.si + kr * gs + it.lo;
-                    T *acc = S.acc + (int64_t)kr * (S.q + 1) + it.go;
-                    T *wn = wnext + kr * wst + it.go;
-                    for (int j = tid; j < it.nq; j += kConsumers) {
-                        wn[j] = y[j];
-                        acc[j] = __ldcg(acc + j) + y[j];
+                const T *y = c.si + it.lo * nr;
+                for (int j = tid; j < it.nq; j += kConsumers)
+                    for (int kr = 0; kr < nr; ++kr) {
+                        const T v = y[j * nr + kr];
+                        T *acc = S.acc + (int64_t)kr * (S.q + 1) + it.go + j;
+                        wnext[kr * wst + it.go + j] = v;
+                        *acc = __ldcg(acc) + v;
                     }
-                }
             }
             csync();
         }
@@ -419,30 +502,33 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
         const IO *bs = P.b + S.voff;
         for (int t = 0; t < g.n; ++t) {
             const ItemRange it = item_range(S, g, t);
-            for (int kr = 0; kr < nr; ++kr) {
-                const IO *bk = bs + (int64_t)kr * S.n;
-                T *x = c.xi + kr * xs + it.xo, *w = c.wi + kr * gs + it.lo;
-                const T *acc = S.acc + (int64_t)kr * (S.q + 1) + it.go;
-                for (int j = tid; j < it.nq; j += kConsumers) w[j] = __ldcg(acc + j);
-                for (int j = tid; j < it.np; j += kConsumers) x[j] = T(bk[S.perm[it.io + j]]);
-                if (tid == 0) {
-                    w[it.nq] = T(0);
-                    x[it.np] = T(0);
-                }
+            T *x = c.xi + it.xo * nr, *w = c.wi + it.lo * nr;
+            for (int j = tid; j < it.nq; j += kConsumers)
+                for (int kr = 0; kr < nr; ++kr) w[j * nr + kr] = __ldcg(S.acc + (int64_t)kr * (S.q + 1) + it.go + j);
+            for (int j = tid; j < it.np; j += kConsumers) {
+                const int o = S.perm[it.io + j];
+                for (int kr = 0; kr < nr; ++kr) x[j * nr + kr] = T(bs[(int64_t)kr * S.n + o]);
+            }
+            for (int kr = tid; kr < nr; kr += kConsumers) {
+                w[it.nq * nr + kr] = T(0);
+                x[it.np * nr + kr] = T(0);
             }
         }
         csync();
-        ell_op_multi<T, false>(c, c.xi, xs, c.wi, gs, nr, true, g.cnt[kE], P.err);
-        tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB1], P.err);
-        tri_sweep_multi(c, c.xi, xs, nr, g.cnt[kB2], P.err);
+        ell_op_multi<T, false, NR>(c, c.xi, c.wi, 0, true, g.cnt[kE], P.err);
+        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB1], P.err);
+        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB2], P.err);
         IO *zs = P.z + S.voff;
         for (int t = 0; t < g.n; ++t) {
             const ItemRange it = item_range(S, g, t);
-            for (int kr = 0; kr < nr; ++kr) {
-                IO *zk = zs + (int64_t)kr * S.n;
-                const T *x = c.xi + kr * xs + it.xo, *w = c.wi + kr * gs + it.lo;
-                for (int j = tid; j < it.np; j += kConsumers) zk[S.perm[it.io + j]] = IO(x[j]);
-                for (int j = tid; j < it.nq; j += kConsumers) zk[S.perm[S.p + it.go + j]] = IO(w[j]);
+            const T *x = c.xi + it.xo * nr, *w = c.wi + it.lo * nr;
+            for (int j = tid; j < it.np; j += kConsumers) {
+                const int o = S.perm[it.io + j];
+                for (int kr = 0; kr < nr; ++kr) zs[(int64_t)kr * S.n + o] = IO(x[j * nr + kr]);
+            }
+            for (int j = tid; j < it.nq; j += kConsumers) {
+                const int o = S.perm[S.p + it.go + j];
+                for (int kr = 0; kr < nr; ++kr) zs[(int64_t)kr * S.n + o] = IO(w[j * nr + kr]);
             }
         }
         csync();
@@ -450,47 +536,6 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
     return;
 abort:
     consumers_abort_drain(c);
-}
-
-// ------------------------------------------------------------------ launchers
-
-template <class T, class VT, class IO>
-static cudaError_t launch_batch_t(const void *prm, int smem, cudaStream_t st) {
-    const BatchParams<T, IO> &P = *static_cast<const BatchParams<T, IO> *>(prm);
-    auto kern = pslr_batch_apply_kernel<T, VT, IO>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    void *args[] = {const_cast<BatchParams<T, IO> *>(&P)};
-    return cudaLaunchCooperativeKernel((const void *)kern, dim3(P.grid), dim3(kThreads), args, smem, st);
-}
-
-// form 0: FP64 in and out; 1: FP32 in and out (BF16 V); 2: FP32 arithmetic on FP64 in and out.
-cudaError_t launch_batch(int form, const void *params, int smem, cudaStream_t st) {
-    switch (form) {
-    case 0: return launch_batch_t<double, double, double>(params, smem, st);
-    case 1: return launch_batch_t<float, __nv_bfloat16, float>(params, smem, st);
-    case 2: return launch_batch_t<float, __nv_bfloat16, double>(params, smem, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template <class K>
-static int coresident(K kern, int smem) {
-    int dev = 0, nsm = 0, per = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem) != cudaSuccess) return 0;
-    return per * nsm;
-}
-
-// Largest cooperative grid of the batched kernel at this shared-memory size
-// (the smaller over the forms that share the layout).
-int max_coresident_batch(int smem, bool fp32) {
-    if (!fp32) return coresident(pslr_batch_apply_kernel<double, double, double>, smem);
-    const int a = coresident(pslr_batch_apply_kernel<float, __nv_bfloat16, float>, smem);
-    const int b = coresident(pslr_batch_apply_kernel<float, __nv_bfloat16, double>, smem);
-    return a < b ? a : b;
 }
 
 }  // namespace pslr

@@ -1,5 +1,5 @@
 // Host side of the batched entry points (include/pslr.h, "batch"): work-item
-// assignment and segment streams of the batched apply (pslr_batch.cu), and
+// assignment and segment streams of the batched apply (pslr_batch.cuh), and
 // the batched FGMRES driver over the kernels of pslr_bkrylov.cu, with each
 // restart cycle captured once as a CUDA graph and replayed.
 #include <cuda_runtime.h>
@@ -20,8 +20,30 @@
 #include "pslr_sys.h"
 
 namespace pslr {
-cudaError_t launch_batch(int form, const void *params, int smem, cudaStream_t st);
-int max_coresident_batch(int smem, bool fp32);
+cudaError_t launch_batch_f64(const void *params, int smem, cudaStream_t st);
+cudaError_t launch_batch_f32(const void *params, int smem, cudaStream_t st);
+cudaError_t launch_batch_f32d(const void *params, int smem, cudaStream_t st);
+int coresident_batch_f64(int smem, int nrhs);
+int coresident_batch_f32(int smem, int nrhs);
+int coresident_batch_f32d(int smem, int nrhs);
+
+// form 0: FP64 in and out; 1: FP32 in and out (BF16 V); 2: FP32 arithmetic on FP64 in and out.
+static cudaError_t launch_batch(int form, const void *params, int smem, cudaStream_t st) {
+    switch (form) {
+    case 0: return launch_batch_f64(params, smem, st);
+    case 1: return launch_batch_f32(params, smem, st);
+    case 2: return launch_batch_f32d(params, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Largest cooperative grid of the batched kernel at this shared-memory size
+// (the smaller over the forms that share the layout).
+static int max_coresident_batch(int smem, bool fp32, int nrhs) {
+    if (!fp32) return coresident_batch_f64(smem, nrhs);
+    const int a = coresident_batch_f32(smem, nrhs), b = coresident_batch_f32d(smem, nrhs);
+    return a < b ? a : b;
+}
 void bk_spmv_dots(int nchunk, int j, const BkChunk *ch, const BkProb *pr, const BkSys *sys, const double *z,
                   double *w, const double *V, int64_t ld, const BkState &S, cudaStream_t st);
 void bk_update(int nchunk, int j, const BkChunk *ch, const BkProb *pr, double *w, const double *V, int64_t ld,
@@ -464,7 +486,7 @@ static pslr_status batch_build(pslr_batch *bt) {
         if (bt->ring[prec] < 2)
             return bfail(bt, PSLR_ERR_TOO_LARGE, "batch: no room for the segment ring (%d-byte slots)", sb);
         bt->smem[prec] = smem_layout(sb, bt->ring[prec], nr * xs - 1, nr * gs - 1, ts, false).total;
-        const int g = max_coresident_batch(bt->smem[prec], prec == 1);
+        const int g = max_coresident_batch(bt->smem[prec], prec == 1, nr);
         if (g < 1) return bfail(bt, PSLR_ERR_CUDA, "batch: the apply kernel cannot be made resident");
         grid = std::min(grid, g);
         bt->ngroups[prec] = (int)groups[prec].size();

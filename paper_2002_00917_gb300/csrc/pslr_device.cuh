@@ -1,5 +1,5 @@
 // Device building blocks shared by the persistent kernels (pslr_apply.cu,
-// pslr_batch.cu): PTX wrappers (mbarrier, cp.async.bulk, named barriers,
+// pslr_batch.cuh): PTX wrappers (mbarrier, cp.async.bulk, named barriers,
 // explicit shared-memory accesses), the producer warp that streams segments
 // into the shared-memory ring, the consumers' ring cursor and waits, the
 // sense-reversing grid barrier, the level-sweep and ELL kernels-within-a-
@@ -730,18 +730,19 @@ __device__ __forceinline__ Counts counts_of(const int32_t *cnt, int i) {
     return k;
 }
 
-// Partial dots part[i*r + c] = sum_j V[go + j, c] * y[j] over this subdomain,
-// eight columns at a time so each thread has many independent loads in flight.
+// Partial dots part[i*r + c] = sum_j V[go + j, c] * y[j * ys] over this
+// subdomain, eight columns at a time so each thread has many independent loads
+// in flight.
 template <class T, class VT>
 __device__ void lowrank_partial(Cta<T> &c, const VT *V, int q, int r, int go, int nq, const T *y,
-                                T *part_i) {
+                                T *part_i, int ys = 1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int c0 = 0; c0 < r; c0 += 8) {
         T a[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) a[k] = T(0);
         for (int j = threadIdx.x; j < nq; j += kConsumers) {
-            const T yj = y[j];
+            const T yj = y[j * ys];
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 if (c0 + k < r) a[k] = fma_t(T(load_v(V, (int64_t)(c0 + k) * q + go + j)), yj, a[k]);
@@ -792,14 +793,14 @@ __device__ void lowrank_coeffs(Cta<T> &c, const T *part, const T *G, int s, int 
     csync();
 }
 
-// y[j] += sum_c V[go + j, c] d[c]
+// y[j * ys] += sum_c V[go + j, c] d[c]
 template <class T, class VT>
-__device__ void lowrank_update(Cta<T> &c, const VT *V, int q, int r, int go, int nq, T *y) {
+__device__ void lowrank_update(Cta<T> &c, const VT *V, int q, int r, int go, int nq, T *y, int ys = 1) {
     const T *d = c.red + (kConsumers / 32) * kMaxRank + kMaxRank;
     for (int j = threadIdx.x; j < nq; j += kConsumers) {
-        T a = y[j];
+        T a = y[j * ys];
         for (int col = 0; col < r; ++col) a = fma_t(T(load_v(V, (int64_t)col * q + go + j)), d[col], a);
-        y[j] = a;
+        y[j * ys] = a;
     }
     csync();
 }

@@ -145,7 +145,7 @@ struct ErrParams {
     long long wait_limit;
 };
 
-// Batched apply (pslr_batch.cu): per-system parameters and launch parameters.
+// Batched apply (pslr_batch.cuh): per-system parameters and launch parameters.
 constexpr int kMaxBatchRhs = 4;             // right-hand sides per system in one batched launch
 constexpr int kMaxGroup = 8;                // subdomains of one system swept in lockstep by one CTA
 
