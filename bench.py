@@ -281,7 +281,7 @@ def run_batch(dev, flush, stream, steps, warmup, seq_stride, solve=True):
         ms = timed(bin_, torch.empty_like(bin_))
         nb = info["apply_bytes_fp64" if name == "apply_fp64" else "apply_bytes_fp32"]
         out[name] = {"ms": ms, "GB/s": nb / ms / 1e6, "frac": nb / ms / 1e6 / peak, "bytes_per_launch": nb,
-                     "traffic": committed_traffic(w["name"], "fp64", BATCH_SOURCES) if name == "apply_fp64" else None}
+                     "traffic": committed_traffic(w["name"], name[len("apply_"):], BATCH_SOURCES)}
     if not solve:
         bt.close()
         for c in ctxs:
