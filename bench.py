@@ -56,8 +56,8 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-APPLY_SOURCES = ("pslr_apply.cu", "pslr_device.cuh", "pslr_internal.h")  # the kernel, its device code, its layout
-BATCH_SOURCES = ("pslr_batch.cuh", "pslr_device.cuh", "pslr_internal.h")
+APPLY_SOURCES = ("pslr_apply.cu", "pslr_device.cuh", "pslr_internal.h", "pslr_reduce.cuh")  # the kernel, its device code, its layout
+BATCH_SOURCES = ("pslr_batch.cuh", "pslr_device.cuh", "pslr_internal.h", "pslr_reduce.cuh")
 
 
 def kernel_source_hash(files=APPLY_SOURCES):

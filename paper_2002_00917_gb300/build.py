@@ -23,6 +23,7 @@ SOURCES = ["pslr_apply.cu", "pslr_krylov.cu", "pslr_host.cpp", "pslr_noalloc.cu"
            "pslr_batch_f32.cu", "pslr_batch_f32d.cu", "pslr_bkrylov.cu", "pslr_batch_host.cpp"]
 HEADERS = [os.path.join(CSRC, "pslr_internal.h"), os.path.join(CSRC, "pslr_device.cuh"),
            os.path.join(CSRC, "pslr_sys.h"), os.path.join(CSRC, "pslr_batch.cuh"),
+           os.path.join(CSRC, "pslr_reduce.cuh"),
            os.path.join(ROOT, "include", "pslr.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -12,6 +12,7 @@
 #include <type_traits>
 
 #include "pslr_internal.h"
+#include "pslr_reduce.cuh"
 
 namespace pslr {
 
@@ -747,12 +748,8 @@ __device__ void lowrank_partial(Cta<T> &c, const VT *V, int q, int r, int go, in
             for (int k = 0; k < 8; ++k)
                 if (c0 + k < r) a[k] = fma_t(T(load_v(V, (int64_t)(c0 + k) * q + go + j)), yj, a[k]);
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            T v = a[k];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && c0 + k < r) c.red[warp * kMaxRank + c0 + k] = v;
-        }
+        const T v = warp_reduce8(a);
+        if ((lane & 3) == 0 && c0 + (lane >> 2) < r) c.red[warp * kMaxRank + c0 + (lane >> 2)] = v;
     }
     csync();
     for (int col = threadIdx.x; col < r; col += kConsumers) {

@@ -292,3 +292,25 @@ def test_batch_degenerate_systems(dev, group, nrhs):
         for j in range(nrhs):
             r2, rinf = _rel(zk[:, j], orc.apply(np.ascontiguousarray(bk[:, j])))
             assert r2 <= TOL64 and rinf <= TOL64, (w["A"].n, j, r2, rinf)
+
+
+def test_autotune_group_picks_a_candidate_and_stays_exact(dev):
+    """The group-size autotuner times each candidate and returns the fastest;
+    the batch built with its choice still matches the oracle."""
+    from paper_2002_00917_gb300 import autotune, pslr
+
+    sy = _systems(SYSTEMS)
+    ctxs = [c for _, c, _ in sy]
+    best, table = autotune.tune_group(ctxs, 2, prec=pslr.PSLR_FP64, candidates=(1, 2, 0), steps=3, warmup=1)
+    assert best in (1, 2, 0) and set(table) == {1, 2, 0}
+    assert all(ms > 0 for _, ms in table.values())
+    bt = pslr.Batch(ctxs, 2, group=best)
+    b = np.random.default_rng(19).uniform(-1, 1, bt.info["n_total"])
+    bd = torch.tensor(b, device=dev)
+    zd = torch.zeros_like(bd)
+    bt.apply(bd, zd)
+    bt.sync()
+    for (w, ctx, orc), bk, zk in zip(sy, _split(bt, b), _split(bt, zd.cpu().numpy())):
+        for j in range(2):
+            r2, rinf = _rel(zk[:, j], orc.apply(np.ascontiguousarray(bk[:, j])))
+            assert r2 <= TOL64 and rinf <= TOL64
