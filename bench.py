@@ -146,7 +146,8 @@ def workload_by_name(name):
 
 def time_oracle_applies(w, ctx_lowrank, budget_s):
     """The FP64 C oracle as it stands, single-threaded, on a bounded number of
-    applies of the same workload.  Returns (seconds per apply, applies)."""
+    applies of the same workload.  Returns (seconds per apply, applies, the
+    oracle's z = M^{-1} b for the bench's right-hand side)."""
     import oracle as O
 
     orc = O.from_workload(w)
@@ -158,7 +159,7 @@ def time_oracle_applies(w, ctx_lowrank, budget_s):
     from pslr_inputs import generators as Gen
 
     b, _ = Gen.uniform_rhs(w["A"], 0)
-    orc.apply(b)  # warm
+    z = orc.apply(b)  # warm
     t0 = time.perf_counter()
     k = 0
     while True:
@@ -166,7 +167,7 @@ def time_oracle_applies(w, ctx_lowrank, budget_s):
         k += 1
         if time.perf_counter() - t0 >= budget_s:
             break
-    return (time.perf_counter() - t0) / k, k
+    return (time.perf_counter() - t0) / k, k, z
 
 
 def run_reference(args):
@@ -472,8 +473,12 @@ def main():
     res = None
     if rank == 0:
         V, H, G = ctx.get_lowrank()
-        sec, napp = time_oracle_applies(w, (V, H, G), args.cpu_budget)
+        sec, napp, z_orc = time_oracle_applies(w, (V, H, G), args.cpu_budget)
         cpu_value = bytes64 / sec / 1e9
+        # every GPU apply above ran on the same b: its result against the FP64 oracle's
+        nz = np.linalg.norm(z_orc)
+        err64 = float(np.linalg.norm(zd.cpu().numpy() - z_orc) / nz)
+        err32 = float(np.linalg.norm(zf.double().cpu().numpy() - z_orc) / nz)
         traffic = committed_traffic(w["name"], "fp64")
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -487,9 +492,10 @@ def main():
                          "frac": value / world / peak, "peak_kind": peak_kind + " (burst copy)",
                          "traffic": traffic, "bytes_per_launch": bytes64,
                          "launch_us": 1e6 * t64 / args.steps},
+            "rel_err_vs_fp64_oracle": err64,
             "fp32_apply": {"value": value32, "unit": UNIT, "frac": value32 / world / peak,
                            "bytes_per_launch": bytes32, "launch_us": 1e6 * t32 / args.steps,
-                           "dtype": "f32 (BF16 V)"},
+                           "dtype": "f32 (BF16 V)", "rel_err_vs_fp64_oracle": err32},
             "fgmres": fg,
             "batch": batch,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w["A"].n,
