@@ -417,9 +417,7 @@ struct pslr_ctx {
     // Krylov workspace (allocated on demand)
     int kr_restart = 0;
     double *d_kV = nullptr, *d_kZ = nullptr, *d_kw = nullptr, *d_kr = nullptr, *d_kH = nullptr;
-    double *d_krot = nullptr, *d_kgam = nullptr, *d_kh1 = nullptr, *d_kh2 = nullptr, *d_kscal = nullptr;
-    double *d_kpart = nullptr;
-    unsigned *d_kticket = nullptr;
+    double *d_krot = nullptr, *d_kgam = nullptr;
     int *d_kstate = nullptr, *d_kskip = nullptr;
     float *d_kf_in = nullptr, *d_kf_out = nullptr;
     double *d_eab = nullptr;  // E_rr scratch 2(q+1)
@@ -464,13 +462,10 @@ void free_opset(OpSetHost &o) {
 
 void free_krylov(pslr_ctx *c) {
     for (void *p : {(void *)c->d_kV, (void *)c->d_kZ, (void *)c->d_kw, (void *)c->d_kr, (void *)c->d_kH,
-                    (void *)c->d_krot, (void *)c->d_kgam, (void *)c->d_kh1, (void *)c->d_kh2,
-                    (void *)c->d_kscal, (void *)c->d_kpart, (void *)c->d_kticket, (void *)c->d_kstate,
-                    (void *)c->d_kskip, (void *)c->d_kf_in, (void *)c->d_kf_out})
+                    (void *)c->d_krot, (void *)c->d_kgam, (void *)c->d_kstate, (void *)c->d_kskip,
+                    (void *)c->d_kf_in, (void *)c->d_kf_out})
         cfree(p);
     c->d_kV = c->d_kZ = c->d_kw = c->d_kr = c->d_kH = c->d_krot = c->d_kgam = nullptr;
-    c->d_kh1 = c->d_kh2 = c->d_kscal = c->d_kpart = nullptr;
-    c->d_kticket = nullptr;
     c->d_kstate = c->d_kskip = nullptr;
     c->d_kf_in = c->d_kf_out = nullptr;
     c->kr_restart = 0;

@@ -282,7 +282,9 @@ class Batch:
     Batched vectors are 1-D device tensors of ``info["n_total"]`` elements:
     the systems in order, each an n_k x nrhs column-major block;
     :meth:`offsets` gives the blocks' starts.  The contexts must outlive the
-    batch; the batch keeps references to them."""
+    batch; the batch keeps references to them.  ``group``: subdomains of one
+    system a CTA sweeps in lockstep (0: the largest that fits; see
+    :func:`paper_2002_00917_gb300.autotune.tune_group`)."""
 
     def __init__(self, systems, nrhs, group=0):
         lib = load()
