@@ -153,7 +153,7 @@ def test_apply_equals_block_formula(kind, dims, splits, factor, m, r):
 def test_m0_r0_is_block_jacobi_schur_preconditioner():
     """m = 0, r = 0: S is replaced by C0 alone, so M is the block-triangular
     factorisation [[B, 0], [F, C0]] [[I, B^{-1}E], [0, I]] with the interface
-    block solved block-diagonally (spec reduction of the method)."""
+    block solved block-diagonally (the plain block-diagonal Schur preconditioner)."""
     w, o, D, Es = _ops("lap", (12, 10), (3, 2), 1)
     o.set_lowrank(0, None, None)
     p, q = o.p, o.q
