@@ -144,6 +144,23 @@ def workload_by_name(name):
     return C.WORKLOADS[name]()
 
 
+def replica_aggregate(seconds, units_per_rank, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank processed
+    units_per_rank units in its own `seconds` (one value or a list); the job
+    took the slowest rank's time, so the times are max-reduced over ranks and
+    the value is world * units_per_rank / time.  Returns (values, times)."""
+    import torch
+
+    ts = [float(v) for v in (seconds if isinstance(seconds, (list, tuple)) else [seconds])]
+    world = 1
+    if dist is not None:
+        world = dist.get_world_size()
+        tt = torch.tensor(ts, dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ts = tt.tolist()
+    return [world * units_per_rank / t for t in ts], ts
+
+
 def time_oracle_applies(w, ctx_lowrank, budget_s):
     """The FP64 C oracle as it stands, single-threaded, on a bounded number of
     applies of the same workload.  Returns (seconds per apply, applies, the
@@ -409,14 +426,9 @@ def main():
     clk = ClockSampler(local).__enter__()  # sampled over every timed region of the line
     ms64 = timed_applies(bd, zd, args.steps, args.warmup)
     ms32 = timed_applies(bf, zf, args.steps, args.warmup)
-    t64 = sum(ms64) / 1e3
-    t32 = sum(ms32) / 1e3
-    if dist:
-        tt = torch.tensor([t64, t32], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t64, t32 = tt.tolist()
-    value = world * args.steps * bytes64 / t64 / 1e9
-    value32 = world * args.steps * bytes32 / t32 / 1e9
+    (runs64, runs32), (t64, t32) = replica_aggregate([sum(ms64) / 1e3, sum(ms32) / 1e3], args.steps, dist, dev)
+    value = runs64 * bytes64 / 1e9
+    value32 = runs32 * bytes32 / 1e9
     peak, peak_kind = measured_peaks()
 
     # end to end: host (pinned) b -> device -> apply -> host z, through the C ABI
@@ -437,11 +449,8 @@ def main():
         te2e += time.perf_counter() - c0
         assert st == 0, st
     clk.__exit__(None, None, None)
-    if dist:
-        tt = torch.tensor([te2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te2e = tt.item()
-    e2e_value = world * args.steps * bytes64 / te2e / 1e9
+    (runs_e2e,), (te2e,) = replica_aggregate(te2e, args.steps, dist, dev)
+    e2e_value = runs_e2e * bytes64 / 1e9
 
     # FGMRES to 1e-8 with the FP64 and the FP32 preconditioner: restart 40 (the
     # workload's setting) and restart 120 (a longer Krylov space, for problems
