@@ -37,7 +37,7 @@ void launch_cgs_pass(int n, int k, const double *V, int64_t ld, double *w, const
                      double *part, double *res, unsigned *ticket, const int32_t *rp, const int32_t *ci,
                      const double *av, const double *z, const int *skip, cudaStream_t st);
 void launch_hessenberg(int j, const double *h1, const double *h2, const double *wn2, double *H, int ldh,
-                       double *hn, int givens, double *rot, double *gam, double tol_abs, int *state,
+                       double *hn, int givens, double *rot, double *gam, const double *tol_abs, int *state,
                        int *skip, cudaStream_t st);
 void launch_normalize(int n, const double *w, double *v, const double *hn, const int *skip,
                       cudaStream_t st);
@@ -387,6 +387,14 @@ struct OpSetHost {
     std::map<std::string, StreamDev> streams;  // keyed by launch shape
 };
 
+// Krylov workspace for vectors of length len and up to kcols basis columns:
+// Gram-Schmidt partial sums, coefficients, norms and reduction tickets.
+struct KWork {
+    double *part = nullptr, *h1 = nullptr, *h2 = nullptr, *wn2 = nullptr, *hn = nullptr;
+    unsigned *ticket = nullptr;
+    int nblk = 0;
+};
+
 struct pslr_ctx {
     int n = 0, s = 0, p = 0, q = 0, factor = 0;
     uint64_t seed = 0;
@@ -414,8 +422,12 @@ struct pslr_ctx {
     unsigned *d_bar = nullptr;
     int *d_err = nullptr;
     long long wait_limit = 1ll << 22;
-    // Krylov workspace (allocated on demand)
+    // Krylov workspace (allocated on demand) and the captured restart cycles
     int kr_restart = 0;
+    KWork kw;
+    double *d_ktol = nullptr;  // FGMRES absolute tolerance rtol ||b||
+    cudaStream_t kcap = nullptr;
+    std::map<std::pair<int, int>, cudaGraphExec_t> kgraphs;  // keyed by (precision, direction)
     double *d_kV = nullptr, *d_kZ = nullptr, *d_kw = nullptr, *d_kr = nullptr, *d_kH = nullptr;
     double *d_krot = nullptr, *d_kgam = nullptr;
     int *d_kstate = nullptr, *d_kskip = nullptr;
@@ -460,14 +472,27 @@ void free_opset(OpSetHost &o) {
     o = OpSetHost();
 }
 
+// The captured FGMRES cycles hold the apply's launch parameters (low-rank
+// pointers, wait limit) and the Krylov workspace: drop them whenever either
+// changes.
+void drop_graphs(pslr_ctx *c) {
+    for (auto &kv : c->kgraphs) cudaGraphExecDestroy(kv.second);
+    c->kgraphs.clear();
+}
+
 void free_krylov(pslr_ctx *c) {
+    drop_graphs(c);
+    KWork &W = c->kw;
     for (void *p : {(void *)c->d_kV, (void *)c->d_kZ, (void *)c->d_kw, (void *)c->d_kr, (void *)c->d_kH,
                     (void *)c->d_krot, (void *)c->d_kgam, (void *)c->d_kstate, (void *)c->d_kskip,
-                    (void *)c->d_kf_in, (void *)c->d_kf_out})
+                    (void *)c->d_kf_in, (void *)c->d_kf_out, (void *)c->d_ktol, (void *)W.part, (void *)W.h1,
+                    (void *)W.h2, (void *)W.wn2, (void *)W.hn, (void *)W.ticket})
         cfree(p);
     c->d_kV = c->d_kZ = c->d_kw = c->d_kr = c->d_kH = c->d_krot = c->d_kgam = nullptr;
     c->d_kstate = c->d_kskip = nullptr;
     c->d_kf_in = c->d_kf_out = nullptr;
+    c->d_ktol = nullptr;
+    W = KWork();
     c->kr_restart = 0;
 }
 
@@ -478,6 +503,7 @@ void free_lowrank(pslr_ctx *c) {
     c->d_part = nullptr;
     c->r = 0;
     ++c->lr_gen;
+    drop_graphs(c);
     c->V.clear(); c->H.clear(); c->G.clear();
 }
 
@@ -620,6 +646,7 @@ void pslr_destroy(pslr_ctx *c) {
         for (auto &o : d) free_opset(o);
     free_krylov(c);
     free_lowrank(c);
+    if (c->kcap) cudaStreamDestroy(c->kcap);
     for (void *p : {(void *)c->d_perm, (void *)c->d_ioff, (void *)c->d_goff, (void *)c->d_bpiv,
                     (void *)c->d_cpiv, (void *)c->d_rp, (void *)c->d_ci, (void *)c->d_rpT, (void *)c->d_ciT,
                     (void *)c->d_av, (void *)c->d_avT, (void *)c->d_wbuf, (void *)c->d_acc, (void *)c->d_bar,
@@ -1197,6 +1224,7 @@ pslr_status pslr_apply_host(pslr_ctx *c, const void *b_host, void *z_host, int32
 int64_t pslr_set_wait_limit(pslr_ctx *c, int64_t polls) {
     if (!c) return -1;
     int64_t old = c->wait_limit;
+    if (polls != old) drop_graphs(c);
     c->wait_limit = polls;
     return old;
 }
@@ -1323,6 +1351,7 @@ static bool compute_G(int r, const std::vector<double> &H, std::vector<double> &
 static pslr_status install_lowrank(pslr_ctx *c, int m, int r, const std::vector<double> &G) {
     const int q = c->q;
     ++c->lr_gen;
+    drop_graphs(c);
     c->m = m;
     c->r = r;
     c->G = G;
@@ -1378,13 +1407,6 @@ pslr_status pslr_get_lowrank(const pslr_ctx *c, double *V, double *H, double *G)
 }
 
 }  // extern "C"
-
-// Krylov workspace for vectors of length len and up to kcols basis columns.
-struct KWork {
-    double *part = nullptr, *h1 = nullptr, *h2 = nullptr, *wn2 = nullptr, *hn = nullptr;
-    unsigned *ticket = nullptr;
-    int nblk = 0;
-};
 
 static pslr_status kwork_alloc(pslr_ctx *c, KWork &W, int len, int kcols) {
     W.nblk = krylov_blocks(len);
@@ -1579,8 +1601,67 @@ static pslr_status krylov_alloc(pslr_ctx *c, int restart) {
     CK(cudaMalloc(&c->d_kf_out, sizeof(float) * n));
     CK(cudaMalloc(&c->d_kstate, sizeof(int) * 2));
     CK(cudaMalloc(&c->d_kskip, sizeof(int)));
+    CK(cudaMalloc(&c->d_ktol, sizeof(double)));
+    pslr_status ks = kwork_alloc(c, c->kw, (int)n, restart + 1);
+    if (ks != PSLR_OK) return ks;
+    if (!c->kcap) CK(cudaStreamCreateWithFlags(&c->kcap, cudaStreamNonBlocking));
     c->kr_restart = restart;
     return PSLR_OK;
+}
+
+// The Arnoldi steps j = 0 .. k-1 of one restart cycle (Section 4): apply the
+// preconditioner to v_j (FP32 form through a conversion on either side),
+// orthogonalise A z_j against V by CGS2, update H, the Givens rotations and
+// gamma, and normalise v_{j+1}.  Once the Hessenberg kernel meets the
+// tolerance it raises the skip flag and every later kernel of the cycle
+// returns at once, so a full cycle can be enqueued (or replayed) blind.
+static pslr_status enqueue_arnoldi(pslr_ctx *c, int j0, int j1, int prec, int dir, cudaStream_t st) {
+    const int n = c->n, k = c->kr_restart;
+    const int32_t *rp = dir ? c->d_rpT : c->d_rp, *ci = dir ? c->d_ciT : c->d_ci;
+    const double *av = dir ? c->d_avT : c->d_av;
+    KWork &W = c->kw;
+    for (int j = j0; j < j1; ++j) {
+        double *vj = c->d_kV + (size_t)j * n, *zj = c->d_kZ + (size_t)j * n;
+        pslr_status a;
+        if (prec == PSLR_FP64) {
+            a = apply_one(c, vj, zj, 0, dir, c->d_kskip, st);
+        } else {
+            launch_d2f(n, vj, c->d_kf_in, c->d_kskip, st);
+            a = apply_one(c, c->d_kf_in, c->d_kf_out, 1, dir, c->d_kskip, st);
+            launch_f2d(n, c->d_kf_out, zj, c->d_kskip, st);
+        }
+        if (a != PSLR_OK) return a;
+        cgs2(W, n, j + 1, c->d_kV, n, c->d_kw, rp, ci, av, zj, c->d_kskip, st);
+        launch_hessenberg(j, W.h1, W.h2, W.wn2, c->d_kH, k + 1, W.hn, 1, c->d_krot, c->d_kgam, c->d_ktol,
+                          c->d_kstate, c->d_kskip, st);
+        launch_normalize(n, c->d_kw, c->d_kV + (size_t)(j + 1) * n, W.hn, c->d_kskip, st);
+    }
+    return PSLR_OK;
+}
+
+// A full restart cycle as a CUDA graph, captured once per (precision,
+// direction) on the context's private stream; nullptr when capture fails
+// (the caller then launches the cycle directly).
+static cudaGraphExec_t arnoldi_graph(pslr_ctx *c, int prec, int dir) {
+    const auto key = std::make_pair(prec, dir);
+    auto it = c->kgraphs.find(key);
+    if (it != c->kgraphs.end()) return it->second;
+    // the apply's segment stream must exist before capture: building it allocates
+    const StreamDev *sd = nullptr;
+    if (get_stream(c, c->ops[dir][prec], 0, c->m, c->r > 0 && dir == 0, &sd) != PSLR_OK) return nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    if (cudaStreamBeginCapture(c->kcap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const pslr_status st = enqueue_arnoldi(c, 0, c->kr_restart, prec, dir, c->kcap);
+    const cudaError_t e = cudaStreamEndCapture(c->kcap, &g);
+    if (st != PSLR_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) x = nullptr;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (x) c->kgraphs[key] = x;
+    return x;
 }
 
 extern "C" {
@@ -1598,10 +1679,7 @@ pslr_status pslr_solve(pslr_ctx *c, const double *b_dev, double *x_dev, double r
     const int dir = transpose ? 1 : 0;
     const int32_t *rp = dir ? c->d_rpT : c->d_rp, *ci = dir ? c->d_ciT : c->d_ci;
     const double *av = dir ? c->d_avT : c->d_av;
-    KWork W;
-    pslr_status ks = kwork_alloc(c, W, n, k + 1);
-    if (ks != PSLR_OK) { kwork_free(W); return ks; }
-    struct Guard { KWork &w; ~Guard() { kwork_free(w); } } guard{W};
+    KWork &W = c->kw;
     int its = 0;
     double bn2 = 0.0;
     cgs2(W, n, 0, nullptr, n, const_cast<double *>(b_dev), nullptr, nullptr, nullptr, nullptr, nullptr, st);
@@ -1614,6 +1692,8 @@ pslr_status pslr_solve(pslr_ctx *c, const double *b_dev, double *x_dev, double r
     if (relres) *relres = 0.0;
     if (bn == 0.0) return PSLR_OK;
     if (!std::isfinite(bn)) return fail(c, PSLR_ERR_NAN, "right-hand side is not finite");
+    const double tol_abs = rtol * bn;
+    CK(cudaMemcpyAsync(c->d_ktol, &tol_abs, sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_kr, b_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     double rn = bn;
     std::vector<double> H((size_t)(k + 1) * k), gam(k + 1), y(k);
@@ -1629,21 +1709,12 @@ pslr_status pslr_solve(pslr_ctx *c, const double *b_dev, double *x_dev, double r
         launch_normalize(n, c->d_kr, c->d_kV, W.hn, nullptr, st);
         CK(cudaStreamSynchronize(st));
         const int jmax = std::min(k, maxit - its);
-        for (int j = 0; j < jmax; ++j) {
-            double *vj = c->d_kV + (size_t)j * n, *zj = c->d_kZ + (size_t)j * n;
-            pslr_status a;
-            if (prec == PSLR_FP64) {
-                a = apply_one(c, vj, zj, 0, dir, c->d_kskip, st);
-            } else {
-                launch_d2f(n, vj, c->d_kf_in, c->d_kskip, st);
-                a = apply_one(c, c->d_kf_in, c->d_kf_out, 1, dir, c->d_kskip, st);
-                launch_f2d(n, c->d_kf_out, zj, c->d_kskip, st);
-            }
+        cudaGraphExec_t g = jmax == k ? arnoldi_graph(c, prec, dir) : nullptr;
+        if (g) {
+            CK(cudaGraphLaunch(g, st));
+        } else {
+            pslr_status a = enqueue_arnoldi(c, 0, jmax, prec, dir, st);
             if (a != PSLR_OK) return a;
-            cgs2(W, n, j + 1, c->d_kV, n, c->d_kw, rp, ci, av, zj, c->d_kskip, st);
-            launch_hessenberg(j, W.h1, W.h2, W.wn2, c->d_kH, k + 1, W.hn, 1, c->d_krot, c->d_kgam, rtol * bn,
-                              c->d_kstate, c->d_kskip, st);
-            launch_normalize(n, c->d_kw, c->d_kV + (size_t)(j + 1) * n, W.hn, c->d_kskip, st);
         }
         int state[2] = {0, 0};
         CK(cudaMemcpyAsync(state, c->d_kstate, sizeof(state), cudaMemcpyDeviceToHost, st));

@@ -150,13 +150,15 @@ __global__ void __launch_bounds__(kKThreads) k_cgs_pass(
     finish_reduction(part, nres, res, ticket, false);
 }
 
-// One thread: column j of the Hessenberg matrix from h1 + h2 and ||w||^2, and
-// (givens != 0) the FGMRES least-squares update with Givens rotations.
+// Column j of the Hessenberg matrix from h1 + h2 and ||w||^2, and
+// (givens != 0) the FGMRES least-squares update with Givens rotations; the
+// cycle stops once |gam(j+1)| <= *tol_abs (device memory, so a captured
+// cycle serves every tolerance).
 // H is (ldh x *) column-major; rot = [cs(0:ldh), sn(0:ldh)]; gam (ldh).
 // state: [0] = iterations done in this cycle, [1] = converged/stop flag.
 __global__ void k_hessenberg(int j, const double *h1, const double *h2, const double *wn2, double *H,
                              int ldh, double *hn_out, int givens, double *rot, double *gam,
-                             double tol_abs, int *state, int *skip) {
+                             const double *tol_abs, int *state, int *skip) {
     // one warp: the column and the rotations are staged in shared memory, so
     // the sequential rotation chain runs on shared-memory and register latency
     __shared__ double c[kMaxK + 2], scs[kMaxK + 1], ssn[kMaxK + 1];
@@ -194,7 +196,7 @@ __global__ void k_hessenberg(int j, const double *h1, const double *h2, const do
             const double g = gam[j];
             gam[j + 1] = -sj * g;
             gam[j] = cj * g;
-            if (fabs(gam[j + 1]) <= tol_abs || hn == 0.0 || !(den == den)) {
+            if (fabs(gam[j + 1]) <= *tol_abs || hn == 0.0 || !(den == den)) {
                 state[1] = 1;
                 if (skip) *skip = 1;
             }
@@ -297,7 +299,7 @@ void launch_cgs_pass(int n, int k, const double *V, int64_t ld, double *w, const
 }
 
 void launch_hessenberg(int j, const double *h1, const double *h2, const double *wn2, double *H,
-                       int ldh, double *hn, int givens, double *rot, double *gam, double tol_abs,
+                       int ldh, double *hn, int givens, double *rot, double *gam, const double *tol_abs,
                        int *state, int *skip, cudaStream_t st) {
     k_hessenberg<<<1, 32, 0, st>>>(j, h1, h2, wn2, H, ldh, hn, givens, rot, gam, tol_abs, state, skip);
 }

@@ -201,6 +201,57 @@ def test_transposed_solve(dev):
     assert np.linalg.norm(b - At @ x.cpu().numpy()) <= 1.0001e-8 * np.linalg.norm(b)
 
 
+
+def test_solve_cycle_graph_reuse(dev):
+    """Full restart cycles replay a CUDA graph captured once per (precision,
+    direction).  A second solve gives the same x bit for bit; a looser
+    tolerance takes effect (it is read from device memory, not baked into the
+    graph); the transposed and FP32 cycles get graphs of their own; a new wait
+    limit, a new low-rank term or a new restart length replaces the graph, and
+    every solve meets its tolerance in the true residual with the oracle's
+    iteration count (+-1)."""
+    from paper_2002_00917_gb300 import pslr
+
+    w, ctx, orc = _setup(CASES[1])
+    m = w["m"]
+    b, _ = G.uniform_rhs(w["A"], 0)
+    bd = torch.tensor(b, device=dev)
+    A = G.dense_from_csr(w["A"])
+
+    def run(rtol, restart, prec=0, transpose=False):
+        x = torch.empty_like(bd)
+        its, rel, st = ctx.solve(bd, x, rtol=rtol, restart=restart, maxit=500, prec=prec, transpose=transpose)
+        assert st == 0 and rel <= rtol
+        xr = x.cpu().numpy()
+        M = A.T if transpose else A
+        assert np.linalg.norm(b - M @ xr) <= 1.0001 * rtol * np.linalg.norm(b)
+        if prec == 0:
+            its_o = orc.fgmres(b, rtol=rtol, restart=restart, maxit=500, transpose=transpose)[1]
+            assert abs(its - its_o) <= 1, (rtol, restart, transpose, its, its_o)
+        return its, xr
+
+    its1, x1 = run(1e-8, 5)
+    assert its1 > 5  # at least one full (captured) cycle
+    its2, x2 = run(1e-8, 5)
+    assert its2 == its1 and np.array_equal(x2, x1)
+    its3, _ = run(1e-4, 5)
+    assert its3 < its1
+    run(1e-8, 5, transpose=True)
+    run(1e-8, 5, prec=1)
+    old = ctx.set_wait_limit(0)
+    x = torch.empty_like(bd)
+    st = ctx.solve(bd, x, rtol=1e-8, restart=5, maxit=500, check=False)[2]
+    assert st == pslr.PSLR_ERR_TIMEOUT
+    ctx.set_wait_limit(old)
+    its4, x4 = run(1e-8, 5)
+    assert its4 == its1 and np.array_equal(x4, x1)
+    orc.build_lowrank(m, 3, seed=0)
+    V, H, Gm = orc.lowrank()
+    ctx.set_lowrank(m, V, Gm)
+    run(1e-8, 5)
+    run(1e-8, 7)
+
+
 def test_matvec(dev):
     w, ctx, orc = _setup(CASES[2])
     x = np.random.default_rng(6).uniform(-1, 1, w["A"].n)
