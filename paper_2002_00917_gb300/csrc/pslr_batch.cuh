@@ -143,7 +143,9 @@ __device__ __noinline__ void ell_row_general_rhs(const char *seg, T *out, int nr
 }
 
 // One level sweep per segment for the nr interleaved right-hand sides of x:
-// x_k[r] = (x_k[r] - sum_e T_re x_k[c_e]) (* dinv[r]).
+// x_k[r] = (x_k[r] - sum_e T_re x_k[c_e]) (* dinv[r]).  As in tri_sweep, the
+// arrival of each segment after the first is awaited by the last consumer
+// thread before the level barrier.
 template <class T, int NR>
 __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int nseg, int *err) {
     constexpr int nr = NR;
@@ -158,8 +160,8 @@ __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int nseg, int *err
     constexpr uint32_t ts = sizeof(T);
     const uint32_t es = ts * (uint32_t)nr;  // bytes per entry (all rhs)
     const int j = threadIdx.x;
+    if (nseg > 0 && !mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
     for (int L = 0; L < nseg; ++L) {
-        if (!mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
         const uint2 h = lds_u2(ptr_s);
         if (sizeof(T) == 8 && nr > 1 && ((h.y >> 16) & 0xffu) == kRec3) {
             const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu);
@@ -197,6 +199,11 @@ __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int nseg, int *err
         } else {
             const char *seg = R.base + (ptr_s - base_s);
             for (int k = 0; k < nr; ++k) level_row_general_rhs(seg, x, nr, k, j);
+        }
+        if (j == kConsumers - 1 && L + 1 < nseg) {
+            const bool wrap = slot + 1 == R.slots;
+            const uint32_t nbar = wrap ? R.full_s : fbar + 8, nph = wrap ? phase ^ 1u : phase;
+            if (!mbar_try_wait(nbar, nph)) wait_full_slow(nbar, nph, err);
         }
         csync();
         if (j == 0) mbar_arrive_cnt(fbar + edelta, kConsumerWarps);

@@ -579,8 +579,13 @@ __device__ __forceinline__ Rec3<T> rec3_shared(uint32_t seg, int np, int j) {
 // x[r] = (x[r] - sum_k T_rk x[c_k]) (* dinv[r]).  The loop is kept to a few
 // instructions per level (the level chain is latency-bound with two warps per
 // scheduler, so every instruction costs): ring cursor in registers advanced
-// incrementally, one wait, one header load, the 3-entry record path inline and
-// everything else out of line.
+// incrementally, one header load, the 3-entry record path inline and
+// everything else out of line.  Only the first segment is awaited by every
+// consumer; the arrival of each later one is awaited by the last consumer
+// thread just before the level barrier, and the barrier passes it on to the
+// others (the same ordering as waiting for one's own asynchronous copies and
+// then synchronising), which takes the mbarrier poll of 256 threads out of
+// every level step.
 template <class T>
 __device__ void tri_sweep(Cta<T> &c, T *x, int nseg, int *err) {
     Ring &R = c.ring;
@@ -593,8 +598,8 @@ __device__ void tri_sweep(Cta<T> &c, T *x, int nseg, int *err) {
     const uint32_t xs = smem_addr(x);
     const int j = threadIdx.x;
     constexpr uint32_t ts = sizeof(T);
+    if (nseg > 0 && !mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
     for (int L = 0; L < nseg; ++L) {
-        if (!mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
         const uint2 h = lds_u2(ptr_s);
         if (((h.y >> 16) & 0xffu) == kRec3) {
             if (j < (int)(h.x & 0xffffu)) {
@@ -609,6 +614,11 @@ __device__ void tri_sweep(Cta<T> &c, T *x, int nseg, int *err) {
             }
         } else {
             level_row_general(R.base + (ptr_s - base_s), x, j);
+        }
+        if (j == kConsumers - 1 && L + 1 < nseg) {
+            const bool wrap = slot + 1 == R.slots;
+            const uint32_t nbar = wrap ? R.full_s : fbar + 8, nph = wrap ? phase ^ 1u : phase;
+            if (!mbar_try_wait(nbar, nph)) wait_full_slow(nbar, nph, err);
         }
         csync();
         if (j == 0) mbar_arrive_cnt(fbar + edelta, kConsumerWarps);
