@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyPara
         solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2], P.err);
         ell_op<T, false>(c, c.si, c.xi, true, k.n[kF], P.err);
         if (lr_before) {
-            lowrank_partial(c, V, q, r, go, nq, c.si, P.part + (int64_t)i * r);
+            lowrank_partial(c, V, P.ldv, r, go, nq, c.si, P.part + (int64_t)i * r);
             for (int j = tid; j < nq; j += kConsumers) P.acc[go + j] = c.si[j];
         } else {
             if (tid == 0) c.si[nq] = T(0);
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyPara
             for (int j = tid; j < nq; j += kConsumers) c.si[j] = __ldcg(P.acc + go + j);
             if (tid == 0) c.si[nq] = T(0);
             csync();
-            lowrank_update(c, V, q, r, go, nq, c.si);
+            lowrank_update(c, V, P.ldv, r, go, nq, c.si);
             solve_local(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1], k.n[kC2], P.err);
             for (int j = tid; j < nq; j += kConsumers) {
                 P.wbuf[go + j] = c.si[j];
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyPara
             const int go = P.goff[i], nq = P.goff[i + 1] - go;
             for (int j = tid; j < nq; j += kConsumers) c.si[j] = __ldcg(P.acc + go + j);
             csync();
-            lowrank_partial(c, V, q, r, go, nq, c.si, P.part + (int64_t)i * r);
+            lowrank_partial(c, V, P.ldv, r, go, nq, c.si, P.part + (int64_t)i * r);
         }
         grid_arrive(c, P.bar, P.grid);
         ok = grid_wait(c, P.bar, P.err, P.wait_limit);
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyPara
         for (int j = tid; j < np_; j += kConsumers) c.xi[j] = P.b[P.perm[io + j]];
         if (tid == 0) c.xi[np_] = T(0);
         csync();
-        if (lr_after) lowrank_update(c, V, q, r, go, nq, c.wi);
+        if (lr_after) lowrank_update(c, V, P.ldv, r, go, nq, c.wi);
         ell_op<T, false>(c, c.xi, c.wi, true, k.n[kE], P.err);
         solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2], P.err);
         for (int j = tid; j < np_; j += kConsumers) P.z[P.perm[io + j]] = c.xi[j];

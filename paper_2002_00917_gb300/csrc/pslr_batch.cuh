@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
             const T *y = c.si + it.lo * nr;
             if (S.r > 0)
                 for (int kr = 0; kr < nr; ++kr)
-                    lowrank_partial(c, V, S.q, S.r, it.go, it.nq, y + kr, S.part + ((int64_t)kr * S.s + it.i) * S.r,
+                    lowrank_partial(c, V, S.ldv, S.r, it.go, it.nq, y + kr, S.part + ((int64_t)kr * S.s + it.i) * S.r,
                                     nr);
             for (int j = tid; j < it.nq; j += kConsumers)
                 for (int kr = 0; kr < nr; ++kr) {
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
                 csync();
                 for (int t = 0; t < g.n; ++t) {
                     const ItemRange it = item_range(S, g, t);
-                    lowrank_update(c, V, S.q, S.r, it.go, it.nq, c.si + it.lo * nr + kr, nr);
+                    lowrank_update(c, V, S.ldv, S.r, it.go, it.nq, c.si + it.lo * nr + kr, nr);
                 }
             }
             tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC1], P.err);

@@ -633,6 +633,7 @@ static pslr_status batch_build(pslr_batch *bt) {
             B.goff = e.goff;
             B.perm = e.perm;
             B.V = prec == 0 ? (const void *)e.V : (const void *)e.Vb;
+            B.ldv = e.ldv;
             B.G = reinterpret_cast<const T *>(prec == 0 ? (const void *)e.G : (const void *)e.Gf);
             B.wbuf = reinterpret_cast<T *>(w);
             B.acc = reinterpret_cast<T *>(a);

@@ -127,9 +127,25 @@ __device__ __forceinline__ T fma_t(T a, T b, T c) {
     return fma(a, b, c);
 }
 
-__device__ __forceinline__ double load_v(const double *V, int64_t i) { return V[i]; }
-__device__ __forceinline__ float load_v(const __nv_bfloat16 *V, int64_t i) {
-    return __bfloat162float(V[i]);
+// Eight consecutive entries of one row of the row-major V (16-byte aligned:
+// the row stride is a multiple of 8 entries), with read-only vector loads.
+__device__ __forceinline__ void load_v8(const double *p, double (&v)[8]) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double2 t = __ldg(q + k);
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+}
+__device__ __forceinline__ void load_v8(const __nv_bfloat16 *p, float (&v)[8]) {
+    const uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = __uint_as_float(w[k] << 16);           // bf16 -> f32: the bits move up
+        v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
 }
 
 // ----------------------------------------------------------- shared state
@@ -742,21 +758,25 @@ __device__ __forceinline__ Counts counts_of(const int32_t *cnt, int i) {
 }
 
 // Partial dots part[i*r + c] = sum_j V[go + j, c] * y[j * ys] over this
-// subdomain, eight columns at a time so each thread has many independent loads
-// in flight.
+// subdomain.  V is row-major with row stride ldv (a multiple of 8, zero
+// padded), so a thread reads eight columns of a row with vector loads; rows
+// are taken four at a time so that many loads are in flight.
 template <class T, class VT>
-__device__ void lowrank_partial(Cta<T> &c, const VT *V, int q, int r, int go, int nq, const T *y,
+__device__ void lowrank_partial(Cta<T> &c, const VT *V, int ldv, int r, int go, int nq, const T *y,
                                 T *part_i, int ys = 1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const VT *Vs = V + (int64_t)go * ldv;
     for (int c0 = 0; c0 < r; c0 += 8) {
         T a[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) a[k] = T(0);
+#pragma unroll 4
         for (int j = threadIdx.x; j < nq; j += kConsumers) {
+            T v[8];
+            load_v8(Vs + (int64_t)j * ldv + c0, v);
             const T yj = y[j * ys];
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (c0 + k < r) a[k] = fma_t(T(load_v(V, (int64_t)(c0 + k) * q + go + j)), yj, a[k]);
+            for (int k = 0; k < 8; ++k) a[k] = fma_t(v[k], yj, a[k]);
         }
         const T v = warp_reduce8(a);
         if ((lane & 3) == 0 && c0 + (lane >> 2) < r) c.red[warp * kMaxRank + c0 + (lane >> 2)] = v;
@@ -800,13 +820,22 @@ __device__ void lowrank_coeffs(Cta<T> &c, const T *part, const T *G, int s, int 
     csync();
 }
 
-// y[j * ys] += sum_c V[go + j, c] d[c]
+// y[j * ys] += sum_c V[go + j, c] d[c] (V row-major with row stride ldv, as
+// in lowrank_partial; entries of d past r are not read).
 template <class T, class VT>
-__device__ void lowrank_update(Cta<T> &c, const VT *V, int q, int r, int go, int nq, T *y, int ys = 1) {
+__device__ void lowrank_update(Cta<T> &c, const VT *V, int ldv, int r, int go, int nq, T *y, int ys = 1) {
     const T *d = c.red + (kConsumers / 32) * kMaxRank + kMaxRank;
+    const VT *Vs = V + (int64_t)go * ldv;
+#pragma unroll 2
     for (int j = threadIdx.x; j < nq; j += kConsumers) {
         T a = y[j * ys];
-        for (int col = 0; col < r; ++col) a = fma_t(T(load_v(V, (int64_t)col * q + go + j)), d[col], a);
+        for (int c0 = 0; c0 < r; c0 += 8) {
+            T v[8];
+            load_v8(Vs + (int64_t)j * ldv + c0, v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (c0 + k < r) a = fma_t(v[k], d[c0 + k], a);
+        }
         y[j * ys] = a;
     }
     csync();

@@ -414,7 +414,10 @@ struct pslr_ctx {
     uint64_t lr_gen = 0;         // incremented whenever the low-rank term is replaced
     std::vector<double> V, H, G;
     double *d_V = nullptr;       // q x r FP64 (leading dimension q)
-    uint16_t *d_Vb = nullptr;    // q x r BF16
+    // the copies the apply reads: row-major, row stride ldv = r rounded up to 8, zero padded
+    int ldv = 0;
+    double *d_Vr = nullptr;      // FP64
+    uint16_t *d_Vb = nullptr;    // BF16
     double *d_G = nullptr, *d_GT = nullptr;
     float *d_Gf = nullptr, *d_GTf = nullptr;
     // apply scratch
@@ -497,9 +500,9 @@ void free_krylov(pslr_ctx *c) {
 }
 
 void free_lowrank(pslr_ctx *c) {
-    cfree(c->d_V); cfree(c->d_Vb); cfree(c->d_G); cfree(c->d_GT);
+    cfree(c->d_V); cfree(c->d_Vr); cfree(c->d_Vb); cfree(c->d_G); cfree(c->d_GT);
     cfree(c->d_Gf); cfree(c->d_GTf); cfree(c->d_part);
-    c->d_V = nullptr; c->d_Vb = nullptr; c->d_G = c->d_GT = nullptr; c->d_Gf = c->d_GTf = nullptr;
+    c->d_V = nullptr; c->d_Vr = nullptr; c->d_Vb = nullptr; c->d_G = c->d_GT = nullptr; c->d_Gf = c->d_GTf = nullptr;
     c->d_part = nullptr;
     c->r = 0;
     ++c->lr_gen;
@@ -1007,6 +1010,7 @@ static void fill_params(pslr_ctx *c, ApplyParams<T> &P, int dir, int prec, const
     P.p = c->p;
     P.q = c->q;
     P.r = c->r;
+    P.ldv = c->ldv;
     P.m = c->m;
     P.grid = o.grid;
     P.max_p = c->max_p;
@@ -1055,7 +1059,7 @@ static pslr_status apply_launch(pslr_ctx *c, const void *b, void *z, int prec, i
     if (prec == PSLR_FP64) {
         ApplyParams<double> P;
         fill_params(c, P, dir, prec, sd);
-        P.V = c->d_V;
+        P.V = c->d_Vr;
         P.G = dir ? c->d_GT : c->d_G;
         P.b = static_cast<const double *>(b);
         P.z = static_cast<double *>(z);
@@ -1347,7 +1351,8 @@ static bool compute_G(int r, const std::vector<double> &H, std::vector<double> &
     return true;
 }
 
-// Install V (device FP64 q x r, already in c->d_V) plus host G: derived copies.
+// Install V (device FP64 q x r, already in c->d_V) plus host G: derived copies
+// (row-major FP64 and BF16 V for the apply, G^T, FP32 G and G^T).
 static pslr_status install_lowrank(pslr_ctx *c, int m, int r, const std::vector<double> &G) {
     const int q = c->q;
     ++c->lr_gen;
@@ -1355,14 +1360,22 @@ static pslr_status install_lowrank(pslr_ctx *c, int m, int r, const std::vector<
     c->m = m;
     c->r = r;
     c->G = G;
-    cudaFree(c->d_Vb); cudaFree(c->d_G); cudaFree(c->d_GT); cudaFree(c->d_Gf); cudaFree(c->d_GTf);
+    cudaFree(c->d_Vr); cudaFree(c->d_Vb); cudaFree(c->d_G); cudaFree(c->d_GT); cudaFree(c->d_Gf); cudaFree(c->d_GTf);
     cudaFree(c->d_part);
-    c->d_Vb = nullptr; c->d_G = c->d_GT = nullptr; c->d_Gf = c->d_GTf = nullptr; c->d_part = nullptr;
+    c->d_Vr = nullptr; c->d_Vb = nullptr; c->d_G = c->d_GT = nullptr; c->d_Gf = c->d_GTf = nullptr; c->d_part = nullptr;
+    c->ldv = 0;
     if (r == 0) return prebuild_streams(c);
     c->V.resize((size_t)q * r);
     CK(cudaMemcpy(c->V.data(), c->d_V, sizeof(double) * (size_t)q * r, cudaMemcpyDeviceToHost));
-    std::vector<uint16_t> vb((size_t)q * r);
-    for (size_t i = 0; i < vb.size(); ++i) vb[i] = f32_to_bf16((float)c->V[i]);
+    c->ldv = (r + 7) & ~7;
+    std::vector<double> vr((size_t)q * c->ldv, 0.0);
+    std::vector<uint16_t> vb((size_t)q * c->ldv, 0);
+    for (int col = 0; col < r; ++col)
+        for (int i = 0; i < q; ++i) {
+            const double v = c->V[(size_t)col * q + i];
+            vr[(size_t)i * c->ldv + col] = v;
+            vb[(size_t)i * c->ldv + col] = f32_to_bf16((float)v);
+        }
     std::vector<double> GT((size_t)r * r);
     std::vector<float> Gf((size_t)r * r), GTf((size_t)r * r);
     for (int i = 0; i < r; ++i)
@@ -1371,6 +1384,7 @@ static pslr_status install_lowrank(pslr_ctx *c, int m, int r, const std::vector<
             Gf[(size_t)j * r + i] = (float)G[(size_t)j * r + i];
             GTf[(size_t)j * r + i] = (float)G[(size_t)i * r + j];
         }
+    CK(upload(&c->d_Vr, vr));
     CK(upload(&c->d_Vb, vb));
     CK(upload(&c->d_G, G));
     CK(upload(&c->d_GT, GT));
@@ -1778,8 +1792,9 @@ bool sys_export(const pslr_ctx *c, SysExport *e) {
     e->rp = c->d_rp;
     e->ci = c->d_ci;
     e->av = c->d_av;
-    e->V = c->d_V;
+    e->V = c->d_Vr;
     e->Vb = c->d_Vb;
+    e->ldv = c->ldv;
     e->G = c->d_G;
     e->Gf = c->d_Gf;
     for (int prec = 0; prec < 2; ++prec) {

@@ -112,7 +112,8 @@ struct ApplyParams {
     const int32_t *perm;         // n: reordered index -> original index
     const uint16_t *bpiv;        // p: exact-LU row permutation of B (local), or nullptr
     const uint16_t *cpiv;        // q: exact-LU row permutation of C0 (local), or nullptr
-    const void *V;               // q x r column-major: double (FP64) or bf16 (FP32)
+    const void *V;               // q x r row-major, row stride ldv: double (FP64) or bf16 (FP32)
+    int ldv;                     // row stride of V: r rounded up to a multiple of 8 (zero padded)
     const T *G;                  // r x r column-major (G, or G^T for the transpose)
     const T *b;                  // n input, original order
     T *z;                        // n output, original order
@@ -165,7 +166,7 @@ struct BatchGroup {
 template <class T>
 struct BatchSys {
     const int32_t *ioff, *goff, *perm;
-    const void *V;              // q x r: double (FP64) or bf16 (FP32)
+    const void *V;              // q x r row-major, row stride ldv: double (FP64) or bf16 (FP32)
     const T *G;                 // r x r column-major
     T *wbuf;                    // nrhs blocks of 2(q+1): series iterates (ping-pong, slot q = 0)
     T *acc;                     // nrhs blocks of q+1: accumulator
@@ -173,6 +174,7 @@ struct BatchSys {
     T *dco;                     // nrhs blocks of r: low-rank coefficients d = G V^T t
     int64_t voff;               // start of the system's n x nrhs block in b and z
     int n, s, p, q, r, m;
+    int ldv;                    // row stride of V (r rounded up to a multiple of 8)
 };
 
 template <class T, class IO>

@@ -15,8 +15,9 @@ struct SysExport {
     const int32_t *ioff, *goff, *perm;      // device
     const int32_t *rp, *ci;                 // device CSR of A (original ordering)
     const double *av;
-    const double *V;                        // device q x r FP64
-    const uint16_t *Vb;                     // device q x r BF16
+    const double *V;                        // device q x r FP64, row-major (row stride ldv)
+    const uint16_t *Vb;                     // device q x r BF16, row-major (row stride ldv)
+    int ldv;                                // r rounded up to a multiple of 8 (zero padded)
     const double *G;                        // device r x r
     const float *Gf;
     const char *seg[2];                     // device forward segments [FP64, FP32]
