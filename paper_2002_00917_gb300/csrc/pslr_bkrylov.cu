@@ -21,6 +21,7 @@
 #include <cstdint>
 
 #include "pslr_internal.h"
+#include "pslr_reduce.cuh"
 
 namespace pslr {
 
@@ -28,55 +29,58 @@ constexpr int kBkThreads = 256;
 constexpr int kBkCols = 8;      // basis columns per register block
 constexpr int kBkMaxK = 128;    // restart length + 1 at most
 
-// Block-reduce kBkCols values; every thread gets the sums in out[].
-__device__ __forceinline__ void bk_reduce(double (&a)[kBkCols], double *sh, double *out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kBkCols; ++k) {
-        double v = a[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[warp * kBkCols + k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < kBkCols) {
-        double v = 0.0;
-        for (int w = 0; w < kBkThreads / 32; ++w) v += sh[w * kBkCols + threadIdx.x];
-        out[threadIdx.x] = v;
-    }
-    __syncthreads();
-}
-
-// part[blk * ld + t] = V(:, t)^T w over the chunk, t = 0..k-1.
+// part[blk * ldp + t] = V(:, t)^T w over the chunk [b, e), t = 0..k-1.  The
+// rows of w were written by this block just before.  Column-wise: a warp
+// takes a chunk of eight columns and a subset of the rows, lanes stride over
+// the rows, one butterfly reduction per chunk (as in the single-system CGS
+// pass: a per-thread reduction spends more FP64 instructions on the shuffle
+// trees than on the products); subsets are added in a fixed order.
 __device__ void bk_dots(int k, const double *__restrict__ V, int64_t ldv, const double *__restrict__ w,
                         int64_t b, int64_t e, double *part, int ldp) {
-    __shared__ double sh[(kBkThreads / 32) * kBkCols];
-    __shared__ double outs[kBkCols];
-    for (int c0 = 0; c0 < k; c0 += kBkCols) {
+    __shared__ double sh[(kBkThreads / 32) * kBkMaxK];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kBkThreads / 32;
+    const int nch = (k + kBkCols - 1) / kBkCols;
+    const int nsub = nw / nch > 1 ? nw / nch : 1;
+    const int64_t rs = (e - b + nsub - 1) / nsub;
+    for (int t = warp; t < nch * nsub; t += nw) {
+        const int c0 = (t % nch) * kBkCols, sub = t / nch;
+        const int64_t sb = b + sub * rs, se = sb + rs < e ? sb + rs : e;
         double a[kBkCols];
 #pragma unroll
-        for (int t = 0; t < kBkCols; ++t) a[t] = 0.0;
-        for (int64_t i = b + threadIdx.x; i < e; i += kBkThreads) {
+        for (int u = 0; u < kBkCols; ++u) a[u] = 0.0;
+#pragma unroll 4
+        for (int64_t i = sb + lane; i < se; i += 32) {
             const double wi = w[i];
 #pragma unroll
-            for (int t = 0; t < kBkCols; ++t)
-                if (c0 + t < k) a[t] = fma(V[(int64_t)(c0 + t) * ldv + i], wi, a[t]);
+            for (int u = 0; u < kBkCols; ++u)
+                if (c0 + u < k) a[u] = fma(V[(int64_t)(c0 + u) * ldv + i], wi, a[u]);
         }
-        bk_reduce(a, sh, outs);
-        if (threadIdx.x < kBkCols && c0 + threadIdx.x < k)
-            part[(int64_t)blockIdx.x * ldp + c0 + threadIdx.x] = outs[threadIdx.x];
+        const double v = warp_reduce8(a);
+        if ((lane & 3) == 0 && c0 + (lane >> 2) < k) sh[sub * kBkMaxK + c0 + (lane >> 2)] = v;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += kBkThreads) {
+        double v = 0.0;
+        for (int u = 0; u < nsub; ++u) v += sh[u * kBkMaxK + c];
+        part[(int64_t)blockIdx.x * ldp + c] = v;
     }
 }
 
-// part[blk * ld] = ||w||^2 over the chunk.
+// part[blk * ld] = ||w||^2 over the chunk (rows this thread wrote).
 __device__ void bk_norm2(const double *__restrict__ w, int64_t b, int64_t e, double *part, int ldp) {
-    __shared__ double sh[(kBkThreads / 32) * kBkCols];
-    __shared__ double outs[kBkCols];
-    double a[kBkCols];
-#pragma unroll
-    for (int t = 0; t < kBkCols; ++t) a[t] = 0.0;
-    for (int64_t i = b + threadIdx.x; i < e; i += kBkThreads) a[0] = fma(w[i], w[i], a[0]);
-    bk_reduce(a, sh, outs);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * ldp] = outs[0];
+    __shared__ double sh[kBkThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double a = 0.0;
+    for (int64_t i = b + threadIdx.x; i < e; i += kBkThreads) a = fma(w[i], w[i], a);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[warp] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int u = 0; u < kBkThreads / 32; ++u) v += sh[u];
+        part[(int64_t)blockIdx.x * ldp] = v;
+    }
 }
 
 // CGS2 pass 1: w = A z_j on the chunk's rows, then partials of V(:, 0:j+1)^T w.

@@ -2,10 +2,10 @@
 // process of Algorithm 1 (steps 6-7) share them.
 //
 // Classical Gram-Schmidt applied twice (CGS2) is split into three passes over
-// the rows, each one launch whose blocks stream the basis V column-chunk by
-// column-chunk (coalesced along rows) and leave one partial per block; the
-// partials are added in a fixed two-level order (finish_reduction), so every
-// reduction is deterministic:
+// the rows, each one launch whose blocks own contiguous row ranges, stream
+// the basis V column-chunk by column-chunk (coalesced along rows) and leave
+// one partial per block; the partials are added in a fixed two-level order
+// (finish_reduction), so every reduction is deterministic:
 //   pass 1  w = A z (optional, fused CSR SpMV), h1 = V^T w
 //   pass 2  w -= V h1,                        h2 = V^T w
 //   pass 3  w -= V h2,                        ||w||^2
@@ -19,6 +19,8 @@
 
 #include <cstdint>
 
+#include "pslr_reduce.cuh"
+
 namespace pslr {
 
 constexpr int kKThreads = 256;
@@ -27,24 +29,6 @@ constexpr int kMaxK = 128; // basis columns of one CGS pass (Arnoldi rank <= 128
 
 __device__ __forceinline__ bool skipping(const int *skip) {
     return skip != nullptr && *(volatile const int *)skip != 0;
-}
-
-// Block-reduce kChunk values; thread 0 of the block gets the sums in out[].
-__device__ __forceinline__ void block_reduce8(double (&a)[kChunk], double *sh, double *out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kChunk; ++k) {
-        double v = a[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[warp * kChunk + k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < kChunk) {
-        double v = 0.0;
-        for (int w = 0; w < nw; ++w) v += sh[w * kChunk + threadIdx.x];
-        out[threadIdx.x] = v;
-    }
-    __syncthreads();
 }
 
 // Two-level deterministic reduction of the per-block partials (nres values
@@ -92,27 +76,46 @@ __device__ bool finish_reduction(double *part, int nres, double *res, unsigned *
     return true;
 }
 
+// Block sum of one value per thread; thread 0 gets it.
+__device__ __forceinline__ double block_reduce1(double v, double *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double a = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w) a += sh[w];
+    return a;
+}
+
 // One CGS pass.  If rp != nullptr: w = A z first (CSR, FP64).  If hsub !=
 // nullptr: w -= V(:, 0:k) hsub.  Then either h = V(:, 0:k)^T w (norm == 0) or
 // res[0] = ||w||^2 (norm != 0).
+//
+// Block b owns the contiguous rows [b R, (b+1) R).  The row-wise parts (SpMV,
+// update, norm) take one thread per row.  The dot products run column-wise:
+// a warp takes a chunk of eight columns and a subset of the block's rows,
+// lanes stride over the rows (coalesced loads of V and w), and one butterfly
+// reduction per chunk leaves eight column sums.  Reducing per thread instead
+// (each thread a few rows, then eight shuffle trees per chunk) spent more
+// FP64 instructions on the trees than on the products themselves, and FP64
+// instructions are what this pass is bound by on GB300.
 __global__ void __launch_bounds__(kKThreads) k_cgs_pass(
     int n, int k, const double *__restrict__ V, int64_t ld, double *__restrict__ w,
     const double *__restrict__ hsub, int norm, double *part, double *res, unsigned *ticket,
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ av,
     const double *__restrict__ z, const int *skip) {
     if (skipping(skip)) return;
-    __shared__ double sh[(kKThreads / 32) * kChunk];
+    __shared__ double sh[(kKThreads / 32) * kMaxK];  // [row subset][column] partial sums
     __shared__ double hs[kMaxK];
-    __shared__ double outs[kChunk];
-    const int stride = gridDim.x * blockDim.x;
-    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int R = (n + gridDim.x - 1) / gridDim.x;
+    const int rb = min(n, blockIdx.x * R), re = min(n, rb + R);
     if (hsub) {
         for (int c = threadIdx.x; c < k; c += blockDim.x) hs[c] = __ldcg(hsub + c);
         __syncthreads();
     }
-    // rows owned by this thread: i0, i0 + stride, ...  (update in place)
     if (rp || hsub) {
-        for (int i = i0; i < n; i += stride) {
+        for (int i = rb + threadIdx.x; i < re; i += blockDim.x) {
             double wi;
             if (rp) {
                 wi = 0.0;
@@ -127,24 +130,37 @@ __global__ void __launch_bounds__(kKThreads) k_cgs_pass(
     }
     const int nres = norm ? 1 : k;
     if (norm) {
-        double a[kChunk] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int i = i0; i < n; i += stride) a[0] = fma(w[i], w[i], a[0]);
-        block_reduce8(a, sh, outs);
-        if (threadIdx.x == 0) part[blockIdx.x] = outs[0];
+        double a = 0.0;
+        for (int i = rb + threadIdx.x; i < re; i += blockDim.x) a = fma(w[i], w[i], a);
+        a = block_reduce1(a, sh);
+        if (threadIdx.x == 0) part[blockIdx.x] = a;
     } else {
-        for (int c0 = 0; c0 < k; c0 += kChunk) {
+        __syncthreads();  // the block's rows of w are written
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const int nch = (k + kChunk - 1) / kChunk;
+        const int nsub = nw / nch > 1 ? nw / nch : 1;
+        const int rs = (re - rb + nsub - 1) / nsub;
+        for (int t = warp; t < nch * nsub; t += nw) {
+            const int c0 = (t % nch) * kChunk, sub = t / nch;
+            const int sb = rb + sub * rs, se = min(re, sb + rs);
             double a[kChunk];
 #pragma unroll
-            for (int t = 0; t < kChunk; ++t) a[t] = 0.0;
-            for (int i = i0; i < n; i += stride) {
+            for (int u = 0; u < kChunk; ++u) a[u] = 0.0;
+#pragma unroll 4
+            for (int i = sb + lane; i < se; i += 32) {
                 const double wi = w[i];
 #pragma unroll
-                for (int t = 0; t < kChunk; ++t)
-                    if (c0 + t < k) a[t] = fma(V[(int64_t)(c0 + t) * ld + i], wi, a[t]);
+                for (int u = 0; u < kChunk; ++u)
+                    if (c0 + u < k) a[u] = fma(V[(int64_t)(c0 + u) * ld + i], wi, a[u]);
             }
-            block_reduce8(a, sh, outs);
-            if (threadIdx.x < kChunk && c0 + threadIdx.x < k)
-                part[(int64_t)blockIdx.x * nres + c0 + threadIdx.x] = outs[threadIdx.x];
+            const double v = warp_reduce8(a);
+            if ((lane & 3) == 0 && c0 + (lane >> 2) < k) sh[sub * kMaxK + c0 + (lane >> 2)] = v;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < k; c += blockDim.x) {
+            double v = 0.0;
+            for (int u = 0; u < nsub; ++u) v += sh[u * kMaxK + c];
+            part[(int64_t)blockIdx.x * nres + c] = v;
         }
     }
     finish_reduction(part, nres, res, ticket, false);
@@ -270,14 +286,15 @@ __global__ void k_grad_values(int n, const int32_t *rp, const int32_t *ci, const
 
 // ---------------------------------------------------------------- launchers
 
-// Blocks of the row-parallel Krylov kernels: four rows per thread, at most
-// two blocks per SM, and within the reduction's ticket array.  (On the 64^3
-// FGMRES, 256 blocks beat 128, 152 and 512 by 5-10%.)
+// Blocks of the Krylov kernels: two rows per thread, at most two blocks per
+// SM (so large vectors spread evenly over every SM's FP64 pipe), and within
+// the reduction's ticket array.  (64^3 FGMRES(120): 304 blocks beat 256 by
+// 1.5% with the column-wise dot products.)
 int krylov_blocks(int n) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int want = (n + kKThreads * 4 - 1) / (kKThreads * 4);
+    int want = (n + kKThreads * 2 - 1) / (kKThreads * 2);
     int cap = 2 * nsm;
     if (cap > (kMaxTickets - 1) * kRedGroup) cap = (kMaxTickets - 1) * kRedGroup;
     if (want > cap) want = cap;
