@@ -252,6 +252,41 @@ def test_solve_cycle_graph_reuse(dev):
     run(1e-8, 7)
 
 
+
+def test_solve_partial_cycles_and_maxit(dev):
+    """Cycle lengths around the captured graph: maxit = 0 (no iteration, x =
+    0, relres 1), maxit below the restart length (one partial cycle, launched
+    directly), maxit not a multiple of it (captured cycles then a direct
+    partial one), restart 2 and 5.  Where the iteration limit stops the
+    solve, the returned relative residual equals the oracle's after the same
+    number of iterations."""
+    from paper_2002_00917_gb300 import pslr
+
+    w, ctx, orc = _setup(CASES[1])
+    b, _ = G.uniform_rhs(w["A"], 0)
+    bd = torch.tensor(b, device=dev)
+    x = torch.full_like(bd, 7.0)
+    its, rel, st = ctx.solve(bd, x, rtol=1e-8, restart=10, maxit=0, check=False)
+    assert (its, rel, st) == (0, 1.0, pslr.PSLR_ERR_NOT_CONVERGED)
+    assert torch.count_nonzero(x).item() == 0
+    for restart, maxit in ((10, 7), (5, 12), (2, 9)):
+        x = torch.empty_like(bd)
+        its, rel, st = ctx.solve(bd, x, rtol=1e-14, restart=restart, maxit=maxit, check=False)
+        xo, its_o, rel_o, st_o = orc.fgmres(b, rtol=1e-14, restart=restart, maxit=maxit)
+        assert st == pslr.PSLR_ERR_NOT_CONVERGED and its == its_o == maxit, (restart, maxit, its, its_o)
+        assert abs(rel - rel_o) <= 1e-8 * rel_o, (restart, maxit, rel, rel_o)
+        r = b - G.dense_from_csr(w["A"]) @ x.cpu().numpy()
+        assert abs(np.linalg.norm(r) / np.linalg.norm(b) - rel) <= 1e-10, (restart, maxit)
+    # to convergence with a short restart: 5, not 2 - on this problem the
+    # oracle's own FGMRES(2) count moves between 310 and 444 when b changes by
+    # 1e-15 relative (restarting every two steps amplifies rounding), while
+    # FGMRES(5) stays at 328
+    x = torch.empty_like(bd)
+    its, rel, st = ctx.solve(bd, x, rtol=1e-8, restart=5, maxit=2000)
+    its_o = orc.fgmres(b, rtol=1e-8, restart=5, maxit=2000)[1]
+    assert st == 0 and rel <= 1e-8 and abs(its - its_o) <= 1, (its, its_o)
+
+
 def test_matvec(dev):
     w, ctx, orc = _setup(CASES[2])
     x = np.random.default_rng(6).uniform(-1, 1, w["A"].n)
