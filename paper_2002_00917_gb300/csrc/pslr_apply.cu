@@ -30,8 +30,8 @@ namespace pslr {
 
 // ------------------------------------------------------------------ the apply
 
-template <class T, class VT>
-__global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyParams<T> P) {
+template <class T, class VT, class IO>
+__global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyParams<T, IO> P) {
     extern __shared__ __align__(128) char smem[];
     if (P.skip != nullptr && ld_volatile(P.skip) != 0) return;
     if (ld_volatile(P.err) != 0) return;
@@ -53,9 +53,9 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyPara
         const Counts k = counts_of(P.cnt, i);
         const int io = P.ioff[i], np_ = P.ioff[i + 1] - io;
         const int go = P.goff[i], nq = P.goff[i + 1] - go;
-        for (int j = tid; j < np_; j += kConsumers) c.xi[j] = P.b[P.perm[io + j]];
+        for (int j = tid; j < np_; j += kConsumers) c.xi[j] = T(P.b[P.perm[io + j]]);
         if (tid == 0) c.xi[np_] = T(0);
-        for (int j = tid; j < nq; j += kConsumers) c.si[j] = P.b[P.perm[p + go + j]];
+        for (int j = tid; j < nq; j += kConsumers) c.si[j] = T(P.b[P.perm[p + go + j]]);
         csync();
         solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2], P.err);
         ell_op<T, false>(c, c.si, c.xi, true, k.n[kF], P.err);
@@ -161,14 +161,14 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyPara
         const int go = P.goff[i], nq = P.goff[i + 1] - go;
         for (int j = tid; j < nq; j += kConsumers) c.wi[j] = __ldcg(P.acc + go + j);
         if (tid == 0) c.wi[nq] = T(0);
-        for (int j = tid; j < np_; j += kConsumers) c.xi[j] = P.b[P.perm[io + j]];
+        for (int j = tid; j < np_; j += kConsumers) c.xi[j] = T(P.b[P.perm[io + j]]);
         if (tid == 0) c.xi[np_] = T(0);
         csync();
         if (lr_after) lowrank_update(c, V, P.ldv, r, go, nq, c.wi);
         ell_op<T, false>(c, c.xi, c.wi, true, k.n[kE], P.err);
         solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2], P.err);
-        for (int j = tid; j < np_; j += kConsumers) P.z[P.perm[io + j]] = c.xi[j];
-        for (int j = tid; j < nq; j += kConsumers) P.z[P.perm[p + go + j]] = c.wi[j];
+        for (int j = tid; j < np_; j += kConsumers) P.z[P.perm[io + j]] = IO(c.xi[j]);
+        for (int j = tid; j < nq; j += kConsumers) P.z[P.perm[p + go + j]] = IO(c.wi[j]);
         csync();
     }
     return;
@@ -252,28 +252,35 @@ static cudaError_t launch_coop(K kern, const Prm &P, int grid, int smem, cudaStr
 }
 
 cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, cudaStream_t st) {
-    return launch_coop(pslr_apply_kernel<double, double>, P, P.grid, smem, st);
+    return launch_coop(pslr_apply_kernel<double, double, double>, P, P.grid, smem, st);
 }
 cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, cudaStream_t st) {
-    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16>, P, P.grid, smem, st);
+    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, float>, P, P.grid, smem, st);
+}
+cudaError_t launch_apply_f32d(const ApplyParams<float, double> &P, int smem, cudaStream_t st) {
+    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, double>, P, P.grid, smem, st);
 }
 cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, cudaStream_t st) {
     return launch_coop(pslr_err_kernel<double>, P, P.grid, smem, st);
 }
 
 // Largest cooperative grid of the persistent kernels for a dynamic smem size
-// (the smaller of the apply and E_rr kernels' occupancies).
+// (the smallest occupancy of the kernels that launch with it: FP64 apply and
+// E_rr, or the two FP32 apply forms).
 int max_coresident_apply(int smem, bool fp32) {
     int dev = 0, nsm = 0, per = 0, per2 = 1 << 30;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e;
     if (fp32) {
-        auto k = pslr_apply_kernel<float, __nv_bfloat16>;
+        auto k = pslr_apply_kernel<float, __nv_bfloat16, float>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreads, smem);
+        auto k2 = pslr_apply_kernel<float, __nv_bfloat16, double>;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k2, kThreads, smem);
     } else {
-        auto k = pslr_apply_kernel<double, double>;
+        auto k = pslr_apply_kernel<double, double, double>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreads, smem);
         auto k2 = pslr_err_kernel<double>;

@@ -28,6 +28,7 @@ namespace pslr {
 // kernels (pslr_apply.cu, pslr_krylov.cu)
 cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, cudaStream_t st);
 cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, cudaStream_t st);
+cudaError_t launch_apply_f32d(const ApplyParams<float, double> &P, int smem, cudaStream_t st);
 cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, cudaStream_t st);
 int max_coresident_apply(int smem, bool fp32);
 int krylov_blocks(int n);
@@ -45,8 +46,6 @@ void launch_gemv_add(int n, int k, const double *Z, int64_t ld, const double *y,
                      cudaStream_t st);
 void launch_residual(int n, const int32_t *rp, const int32_t *ci, const double *av, const double *x,
                      const double *b, double *r, cudaStream_t st);
-void launch_d2f(int n, const double *a, float *b, const int *skip, cudaStream_t st);
-void launch_f2d(int n, const float *a, double *b, const int *skip, cudaStream_t st);
 void launch_splitmix(int n, uint64_t seed, uint64_t j0, double *v, cudaStream_t st);
 void launch_grad_values(int n, const int32_t *rp, const int32_t *ci, const double *lambda, const double *u,
                         double *g, cudaStream_t st);
@@ -434,7 +433,6 @@ struct pslr_ctx {
     double *d_kV = nullptr, *d_kZ = nullptr, *d_kw = nullptr, *d_kr = nullptr, *d_kH = nullptr;
     double *d_krot = nullptr, *d_kgam = nullptr;
     int *d_kstate = nullptr, *d_kskip = nullptr;
-    float *d_kf_in = nullptr, *d_kf_out = nullptr;
     double *d_eab = nullptr;  // E_rr scratch 2(q+1)
     void *d_io_b = nullptr, *d_io_z = nullptr;  // pslr_apply_host staging
     size_t io_bytes = 0;
@@ -488,12 +486,11 @@ void free_krylov(pslr_ctx *c) {
     KWork &W = c->kw;
     for (void *p : {(void *)c->d_kV, (void *)c->d_kZ, (void *)c->d_kw, (void *)c->d_kr, (void *)c->d_kH,
                     (void *)c->d_krot, (void *)c->d_kgam, (void *)c->d_kstate, (void *)c->d_kskip,
-                    (void *)c->d_kf_in, (void *)c->d_kf_out, (void *)c->d_ktol, (void *)W.part, (void *)W.h1,
+                    (void *)c->d_ktol, (void *)W.part, (void *)W.h1,
                     (void *)W.h2, (void *)W.wn2, (void *)W.hn, (void *)W.ticket})
         cfree(p);
     c->d_kV = c->d_kZ = c->d_kw = c->d_kr = c->d_kH = c->d_krot = c->d_kgam = nullptr;
     c->d_kstate = c->d_kskip = nullptr;
-    c->d_kf_in = c->d_kf_out = nullptr;
     c->d_ktol = nullptr;
     W = KWork();
     c->kr_restart = 0;
@@ -995,8 +992,8 @@ static pslr_status get_stream(pslr_ctx *c, OpSetHost &o, int kind, int m, bool l
     return PSLR_OK;
 }
 
-template <class T>
-static void fill_params(pslr_ctx *c, ApplyParams<T> &P, int dir, int prec, const StreamDev *sd) {
+template <class T, class IO>
+static void fill_params(pslr_ctx *c, ApplyParams<T, IO> &P, int dir, int prec, const StreamDev *sd) {
     const OpSetHost &o = c->ops[dir][prec];
     P.segbase = o.seg;
     P.stream = sd->ent;
@@ -1044,8 +1041,28 @@ static const StreamDev *find_stream(const OpSetHost &o, int kind, int m, bool lr
     return it == o.streams.end() ? nullptr : &it->second;
 }
 
-static pslr_status apply_launch(pslr_ctx *c, const void *b, void *z, int prec, int dir, const int *skip,
+// Precision forms of one apply launch: PSLR_FP64, PSLR_FP32, and (internal)
+// kF32OnF64: FP32 arithmetic and BF16 V on FP64 input and output vectors, the
+// FGMRES form with the FP32 preconditioner (no conversion kernels).
+constexpr int kF32OnF64 = 2;
+
+template <class T, class IO>
+static void set_io(ApplyParams<T, IO> &P, const void *b, void *z, const int *skip, const ApplyScratch *scr) {
+    P.b = static_cast<const IO *>(b);
+    P.z = static_cast<IO *>(z);
+    P.skip = skip;
+    if (scr) {
+        P.wbuf = static_cast<T *>(scr->wbuf);
+        P.acc = static_cast<T *>(scr->acc);
+        P.part = static_cast<T *>(scr->part);
+        P.bar = scr->bar;
+        P.err = scr->err;
+    }
+}
+
+static pslr_status apply_launch(pslr_ctx *c, const void *b, void *z, int form, int dir, const int *skip,
                                 cudaStream_t st, const ApplyScratch *scr, bool may_allocate) {
+    const int prec = form == PSLR_FP64 ? 0 : 1;  // operator set: FP64 or FP32 segments
     OpSetHost &o = c->ops[dir][prec];
     const bool lr_before = c->r > 0 && dir == 0;
     const StreamDev *sd = find_stream(o, 0, c->m, lr_before);
@@ -1056,38 +1073,27 @@ static pslr_status apply_launch(pslr_ctx *c, const void *b, void *z, int prec, i
         if (ss != PSLR_OK) return ss;
     }
     cudaError_t e;
-    if (prec == PSLR_FP64) {
+    if (form == PSLR_FP64) {
         ApplyParams<double> P;
         fill_params(c, P, dir, prec, sd);
         P.V = c->d_Vr;
         P.G = dir ? c->d_GT : c->d_G;
-        P.b = static_cast<const double *>(b);
-        P.z = static_cast<double *>(z);
-        P.skip = skip;
-        if (scr) {
-            P.wbuf = static_cast<double *>(scr->wbuf);
-            P.acc = static_cast<double *>(scr->acc);
-            P.part = static_cast<double *>(scr->part);
-            P.bar = scr->bar;
-            P.err = scr->err;
-        }
+        set_io(P, b, z, skip, scr);
         e = launch_apply_fp64(P, o.smem, st);
-    } else {
+    } else if (form == PSLR_FP32) {
         ApplyParams<float> P;
         fill_params(c, P, dir, prec, sd);
         P.V = c->d_Vb;
         P.G = dir ? c->d_GTf : c->d_Gf;
-        P.b = static_cast<const float *>(b);
-        P.z = static_cast<float *>(z);
-        P.skip = skip;
-        if (scr) {
-            P.wbuf = static_cast<float *>(scr->wbuf);
-            P.acc = static_cast<float *>(scr->acc);
-            P.part = static_cast<float *>(scr->part);
-            P.bar = scr->bar;
-            P.err = scr->err;
-        }
+        set_io(P, b, z, skip, scr);
         e = launch_apply_fp32(P, o.smem, st);
+    } else {
+        ApplyParams<float, double> P;
+        fill_params(c, P, dir, prec, sd);
+        P.V = c->d_Vb;
+        P.G = dir ? c->d_GTf : c->d_Gf;
+        set_io(P, b, z, skip, scr);
+        e = launch_apply_f32d(P, o.smem, st);
     }
     if (e != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "apply launch: %s", cudaGetErrorString(e));
     return PSLR_OK;
@@ -1611,8 +1617,6 @@ static pslr_status krylov_alloc(pslr_ctx *c, int restart) {
     CK(cudaMalloc(&c->d_kH, sizeof(double) * (restart + 1) * restart));
     CK(cudaMalloc(&c->d_krot, sizeof(double) * 2 * (restart + 1)));
     CK(cudaMalloc(&c->d_kgam, sizeof(double) * (restart + 1)));
-    CK(cudaMalloc(&c->d_kf_in, sizeof(float) * n));
-    CK(cudaMalloc(&c->d_kf_out, sizeof(float) * n));
     CK(cudaMalloc(&c->d_kstate, sizeof(int) * 2));
     CK(cudaMalloc(&c->d_kskip, sizeof(int)));
     CK(cudaMalloc(&c->d_ktol, sizeof(double)));
@@ -1624,7 +1628,7 @@ static pslr_status krylov_alloc(pslr_ctx *c, int restart) {
 }
 
 // The Arnoldi steps j = 0 .. k-1 of one restart cycle (Section 4): apply the
-// preconditioner to v_j (FP32 form through a conversion on either side),
+// preconditioner to v_j (the FP32 form reads and writes the FP64 vectors),
 // orthogonalise A z_j against V by CGS2, update H, the Givens rotations and
 // gamma, and normalise v_{j+1}.  Once the Hessenberg kernel meets the
 // tolerance it raises the skip flag and every later kernel of the cycle
@@ -1637,13 +1641,7 @@ static pslr_status enqueue_arnoldi(pslr_ctx *c, int j0, int j1, int prec, int di
     for (int j = j0; j < j1; ++j) {
         double *vj = c->d_kV + (size_t)j * n, *zj = c->d_kZ + (size_t)j * n;
         pslr_status a;
-        if (prec == PSLR_FP64) {
-            a = apply_one(c, vj, zj, 0, dir, c->d_kskip, st);
-        } else {
-            launch_d2f(n, vj, c->d_kf_in, c->d_kskip, st);
-            a = apply_one(c, c->d_kf_in, c->d_kf_out, 1, dir, c->d_kskip, st);
-            launch_f2d(n, c->d_kf_out, zj, c->d_kskip, st);
-        }
+        a = apply_one(c, vj, zj, prec == PSLR_FP64 ? (int)PSLR_FP64 : kF32OnF64, dir, c->d_kskip, st);
         if (a != PSLR_OK) return a;
         cgs2(W, n, j + 1, c->d_kV, n, c->d_kw, rp, ci, av, zj, c->d_kskip, st);
         launch_hessenberg(j, W.h1, W.h2, W.wn2, c->d_kH, k + 1, W.hn, 1, c->d_krot, c->d_kgam, c->d_ktol,

@@ -95,8 +95,10 @@ PSLR_HD inline int64_t seg_bytes(int n, int w, bool diag) {
 // E_i^T and the rows of C_g^T of subdomain i.
 enum { kE = 0, kF = 1, kCg = 2, kB1 = 3, kB2 = 4, kC1 = 5, kC2 = 6, kNCnt = 7 };
 
-// Parameters of one launch of the persistent apply kernel.
-template <class T>
+// Parameters of one launch of the persistent apply kernel: arithmetic in T,
+// the caller's vectors b and z in IO (IO = double with T = float is the FP32
+// preconditioner applied to FP64 Krylov vectors, converting on the fly).
+template <class T, class IO = T>
 struct ApplyParams {
     const char *segbase;         // segments of this direction and precision
     const StreamEnt *stream;     // all CTAs' streams
@@ -115,8 +117,8 @@ struct ApplyParams {
     const void *V;               // q x r row-major, row stride ldv: double (FP64) or bf16 (FP32)
     int ldv;                     // row stride of V: r rounded up to a multiple of 8 (zero padded)
     const T *G;                  // r x r column-major (G, or G^T for the transpose)
-    const T *b;                  // n input, original order
-    T *z;                        // n output, original order
+    const IO *b;                 // n input, original order
+    IO *z;                       // n output, original order
     T *wbuf;                     // 2*(q+1): series iterates (ping-pong; slot q stays 0)
     T *acc;                      // q: series accumulator / low-rank staging
     T *part;                     // s*r: per-subdomain partial V^T t

@@ -250,18 +250,6 @@ __global__ void k_residual(int n, const int32_t *rp, const int32_t *ci, const do
     }
 }
 
-// Precision conversions for the FP32 preconditioner inside FP64 FGMRES.
-__global__ void k_d2f(int n, const double *a, float *b, const int *skip) {
-    if (skipping(skip)) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        b[i] = (float)a[i];
-}
-__global__ void k_f2d(int n, const float *a, double *b, const int *skip) {
-    if (skipping(skip)) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        b[i] = (double)a[i];
-}
-
 // SplitMix64 (Steele, Lea, Flood 2014), output j of the generator seeded with
 // seed, mapped to [-1, 1) from its top 53 bits: the Arnoldi start vector.
 __global__ void k_splitmix(int n, uint64_t seed, uint64_t j0, double *v) {
@@ -334,14 +322,6 @@ void launch_gemv_add(int n, int k, const double *Z, int64_t ld, const double *y,
 void launch_residual(int n, const int32_t *rp, const int32_t *ci, const double *av, const double *x,
                      const double *b, double *r, cudaStream_t st) {
     k_residual<<<krylov_blocks(n), kKThreads, 0, st>>>(n, rp, ci, av, x, b, r);
-}
-
-void launch_d2f(int n, const double *a, float *b, const int *skip, cudaStream_t st) {
-    k_d2f<<<krylov_blocks(n), kKThreads, 0, st>>>(n, a, b, skip);
-}
-
-void launch_f2d(int n, const float *a, double *b, const int *skip, cudaStream_t st) {
-    k_f2d<<<krylov_blocks(n), kKThreads, 0, st>>>(n, a, b, skip);
 }
 
 void launch_grad_values(int n, const int32_t *rp, const int32_t *ci, const double *lambda, const double *u,
