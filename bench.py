@@ -337,6 +337,7 @@ def run_batch(dev, flush, stream, steps, warmup, seq_stride, solve=True):
         out[name] = {"ms": 1e3 * (time.perf_counter() - c0), "restart": restart, "iters_max": int(its.max()),
                      "iters_mean": float(its.mean()), "converged": int((rel <= 1e-8).sum()),
                      "relres_max": float(rel.max()), "graph": bt.info["graph"],
+                     "finished_per_system": bt.info["handoff"],
                      "rel_err_vs_xstar": float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))}
     # the plain FP64 GPU form: one pslr_solve per (system, rhs), on a sample
     t_seq, n_seq, its_seq, conv_seq = 0.0, 0, 0, 0

@@ -271,6 +271,7 @@ typedef struct {
     int64_t apply_bytes_fp64;       /* algorithmic bytes of one batched apply        */
     int64_t apply_bytes_fp32;
     int32_t graph;                  /* 1: the last solve replayed its cycles as CUDA graphs */
+    int32_t handoff;                /* problems the last solve finished one by one (pslr_solve) */
 } pslr_batch_info;
 
 /*
@@ -306,8 +307,14 @@ pslr_status pslr_batch_apply(pslr_batch *bt, const void *b_dev, void *z_dev, psl
  * (double, nprob) are optional host arrays, problem order.  Each restart
  * cycle is captured once as a CUDA graph and replayed; if capture is not
  * available the same launches are issued directly (pslr_batch_info.graph
- * says which).  Synchronises `stream` once per cycle.  Returns PSLR_OK when
- * every problem converged, PSLR_ERR_NAN if one went non-finite, else
+ * says which).  Synchronises `stream` once per cycle.  When at most 4 of
+ * more than 4 problems are still running at the end of a cycle, each of them
+ * is finished on its own system with pslr_solve on its current residual
+ * (solving A e = b - A x to the tolerance rtol ||b|| and adding e): the same
+ * restarted iteration, without a whole batched step per iteration
+ * (pslr_batch_info.handoff counts them; it uses the system contexts' own
+ * Krylov workspace and `stream`).  Returns PSLR_OK when every problem
+ * converged, PSLR_ERR_NAN if one went non-finite, else
  * PSLR_ERR_NOT_CONVERGED.  restart: 1..127.
  */
 pslr_status pslr_batch_solve(pslr_batch *bt, const double *b_dev, double *x_dev, double rtol, int32_t restart,

@@ -57,6 +57,7 @@ void bk_residual(int nchunk, const BkChunk *ch, const BkProb *pr, const BkSys *s
                  const double *b, double *r, const BkState &S, cudaStream_t st);
 void bk_restart(int first, int nprob, const BkProb *pr, const BkState &S, cudaStream_t st);
 void bk_start(int nchunk, const BkChunk *ch, const double *r, double *v, const BkState &S, cudaStream_t st);
+void launch_axpy(int n, double a, const double *x, double *y, cudaStream_t st);
 }  // namespace pslr
 
 using namespace pslr;
@@ -101,6 +102,9 @@ struct pslr_batch {
     cudaStream_t cap = nullptr;
     std::map<std::tuple<int, int, long long>, cudaGraphExec_t> graphs;  // (form, restart, wait limit)
     int graph_used = 0;
+    std::vector<BkProb> h_probs;  // host copy of the problem table
+    double *d_e = nullptr;        // correction of one problem finished on its own system
+    int handoff = 0;              // problems the last solve finished one by one
     std::string err;
 };
 
@@ -140,8 +144,8 @@ void free_krylov(pslr_batch *bt) {
     for (auto &kv : bt->graphs) cudaGraphExecDestroy(kv.second);
     bt->graphs.clear();
     dfree(bt->d_V); dfree(bt->d_Z); dfree(bt->d_w); dfree(bt->d_r); dfree(bt->d_b); dfree(bt->d_x);
-    dfree(bt->d_state);
-    bt->d_V = bt->d_Z = bt->d_w = bt->d_r = bt->d_b = bt->d_x = nullptr;
+    dfree(bt->d_state); dfree(bt->d_e);
+    bt->d_V = bt->d_Z = bt->d_w = bt->d_r = bt->d_b = bt->d_x = bt->d_e = nullptr;
     bt->d_state = nullptr;
     bt->kK = 0;
 }
@@ -691,6 +695,7 @@ static pslr_status batch_build(pslr_batch *bt) {
         bs[k].av = bt->sx[k].av;
     }
     bt->nchunk = (int)chunks.size();
+    bt->h_probs = probs;
     BCK(upload(&bt->d_chunks, chunks));
     BCK(upload(&bt->d_probs, probs));
     BCK(upload(&bt->d_bsys, bs));
@@ -847,6 +852,55 @@ static pslr_status enqueue_cycle(pslr_batch *bt, int form, cudaStream_t st) {
 
 // The cycle as a CUDA graph (captured on the batch's own stream), or nullptr
 // when capture or instantiation is not available.
+// Problems that still run when at most this many remain are finished one by
+// one on their own system (pslr_solve), which costs one single-system
+// iteration per step instead of a whole batched step.
+constexpr int kHandoffProblems = 4;
+
+// Finish the running problems one by one.  At a cycle boundary the restarted
+// FGMRES of problem p depends only on its current residual r = b - A x (in
+// d_r after the cycle end), so solving A e = r with the relative tolerance
+// rtol ||b|| / ||r|| and adding e to x continues exactly the same iteration
+// (the same Krylov spaces, the same stopping test rtol ||b||), up to rounding.
+static pslr_status handoff(pslr_batch *bt, double rtol, int restart, int maxit, pslr_prec prec, cudaStream_t s) {
+    const BkState &S = bt->S;
+    const int P = bt->nprob;
+    std::vector<int> conv(P), its(P);
+    std::vector<double> bn(P), rn(P), rel(P);
+    BCK(cudaMemcpyAsync(conv.data(), S.conv, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(its.data(), S.its, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(bn.data(), S.bn, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(rn.data(), S.rn, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(rel.data(), S.relres, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    if (!bt->d_e) {
+        int nmax = 1;
+        for (const SysExport &e : bt->sx) nmax = std::max(nmax, e.n);
+        BCK(cudaMalloc(&bt->d_e, sizeof(double) * nmax));
+    }
+    for (int p = 0; p < P; ++p) {
+        if (conv[p] != 0) continue;
+        const BkProb &pr = bt->h_probs[p];
+        int its2 = 0;
+        double rel2 = 0.0;
+        const pslr_status st = pslr_solve(bt->ctx[pr.sys], bt->d_r + pr.off, bt->d_e, rtol * bn[p] / rn[p], restart,
+                                          maxit - its[p], prec, 0, &its2, &rel2, s);
+        if (st != PSLR_OK && st != PSLR_ERR_NOT_CONVERGED && st != PSLR_ERR_NAN)
+            return bfail(bt, st, "batch_solve: finishing problem %d on its system: %s", p,
+                         pslr_last_error(bt->ctx[pr.sys]));
+        if (st != PSLR_ERR_NAN) launch_axpy(pr.n, 1.0, bt->d_e, bt->d_x + pr.off, s);
+        its[p] += its2;
+        rel[p] = rel2 * rn[p] / bn[p];
+        conv[p] = st == PSLR_OK ? 1 : (st == PSLR_ERR_NAN ? 3 : 2);
+        ++bt->handoff;
+    }
+    BCK(cudaMemcpyAsync(S.conv, conv.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(S.its, its.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(S.relres, rel.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s));
+    BCK(cudaStreamSynchronize(s));  // the host vectors above must outlive the copies
+    return PSLR_OK;
+}
+
 static cudaGraphExec_t cycle_graph(pslr_batch *bt, int form) {
     const auto key = std::make_tuple(form, bt->S.K, bt->wait_limit);
     auto it = bt->graphs.find(key);
@@ -951,6 +1005,7 @@ pslr_status pslr_batch_solve(pslr_batch *bt, const double *b_dev, double *x_dev,
     BCK(cudaStreamSynchronize(s));
     cudaGraphExec_t g = remaining > 0 ? cycle_graph(bt, form) : nullptr;
     bt->graph_used = g != nullptr;
+    bt->handoff = 0;
     for (int cyc = 0; remaining > 0 && cyc <= maxit; ++cyc) {
         if (g) {
             BCK(cudaGraphLaunch(g, s));
@@ -961,6 +1016,11 @@ pslr_status pslr_batch_solve(pslr_batch *bt, const double *b_dev, double *x_dev,
         BCK(cudaMemcpyAsync(&remaining, S.remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
         st = pslr_batch_sync(bt, stream);
         if (st != PSLR_OK) return st;
+        if (remaining > 0 && remaining <= kHandoffProblems && P > kHandoffProblems) {
+            st = handoff(bt, rtol, restart, maxit, prec, s);
+            if (st != PSLR_OK) return st;
+            remaining = 0;
+        }
     }
     BCK(cudaMemcpyAsync(x_dev, bt->d_x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
     std::vector<int> conv(P), its(P);
@@ -1003,6 +1063,7 @@ pslr_status pslr_batch_get_info(const pslr_batch *bt, pslr_batch_info *info) {
     info->apply_bytes_fp64 = bt->apply_bytes[0];
     info->apply_bytes_fp32 = bt->apply_bytes[1];
     info->graph = bt->graph_used;
+    info->handoff = bt->handoff;
     return PSLR_OK;
 }
 

@@ -231,6 +231,11 @@ __global__ void k_normalize(int n, const double *w, double *v, const double *hn,
         v[i] = w[i] * s;
 }
 
+// y += a x.
+__global__ void k_axpy(int n, double a, const double *x, double *y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = fma(a, x[i], y[i]);
+}
+
 // x += Z(:, 0:k) y  (y on the device).
 __global__ void k_gemv_add(int n, int k, const double *Z, int64_t ld, const double *y, double *x) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -312,6 +317,10 @@ void launch_hessenberg(int j, const double *h1, const double *h2, const double *
 void launch_normalize(int n, const double *w, double *v, const double *hn, const int *skip,
                       cudaStream_t st) {
     k_normalize<<<krylov_blocks(n), kKThreads, 0, st>>>(n, w, v, hn, skip);
+}
+
+void launch_axpy(int n, double a, const double *x, double *y, cudaStream_t st) {
+    k_axpy<<<krylov_blocks(n), kKThreads, 0, st>>>(n, a, x, y);
 }
 
 void launch_gemv_add(int n, int k, const double *Z, int64_t ld, const double *y, double *x,

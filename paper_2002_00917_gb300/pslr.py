@@ -55,7 +55,7 @@ class pslr_batch_info(C.Structure):
                 ("items", C.c_int32), ("grid", C.c_int32), ("ring", C.c_int32 * 2),
                 ("group", C.c_int32 * 2), ("groups", C.c_int32 * 2), ("max_m", C.c_int32),
                 ("max_p", C.c_int32), ("max_q", C.c_int32), ("apply_bytes_fp64", C.c_int64),
-                ("apply_bytes_fp32", C.c_int64), ("graph", C.c_int32)]
+                ("apply_bytes_fp32", C.c_int64), ("graph", C.c_int32), ("handoff", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
