@@ -436,6 +436,7 @@ struct pslr_ctx {
     double *d_eab = nullptr;  // E_rr scratch 2(q+1)
     void *d_io_b = nullptr, *d_io_z = nullptr;  // pslr_apply_host staging
     size_t io_bytes = 0;
+    int *h_err = nullptr;  // pinned host copy of the error word (pslr_sync)
     std::string err;
 };
 
@@ -647,6 +648,7 @@ void pslr_destroy(pslr_ctx *c) {
     free_krylov(c);
     free_lowrank(c);
     if (c->kcap) cudaStreamDestroy(c->kcap);
+    if (c->h_err) cudaFreeHost(c->h_err);
     for (void *p : {(void *)c->d_perm, (void *)c->d_ioff, (void *)c->d_goff, (void *)c->d_bpiv,
                     (void *)c->d_cpiv, (void *)c->d_rp, (void *)c->d_ci, (void *)c->d_rpT, (void *)c->d_ciT,
                     (void *)c->d_av, (void *)c->d_avT, (void *)c->d_wbuf, (void *)c->d_acc, (void *)c->d_bar,
@@ -1196,9 +1198,12 @@ pslr_status pslr_apply_T(pslr_ctx *c, const void *b_dev, void *z_dev, int32_t nr
 
 pslr_status pslr_sync(pslr_ctx *c, void *stream) {
     if (!c) return PSLR_ERR_ARG;
-    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
-    int e = 0;
-    CK(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!c->h_err) CK(cudaMallocHost(&c->h_err, sizeof(int)));
+    // the error word rides on the stream: one synchronisation, no blocking copy after it
+    CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int e = *c->h_err;
     if (e != 0) {
         CK(cudaMemset(c->d_err, 0, sizeof(int)));
         CK(cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned)));
