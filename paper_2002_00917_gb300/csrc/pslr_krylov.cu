@@ -279,16 +279,17 @@ __global__ void k_grad_values(int n, const int32_t *rp, const int32_t *ci, const
 
 // ---------------------------------------------------------------- launchers
 
-// Blocks of the Krylov kernels: two rows per thread, at most two blocks per
-// SM (so large vectors spread evenly over every SM's FP64 pipe), and within
-// the reduction's ticket array.  (64^3 FGMRES(120): 304 blocks beat 256 by
-// 1.5% with the column-wise dot products.)
+// Blocks of the Krylov kernels: one row per thread, at most three blocks per
+// SM (so large vectors spread evenly over every SM's FP64 pipe, with enough
+// warps to cover the loads of V), and within the reduction's ticket array.
+// (64^3 FGMRES(120) with the column-wise dot products: 3 blocks per SM
+// 442 ms, 4 per SM 443 ms, 2 per SM 454 ms, 256 blocks 460 ms.)
 int krylov_blocks(int n) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int want = (n + kKThreads * 2 - 1) / (kKThreads * 2);
-    int cap = 2 * nsm;
+    int want = (n + kKThreads - 1) / kKThreads;
+    int cap = 3 * nsm;
     if (cap > (kMaxTickets - 1) * kRedGroup) cap = (kMaxTickets - 1) * kRedGroup;
     if (want > cap) want = cap;
     return want < 1 ? 1 : want;
