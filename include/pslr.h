@@ -307,15 +307,17 @@ pslr_status pslr_batch_apply(pslr_batch *bt, const void *b_dev, void *z_dev, psl
  * (double, nprob) are optional host arrays, problem order.  Each restart
  * cycle is captured once as a CUDA graph and replayed; if capture is not
  * available the same launches are issued directly (pslr_batch_info.graph
- * says which).  Synchronises `stream` once per cycle.  When at most 4 of
- * more than 4 problems are still running at the end of a cycle, each of them
+ * says which).  Synchronises `stream` once per cycle.  When at most 16 of
+ * more than 16 problems are still running at the end of a cycle, each of them
  * is finished on its own system with pslr_solve on its current residual
  * (solving A e = b - A x to the tolerance rtol ||b|| and adding e): the same
- * restarted iteration, without a whole batched step per iteration
- * (pslr_batch_info.handoff counts them; it uses the system contexts' own
- * Krylov workspace and `stream`).  Returns PSLR_OK when every problem
- * converged, PSLR_ERR_NAN if one went non-finite, else
- * PSLR_ERR_NOT_CONVERGED.  restart: 1..127.
+ * restarted iteration, without a whole batched step per iteration.  The
+ * systems involved run at once, each from its own host thread on its own
+ * stream (created by the batch), their problems one after another; this
+ * uses the system contexts' own Krylov workspace, so no other call may use
+ * those contexts meanwhile.  pslr_batch_info.handoff counts these problems.
+ * Returns PSLR_OK when every problem converged, PSLR_ERR_NAN if one went
+ * non-finite, else PSLR_ERR_NOT_CONVERGED.  restart: 1..127.
  */
 pslr_status pslr_batch_solve(pslr_batch *bt, const double *b_dev, double *x_dev, double rtol, int32_t restart,
                              int32_t maxit, pslr_prec prec, int32_t *iters, double *relres, void *stream);

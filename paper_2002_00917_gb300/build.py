@@ -46,7 +46,7 @@ def _compile(src):
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     if not _stale(obj, [src] + HEADERS):
         return obj
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-pthread",
            "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj + ".tmp"]
     if src.endswith(".cpp"):
         cmd[1:1] = ["-x", "cu"]
@@ -69,7 +69,7 @@ def build(force=False, verbose=False):
     with cf.ThreadPoolExecutor(len(srcs)) as ex:
         objs = list(ex.map(_compile, srcs))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC,-pthread", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

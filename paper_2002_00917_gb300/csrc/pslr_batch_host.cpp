@@ -9,8 +9,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <type_traits>
 #include <vector>
@@ -102,9 +104,10 @@ struct pslr_batch {
     cudaStream_t cap = nullptr;
     std::map<std::tuple<int, int, long long>, cudaGraphExec_t> graphs;  // (form, restart, wait limit)
     int graph_used = 0;
-    std::vector<BkProb> h_probs;  // host copy of the problem table
-    double *d_e = nullptr;        // correction of one problem finished on its own system
-    int handoff = 0;              // problems the last solve finished one by one
+    std::vector<BkProb> h_probs;       // host copy of the problem table
+    std::vector<cudaStream_t> hstream;  // per system: stream of the problems finished on it
+    std::vector<double *> he;           // per system: correction of one such problem
+    int handoff = 0;                    // problems the last solve finished on their systems
     std::string err;
 };
 
@@ -144,8 +147,12 @@ void free_krylov(pslr_batch *bt) {
     for (auto &kv : bt->graphs) cudaGraphExecDestroy(kv.second);
     bt->graphs.clear();
     dfree(bt->d_V); dfree(bt->d_Z); dfree(bt->d_w); dfree(bt->d_r); dfree(bt->d_b); dfree(bt->d_x);
-    dfree(bt->d_state); dfree(bt->d_e);
-    bt->d_V = bt->d_Z = bt->d_w = bt->d_r = bt->d_b = bt->d_x = bt->d_e = nullptr;
+    dfree(bt->d_state);
+    for (double *&e : bt->he) {
+        dfree(e);
+        e = nullptr;
+    }
+    bt->d_V = bt->d_Z = bt->d_w = bt->d_r = bt->d_b = bt->d_x = nullptr;
     bt->d_state = nullptr;
     bt->kK = 0;
 }
@@ -164,6 +171,8 @@ void free_batch(pslr_batch *bt) {
     dfree(bt->d_scratch); dfree(bt->d_bar); dfree(bt->d_err);
     dfree(bt->d_chunks); dfree(bt->d_probs); dfree(bt->d_bsys);
     if (bt->cap) cudaStreamDestroy(bt->cap);
+    for (cudaStream_t h : bt->hstream)
+        if (h) cudaStreamDestroy(h);
 }
 
 // ------------------------------------------------- merged segments of a group
@@ -852,16 +861,18 @@ static pslr_status enqueue_cycle(pslr_batch *bt, int form, cudaStream_t st) {
 
 // The cycle as a CUDA graph (captured on the batch's own stream), or nullptr
 // when capture or instantiation is not available.
-// Problems that still run when at most this many remain are finished one by
-// one on their own system (pslr_solve), which costs one single-system
-// iteration per step instead of a whole batched step.
-constexpr int kHandoffProblems = 4;
+// Problems that still run when at most this many remain are finished on
+// their own systems (pslr_solve): one single-system iteration per step
+// instead of a whole batched step, and the systems in parallel.
+constexpr int kHandoffProblems = 16;
 
-// Finish the running problems one by one.  At a cycle boundary the restarted
-// FGMRES of problem p depends only on its current residual r = b - A x (in
-// d_r after the cycle end), so solving A e = r with the relative tolerance
-// rtol ||b|| / ||r|| and adding e to x continues exactly the same iteration
-// (the same Krylov spaces, the same stopping test rtol ||b||), up to rounding.
+// Finish the running problems on their own systems.  At a cycle boundary the
+// restarted FGMRES of problem p depends only on its current residual r =
+// b - A x (in d_r after the cycle end), so solving A e = r with the relative
+// tolerance rtol ||b|| / ||r|| and adding e to x continues exactly the same
+// iteration (the same Krylov spaces, the same stopping test rtol ||b||), up
+// to rounding.  One host thread and stream per system: a system's problems
+// run one after another (they share its context), different systems at once.
 static pslr_status handoff(pslr_batch *bt, double rtol, int restart, int maxit, pslr_prec prec, cudaStream_t s) {
     const BkState &S = bt->S;
     const int P = bt->nprob;
@@ -872,28 +883,71 @@ static pslr_status handoff(pslr_batch *bt, double rtol, int restart, int maxit, 
     BCK(cudaMemcpyAsync(bn.data(), S.bn, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
     BCK(cudaMemcpyAsync(rn.data(), S.rn, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
     BCK(cudaMemcpyAsync(rel.data(), S.relres, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
-    BCK(cudaStreamSynchronize(s));
-    if (!bt->d_e) {
-        int nmax = 1;
-        for (const SysExport &e : bt->sx) nmax = std::max(nmax, e.n);
-        BCK(cudaMalloc(&bt->d_e, sizeof(double) * nmax));
+    BCK(cudaStreamSynchronize(s));  // also: d_r and d_x of the last cycle are complete
+    std::map<int, std::vector<int>> by_sys;
+    for (int p = 0; p < P; ++p)
+        if (conv[p] == 0) by_sys[bt->h_probs[p].sys].push_back(p);
+    if (bt->hstream.empty()) {
+        bt->hstream.assign(bt->nsys, nullptr);
+        bt->he.assign(bt->nsys, nullptr);
     }
-    for (int p = 0; p < P; ++p) {
-        if (conv[p] != 0) continue;
-        const BkProb &pr = bt->h_probs[p];
-        int its2 = 0;
-        double rel2 = 0.0;
-        const pslr_status st = pslr_solve(bt->ctx[pr.sys], bt->d_r + pr.off, bt->d_e, rtol * bn[p] / rn[p], restart,
-                                          maxit - its[p], prec, 0, &its2, &rel2, s);
-        if (st != PSLR_OK && st != PSLR_ERR_NOT_CONVERGED && st != PSLR_ERR_NAN)
-            return bfail(bt, st, "batch_solve: finishing problem %d on its system: %s", p,
-                         pslr_last_error(bt->ctx[pr.sys]));
-        if (st != PSLR_ERR_NAN) launch_axpy(pr.n, 1.0, bt->d_e, bt->d_x + pr.off, s);
-        its[p] += its2;
-        rel[p] = rel2 * rn[p] / bn[p];
-        conv[p] = st == PSLR_OK ? 1 : (st == PSLR_ERR_NAN ? 3 : 2);
-        ++bt->handoff;
+    for (const auto &kv : by_sys) {
+        const int k = kv.first;
+        if (!bt->hstream[k]) BCK(cudaStreamCreateWithFlags(&bt->hstream[k], cudaStreamNonBlocking));
+        if (!bt->he[k]) BCK(cudaMalloc(&bt->he[k], sizeof(double) * std::max(1, bt->sx[k].n)));
     }
+    int dev = 0;
+    BCK(cudaGetDevice(&dev));
+    struct Job {
+        int sys;
+        const std::vector<int> *probs;
+        pslr_status status = PSLR_OK;
+        int failed = -1;
+    };
+    std::vector<Job> jobs;
+    for (const auto &kv : by_sys) jobs.push_back(Job{kv.first, &kv.second});
+    auto work = [&](Job &J) {
+        if (cudaSetDevice(dev) != cudaSuccess) {
+            J.status = PSLR_ERR_CUDA;
+            return;
+        }
+        cudaStream_t hs = bt->hstream[J.sys];
+        double *e = bt->he[J.sys];
+        for (int p : *J.probs) {  // each p belongs to this job alone
+            const BkProb &pr = bt->h_probs[p];
+            int its2 = 0;
+            double rel2 = 0.0;
+            const pslr_status st = pslr_solve(bt->ctx[J.sys], bt->d_r + pr.off, e, rtol * bn[p] / rn[p], restart,
+                                              maxit - its[p], prec, 0, &its2, &rel2, hs);
+            if (st != PSLR_OK && st != PSLR_ERR_NOT_CONVERGED && st != PSLR_ERR_NAN) {
+                J.status = st;
+                J.failed = p;
+                return;
+            }
+            if (st != PSLR_ERR_NAN) launch_axpy(pr.n, 1.0, e, bt->d_x + pr.off, hs);
+            its[p] += its2;
+            rel[p] = rel2 * rn[p] / bn[p];
+            conv[p] = st == PSLR_OK ? 1 : (st == PSLR_ERR_NAN ? 3 : 2);
+        }
+        if (cudaStreamSynchronize(hs) != cudaSuccess) J.status = PSLR_ERR_CUDA;
+    };
+    if (jobs.size() == 1) {
+        work(jobs[0]);
+    } else {
+        std::vector<std::thread> th;
+        th.reserve(jobs.size());
+        for (Job &J : jobs) th.emplace_back(work, std::ref(J));
+        for (std::thread &t : th) t.join();
+    }
+    for (const Job &J : jobs) {
+        if (J.status == PSLR_OK) continue;
+        if (J.failed >= 0)
+            return bfail(bt, J.status, "batch_solve: finishing problem %d on its system: %s", J.failed,
+                         pslr_last_error(bt->ctx[J.sys]));
+        return bfail(bt, J.status, "batch_solve: finishing problems on system %d: %s", J.sys,
+                     cudaGetErrorString(cudaGetLastError()));
+    }
+    for (const Job &J : jobs) bt->handoff += (int)J.probs->size();
     BCK(cudaMemcpyAsync(S.conv, conv.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
     BCK(cudaMemcpyAsync(S.its, its.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
     BCK(cudaMemcpyAsync(S.relres, rel.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s));

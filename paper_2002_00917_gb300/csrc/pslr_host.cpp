@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -30,6 +31,12 @@ cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, cudaStream
 cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, cudaStream_t st);
 cudaError_t launch_apply_f32d(const ApplyParams<float, double> &P, int smem, cudaStream_t st);
 cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, cudaStream_t st);
+
+// The persistent kernels' launchers set the kernel's dynamic shared-memory
+// limit and then launch; contexts applied from several host threads at once
+// (the batched solve finishing problems on their systems) must not interleave
+// these two steps, or one launch can meet another context's smaller limit.
+static std::mutex g_launch_mutex;
 int max_coresident_apply(int smem, bool fp32);
 int krylov_blocks(int n);
 size_t krylov_part_doubles(int nblk, int nres);
@@ -1075,6 +1082,7 @@ static pslr_status apply_launch(pslr_ctx *c, const void *b, void *z, int form, i
         if (ss != PSLR_OK) return ss;
     }
     cudaError_t e;
+    std::lock_guard<std::mutex> lock(g_launch_mutex);
     if (form == PSLR_FP64) {
         ApplyParams<double> P;
         fill_params(c, P, dir, prec, sd);
@@ -1494,7 +1502,11 @@ static pslr_status launch_err(pslr_ctx *c, const double *vin, double *vout, int 
     P.bar = c->d_bar;
     P.err = c->d_err;
     P.wait_limit = c->wait_limit;
-    cudaError_t e = launch_err_fp64(P, o.smem, st);
+    cudaError_t e;
+    {
+        std::lock_guard<std::mutex> lock(g_launch_mutex);
+        e = launch_err_fp64(P, o.smem, st);
+    }
     if (e != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "E_rr launch: %s", cudaGetErrorString(e));
     return PSLR_OK;
 }
