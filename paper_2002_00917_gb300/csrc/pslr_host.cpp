@@ -44,9 +44,9 @@ int krylov_tickets();
 void launch_cgs_pass(int n, int k, const double *V, int64_t ld, double *w, const double *hsub, int norm,
                      double *part, double *res, unsigned *ticket, const int32_t *rp, const int32_t *ci,
                      const double *av, const double *z, const int *skip, cudaStream_t st);
-void launch_hessenberg(int j, const double *h1, const double *h2, const double *wn2, double *H, int ldh,
-                       double *hn, int givens, double *rot, double *gam, const double *tol_abs, int *state,
-                       int *skip, cudaStream_t st);
+void launch_hess_normalize(int j, const double *h1, const double *h2, const double *wn2, double *H, int ldh,
+                           double *rot, double *gam, const double *tol_abs, int *state, int *skip, int n,
+                           const double *w, double *v, cudaStream_t st);
 void launch_normalize(int n, const double *w, double *v, const double *hn, const int *skip,
                       cudaStream_t st);
 void launch_gemv_add(int n, int k, const double *Z, int64_t ld, const double *y, double *x,
@@ -1661,9 +1661,8 @@ static pslr_status enqueue_arnoldi(pslr_ctx *c, int j0, int j1, int prec, int di
         a = apply_one(c, vj, zj, prec == PSLR_FP64 ? (int)PSLR_FP64 : kF32OnF64, dir, c->d_kskip, st);
         if (a != PSLR_OK) return a;
         cgs2(W, n, j + 1, c->d_kV, n, c->d_kw, rp, ci, av, zj, c->d_kskip, st);
-        launch_hessenberg(j, W.h1, W.h2, W.wn2, c->d_kH, k + 1, W.hn, 1, c->d_krot, c->d_kgam, c->d_ktol,
-                          c->d_kstate, c->d_kskip, st);
-        launch_normalize(n, c->d_kw, c->d_kV + (size_t)(j + 1) * n, W.hn, c->d_kskip, st);
+        launch_hess_normalize(j, W.h1, W.h2, W.wn2, c->d_kH, k + 1, c->d_krot, c->d_kgam, c->d_ktol, c->d_kstate,
+                              c->d_kskip, n, c->d_kw, c->d_kV + (size_t)(j + 1) * n, st);
     }
     return PSLR_OK;
 }

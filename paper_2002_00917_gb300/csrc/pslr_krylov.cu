@@ -9,8 +9,9 @@
 //   pass 1  w = A z (optional, fused CSR SpMV), h1 = V^T w
 //   pass 2  w -= V h1,                        h2 = V^T w
 //   pass 3  w -= V h2,                        ||w||^2
-// then one thread forms h = h1 + h2, h_{j+1,j} = ||w|| and (FGMRES) applies
-// the Givens rotations, and a last launch writes v_{j+1} = w / h_{j+1,j}.
+// then, in FGMRES, one launch writes v_{j+1} = w / h_{j+1,j} while one warp
+// of it forms h = h1 + h2, h_{j+1,j} = ||w|| and applies the Givens
+// rotations (the Arnoldi of Algorithm 1 normalises with host-side norms).
 // The second pass is not optional here: with a good preconditioner
 // A M^{-1} v_j is close to v_j, so the first projection removes almost all of
 // w and a selective test (norm drop below 1/sqrt(2)) asks for it every step.
@@ -166,36 +167,32 @@ __global__ void __launch_bounds__(kKThreads) k_cgs_pass(
     finish_reduction(part, nres, res, ticket, false);
 }
 
-// Column j of the Hessenberg matrix from h1 + h2 and ||w||^2, and
-// (givens != 0) the FGMRES least-squares update with Givens rotations; the
-// cycle stops once |gam(j+1)| <= *tol_abs (device memory, so a captured
-// cycle serves every tolerance).
+// Column j of the Hessenberg matrix from h1 + h2 and ||w||^2, and the FGMRES
+// least-squares update with Givens rotations; the cycle stops once
+// |gam(j+1)| <= *tol_abs (device memory, so a captured cycle serves every
+// tolerance).
 // H is (ldh x *) column-major; rot = [cs(0:ldh), sn(0:ldh)]; gam (ldh).
 // state: [0] = iterations done in this cycle, [1] = converged/stop flag.
-__global__ void k_hessenberg(int j, const double *h1, const double *h2, const double *wn2, double *H,
-                             int ldh, double *hn_out, int givens, double *rot, double *gam,
-                             const double *tol_abs, int *state, int *skip) {
-    // one warp: the column and the rotations are staged in shared memory, so
-    // the sequential rotation chain runs on shared-memory and register latency
-    __shared__ double c[kMaxK + 2], scs[kMaxK + 1], ssn[kMaxK + 1];
-    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-    if (skipping(skip)) return;
-    const int lane = threadIdx.x;
+// One warp: the column and the rotations are staged in shared memory (c,
+// scs, ssn), so the sequential rotation chain runs on shared-memory and
+// register latency.
+__device__ void hess_column(int j, const double *h1, const double *h2, const double *wn2, double *H, int ldh,
+                            double *rot, double *gam, const double *tol_abs, int *state, int *skip, double *c,
+                            double *scs, double *ssn) {
+    const int lane = threadIdx.x & 31;
     double *col = H + (int64_t)j * ldh;
     double *cs = rot, *sn = rot + ldh;
     const double hn = sqrt(*wn2);
     for (int i = lane; i <= j; i += 32) c[i] = h1[i] + h2[i];
-    if (givens)
-        for (int i = lane; i < j; i += 32) {
-            scs[i] = cs[i];
-            ssn[i] = sn[i];
-        }
+    for (int i = lane; i < j; i += 32) {
+        scs[i] = cs[i];
+        ssn[i] = sn[i];
+    }
     __syncwarp();
     if (lane == 0) {
         c[j + 1] = hn;
-        *hn_out = hn;
         state[0] = j + 1;
-        if (givens) {
+        {
             double carry = c[0];  // entry i after the rotations before i
             for (int i = 0; i < j; ++i) {
                 const double a = carry, b = c[i + 1], ci = scs[i], si = ssn[i];
@@ -220,6 +217,26 @@ __global__ void k_hessenberg(int j, const double *h1, const double *h2, const do
     }
     __syncwarp();
     for (int i = lane; i <= j + 1; i += 32) col[i] = c[i];
+}
+
+// The FGMRES step's last launch: v = w / ||w|| in blocks 0 .. gridDim.x-2
+// (each block takes ||w|| from ||w||^2 itself, as hess_column does, so the
+// results are those of the separate kernels), while one warp of the last
+// block forms the Hessenberg column and applies the rotations.  If that stops
+// the cycle, v is not used, so normalising blocks that start later may skip.
+__global__ void k_hess_normalize(int j, const double *h1, const double *h2, const double *wn2, double *H,
+                                 int ldh, double *rot, double *gam, const double *tol_abs, int *state,
+                                 int *skip, int n, const double *w, double *v) {
+    __shared__ double c[kMaxK + 2], scs[kMaxK + 1], ssn[kMaxK + 1];
+    if (skipping(skip)) return;
+    const int nb = gridDim.x - 1;
+    if ((int)blockIdx.x == nb) {
+        if (threadIdx.x < 32) hess_column(j, h1, h2, wn2, H, ldh, rot, gam, tol_abs, state, skip, c, scs, ssn);
+        return;
+    }
+    const double h = sqrt(*wn2);
+    const double s = h > 0.0 ? 1.0 / h : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nb * blockDim.x) v[i] = w[i] * s;
 }
 
 // v = w / *hn  (hn == 0 leaves v = 0).
@@ -309,10 +326,11 @@ void launch_cgs_pass(int n, int k, const double *V, int64_t ld, double *w, const
                                                        rp, ci, av, z, skip);
 }
 
-void launch_hessenberg(int j, const double *h1, const double *h2, const double *wn2, double *H,
-                       int ldh, double *hn, int givens, double *rot, double *gam, const double *tol_abs,
-                       int *state, int *skip, cudaStream_t st) {
-    k_hessenberg<<<1, 32, 0, st>>>(j, h1, h2, wn2, H, ldh, hn, givens, rot, gam, tol_abs, state, skip);
+void launch_hess_normalize(int j, const double *h1, const double *h2, const double *wn2, double *H, int ldh,
+                           double *rot, double *gam, const double *tol_abs, int *state, int *skip, int n,
+                           const double *w, double *v, cudaStream_t st) {
+    k_hess_normalize<<<krylov_blocks(n) + 1, kKThreads, 0, st>>>(j, h1, h2, wn2, H, ldh, rot, gam, tol_abs,
+                                                                 state, skip, n, w, v);
 }
 
 void launch_normalize(int n, const double *w, double *v, const double *hn, const int *skip,
