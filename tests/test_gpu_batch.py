@@ -251,7 +251,33 @@ def test_batch_solve_finishes_stragglers_per_system(dev, prec):
             assert np.linalg.norm(r) <= 1.0001e-8 * np.linalg.norm(bk[j]), (k, j)
 
 
-def test_batch_solve_maxit_and_zero_rhs(dev):
+
+def test_batch_solve_handoff_reaches_maxit(dev):
+    """Problems finished on their own systems keep the batch's iteration
+    limit: with maxit 60 (restart 20) the six problems still running after
+    two cycles are handed off with 20 iterations left; they stop at exactly
+    60, the call reports PSLR_ERR_NOT_CONVERGED, and every returned relative
+    residual is the true one of the returned x."""
+    from paper_2002_00917_gb300 import pslr
+
+    sy = _systems(SYSTEMS)
+    nrhs = 3
+    bt = pslr.Batch([c for _, c, _ in sy], nrhs)
+    rng = np.random.default_rng(26)
+    bs = [[G.csr_matvec(w["A"], rng.uniform(-1, 1, w["A"].n)) for _ in range(nrhs)] for w, _, _ in sy]
+    bd = torch.tensor(np.concatenate([np.concatenate(c) for c in bs]), device=dev)
+    x = torch.zeros_like(bd)
+    its, rel, st = bt.solve(bd, x, rtol=1e-8, restart=20, maxit=60, check=False)
+    assert st == pslr.PSLR_ERR_NOT_CONVERGED
+    assert np.all(its <= 60)
+    stopped = its == 60
+    assert stopped.any() and np.all(rel[stopped] > 1e-8)
+    assert bt.info["handoff"] >= 1
+    xs = _split(bt, x.cpu().numpy())
+    for k, ((w, _, _), bk) in enumerate(zip(sy, bs)):
+        for j in range(nrhs):
+            r = np.linalg.norm(bk[j] - G.csr_matvec(w["A"], xs[k][:, j])) / np.linalg.norm(bk[j])
+            assert abs(r - rel[k * nrhs + j]) <= 1e-6 * max(r, 1e-12) + 1e-14, (k, j, r, rel[k * nrhs + j])
     """A zero right-hand side is solved by x = 0 in 0 iterations; the others
     stop at maxit and the call reports PSLR_ERR_NOT_CONVERGED."""
     from paper_2002_00917_gb300 import pslr
