@@ -936,7 +936,12 @@ static pslr_status handoff(pslr_batch *bt, double rtol, int restart, int maxit, 
     } else {
         std::vector<std::thread> th;
         th.reserve(jobs.size());
-        for (Job &J : jobs) th.emplace_back(work, std::ref(J));
+        size_t started = 0;
+        try {  // no exception may leave the C ABI: jobs without a thread run here
+            for (; started < jobs.size(); ++started) th.emplace_back(work, std::ref(jobs[started]));
+        } catch (...) {
+        }
+        for (size_t u = started; u < jobs.size(); ++u) work(jobs[u]);
         for (std::thread &t : th) t.join();
     }
     for (const Job &J : jobs) {
