@@ -66,8 +66,12 @@ typedef struct {
     int32_t splits[3];
     const int32_t *part;  /* optional host array (length n) of subdomain ids 0..s-1 */
     int32_t factor;       /* local factors of B_i and C_i: 0 = ILU(0), 1 = exact LU
-                             with partial pivoting (Algorithm 1, steps 2-5)         */
+                             with partial pivoting, 2 = ILUT(drop_tol) with no fill
+                             limit (Algorithm 1, steps 2-5; Section 4 runs ILUT
+                             with threshold 1e-2): row i drops entries below
+                             drop_tol ||a_i||_2, the diagonal always kept          */
     uint64_t seed;        /* SplitMix64 seed of the Arnoldi start vector            */
+    double drop_tol;      /* ILUT threshold (factor 2), >= 0; ignored otherwise     */
 } pslr_opts;
 
 typedef struct {

@@ -49,7 +49,7 @@ def _load():
             lib = C.CDLL(build())
             P, I32, D, U64 = C.c_void_p, C.c_int32, C.c_double, C.c_uint64
             sig = {
-                "orc_setup": (P, [I32, P, P, P, P, P, P, I32, P]),
+                "orc_setup": (P, [I32, P, P, P, P, P, P, I32, D, P]),
                 "orc_destroy": (None, [P]),
                 "orc_sizes": (None, [P, P, P, P, P]),
                 "orc_maps": (None, [P, P, P, P]),
@@ -94,7 +94,7 @@ class OracleError(RuntimeError):
 class Oracle:
     """One PSLR set-up (reordering + blocks + local factors) on the CPU."""
 
-    def __init__(self, A, dims=None, splits=None, part=None, factor=0):
+    def __init__(self, A, dims=None, splits=None, part=None, factor=0, drop_tol=0.0):
         lib = _load()
         self._lib = lib
         self.A = A
@@ -104,7 +104,7 @@ class Oracle:
         pa = None if part is None else np.ascontiguousarray(part, dtype=np.int32)
         self._keep = (A.rowptr, A.col, A.val, d, s, pa)
         h = lib.orc_setup(A.n, _p(A.rowptr), _p(A.col), _p(A.val), _p(d), _p(s), _p(pa), factor,
-                          C.byref(st))
+                          float(drop_tol), C.byref(st))
         if not h:
             raise OracleError(st.value, "orc_setup")
         self.h = C.c_void_p(h)
@@ -239,4 +239,4 @@ def splitmix_uniform(seed, j):
 
 def from_workload(w):
     """Oracle set-up for a workload dict from ``pslr_inputs.configs``."""
-    return Oracle(w["A"], dims=w["dims"], splits=w["splits"], factor=w["factor"])
+    return Oracle(w["A"], dims=w["dims"], splits=w["splits"], factor=w["factor"], drop_tol=w.get("drop_tol", 0.0))

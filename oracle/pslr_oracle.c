@@ -271,6 +271,93 @@ static int32_t ilu0(ocsr *M) {
     return ORC_OK;
 }
 
+/*
+ * ILUT(tau) without a fill limit (Saad, Iterative Methods, Sec. 10.4; the
+ * paper's Section 4 factors with threshold 1e-2), row by row in natural
+ * order.  For row i, with tol = tau * ||a_i||_2 (sum of squares in column
+ * order): the dense work row w = a_i; for every k < i, smallest first, with
+ * w_k nonzero: w_k /= u_kk, and either w_k is dropped (|w_k| < tol) or the
+ * strictly upper part of row k of U, scaled by w_k, is subtracted from w;
+ * afterwards every entry except the diagonal with |w_j| < tol is dropped.
+ * The result replaces *M (strictly lower = L with unit diagonal, upper
+ * including the diagonal = U), columns ascending.  As with ilu0, the
+ * block-diagonal matrix may be factored as a whole: no row reaches into
+ * another block.
+ */
+static int32_t ilut(ocsr *M, double tau) {
+    int32_t n = M->nr;
+    size_t cap = (size_t)M->rp[n] + 16, nnz = 0;
+    int32_t *rp = malloc(sizeof(int32_t) * (n + 1));
+    int32_t *ci = malloc(sizeof(int32_t) * cap);
+    double *v = malloc(sizeof(double) * cap);
+    int32_t *dpos = malloc(sizeof(int32_t) * (n ? n : 1));
+    double *w = calloc(n ? n : 1, sizeof(double));
+    char *state = calloc(n ? n : 1, 1); /* 0 empty, 1 live entry, 2 dropped multiplier */
+    int32_t st = ORC_OK;
+    rp[0] = 0;
+    for (int32_t i = 0; i < n && st == ORC_OK; ++i) {
+        double s2 = 0.0;
+        int32_t first = i, last = i;
+        for (int32_t t = M->rp[i]; t < M->rp[i + 1]; ++t) {
+            s2 += M->v[t] * M->v[t];
+            w[M->ci[t]] = M->v[t];
+            state[M->ci[t]] = 1;
+            if (M->ci[t] < first) first = M->ci[t];
+            if (M->ci[t] > last) last = M->ci[t];
+        }
+        double tol = tau * sqrt(s2);
+        for (int32_t k = first; k < i; ++k) {
+            if (state[k] != 1) continue;
+            double mult = w[k] / v[dpos[k]];
+            if (fabs(mult) < tol) {
+                w[k] = 0.0;
+                state[k] = 2;
+                continue;
+            }
+            w[k] = mult;
+            for (int32_t t = dpos[k] + 1; t < rp[k + 1]; ++t) {
+                int32_t j = ci[t];
+                if (state[j] == 0) {
+                    state[j] = 1;
+                    w[j] = 0.0;
+                    if (j > last) last = j;
+                }
+                w[j] -= mult * v[t];
+            }
+        }
+        dpos[i] = -1;
+        for (int32_t j = first; j <= last; ++j) { /* columns in ascending order */
+            if (state[j] == 1 && (j == i || fabs(w[j]) >= tol)) {
+                if (nnz == cap) {
+                    cap *= 2;
+                    ci = realloc(ci, sizeof(int32_t) * cap);
+                    v = realloc(v, sizeof(double) * cap);
+                }
+                if (j == i) dpos[i] = (int32_t)nnz;
+                ci[nnz] = j;
+                v[nnz] = w[j];
+                ++nnz;
+            }
+            w[j] = 0.0;
+            state[j] = 0;
+        }
+        rp[i + 1] = (int32_t)nnz;
+        if (dpos[i] < 0 || v[dpos[i]] == 0.0 || !isfinite(v[dpos[i]])) st = ORC_ERR_ZERO_PIVOT;
+    }
+    free(w);
+    free(state);
+    free(dpos);
+    if (st != ORC_OK) {
+        free(rp); free(ci); free(v);
+        return st;
+    }
+    free(M->rp); free(M->ci); free(M->v);
+    M->rp = rp;
+    M->ci = ci;
+    M->v = v;
+    return ORC_OK;
+}
+
 /* Dense LU with partial pivoting (largest |a|, ties -> smallest row) of the
  * diagonal block rows/cols [lo, hi) of M.  a is row-major nb x nb. */
 static int32_t dense_lu_block(const ocsr *M, int32_t lo, int32_t hi, double **out, int32_t **piv) {
@@ -386,9 +473,10 @@ static void dense_solve_t(int32_t nb, const double *a, const int32_t *pv, const 
 
 orc_ctx *orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
                    const int32_t dims[3], const int32_t splits[3], const int32_t *part,
-                   int32_t factor, int32_t *status) {
+                   int32_t factor, double drop_tol, int32_t *status) {
     *status = ORC_ERR_ARG;
     if (n <= 0 || !rowptr || !col || !val) return NULL;
+    if (factor < 0 || factor > 2 || (factor == 2 && !(drop_tol >= 0.0 && isfinite(drop_tol)))) return NULL;
     if (!part && (!dims || !splits || (int64_t)dims[0] * dims[1] * dims[2] != n)) return NULL;
     if (!part)
         for (int d = 0; d < 3; ++d)
@@ -401,11 +489,11 @@ orc_ctx *orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const d
     reorder(c, dims, splits, part);
     extract_blocks(c);
     int32_t st = ORC_OK;
-    if (factor == 0) {
+    if (factor == 0 || factor == 2) {
         c->luB = csr_copy(&c->B);
         c->luC = csr_copy(&c->C0);
-        st = ilu0(&c->luB);
-        if (st == ORC_OK) st = ilu0(&c->luC);
+        st = factor == 0 ? ilu0(&c->luB) : ilut(&c->luB, drop_tol);
+        if (st == ORC_OK) st = factor == 0 ? ilu0(&c->luC) : ilut(&c->luC, drop_tol);
     } else {
         c->dB = calloc(c->s, sizeof(double *));
         c->dC = calloc(c->s, sizeof(double *));
@@ -465,8 +553,8 @@ static const ocsr *pick(const orc_ctx *c, int32_t which) {
     case ORC_C: return &c->C;
     case ORC_C0: return &c->C0;
     case ORC_CG: return &c->Cg;
-    case ORC_LU_B: return c->factor == 0 ? &c->luB : NULL;
-    case ORC_LU_C0: return c->factor == 0 ? &c->luC : NULL;
+    case ORC_LU_B: return c->factor != 1 ? &c->luB : NULL;
+    case ORC_LU_C0: return c->factor != 1 ? &c->luC : NULL;
     }
     return NULL;
 }
@@ -487,7 +575,7 @@ void orc_get_block(const orc_ctx *c, int32_t which, int32_t *rowptr, int32_t *co
 /* ------------------------------------------ B~^{-1}, C0~^{-1} and transposes */
 
 void orc_solve_B(const orc_ctx *c, const double *in, double *out) {
-    if (c->factor == 0) {
+    if (c->factor != 1) {
         ilu_solve(&c->luB, in, out);
         return;
     }
@@ -498,7 +586,7 @@ void orc_solve_B(const orc_ctx *c, const double *in, double *out) {
 }
 
 void orc_solve_BT(const orc_ctx *c, const double *in, double *out) {
-    if (c->factor == 0) {
+    if (c->factor != 1) {
         ilu_solve_t(&c->luB, in, out);
         return;
     }
@@ -509,7 +597,7 @@ void orc_solve_BT(const orc_ctx *c, const double *in, double *out) {
 }
 
 void orc_solve_C0(const orc_ctx *c, const double *in, double *out) {
-    if (c->factor == 0) {
+    if (c->factor != 1) {
         ilu_solve(&c->luC, in, out);
         return;
     }
@@ -520,7 +608,7 @@ void orc_solve_C0(const orc_ctx *c, const double *in, double *out) {
 }
 
 void orc_solve_C0T(const orc_ctx *c, const double *in, double *out) {
-    if (c->factor == 0) {
+    if (c->factor != 1) {
         ilu_solve_t(&c->luC, in, out);
         return;
     }

@@ -40,10 +40,11 @@ enum { ORC_B = 0, ORC_E = 1, ORC_F = 2, ORC_C = 3, ORC_C0 = 4, ORC_CG = 5,
 /* Reorder A (Section 2), extract [B E; F C], C0, C_g (Eq. 3.1, Lemma 2) and
  * factor every B_i and C_i (Algorithm 1, steps 2-5).  part may be NULL, then the
  * geometric split of dims by splits is used.  factor: 0 = ILU(0), 1 = exact
- * dense LU with partial pivoting.  On failure returns NULL and sets *status. */
+ * dense LU with partial pivoting, 2 = ILUT(drop_tol) without a fill limit.
+ * On failure returns NULL and sets *status. */
 orc_ctx *orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
                    const int32_t dims[3], const int32_t splits[3], const int32_t *part,
-                   int32_t factor, int32_t *status);
+                   int32_t factor, double drop_tol, int32_t *status);
 void orc_destroy(orc_ctx *c);
 
 void orc_sizes(const orc_ctx *c, int32_t *n, int32_t *s, int32_t *p, int32_t *q);

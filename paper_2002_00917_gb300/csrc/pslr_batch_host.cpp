@@ -992,9 +992,9 @@ pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nr
     for (int k = 0; k < nsys; ++k) {
         if (!systems[k] || !sys_export(systems[k], &sx[k]))
             return bfail(nullptr, PSLR_ERR_ARG, "batch_create: system %d is not set up", k);
-        if (sx[k].factor != 0)
+        if (sx[k].factor == 1)
             return bfail(nullptr, PSLR_ERR_ARG,
-                         "batch_create: system %d uses exact LU factors; the batch takes ILU(0) systems", k);
+                         "batch_create: system %d uses exact LU factors; the batch takes ILU(0) and ILUT systems", k);
         if (sx[k].r > 0 && (!sx[k].V || !sx[k].Vb || !sx[k].G || !sx[k].Gf))
             return bfail(nullptr, PSLR_ERR_STATE, "batch_create: system %d has no low-rank term on the device", k);
     }

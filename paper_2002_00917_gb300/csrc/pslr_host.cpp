@@ -338,6 +338,72 @@ bool dense_lu(const Csr &M, Csr &LU, std::vector<uint16_t> &piv) {
     return true;
 }
 
+// ILUT(tau) of a local block with no fill limit (the threshold incomplete LU
+// the paper's Section 4 runs use, drop threshold 1e-2; Saad, Iterative
+// Methods, Sec. 10.4): row i starts as a_i; for k < i in increasing order with
+// w_k != 0, w_k <- w_k / u_kk, dropped if |w_k| < tau ||a_i||_2, else
+// w <- w - w_k u_k (the upper part of row k, diagonal excluded); then every
+// entry but the diagonal below tau ||a_i||_2 is dropped.  The result is L
+// (strictly lower, unit diagonal implied) and U (with diagonal) in one CSR,
+// columns ascending.  false on a zero pivot.
+bool ilut(const Csr &M, double tau, Csr &out) {
+    const int n = M.nr;
+    out.nr = out.nc = n;
+    out.rp.assign(1, 0);
+    out.ci.clear();
+    out.v.clear();
+    std::vector<double> w(n, 0.0);
+    std::vector<char> nz(n, 0);
+    std::vector<int32_t> diagpos(n, -1), cols;
+    for (int i = 0; i < n; ++i) {
+        double s2 = 0.0;
+        for (int t = M.rp[i]; t < M.rp[i + 1]; ++t) s2 += M.v[t] * M.v[t];
+        const double tol = tau * std::sqrt(s2);
+        cols.clear();
+        int lo = i;
+        for (int t = M.rp[i]; t < M.rp[i + 1]; ++t) {
+            const int j = M.ci[t];
+            w[j] = M.v[t];
+            nz[j] = 1;
+            cols.push_back(j);
+            lo = std::min(lo, j);
+        }
+        for (int k = lo; k < i; ++k) {
+            if (!nz[k]) continue;
+            const double wk = w[k] / out.v[diagpos[k]];
+            if (std::fabs(wk) < tol) {
+                w[k] = 0.0;
+                nz[k] = 2;  // dropped: not kept, not used
+                continue;
+            }
+            w[k] = wk;
+            for (int t = diagpos[k] + 1; t < out.rp[k + 1]; ++t) {
+                const int j = out.ci[t];
+                if (!nz[j]) {
+                    nz[j] = 1;
+                    w[j] = 0.0;
+                    cols.push_back(j);
+                }
+                w[j] -= wk * out.v[t];
+            }
+        }
+        std::sort(cols.begin(), cols.end());
+        for (int j : cols) {
+            const bool keep = nz[j] == 1 && (j == i || std::fabs(w[j]) >= tol);
+            if (keep) {
+                if (j == i) diagpos[i] = (int32_t)out.ci.size();
+                out.ci.push_back(j);
+                out.v.push_back(w[j]);
+            }
+            w[j] = 0.0;
+            nz[j] = 0;
+        }
+        out.rp.push_back((int32_t)out.ci.size());
+        if (diagpos[i] < 0 || out.v[diagpos[i]] == 0.0 || !std::isfinite(out.v[diagpos[i]])) return false;
+    }
+    return true;
+}
+
 // Split the combined factor into L (strictly lower entries) and U.
 void split_lu(const Csr &LU, Csr &Lo, Csr &Up) {
     Lo.nr = Lo.nc = Up.nr = Up.nc = LU.nr;
@@ -403,6 +469,7 @@ struct KWork {
 
 struct pslr_ctx {
     int n = 0, s = 0, p = 0, q = 0, factor = 0;
+    double drop_tol = 0.0;  // ILUT threshold (factor 2)
     uint64_t seed = 0;
     std::vector<int32_t> part, iface, perm, ioff, goff;
     int max_p = 0, max_q = 0, levels_B = 0, levels_C = 0;
@@ -676,7 +743,10 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
     c->n = n;
     c->factor = opts->factor;
     c->seed = opts->seed;
-    if (opts->factor != 0 && opts->factor != 1) return bail(fail(c, PSLR_ERR_ARG, "factor must be 0 or 1"));
+    if (opts->factor < 0 || opts->factor > 2) return bail(fail(c, PSLR_ERR_ARG, "factor must be 0, 1 or 2"));
+    if (opts->factor == 2 && !(opts->drop_tol >= 0.0 && std::isfinite(opts->drop_tol)))
+        return bail(fail(c, PSLR_ERR_ARG, "ILUT needs a finite drop tolerance >= 0"));
+    c->drop_tol = opts->drop_tol;
     // --- validate CSR: monotone row pointers, columns in range and ascending, diagonal present
     if (rowptr[0] != 0) return bail(fail(c, PSLR_ERR_ARG, "rowptr[0] != 0"));
     for (int i = 0; i < n; ++i) {
@@ -819,6 +889,9 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
             fc = Lc.C0;
             if (!ilu0_inplace(fb) || !ilu0_inplace(fc))
                 return bail(fail(c, PSLR_ERR_ZERO_PIVOT, "ILU(0) met a zero pivot in subdomain %d", i));
+        } else if (c->factor == 2) {
+            if (!ilut(Lc.B, c->drop_tol, fb) || !ilut(Lc.C0, c->drop_tol, fc))
+                return bail(fail(c, PSLR_ERR_ZERO_PIVOT, "ILUT met a zero pivot in subdomain %d", i));
         } else {
             if (np[i] > 4096 || nq[i] > 4096)
                 return bail(fail(c, PSLR_ERR_TOO_LARGE, "exact local LU is limited to blocks of 4096 rows"));

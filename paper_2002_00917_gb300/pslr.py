@@ -35,7 +35,7 @@ PSLR_FP32 = 1
 
 class pslr_opts(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("splits", C.c_int32 * 3), ("part", C.c_void_p),
-                ("factor", C.c_int32), ("seed", C.c_uint64)]
+                ("factor", C.c_int32), ("seed", C.c_uint64), ("drop_tol", C.c_double)]
 
 
 class pslr_info(C.Structure):
@@ -144,7 +144,7 @@ class Pslr:
     """
 
     def __init__(self, A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, seed=0,
-                 stream=None):
+                 stream=None, drop_tol=0.0):
         lib = load()
         self.lib = lib
         self.n = int(A.n)
@@ -159,6 +159,7 @@ class Pslr:
         o.part = None if self._part is None else self._part.ctypes.data
         o.factor = int(factor)
         o.seed = int(seed)
+        o.drop_tol = float(drop_tol)
         h = C.c_void_p()
         st = lib.pslr_setup(self.n, self._rp.ctypes.data, self._ci.ctypes.data, self._av.ctypes.data,
                             C.byref(o), _stream(stream), C.byref(h))
@@ -359,7 +360,7 @@ class Batch:
         return self.lib.pslr_batch_set_wait_limit(self.h, int(polls))
 
 
-def _opts(dims, splits, part, factor, seed):
+def _opts(dims, splits, part, factor, seed, drop_tol=0.0):
     o = pslr_opts()
     for d in range(3):
         o.dims[d] = int(dims[d])
@@ -367,10 +368,11 @@ def _opts(dims, splits, part, factor, seed):
     o.part = None if part is None else part.ctypes.data
     o.factor = int(factor)
     o.seed = int(seed)
+    o.drop_tol = float(drop_tol)
     return o
 
 
-def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0):
+def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, drop_tol=0.0):
     """Host-only dry run of the set-up (no GPU needed): returns (info dict,
     part, is_interface, perm) exactly as a device context would report them."""
     lib = load()
@@ -378,7 +380,7 @@ def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0):
     ci = np.ascontiguousarray(A.col, dtype=np.int32)
     av = np.ascontiguousarray(A.val, dtype=np.float64)
     pa = None if part is None else np.ascontiguousarray(part, dtype=np.int32)
-    o = _opts(dims, splits, pa, factor, 0)
+    o = _opts(dims, splits, pa, factor, 0, drop_tol)
     info = pslr_info()
     n = int(A.n)
     mp = [np.empty(n, np.int32) for _ in range(3)]
@@ -392,4 +394,4 @@ def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0):
 def from_workload(w, seed=0, stream=None):
     """Context for a workload dict of ``pslr_inputs.configs``."""
     return Pslr(w["A"], dims=w["dims"], splits=w["splits"], factor=w["factor"], seed=seed,
-                stream=stream)
+                stream=stream, drop_tol=w.get("drop_tol", 0.0))

@@ -16,6 +16,10 @@ Workloads (names say what they are):
 ``cd3d_128_8x8x4_ilu0``   3D 128^3 upwinded convection-diffusion, Pe=50, sigma for
                           20 negative eigenvalues of the shifted operator, 8x8x4
                           split, ILU(0), m=5, r=32.
+``lap3d_50_shift014``     3D 7-pt Laplacian 50^3 shifted by 0.14 (78 negative
+                          eigenvalues: the strongly indefinite case of Section
+                          4.1's rank study), 3x3x4 split (36 subdomains, near the
+                          paper's s = 35), ILU(0), m=3; the rank is the variable.
 """
 from __future__ import annotations
 
@@ -25,6 +29,7 @@ from . import generators as G
 
 FACTOR_ILU0 = 0
 FACTOR_EXACT_LU = 1
+FACTOR_ILUT = 2  # threshold ILU, drop tolerance ``drop_tol`` (Section 4 uses 1e-2)
 
 
 def _lap(dims, K):
@@ -63,6 +68,15 @@ def kappa3d_48_3x3x3(N=48, splits=(3, 3, 3), m=3, rank=16, K=10):
                 kappa=kap)
 
 
+def lap3d_50_shift014(rank=15):
+    dims = (50, 50, 50)
+    sig = 0.14
+    lam = G._sum_spectrum([G.laplacian_1d_eigs(d) for d in dims])
+    A = G.shifted_laplacian(dims, sig)
+    return dict(name="lap3d_50_shift014", A=A, sigma=sig, nneg=int((lam < sig).sum()), ndim=3, dims=dims,
+                splits=(3, 3, 4), factor=FACTOR_ILU0, m=3, rank=rank)
+
+
 def batch2d_64sys(nsys=64, lo=64, hi=256, nrhs=4, seed=0):
     """The batched workload: per system side N ~ U{lo..hi}, split ceil(N/32) per
     side clipped to [4, 8], m ~ U{2..5}, r ~ {8, 16, 32}, sigma for 4 negative
@@ -86,10 +100,11 @@ WORKLOADS = {
     "batch2d_64sys": batch2d_64sys,
     "kappa3d_48_3x3x3": kappa3d_48_3x3x3,
     "cd3d_128_8x8x4_ilu0": cd3d_128_8x8x4_ilu0,
+    "lap3d_50_shift014": lap3d_50_shift014,
 }
 
 
-def small_problem(kind, dims, splits, factor=FACTOR_ILU0, m=3, rank=4, K=2, seed=0):
+def small_problem(kind, dims, splits, factor=FACTOR_ILU0, m=3, rank=4, K=2, seed=0, drop_tol=1e-2):
     """A small problem of any family, for tests that must span several tiles and
     ragged tails while the oracle finishes in seconds."""
     nd = len(dims)
@@ -106,4 +121,4 @@ def small_problem(kind, dims, splits, factor=FACTOR_ILU0, m=3, rank=4, K=2, seed
     d3 = tuple(dims) + (1,) * (3 - nd)
     s3 = tuple(splits) + (1,) * (3 - nd)
     return dict(name=f"{kind}{nd}d_{'x'.join(map(str, dims))}", A=A, sigma=sig, nneg=k, ndim=nd,
-                dims=d3, splits=s3, factor=factor, m=m, rank=rank)
+                dims=d3, splits=s3, factor=factor, m=m, rank=rank, drop_tol=drop_tol)

@@ -103,3 +103,20 @@ def test_plan_rejects_bad_input(pslr):
     with pytest.raises(pslr.PslrError) as e:
         pslr.plan(big, (200, 200, 1), (1, 1, 1))
     assert e.value.status == pslr.PSLR_ERR_TOO_LARGE
+
+
+@pytest.mark.parametrize("kind,dims,splits,tau", [("lap", (9, 8, 7), (2, 2, 2), 1e-2),
+                                                  ("cd", (8, 7, 6), (2, 2, 1), 1e-2),
+                                                  ("kappa", (7, 8, 6), (2, 1, 2), 3e-3)])
+def test_ilut_factors_have_the_oracles_pattern(kind, dims, splits, tau):
+    """The library's ILUT (set-up on the host, dry run) keeps exactly as many
+    entries as the oracle's independent ILUT: the same drop decisions."""
+    from paper_2002_00917_gb300 import pslr
+
+    w = C.small_problem(kind, dims, splits, factor=2, drop_tol=tau)
+    info, *_ = pslr.plan(w["A"], w["dims"], w["splits"], factor=2, m=2, rank=0, drop_tol=tau)
+    o = O.from_workload(w)
+    nnz = sum(np.count_nonzero(o.dense_block(f)) for f in ("LU_B", "LU_C0"))
+    assert info["nnz_ilu"] == nnz
+    o0 = O.from_workload(dict(w, factor=0))
+    assert nnz > sum(np.count_nonzero(o0.dense_block(f)) for f in ("LU_B", "LU_C0"))

@@ -278,6 +278,39 @@ def test_batch_solve_handoff_reaches_maxit(dev):
         for j in range(nrhs):
             r = np.linalg.norm(bk[j] - G.csr_matvec(w["A"], xs[k][:, j])) / np.linalg.norm(bk[j])
             assert abs(r - rel[k * nrhs + j]) <= 1e-6 * max(r, 1e-12) + 1e-14, (k, j, r, rel[k * nrhs + j])
+
+
+def test_batch_apply_ilut_systems(dev):
+    """Systems factored by ILUT(1e-2) (wider rows, fill) in a batch with an
+    ILU(0) one: every (system, rhs) equals its oracle apply (FP64, 1e-12)."""
+    from paper_2002_00917_gb300 import pslr
+
+    specs = [("lap", (20, 17), (3, 2), 3, 6, 2), ("cd", (9, 8, 7), (2, 2, 2), 2, 5, 2),
+             ("lap", (26, 19), (4, 3), 2, 8, 0)]
+    sy = []
+    for kind, dims, splits, m, r, factor in specs:
+        w = C.small_problem(kind, dims, splits, factor=factor, m=m, rank=r, K=3)
+        ctx = pslr.from_workload(w)
+        orc = O.from_workload(w)
+        orc.build_lowrank(m, r, seed=0)
+        V, H, Gm = orc.lowrank()
+        ctx.set_lowrank(m, V, Gm)
+        sy.append((w, ctx, orc))
+    nrhs = 2
+    bt = pslr.Batch([c for _, c, _ in sy], nrhs)
+    b = np.random.default_rng(31).uniform(-1, 1, bt.info["n_total"])
+    bd = torch.tensor(b, device=dev)
+    zd = torch.full_like(bd, np.nan)
+    bt.apply(bd, zd)
+    bt.sync()
+    zs, bs = _split(bt, zd.cpu().numpy()), _split(bt, b)
+    for (w, _, orc), zk, bk in zip(sy, zs, bs):
+        for j in range(nrhs):
+            ref = orc.apply(np.ascontiguousarray(bk[:, j]))
+            assert np.linalg.norm(zk[:, j] - ref) <= 1e-12 * np.linalg.norm(ref), w["name"]
+
+
+def test_batch_solve_maxit_and_zero_rhs(dev):
     """A zero right-hand side is solved by x = 0 in 0 iterations; the others
     stop at maxit and the call reports PSLR_ERR_NOT_CONVERGED."""
     from paper_2002_00917_gb300 import pslr

@@ -57,6 +57,8 @@ CASES = [
     ("lap", (24, 20, 16), (2, 2, 2), 0, 5, 16),
     ("cd", (9, 9, 9), (1, 1, 1), 0, 3, 0),      # one subdomain: no interface at all
     ("lap", (7, 6, 5), (7, 6, 5), 0, 2, 3),     # every node its own part: B empty
+    ("lap", (13, 11, 9), (3, 2, 2), 2, 3, 6),   # ILUT(1e-2): wider rows, fill, deeper levels
+    ("cd", (12, 10, 8), (3, 2, 2), 2, 2, 5),
 ]
 
 

@@ -67,3 +67,96 @@ def test_zero_pivot_is_reported():
     with pytest.raises(O.OracleError) as e:
         O.Oracle(A, dims=(6, 5, 1), splits=(2, 1, 1), factor=0)
     assert e.value.status == O.ERR_ZERO_PIVOT
+
+
+# ---------------------------------------------------------------- ILUT(tau)
+
+def _row_norms(M):
+    return np.sqrt((M * M).sum(axis=1))
+
+
+def test_ilut_without_dropping_is_exact_lu():
+    """tau = 0 drops nothing: ILUT is the complete LU without pivoting, so
+    L U = B exactly and the solves equal LAPACK's (an SPD shifted Laplacian,
+    where LU without pivoting exists)."""
+    A = G.shifted_laplacian((7, 6, 5), -0.5)
+    o = O.Oracle(A, dims=(7, 6, 5), splits=(2, 2, 1), factor=2, drop_tol=0.0)
+    for blk, fac, solve, n in (("B", "LU_B", o.solve_B, o.p), ("C0", "LU_C0", o.solve_C0, o.q)):
+        M = o.dense_block(blk)
+        np.testing.assert_allclose(dense_lu_product(o, fac), M, atol=1e-12 * np.abs(M).max())
+        v = np.random.default_rng(3).uniform(-1, 1, n)
+        np.testing.assert_allclose(solve(v), np.linalg.solve(M, v), rtol=1e-10, atol=1e-12)
+
+
+def test_ilut_on_tridiagonal_blocks_equals_ilu0():
+    """A 1D chain's blocks are tridiagonal: their LU has no fill and every
+    multiplier is far above 1e-2 of the row norm, so ILUT(1e-2) = ILU(0)."""
+    A = G.shifted_laplacian((40,), 0.3)
+    o0 = O.Oracle(A, dims=(40, 1, 1), splits=(4, 1, 1), factor=0)
+    ot = O.Oracle(A, dims=(40, 1, 1), splits=(4, 1, 1), factor=2, drop_tol=1e-2)
+    for fac in ("LU_B", "LU_C0"):
+        a, b = o0.dense_block(fac), ot.dense_block(fac)
+        np.testing.assert_array_equal(a != 0, b != 0)
+        np.testing.assert_allclose(b, a, rtol=1e-14, atol=0)
+
+
+def test_ilut_huge_tolerance_keeps_only_the_diagonal():
+    """With tau far above every ratio |a_ij| / ||a_i||, every multiplier and
+    every off-diagonal entry is dropped: L = 0 and U = diag(B)."""
+    w = C.small_problem("cd", (6, 5, 4), (2, 2, 1), factor=2, drop_tol=10.0)
+    o = O.from_workload(w)
+    for blk, fac in (("B", "LU_B"), ("C0", "LU_C0")):
+        F = o.dense_block(fac)
+        np.testing.assert_array_equal(F, np.diag(np.diag(o.dense_block(blk))))
+
+
+@pytest.mark.parametrize("kind,dims,splits", [("lap", (8, 7, 6), (2, 2, 1)), ("cd", (7, 6, 5), (2, 2, 2))])
+def test_ilut_keeps_only_entries_above_the_threshold(kind, dims, splits):
+    """Every stored off-diagonal entry of the factors is at least
+    tau ||a_i||_2 in modulus (row norm of the block), every diagonal is
+    stored, and the fill lies between ILU(0)'s and the exact LU's."""
+    tau = 1e-2
+    w = C.small_problem(kind, dims, splits, factor=2, drop_tol=tau)
+    o = O.from_workload(w)
+    o0 = O.from_workload(dict(w, factor=0))
+    for blk, fac in (("B", "LU_B"), ("C0", "LU_C0")):
+        M, F = o.dense_block(blk), o.dense_block(fac)
+        tol = tau * _row_norms(M)
+        off = F.copy()
+        np.fill_diagonal(off, 0.0)
+        rows, cols = np.nonzero(off)
+        assert np.all(np.abs(off[rows, cols]) >= tol[rows])
+        assert np.all(np.diag(F) != 0)
+        nnz_t, nnz_0 = np.count_nonzero(F), np.count_nonzero(o0.dense_block(fac))
+        assert nnz_t >= nnz_0 * 0.5 and nnz_t <= F.shape[0] ** 2
+
+
+def test_ilut_matches_its_definition_on_a_tiny_block():
+    """Brute force: ILUT(tau) row by row on dense rows, as the definition
+    reads, on a tiny convection-diffusion block; the oracle's sparse version
+    must store exactly these values."""
+    tau = 0.05
+    w = C.small_problem("cd", (4, 3, 3), (2, 1, 1), factor=2, drop_tol=tau)
+    o = O.from_workload(w)
+    M = o.dense_block("B")
+    n = M.shape[0]
+    LU = np.zeros((n, n))
+    for i in range(n):
+        wrow = M[i].copy()
+        tol = tau * np.sqrt(sum(x * x for x in M[i][M[i] != 0]))
+        for k in range(i):
+            if wrow[k] == 0.0:
+                continue
+            mult = wrow[k] / LU[k, k]
+            if abs(mult) < tol:
+                wrow[k] = 0.0
+                continue
+            wrow[k] = mult
+            for j in range(k + 1, n):
+                if LU[k, j] != 0.0:
+                    wrow[j] -= mult * LU[k, j]
+        for j in range(n):
+            if j != i and abs(wrow[j]) < tol:
+                wrow[j] = 0.0
+        LU[i] = wrow
+    np.testing.assert_allclose(o.dense_block("LU_B"), LU, rtol=1e-13, atol=1e-15)
