@@ -69,7 +69,8 @@ typedef struct {
                              with partial pivoting, 2 = ILUT(drop_tol) with no fill
                              limit (Algorithm 1, steps 2-5; Section 4 runs ILUT
                              with threshold 1e-2): row i drops entries below
-                             drop_tol ||a_i||_2, the diagonal always kept          */
+                             drop_tol * mean |a_ij| over its stored entries,
+                             the diagonal always kept                              */
     uint64_t seed;        /* SplitMix64 seed of the Arnoldi start vector            */
     double drop_tol;      /* ILUT threshold (factor 2), >= 0; ignored otherwise     */
 } pslr_opts;

@@ -274,8 +274,10 @@ static int32_t ilu0(ocsr *M) {
 /*
  * ILUT(tau) without a fill limit (Saad, Iterative Methods, Sec. 10.4; the
  * paper's Section 4 factors with threshold 1e-2), row by row in natural
- * order.  For row i, with tol = tau * ||a_i||_2 (sum of squares in column
- * order): the dense work row w = a_i; for every k < i, smallest first, with
+ * order.  The threshold is relative to the mean modulus of the row, as in
+ * Saad's SPARSKIT ilut: for row i, tol = tau * (sum of |a_ij| over the stored
+ * entries, in column order) / (number of stored entries).  The dense work
+ * row w = a_i; for every k < i, smallest first, with
  * w_k nonzero: w_k /= u_kk, and either w_k is dropped (|w_k| < tol) or the
  * strictly upper part of row k of U, scaled by w_k, is subtracted from w;
  * afterwards every entry except the diagonal with |w_j| < tol is dropped.
@@ -296,16 +298,16 @@ static int32_t ilut(ocsr *M, double tau) {
     int32_t st = ORC_OK;
     rp[0] = 0;
     for (int32_t i = 0; i < n && st == ORC_OK; ++i) {
-        double s2 = 0.0;
-        int32_t first = i, last = i;
+        double s1 = 0.0;
+        int32_t first = i, last = i, len = M->rp[i + 1] - M->rp[i];
         for (int32_t t = M->rp[i]; t < M->rp[i + 1]; ++t) {
-            s2 += M->v[t] * M->v[t];
+            s1 += fabs(M->v[t]);
             w[M->ci[t]] = M->v[t];
             state[M->ci[t]] = 1;
             if (M->ci[t] < first) first = M->ci[t];
             if (M->ci[t] > last) last = M->ci[t];
         }
-        double tol = tau * sqrt(s2);
+        double tol = len > 0 ? tau * (s1 / len) : 0.0;
         for (int32_t k = first; k < i; ++k) {
             if (state[k] != 1) continue;
             double mult = w[k] / v[dpos[k]];

@@ -340,10 +340,13 @@ bool dense_lu(const Csr &M, Csr &LU, std::vector<uint16_t> &piv) {
 
 // ILUT(tau) of a local block with no fill limit (the threshold incomplete LU
 // the paper's Section 4 runs use, drop threshold 1e-2; Saad, Iterative
-// Methods, Sec. 10.4): row i starts as a_i; for k < i in increasing order with
-// w_k != 0, w_k <- w_k / u_kk, dropped if |w_k| < tau ||a_i||_2, else
-// w <- w - w_k u_k (the upper part of row k, diagonal excluded); then every
-// entry but the diagonal below tau ||a_i||_2 is dropped.  The result is L
+// Methods, Sec. 10.4, with the row scale of Saad's SPARSKIT ilut): the drop
+// tolerance of row i is tol_i = tau * (sum_j |a_ij|) / nnz(a_i), the mean
+// modulus of the block row (summed in stored column order).  Row i starts as
+// a_i; for k < i in increasing order with w_k != 0, w_k <- w_k / u_kk,
+// dropped if |w_k| < tol_i, else w <- w - w_k u_k (the upper part of row k,
+// diagonal excluded); then every entry but the diagonal below tol_i is
+// dropped.  The result is L
 // (strictly lower, unit diagonal implied) and U (with diagonal) in one CSR,
 // columns ascending.  false on a zero pivot.
 bool ilut(const Csr &M, double tau, Csr &out) {
@@ -356,9 +359,10 @@ bool ilut(const Csr &M, double tau, Csr &out) {
     std::vector<char> nz(n, 0);
     std::vector<int32_t> diagpos(n, -1), cols;
     for (int i = 0; i < n; ++i) {
-        double s2 = 0.0;
-        for (int t = M.rp[i]; t < M.rp[i + 1]; ++t) s2 += M.v[t] * M.v[t];
-        const double tol = tau * std::sqrt(s2);
+        double s1 = 0.0;
+        for (int t = M.rp[i]; t < M.rp[i + 1]; ++t) s1 += std::fabs(M.v[t]);
+        const int len = M.rp[i + 1] - M.rp[i];
+        const double tol = len > 0 ? tau * (s1 / len) : 0.0;
         cols.clear();
         int lo = i;
         for (int t = M.rp[i]; t < M.rp[i + 1]; ++t) {

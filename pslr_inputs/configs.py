@@ -19,7 +19,8 @@ Workloads (names say what they are):
 ``lap3d_50_shift014``     3D 7-pt Laplacian 50^3 shifted by 0.14 (78 negative
                           eigenvalues: the strongly indefinite case of Section
                           4.1's rank study), 3x3x4 split (36 subdomains, near the
-                          paper's s = 35), ILU(0), m=3; the rank is the variable.
+                          paper's s = 35), ILUT(1e-2) as in that study, m=3; the
+                          rank is the variable.
 """
 from __future__ import annotations
 
@@ -68,13 +69,13 @@ def kappa3d_48_3x3x3(N=48, splits=(3, 3, 3), m=3, rank=16, K=10):
                 kappa=kap)
 
 
-def lap3d_50_shift014(rank=15):
+def lap3d_50_shift014(rank=15, factor=FACTOR_ILUT, drop_tol=1e-2):
     dims = (50, 50, 50)
     sig = 0.14
     lam = G._sum_spectrum([G.laplacian_1d_eigs(d) for d in dims])
     A = G.shifted_laplacian(dims, sig)
     return dict(name="lap3d_50_shift014", A=A, sigma=sig, nneg=int((lam < sig).sum()), ndim=3, dims=dims,
-                splits=(3, 3, 4), factor=FACTOR_ILU0, m=3, rank=rank)
+                splits=(3, 3, 4), factor=factor, m=3, rank=rank, drop_tol=drop_tol)
 
 
 def batch2d_64sys(nsys=64, lo=64, hi=256, nrhs=4, seed=0):
