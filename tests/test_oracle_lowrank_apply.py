@@ -88,6 +88,39 @@ def test_full_rank_eigenvalues_match_brute_force():
     np.testing.assert_allclose(ev_h, ev_e, atol=1e-8)
 
 
+def test_partial_rank_finds_the_outlier_and_lowers_iterations():
+    """Sec. 4.1.3 on a small indefinite problem (16^3, 12 negative
+    eigenvalues, 2x2x2, ILUT(1e-2), m = 3): E_rr(m), formed column by column
+    here, has eigenvalues of modulus above 1; 20 Arnoldi steps find the
+    largest of them (largest-modulus eigenvalue of H against the brute-force
+    spectrum), and the low-rank term lowers the FGMRES(127) iteration count
+    as r grows (0 -> 20 -> 40)."""
+    dims = (16, 16, 16)
+    lam = np.sort(G._sum_spectrum([G.laplacian_1d_eigs(d) for d in dims]))
+    A = G.shifted_laplacian(dims, 0.5 * (lam[11] + lam[12]))
+    o = O.Oracle(A, dims=dims, splits=(2, 2, 2), factor=2, drop_tol=1e-2)
+    m, q = 3, o.q
+    Err = np.column_stack([o.Err(m, e) for e in np.eye(q)])
+    ev = np.linalg.eigvals(Err)
+    top = np.abs(ev).max()
+    assert top > 1.0
+    b, _ = G.uniform_rhs(A, 0)
+    its = []
+    for r in (0, 20, 40):
+        if r:
+            k, st = o.build_lowrank(m, r, seed=0)
+            assert k == r
+            H = o.lowrank()[1]
+            if r == 20:
+                assert abs(np.abs(np.linalg.eigvals(H)).max() - top) <= 1e-6 * top
+        else:
+            o.set_lowrank(m, np.zeros((q, 0)), np.zeros((0, 0)))
+        x, it, rel, st = o.fgmres(b, rtol=1e-8, restart=127, maxit=2000)
+        assert st == O.OK
+        its.append(it)
+    assert its[0] > its[1] > its[2], its
+
+
 def test_breakdown_truncates_rank():
     """On a 4x4 grid cut 2x2 the interface operator has the square's symmetry, so
     E_rr(m) has repeated eigenvalues and a Krylov space of dimension < q: Arnoldi
