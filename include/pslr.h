@@ -73,6 +73,11 @@ typedef struct {
                              the diagonal always kept                              */
     uint64_t seed;        /* SplitMix64 seed of the Arnoldi start vector            */
     double drop_tol;      /* ILUT threshold (factor 2), >= 0; ignored otherwise     */
+    int32_t setup_threads; /* host threads of the set-up (blocks, factors and packing
+                              run per subdomain, as the paper's set-up runs over
+                              subdomains in parallel): 0 = the machine's hardware
+                              threads (at most 64), >= 1 that many; the result is
+                              the same for every value                              */
 } pslr_opts;
 
 typedef struct {
@@ -83,6 +88,10 @@ typedef struct {
     int32_t max_interior, max_interface;  /* largest p_i and q_i                    */
     int32_t levels_B, levels_C0;          /* deepest triangular-solve level chain   */
     int64_t apply_bytes_fp64, apply_bytes_fp32; /* algorithmic bytes of one apply   */
+    uint64_t layout_hash; /* pslr_plan only: FNV-1a hash (64-bit prime, 8-byte words) of the packed device
+                             layout (segments, descriptors and counts of both
+                             directions and precisions); 0 from a device context  */
+    int32_t setup_threads; /* host threads the set-up used                        */
 } pslr_info;
 
 /*

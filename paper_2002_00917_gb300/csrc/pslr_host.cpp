@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -18,6 +19,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -97,6 +99,52 @@ struct SegStore {
     std::vector<SegDesc> desc;
     int max_bytes = 0;
 };
+
+// Run f(0) .. f(n-1) on up to `threads` host threads (the calling thread
+// included), indices handed out in increasing order.  f must only write state
+// owned by its index.  Returns false if some f threw (the remaining indices
+// still run); a pool that cannot be started runs the rest on this thread.
+template <class F>
+bool parallel_for(int n, int threads, F &&f) {
+    std::atomic<int> next{0};
+    std::atomic<bool> ok{true};
+    auto work = [&]() {
+        for (int i; (i = next.fetch_add(1)) < n;) {
+            try {
+                f(i);
+            } catch (...) {
+                ok = false;
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    const int t = std::max(1, std::min(threads, n));
+    try {
+        for (int k = 1; k < t; ++k) pool.emplace_back(work);
+    } catch (...) {
+    }
+    work();
+    for (auto &th : pool) th.join();
+    return ok;
+}
+
+// FNV-1a with the 64-bit prime, taken over 8-byte little-endian words (the
+// tail byte by byte), continuing from h.
+uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+        uint64_t w = 0;
+        for (int k = 0; k < 8; ++k) w |= (uint64_t)b[i + k] << (8 * k);
+        h ^= w;
+        h *= 0x100000001b3ull;
+    }
+    for (; i < n; ++i) {
+        h ^= b[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
 
 template <class T, class IDX>
 void pack_segment(SegStore &S, const std::vector<Row> &rows, size_t b, size_t e, bool diag, int zero_col) {
@@ -478,6 +526,8 @@ struct pslr_ctx {
     std::vector<int32_t> part, iface, perm, ioff, goff;
     int max_p = 0, max_q = 0, levels_B = 0, levels_C = 0;
     int64_t nnz_A = 0, nnz_ilu = 0;
+    int threads = 1;            // host threads of the set-up
+    uint64_t layout_hash = 0;   // pslr_plan: hash of the packed device layout
     std::vector<int32_t> h_rp, h_ci;
     std::vector<double> h_av;
     // device: maps and matrices
@@ -593,73 +643,105 @@ struct Local {
     std::vector<uint16_t> bpiv, cpiv;
 };
 
+// The segments of subdomain i in one direction, in the order
+// [E, F, Cg, B1, B2, C1, C2] (transposed: Cg left empty, inserted later),
+// into its own store; k receives the kNCnt segment counts.
 template <class T>
-void pack_direction(const std::vector<Local> &loc, const std::vector<int> &np, const std::vector<int> &nq,
-                    bool transposed, int q, SegStore &S, std::vector<int32_t> &sub_desc,
-                    std::vector<int32_t> &cnt, int &levB, int &levC) {
+void pack_subdomain(const Local &Lc, int npi, int nqi, bool transposed, int q, SegStore &S, int *k, int &levB,
+                    int &levC) {
+    levB = levC = 0;
+    if (!transposed) {
+        k[kE] = pack_rows<T, uint16_t>(S, ell_rows(Lc.E), false, nqi);
+        k[kF] = pack_rows<T, uint16_t>(S, ell_rows(Lc.F), false, npi);
+        k[kCg] = pack_rows<T, int32_t>(S, ell_rows(Lc.Cg), false, q);
+        auto lb = levels(Lc.BL, true), ub = levels(Lc.BU, false);
+        auto lc = levels(Lc.CL, true), uc = levels(Lc.CU, false);
+        levB = (int)(lb.size() + ub.size());
+        levC = (int)(lc.size() + uc.size());
+        for (auto &lv : lb) k[kB1] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.BL, lv, true, false), false, npi);
+        for (auto &lv : ub) k[kB2] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.BU, lv, false, true), true, npi);
+        for (auto &lv : lc) k[kC1] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.CL, lv, true, false), false, nqi);
+        for (auto &lv : uc) k[kC2] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.CU, lv, false, true), true, nqi);
+    } else {
+        // E-slot: F_i^T (interior rows <- interface cols); F-slot: E_i^T.
+        k[kE] = pack_rows<T, uint16_t>(S, ell_rows(transpose(Lc.F)), false, nqi);
+        k[kF] = pack_rows<T, uint16_t>(S, ell_rows(transpose(Lc.E)), false, npi);
+        k[kCg] = 0;  // filled by the caller (needs C_g of every subdomain)
+        // B^{-T} = U^{-T} L^{-T}: sweep 1 is U^T (lower, with diagonal), sweep 2 L^T (upper)
+        Csr BUt = transpose(Lc.BU), BLt = transpose(Lc.BL);
+        Csr CUt = transpose(Lc.CU), CLt = transpose(Lc.CL);
+        auto l1 = levels(BUt, true), l2 = levels(BLt, false);
+        auto l3 = levels(CUt, true), l4 = levels(CLt, false);
+        for (auto &lv : l1) k[kB1] += pack_rows<T, uint16_t>(S, sweep_rows(BUt, lv, true, true), true, npi);
+        for (auto &lv : l2) k[kB2] += pack_rows<T, uint16_t>(S, sweep_rows(BLt, lv, false, false), false, npi);
+        for (auto &lv : l3) k[kC1] += pack_rows<T, uint16_t>(S, sweep_rows(CUt, lv, true, true), true, nqi);
+        for (auto &lv : l4) k[kC2] += pack_rows<T, uint16_t>(S, sweep_rows(CLt, lv, false, false), false, nqi);
+    }
+}
+
+// Every subdomain packed on its own thread into its own stores, then copied
+// into one store in subdomain order.  The bytes are the main segments of
+// every subdomain in turn and, in the transposed direction, the C_g^T
+// segments of every subdomain after them; each subdomain's descriptors are in
+// the order [E, F, Cg, B1, B2, C1, C2].  The result does not depend on the
+// number of threads.
+template <class T>
+bool pack_direction(const std::vector<Local> &loc, const std::vector<int> &np, const std::vector<int> &nq,
+                    bool transposed, int q, const std::vector<Csr> *cgT, int threads, SegStore &S,
+                    std::vector<int32_t> &sub_desc, std::vector<int32_t> &cnt, int &levB, int &levC) {
     const int s = (int)loc.size();
     sub_desc.assign(s, 0);
     cnt.assign((size_t)kNCnt * s, 0);
-    for (int i = 0; i < s; ++i) {
-        const Local &Lc = loc[i];
-        sub_desc[i] = (int32_t)S.desc.size();
+    std::vector<SegStore> part(s), pcg(transposed ? s : 0);
+    std::vector<int> lb(s, 0), lc(s, 0);
+    bool ok = parallel_for(s, threads, [&](int i) {
         int *k = &cnt[(size_t)kNCnt * i];
-        if (!transposed) {
-            k[kE] = pack_rows<T, uint16_t>(S, ell_rows(Lc.E), false, nq[i]);
-            k[kF] = pack_rows<T, uint16_t>(S, ell_rows(Lc.F), false, np[i]);
-            k[kCg] = pack_rows<T, int32_t>(S, ell_rows(Lc.Cg), false, q);
-            auto lb = levels(Lc.BL, true), ub = levels(Lc.BU, false);
-            auto lc = levels(Lc.CL, true), uc = levels(Lc.CU, false);
-            levB = std::max<int>(levB, (int)(lb.size() + ub.size()));
-            levC = std::max<int>(levC, (int)(lc.size() + uc.size()));
-            for (auto &lv : lb) k[kB1] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.BL, lv, true, false), false, np[i]);
-            for (auto &lv : ub) k[kB2] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.BU, lv, false, true), true, np[i]);
-            for (auto &lv : lc) k[kC1] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.CL, lv, true, false), false, nq[i]);
-            for (auto &lv : uc) k[kC2] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.CU, lv, false, true), true, nq[i]);
-        } else {
-            // E-slot: F_i^T (interior rows <- interface cols); F-slot: E_i^T.
-            k[kE] = pack_rows<T, uint16_t>(S, ell_rows(transpose(Lc.F)), false, nq[i]);
-            k[kF] = pack_rows<T, uint16_t>(S, ell_rows(transpose(Lc.E)), false, np[i]);
-            k[kCg] = 0;  // filled by the caller (needs C_g of every subdomain)
-            // B^{-T} = U^{-T} L^{-T}: sweep 1 is U^T (lower, with diagonal), sweep 2 L^T (upper)
-            Csr BUt = transpose(Lc.BU), BLt = transpose(Lc.BL);
-            Csr CUt = transpose(Lc.CU), CLt = transpose(Lc.CL);
-            auto l1 = levels(BUt, true), l2 = levels(BLt, false);
-            auto l3 = levels(CUt, true), l4 = levels(CLt, false);
-            for (auto &lv : l1) k[kB1] += pack_rows<T, uint16_t>(S, sweep_rows(BUt, lv, true, true), true, np[i]);
-            for (auto &lv : l2) k[kB2] += pack_rows<T, uint16_t>(S, sweep_rows(BLt, lv, false, false), false, np[i]);
-            for (auto &lv : l3) k[kC1] += pack_rows<T, uint16_t>(S, sweep_rows(CUt, lv, true, true), true, nq[i]);
-            for (auto &lv : l4) k[kC2] += pack_rows<T, uint16_t>(S, sweep_rows(CLt, lv, false, false), false, nq[i]);
-        }
+        pack_subdomain<T>(loc[i], np[i], nq[i], transposed, q, part[i], k, lb[i], lc[i]);
+        if (transposed) k[kCg] = pack_rows<T, int32_t>(pcg[i], ell_rows((*cgT)[i]), false, q);
+    });
+    if (!ok) return false;
+    std::vector<int64_t> boff(s), coff(s);
+    int64_t total = 0;
+    size_t nd = 0;
+    for (int i = 0; i < s; ++i) {
+        boff[i] = total;
+        total += (int64_t)part[i].bytes.size();
+        sub_desc[i] = (int32_t)nd;
+        nd += part[i].desc.size() + (transposed ? pcg[i].desc.size() : 0);
+        S.max_bytes = std::max(S.max_bytes, part[i].max_bytes);
+        levB = std::max(levB, lb[i]);
+        levC = std::max(levC, lc[i]);
     }
+    for (int i = 0; i < (int)pcg.size(); ++i) {
+        coff[i] = total;
+        total += (int64_t)pcg[i].bytes.size();
+        S.max_bytes = std::max(S.max_bytes, pcg[i].max_bytes);
+    }
+    S.bytes.resize((size_t)total);
+    S.desc.resize(nd);
+    return parallel_for(s, threads, [&](int i) {
+        SegStore &P = part[i];
+        if (!P.bytes.empty()) std::memcpy(S.bytes.data() + boff[i], P.bytes.data(), P.bytes.size());
+        SegDesc *d = S.desc.data() + sub_desc[i];
+        const int *k = &cnt[(size_t)kNCnt * i];
+        const size_t head = transposed ? (size_t)(k[kE] + k[kF]) : P.desc.size();
+        auto put = [&](SegDesc x, int64_t base) {
+            x.off += base;
+            *d++ = x;
+        };
+        for (size_t t = 0; t < head; ++t) put(P.desc[t], boff[i]);
+        if (transposed) {
+            SegStore &Q = pcg[i];
+            if (!Q.bytes.empty()) std::memcpy(S.bytes.data() + coff[i], Q.bytes.data(), Q.bytes.size());
+            for (const SegDesc &x : Q.desc) put(x, coff[i]);
+            Q = SegStore();
+        }
+        for (size_t t = head; t < P.desc.size(); ++t) put(P.desc[t], boff[i]);
+        P = SegStore();
+    });
 }
 
 }  // namespace
-
-// Insert the C_g^T segments of every subdomain into a transposed table.  The
-// table is rebuilt subdomain by subdomain so that each subdomain's descriptors
-// stay contiguous in the [E, F, Cg, B1, B2, C1, C2] order.
-template <class T>
-static void insert_cgT(SegStore &S, std::vector<int32_t> &sub_desc, std::vector<int32_t> &cnt,
-                       const std::vector<Csr> &cgT_rows, int q) {
-    const int s = (int)sub_desc.size();
-    std::vector<SegDesc> nd;
-    std::vector<int32_t> nsub(s);
-    for (int i = 0; i < s; ++i) {
-        nsub[i] = (int32_t)nd.size();
-        int *k = &cnt[(size_t)kNCnt * i];
-        int b = sub_desc[i];
-        for (int t = 0; t < k[kE] + k[kF]; ++t) nd.push_back(S.desc[b + t]);
-        size_t before = S.desc.size();
-        k[kCg] = pack_rows<T, int32_t>(S, ell_rows(cgT_rows[i]), false, q);
-        for (size_t t = before; t < S.desc.size(); ++t) nd.push_back(S.desc[t]);
-        S.desc.resize(before);
-        int nl = k[kB1] + k[kB2] + k[kC1] + k[kC2];
-        for (int t = 0; t < nl; ++t) nd.push_back(S.desc[b + k[kE] + k[kF] + t]);
-    }
-    S.desc.swap(nd);
-    sub_desc.swap(nsub);
-}
 
 template <class T>
 static pslr_status finish_opset(pslr_ctx *c, OpSetHost &o, SegStore &S, const std::vector<int32_t> &sub_desc,
@@ -674,6 +756,16 @@ static pslr_status finish_opset(pslr_ctx *c, OpSetHost &o, SegStore &S, const st
     o.hdesc = S.desc;
     o.hsub = sub_desc;
     o.hcnt = cnt;
+    if (plan_only) {
+        uint64_t h = c->layout_hash ? c->layout_hash : 0xcbf29ce484222325ull;
+        h = fnv1a(h, S.bytes.data(), S.bytes.size());
+        for (const SegDesc &d : S.desc) {  // field by field: the struct has padding
+            h = fnv1a(h, &d.off, sizeof(d.off));
+            h = fnv1a(h, &d.bytes, sizeof(d.bytes));
+        }
+        h = fnv1a(h, sub_desc.data(), sub_desc.size() * sizeof(int32_t));
+        c->layout_hash = fnv1a(h, cnt.data(), cnt.size() * sizeof(int32_t));
+    }
     if (S.bytes.empty()) S.bytes.resize(16, 0);
     const bool piv = c->factor == 1;
     int optin = 227 * 1024;  // sm_100-class opt-in limit; queried from the device when there is one
@@ -751,6 +843,14 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
     if (opts->factor == 2 && !(opts->drop_tol >= 0.0 && std::isfinite(opts->drop_tol)))
         return bail(fail(c, PSLR_ERR_ARG, "ILUT needs a finite drop tolerance >= 0"));
     c->drop_tol = opts->drop_tol;
+    if (opts->setup_threads < 0) return bail(fail(c, PSLR_ERR_ARG, "setup_threads must be >= 0"));
+    if (opts->setup_threads > 0) {
+        c->threads = opts->setup_threads;
+    } else {
+        const unsigned hw = std::thread::hardware_concurrency();
+        c->threads = (int)std::min(64u, std::max(1u, hw));
+    }
+    const int threads = c->threads;
     // --- validate CSR: monotone row pointers, columns in range and ascending, diagonal present
     if (rowptr[0] != 0) return bail(fail(c, PSLR_ERR_ARG, "rowptr[0] != 0"));
     for (int i = 0; i < n; ++i) {
@@ -837,7 +937,7 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
 
     // --- Eq. 2.1 / Eq. 3.1: local blocks (rows visited in the reordered order)
     std::vector<Local> L(s);
-    for (int i = 0; i < s; ++i) {
+    bool blocks_ok = parallel_for(s, threads, [&](int i) {
         Local &Lc = L[i];
         for (Csr *M : {&Lc.B, &Lc.E}) { M->nr = np[i]; M->rp.assign(1, 0); }
         for (Csr *M : {&Lc.F, &Lc.C0, &Lc.Cg}) { M->nr = nq[i]; M->rp.assign(1, 0); }
@@ -877,7 +977,8 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
             Lc.C0.rp.push_back((int32_t)Lc.C0.ci.size());
             Lc.Cg.rp.push_back((int32_t)Lc.Cg.ci.size());
         }
-    }
+    });
+    if (!blocks_ok) return bail(fail(c, PSLR_ERR_ARG, "host set-up failed while extracting the blocks (out of memory?)"));
 
     // --- Algorithm 1, steps 2-5: local factors
     std::vector<uint16_t> bpiv, cpiv;
@@ -885,28 +986,52 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
         bpiv.resize(c->p);
         cpiv.resize(c->q);
     }
-    for (int i = 0; i < s; ++i) {
+    // every subdomain on its own thread; the first failing subdomain (lowest
+    // index) is reported, as a serial loop would
+    enum { kFacOk = 0, kFacZeroPivot, kFacTooLarge };
+    std::vector<int> fac_st(s, kFacOk);
+    std::vector<int64_t> fac_nnz(s, 0);
+    bool fac_ok = parallel_for(s, threads, [&](int i) {
         Local &Lc = L[i];
         Csr fb, fc;
         if (c->factor == 0) {
             fb = Lc.B;
             fc = Lc.C0;
-            if (!ilu0_inplace(fb) || !ilu0_inplace(fc))
-                return bail(fail(c, PSLR_ERR_ZERO_PIVOT, "ILU(0) met a zero pivot in subdomain %d", i));
+            if (!ilu0_inplace(fb) || !ilu0_inplace(fc)) {
+                fac_st[i] = kFacZeroPivot;
+                return;
+            }
         } else if (c->factor == 2) {
-            if (!ilut(Lc.B, c->drop_tol, fb) || !ilut(Lc.C0, c->drop_tol, fc))
-                return bail(fail(c, PSLR_ERR_ZERO_PIVOT, "ILUT met a zero pivot in subdomain %d", i));
+            if (!ilut(Lc.B, c->drop_tol, fb) || !ilut(Lc.C0, c->drop_tol, fc)) {
+                fac_st[i] = kFacZeroPivot;
+                return;
+            }
         } else {
-            if (np[i] > 4096 || nq[i] > 4096)
-                return bail(fail(c, PSLR_ERR_TOO_LARGE, "exact local LU is limited to blocks of 4096 rows"));
-            if (!dense_lu(Lc.B, fb, Lc.bpiv) || !dense_lu(Lc.C0, fc, Lc.cpiv))
-                return bail(fail(c, PSLR_ERR_ZERO_PIVOT, "singular local block in subdomain %d", i));
+            if (np[i] > 4096 || nq[i] > 4096) {
+                fac_st[i] = kFacTooLarge;
+                return;
+            }
+            if (!dense_lu(Lc.B, fb, Lc.bpiv) || !dense_lu(Lc.C0, fc, Lc.cpiv)) {
+                fac_st[i] = kFacZeroPivot;
+                return;
+            }
             std::copy(Lc.bpiv.begin(), Lc.bpiv.end(), bpiv.begin() + c->ioff[i]);
             std::copy(Lc.cpiv.begin(), Lc.cpiv.end(), cpiv.begin() + c->goff[i]);
         }
-        c->nnz_ilu += (int64_t)fb.ci.size() + (int64_t)fc.ci.size();
+        fac_nnz[i] = (int64_t)fb.ci.size() + (int64_t)fc.ci.size();
         split_lu(fb, Lc.BL, Lc.BU);
         split_lu(fc, Lc.CL, Lc.CU);
+    });
+    if (!fac_ok) return bail(fail(c, PSLR_ERR_ARG, "host set-up failed while factoring (out of memory?)"));
+    for (int i = 0; i < s; ++i) {
+        if (fac_st[i] == kFacTooLarge)
+            return bail(fail(c, PSLR_ERR_TOO_LARGE, "exact local LU is limited to blocks of 4096 rows"));
+        if (fac_st[i] == kFacZeroPivot) {
+            const char *what = c->factor == 0 ? "ILU(0) met a zero pivot" : c->factor == 2 ? "ILUT met a zero pivot"
+                                                                                             : "singular local block";
+            return bail(fail(c, PSLR_ERR_ZERO_PIVOT, "%s in subdomain %d", what, i));
+        }
+        c->nnz_ilu += fac_nnz[i];
     }
 
     // --- device layout: both directions, both precisions
@@ -940,15 +1065,15 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
             std::vector<int32_t> sub_desc, cnt;
             int lb = 0, lc = 0;
             pslr_status st;
+            bool ok;
             if (prec == 0) {
-                pack_direction<double>(L, np, nq, dir == 1, c->q, S, sub_desc, cnt, lb, lc);
-                if (dir == 1) insert_cgT<double>(S, sub_desc, cnt, cgT, c->q);
-                st = finish_opset<double>(c, c->ops[dir][prec], S, sub_desc, cnt, false, plan_only);
+                ok = pack_direction<double>(L, np, nq, dir == 1, c->q, &cgT, threads, S, sub_desc, cnt, lb, lc);
+                st = ok ? finish_opset<double>(c, c->ops[dir][prec], S, sub_desc, cnt, false, plan_only) : PSLR_OK;
             } else {
-                pack_direction<float>(L, np, nq, dir == 1, c->q, S, sub_desc, cnt, lb, lc);
-                if (dir == 1) insert_cgT<float>(S, sub_desc, cnt, cgT, c->q);
-                st = finish_opset<float>(c, c->ops[dir][prec], S, sub_desc, cnt, true, plan_only);
+                ok = pack_direction<float>(L, np, nq, dir == 1, c->q, &cgT, threads, S, sub_desc, cnt, lb, lc);
+                st = ok ? finish_opset<float>(c, c->ops[dir][prec], S, sub_desc, cnt, true, plan_only) : PSLR_OK;
             }
+            if (!ok) return bail(fail(c, PSLR_ERR_ARG, "host set-up failed while packing (out of memory?)"));
             if (st != PSLR_OK) return bail(st);
             if (dir == 0 && prec == 0) {
                 c->levels_B = lb;
@@ -1359,6 +1484,8 @@ pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info) {
     I.levels_C0 = c->levels_C;
     I.apply_bytes_fp64 = pslr_apply_bytes(c, 0);
     I.apply_bytes_fp32 = pslr_apply_bytes(c, 1);
+    I.setup_threads = c->threads;
+    I.layout_hash = c->layout_hash;
     *info = I;
     return PSLR_OK;
 }

@@ -35,7 +35,8 @@ PSLR_FP32 = 1
 
 class pslr_opts(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("splits", C.c_int32 * 3), ("part", C.c_void_p),
-                ("factor", C.c_int32), ("seed", C.c_uint64), ("drop_tol", C.c_double)]
+                ("factor", C.c_int32), ("seed", C.c_uint64), ("drop_tol", C.c_double),
+                ("setup_threads", C.c_int32)]
 
 
 class pslr_info(C.Structure):
@@ -44,7 +45,8 @@ class pslr_info(C.Structure):
                 ("nnz_lr", C.c_int64), ("fill_ilu", C.c_double), ("fill_lr", C.c_double),
                 ("fill_total", C.c_double), ("max_interior", C.c_int32),
                 ("max_interface", C.c_int32), ("levels_B", C.c_int32), ("levels_C0", C.c_int32),
-                ("apply_bytes_fp64", C.c_int64), ("apply_bytes_fp32", C.c_int64)]
+                ("apply_bytes_fp64", C.c_int64), ("apply_bytes_fp32", C.c_int64),
+                ("layout_hash", C.c_uint64), ("setup_threads", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -140,11 +142,13 @@ class Pslr:
 
     ``A`` is host CSR (``rowptr``, ``col``, ``val`` numpy arrays, or any object
     with those attributes and ``n``).  ``dims``/``splits`` select the geometric
-    split; ``part`` (length n) overrides it.  ``factor``: 0 ILU(0), 1 exact LU.
+    split; ``part`` (length n) overrides it.  ``factor``: 0 ILU(0), 1 exact LU,
+    2 ILUT(``drop_tol``).  ``setup_threads``: host threads of the set-up (0 =
+    all hardware threads); the context is the same for every value.
     """
 
     def __init__(self, A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, seed=0,
-                 stream=None, drop_tol=0.0):
+                 stream=None, drop_tol=0.0, setup_threads=0):
         lib = load()
         self.lib = lib
         self.n = int(A.n)
@@ -160,6 +164,7 @@ class Pslr:
         o.factor = int(factor)
         o.seed = int(seed)
         o.drop_tol = float(drop_tol)
+        o.setup_threads = int(setup_threads)
         h = C.c_void_p()
         st = lib.pslr_setup(self.n, self._rp.ctypes.data, self._ci.ctypes.data, self._av.ctypes.data,
                             C.byref(o), _stream(stream), C.byref(h))
@@ -360,7 +365,7 @@ class Batch:
         return self.lib.pslr_batch_set_wait_limit(self.h, int(polls))
 
 
-def _opts(dims, splits, part, factor, seed, drop_tol=0.0):
+def _opts(dims, splits, part, factor, seed, drop_tol=0.0, setup_threads=0):
     o = pslr_opts()
     for d in range(3):
         o.dims[d] = int(dims[d])
@@ -369,10 +374,11 @@ def _opts(dims, splits, part, factor, seed, drop_tol=0.0):
     o.factor = int(factor)
     o.seed = int(seed)
     o.drop_tol = float(drop_tol)
+    o.setup_threads = int(setup_threads)
     return o
 
 
-def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, drop_tol=0.0):
+def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, drop_tol=0.0, setup_threads=0):
     """Host-only dry run of the set-up (no GPU needed): returns (info dict,
     part, is_interface, perm) exactly as a device context would report them."""
     lib = load()
@@ -380,7 +386,7 @@ def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, 
     ci = np.ascontiguousarray(A.col, dtype=np.int32)
     av = np.ascontiguousarray(A.val, dtype=np.float64)
     pa = None if part is None else np.ascontiguousarray(part, dtype=np.int32)
-    o = _opts(dims, splits, pa, factor, 0, drop_tol)
+    o = _opts(dims, splits, pa, factor, 0, drop_tol, setup_threads)
     info = pslr_info()
     n = int(A.n)
     mp = [np.empty(n, np.int32) for _ in range(3)]

@@ -105,6 +105,47 @@ def test_plan_rejects_bad_input(pslr):
     assert e.value.status == pslr.PSLR_ERR_TOO_LARGE
 
 
+@pytest.mark.parametrize("kind,dims,splits,factor", [("lap", (16, 14, 12), (4, 3, 3), 0),
+                                                     ("cd", (12, 11, 10), (3, 2, 2), 2),
+                                                     ("lap", (32, 32), (2, 2), 1),
+                                                     ("kappa", (10, 9, 11), (2, 3, 2), 0)])
+def test_setup_threads_do_not_change_the_layout(pslr, kind, dims, splits, factor):
+    """The set-up runs per subdomain on host threads; the packed device layout
+    of both directions and precisions (its hash over every byte, descriptor
+    and count), the fill and the levels are the same for 1, 2, 5 and all
+    threads."""
+    w = C.small_problem(kind, dims, splits, factor=factor, drop_tol=1e-2)
+    infos = []
+    for t in (1, 2, 5, 0):
+        info, part, iface, perm = pslr.plan(w["A"], w["dims"], w["splits"], factor=factor, m=3, rank=4,
+                                            drop_tol=1e-2, setup_threads=t)
+        assert info["setup_threads"] == (t if t else info["setup_threads"]) and info["setup_threads"] >= 1
+        infos.append(({k: v for k, v in info.items() if k != "setup_threads"}, perm.tobytes()))
+    assert infos[0][0]["layout_hash"] != 0
+    assert all(x == infos[0] for x in infos[1:])
+
+
+def test_setup_threads_argument_and_errors(pslr):
+    """A negative thread count is an argument error; a zero pivot is reported
+    with any thread count."""
+    A = G.shifted_laplacian((12, 10), 0.1)
+    with pytest.raises(pslr.PslrError) as e:
+        pslr.plan(A, (12, 10, 1), (2, 2, 1), setup_threads=-1)
+    assert e.value.status == pslr.PSLR_ERR_ARG
+    _, part, iface, perm = pslr.plan(A, (12, 10, 1), (2, 2, 1))
+    zp = G.CSR(A.n, A.rowptr, A.col, A.val.copy())
+    # the first interior row of subdomains 1 and 3 loses its diagonal: nothing
+    # is eliminated before it, so its pivot is exactly zero
+    for sub in (1, 3):
+        v = next(int(u) for u in perm if part[u] == sub and not iface[u])
+        row = slice(zp.rowptr[v], zp.rowptr[v + 1])
+        zp.val[row][zp.col[row] == v] = 0.0
+    for t in (1, 4):
+        with pytest.raises(pslr.PslrError) as e:
+            pslr.plan(zp, (12, 10, 1), (2, 2, 1), setup_threads=t)
+        assert e.value.status == pslr.PSLR_ERR_ZERO_PIVOT
+
+
 @pytest.mark.parametrize("kind,dims,splits,tau", [("lap", (9, 8, 7), (2, 2, 2), 1e-2),
                                                   ("cd", (8, 7, 6), (2, 2, 1), 1e-2),
                                                   ("kappa", (7, 8, 6), (2, 1, 2), 3e-3)])
