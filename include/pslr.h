@@ -61,7 +61,8 @@ typedef struct {
      * 2): unknown idx = i + dims[0]*(j + dims[1]*k) goes to subdomain
      * floor(i*splits[0]/dims[0]) + splits[0]*(floor(j*splits[1]/dims[1])
      * + splits[1]*floor(k*splits[2]/dims[2])).  dims[0]*dims[1]*dims[2] must
-     * equal n.  Ignored when `part` is not NULL. */
+     * equal n.  Ignored when `part` is not NULL.  With dims all zero and
+     * nparts > 0 the graph partition below is used instead. */
     int32_t dims[3];
     int32_t splits[3];
     const int32_t *part;  /* optional host array (length n) of subdomain ids 0..s-1 */
@@ -78,6 +79,13 @@ typedef struct {
                               subdomains in parallel): 0 = the machine's hardware
                               threads (at most 64), >= 1 that many; the result is
                               the same for every value                              */
+    int32_t nparts;       /* with part NULL and dims {0,0,0}: partition the graph of
+                             A + A^T into nparts parts (1 <= nparts <= n) by
+                             recursive bisection of breadth-first level structures
+                             from George-Liu pseudo-peripheral vertices (each cut
+                             splits the breadth-first order of the set at
+                             floor(|U| (k/2) / k)); for matrices without a grid,
+                             standing in for the paper's METIS (Section 2)      */
 } pslr_opts;
 
 typedef struct {

@@ -72,6 +72,7 @@ def _load():
                 "orc_apply_T": (None, [P, P, P]),
                 "orc_fgmres": (I32, [P, I32, P, P, D, I32, I32, P, P]),
                 "orc_splitmix_uniform": (D, [U64, U64]),
+                "orc_graph_partition": (I32, [I32, P, P, I32, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -237,6 +238,22 @@ def splitmix_uniform(seed, j):
     return _load().orc_splitmix_uniform(seed, j)
 
 
+def graph_partition(A, nparts):
+    """Recursive breadth-first bisection of the graph of A + A^T into
+    ``nparts`` parts (the oracle's own implementation)."""
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.col, dtype=np.int32)
+    part = np.empty(A.n, dtype=np.int32)
+    st = _load().orc_graph_partition(A.n, _p(rp), _p(ci), int(nparts), _p(part))
+    if st != OK:
+        raise OracleError(st, "orc_graph_partition")
+    return part
+
+
 def from_workload(w):
-    """Oracle set-up for a workload dict from ``pslr_inputs.configs``."""
+    """Oracle set-up for a workload dict from ``pslr_inputs.configs``; a
+    workload with ``nparts`` is partitioned by :func:`graph_partition`."""
+    if w.get("nparts"):
+        return Oracle(w["A"], part=graph_partition(w["A"], w["nparts"]), factor=w["factor"],
+                      drop_tol=w.get("drop_tol", 0.0))
     return Oracle(w["A"], dims=w["dims"], splits=w["splits"], factor=w["factor"], drop_tol=w.get("drop_tol", 0.0))

@@ -692,6 +692,146 @@ void orc_Err(const orc_ctx *c, int32_t m, const double *in, double *out) {
 
 /* ------------------------------------------ Sec. 3.2: low-rank correction */
 
+/*
+ * Graph partition by recursive bisection of breadth-first level structures
+ * (stands in for METIS in Section 2 when the matrix has no grid).  Graph: the
+ * pattern of A + A^T without the diagonal; neighbours in increasing index.
+ * To cut a vertex set U (ascending) into k > 1 parts: list U breadth-first,
+ * component by component in the order of their smallest vertex, each from a
+ * pseudo-peripheral vertex (George and Liu: start at the smallest vertex of
+ * the component, search, take the vertex of least degree within U on the last
+ * level, smallest index on ties, and repeat from it while the number of
+ * levels increases); the first floor(|U| (k/2) / k) listed vertices get the
+ * parts base .. base+k/2-1, the others the remaining k - k/2 parts, each side
+ * cut again after sorting it.
+ */
+typedef struct {
+    int32_t n;
+    int32_t *start, *adj;  /* adjacency lists of A + A^T, no self loops */
+    int32_t *in_u;         /* 1 for the vertices of the set being cut */
+    int32_t *dist;         /* breadth-first distance, -1 = not reached */
+    int32_t *listed;       /* 1 once a vertex is in the breadth-first listing */
+} gp_graph;
+
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Levels of a search from root over the vertices with in_u set and listed
+ * clear, appended to seq as they are reached (level by level, each level's
+ * vertices expanding in the order they were reached, neighbours ascending).
+ * Returns the number of levels; *last_begin = index in seq of the last level. */
+static int32_t gp_levels(gp_graph *g, const int32_t *U, int32_t nu, int32_t root, int32_t *seq,
+                         int32_t *len, int32_t *last_begin) {
+    for (int32_t i = 0; i < nu; ++i) g->dist[U[i]] = -1;
+    int32_t cnt = 0, lev_begin = 0, nlev = 0;
+    seq[cnt++] = root;
+    g->dist[root] = 0;
+    while (lev_begin < cnt) {
+        int32_t lev_end = cnt;
+        *last_begin = lev_begin;
+        ++nlev;
+        for (int32_t t = lev_begin; t < lev_end; ++t) {
+            int32_t v = seq[t];
+            for (int32_t e = g->start[v]; e < g->start[v + 1]; ++e) {
+                int32_t w = g->adj[e];
+                if (!g->in_u[w] || g->listed[w] || g->dist[w] >= 0) continue;
+                g->dist[w] = nlev;
+                seq[cnt++] = w;
+            }
+        }
+        lev_begin = lev_end;
+    }
+    *len = cnt;
+    return nlev;
+}
+
+static int32_t gp_degree(const gp_graph *g, int32_t v) {
+    int32_t d = 0;
+    for (int32_t e = g->start[v]; e < g->start[v + 1]; ++e) d += g->in_u[g->adj[e]];
+    return d;
+}
+
+static void gp_cut(gp_graph *g, int32_t *U, int32_t nu, int32_t k, int32_t base, int32_t *part) {
+    if (k == 1) {
+        for (int32_t i = 0; i < nu; ++i) part[U[i]] = base;
+        return;
+    }
+    int32_t *order = malloc(sizeof(int32_t) * (nu ? nu : 1));
+    int32_t *seq = malloc(sizeof(int32_t) * (nu ? nu : 1));
+    int32_t norder = 0;
+    for (int32_t i = 0; i < nu; ++i) { g->in_u[U[i]] = 1; g->listed[U[i]] = 0; }
+    for (int32_t i = 0; i < nu; ++i) {
+        int32_t c = U[i], len, lb;
+        if (g->listed[c]) continue;
+        /* pseudo-peripheral vertex of c's component */
+        int32_t r = c, ecc = gp_levels(g, U, nu, r, seq, &len, &lb);
+        for (;;) {
+            int32_t x = -1, dx = 0;
+            for (int32_t t = lb; t < len; ++t) {
+                int32_t d = gp_degree(g, seq[t]);
+                if (x < 0 || d < dx || (d == dx && seq[t] < x)) { x = seq[t]; dx = d; }
+            }
+            int32_t ex = gp_levels(g, U, nu, x, seq, &len, &lb);
+            if (ex <= ecc) break;
+            r = x;
+            ecc = ex;
+        }
+        gp_levels(g, U, nu, r, seq, &len, &lb);
+        for (int32_t t = 0; t < len; ++t) {
+            order[norder++] = seq[t];
+            g->listed[seq[t]] = 1;
+        }
+    }
+    for (int32_t i = 0; i < nu; ++i) g->in_u[U[i]] = 0;
+    int32_t k1 = k / 2;
+    int32_t n1 = (int32_t)(((int64_t)nu * k1) / k);
+    free(seq);
+    qsort(order, (size_t)n1, sizeof(int32_t), cmp_i32);
+    qsort(order + n1, (size_t)(nu - n1), sizeof(int32_t), cmp_i32);
+    gp_cut(g, order, n1, k1, base, part);
+    gp_cut(g, order + n1, nu - n1, k - k1, base + k1, part);
+    free(order);
+}
+
+int32_t orc_graph_partition(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t nparts,
+                            int32_t *part) {
+    if (n <= 0 || nparts < 1 || nparts > n) return ORC_ERR_ARG;
+    gp_graph g;
+    g.n = n;
+    int32_t *cnt = calloc((size_t)n + 1, sizeof(int32_t));
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e)
+            if (col[e] != v) { cnt[v + 1]++; cnt[col[e] + 1]++; }
+    for (int32_t v = 0; v < n; ++v) cnt[v + 1] += cnt[v];
+    int32_t *raw = malloc(sizeof(int32_t) * (cnt[n] ? cnt[n] : 1));
+    int32_t *fill = malloc(sizeof(int32_t) * n);
+    for (int32_t v = 0; v < n; ++v) fill[v] = cnt[v];
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e)
+            if (col[e] != v) { raw[fill[v]++] = col[e]; raw[fill[col[e]]++] = v; }
+    g.start = malloc(sizeof(int32_t) * ((size_t)n + 1));
+    g.adj = malloc(sizeof(int32_t) * (cnt[n] ? cnt[n] : 1));
+    int32_t m = 0;
+    g.start[0] = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        qsort(raw + cnt[v], (size_t)(cnt[v + 1] - cnt[v]), sizeof(int32_t), cmp_i32);
+        for (int32_t e = cnt[v]; e < cnt[v + 1]; ++e)
+            if (e == cnt[v] || raw[e] != raw[e - 1]) g.adj[m++] = raw[e];
+        g.start[v + 1] = m;
+    }
+    free(raw); free(fill); free(cnt);
+    g.in_u = calloc((size_t)n, sizeof(int32_t));
+    g.dist = malloc(sizeof(int32_t) * n);
+    g.listed = calloc((size_t)n, sizeof(int32_t));
+    int32_t *U = malloc(sizeof(int32_t) * n);
+    for (int32_t v = 0; v < n; ++v) U[v] = v;
+    gp_cut(&g, U, n, nparts, 0, part);
+    free(U); free(g.in_u); free(g.dist); free(g.listed); free(g.start); free(g.adj);
+    return ORC_OK;
+}
+
 double orc_splitmix_uniform(uint64_t seed, uint64_t j) {
     uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ULL;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;

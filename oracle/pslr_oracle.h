@@ -47,6 +47,11 @@ orc_ctx *orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const d
                    int32_t factor, double drop_tol, int32_t *status);
 void orc_destroy(orc_ctx *c);
 
+/* Recursive breadth-first bisection of the graph of A + A^T into nparts parts
+ * (1 <= nparts <= n), written to part (length n); ORC_ERR_ARG otherwise. */
+int32_t orc_graph_partition(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t nparts,
+                            int32_t *part);
+
 void orc_sizes(const orc_ctx *c, int32_t *n, int32_t *s, int32_t *p, int32_t *q);
 void orc_maps(const orc_ctx *c, int32_t *part, int32_t *is_interface, int32_t *perm);
 void orc_offsets(const orc_ctx *c, int32_t *interior_off, int32_t *interface_off);

@@ -62,6 +62,10 @@ void launch_grad_values(int n, const int32_t *rp, const int32_t *ci, const doubl
 
 using namespace pslr;
 
+namespace pslr_part {
+void graph_partition(int n, const int32_t *rowptr, const int32_t *colind, int nparts, int32_t *part);
+}
+
 namespace {
 
 // ---------------------------------------------------------------- utilities
@@ -882,6 +886,10 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
             mx = std::max(mx, (int)opts->part[v]);
         }
         c->s = mx + 1;
+    } else if (opts->dims[0] == 0 && opts->dims[1] == 0 && opts->dims[2] == 0 && opts->nparts > 0) {
+        if (opts->nparts > n) return bail(fail(c, PSLR_ERR_ARG, "nparts exceeds n"));
+        pslr_part::graph_partition(n, rowptr, colind, opts->nparts, c->part.data());
+        c->s = opts->nparts;
     } else {
         const int64_t Nx = opts->dims[0], Ny = opts->dims[1], Nz = opts->dims[2];
         const int Px = opts->splits[0], Py = opts->splits[1], Pz = opts->splits[2];

@@ -36,7 +36,7 @@ PSLR_FP32 = 1
 class pslr_opts(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("splits", C.c_int32 * 3), ("part", C.c_void_p),
                 ("factor", C.c_int32), ("seed", C.c_uint64), ("drop_tol", C.c_double),
-                ("setup_threads", C.c_int32)]
+                ("setup_threads", C.c_int32), ("nparts", C.c_int32)]
 
 
 class pslr_info(C.Structure):
@@ -145,10 +145,12 @@ class Pslr:
     split; ``part`` (length n) overrides it.  ``factor``: 0 ILU(0), 1 exact LU,
     2 ILUT(``drop_tol``).  ``setup_threads``: host threads of the set-up (0 =
     all hardware threads); the context is the same for every value.
+    ``nparts`` > 0 with ``dims`` all zero and no ``part``: the library's graph
+    partition (recursive breadth-first bisection) into that many subdomains.
     """
 
     def __init__(self, A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, seed=0,
-                 stream=None, drop_tol=0.0, setup_threads=0):
+                 stream=None, drop_tol=0.0, setup_threads=0, nparts=0):
         lib = load()
         self.lib = lib
         self.n = int(A.n)
@@ -165,6 +167,7 @@ class Pslr:
         o.seed = int(seed)
         o.drop_tol = float(drop_tol)
         o.setup_threads = int(setup_threads)
+        o.nparts = int(nparts)
         h = C.c_void_p()
         st = lib.pslr_setup(self.n, self._rp.ctypes.data, self._ci.ctypes.data, self._av.ctypes.data,
                             C.byref(o), _stream(stream), C.byref(h))
@@ -365,7 +368,7 @@ class Batch:
         return self.lib.pslr_batch_set_wait_limit(self.h, int(polls))
 
 
-def _opts(dims, splits, part, factor, seed, drop_tol=0.0, setup_threads=0):
+def _opts(dims, splits, part, factor, seed, drop_tol=0.0, setup_threads=0, nparts=0):
     o = pslr_opts()
     for d in range(3):
         o.dims[d] = int(dims[d])
@@ -375,10 +378,12 @@ def _opts(dims, splits, part, factor, seed, drop_tol=0.0, setup_threads=0):
     o.seed = int(seed)
     o.drop_tol = float(drop_tol)
     o.setup_threads = int(setup_threads)
+    o.nparts = int(nparts)
     return o
 
 
-def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, drop_tol=0.0, setup_threads=0):
+def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, drop_tol=0.0, setup_threads=0,
+         nparts=0):
     """Host-only dry run of the set-up (no GPU needed): returns (info dict,
     part, is_interface, perm) exactly as a device context would report them."""
     lib = load()
@@ -386,7 +391,7 @@ def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, 
     ci = np.ascontiguousarray(A.col, dtype=np.int32)
     av = np.ascontiguousarray(A.val, dtype=np.float64)
     pa = None if part is None else np.ascontiguousarray(part, dtype=np.int32)
-    o = _opts(dims, splits, pa, factor, 0, drop_tol, setup_threads)
+    o = _opts(dims, splits, pa, factor, 0, drop_tol, setup_threads, nparts)
     info = pslr_info()
     n = int(A.n)
     mp = [np.empty(n, np.int32) for _ in range(3)]
@@ -399,5 +404,5 @@ def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, 
 
 def from_workload(w, seed=0, stream=None):
     """Context for a workload dict of ``pslr_inputs.configs``."""
-    return Pslr(w["A"], dims=w["dims"], splits=w["splits"], factor=w["factor"], seed=seed,
-                stream=stream, drop_tol=w.get("drop_tol", 0.0))
+    return Pslr(w["A"], dims=w.get("dims", (0, 0, 0)), splits=w.get("splits", (1, 1, 1)), factor=w["factor"],
+                seed=seed, stream=stream, drop_tol=w.get("drop_tol", 0.0), nparts=w.get("nparts", 0))

@@ -21,6 +21,11 @@ Workloads (names say what they are):
                           4.1's rank study), 3x3x4 split (36 subdomains, near the
                           paper's s = 35), ILUT(1e-2) as in that study, m=3; the
                           rank is the variable.
+``rgg2d_20k``             a matrix with no grid: the anchored graph Laplacian of
+                          20,000 random points in the unit square (mean degree
+                          12) shifted by 0.0064, between its two smallest
+                          eigenvalues (one negative eigenvalue); 16 parts from
+                          the graph partition, ILU(0), m=3, r=8.
 """
 from __future__ import annotations
 
@@ -78,6 +83,13 @@ def lap3d_50_shift014(rank=15, factor=FACTOR_ILUT, drop_tol=1e-2):
                 splits=(3, 3, 4), factor=factor, m=3, rank=rank, drop_tol=drop_tol)
 
 
+def rgg2d_20k(n=20000, nparts=16, factor=FACTOR_ILU0, m=3, rank=8, drop_tol=1e-2):
+    sig = 0.0064
+    A = G.random_geometric_laplacian(n, 12.0, sig, 0)
+    return dict(name="rgg2d_20k", A=A, sigma=sig, nneg=1, ndim=2, nparts=nparts, factor=factor, m=m, rank=rank,
+                drop_tol=drop_tol)
+
+
 def batch2d_64sys(nsys=64, lo=64, hi=256, nrhs=4, seed=0):
     """The batched workload: per system side N ~ U{lo..hi}, split ceil(N/32) per
     side clipped to [4, 8], m ~ U{2..5}, r ~ {8, 16, 32}, sigma for 4 negative
@@ -102,6 +114,7 @@ WORKLOADS = {
     "kappa3d_48_3x3x3": kappa3d_48_3x3x3,
     "cd3d_128_8x8x4_ilu0": cd3d_128_8x8x4_ilu0,
     "lap3d_50_shift014": lap3d_50_shift014,
+    "rgg2d_20k": rgg2d_20k,
 }
 
 

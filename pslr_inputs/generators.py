@@ -18,6 +18,12 @@ Problems (all on the unit cube / square with zero Dirichlet boundary, 5- or
 * ``variable_kappa`` - ``-div(kappa grad u) - sigma u`` with ``kappa = exp(g)``, g an
   i.i.d. seeded Gaussian per node; face coefficients are arithmetic means.
 
+* ``random_geometric_laplacian`` - a matrix with no grid: the graph Laplacian of
+  seeded random points in the unit square joined within a radius (mean degree
+  about ``degree``), plus 1 on the diagonal of points within that radius of the
+  boundary (as a Dirichlet neighbour would add), minus ``sigma``.  It stands in
+  for the unstructured matrices of Section 4's Test 3, which are not available.
+
 ``sigma_for_negative_count`` turns "exactly / about K negative eigenvalues" into a
 shift: it sorts the closed-form eigenvalues and puts sigma midway in the first gap
 at or after the K-th eigenvalue.
@@ -36,6 +42,7 @@ __all__ = [
     "variable_kappa",
     "kappa_field",
     "variable_kappa_values",
+    "random_geometric_laplacian",
     "uniform_rhs",
     "csr_matvec",
     "dense_from_csr",
@@ -243,6 +250,27 @@ def variable_kappa_values(dims, A, kappa, sigma, xp=np):
     diag = torch.zeros(n, dtype=kappa.dtype, device=kappa.device)
     diag = diag.index_add(0, rows_t[off_t], face[off_t]) + nb * kappa - sigma
     return torch.where(off_t, -face, diag[rows_t])
+
+
+def random_geometric_laplacian(n, degree=8.0, sigma=0.05, seed=0):
+    """Graph Laplacian of n seeded uniform points in [0,1]^2, pairs closer than
+    r = sqrt(degree / (pi n)) joined with weight -1, the diagonal holding the
+    number of neighbours, +1 for points within r of the boundary, - sigma.
+    Rows in the order the points were drawn (no spatial ordering)."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, 2))
+    r = float(np.sqrt(degree / (np.pi * n)))
+    pairs = cKDTree(pts).query_pairs(r, output_type="ndarray").astype(np.int64)
+    i, j = pairs[:, 0], pairs[:, 1]
+    deg = np.bincount(i, minlength=n) + np.bincount(j, minlength=n)
+    near = ((pts < r) | (pts > 1.0 - r)).any(axis=1)
+    diag = deg + near.astype(np.float64) - sigma
+    rows = np.concatenate([i, j, np.arange(n)])
+    cols = np.concatenate([j, i, np.arange(n)])
+    vals = np.concatenate([-np.ones(2 * len(i)), diag])
+    return _assemble(n, rows, cols, vals, None)
 
 
 def uniform_rhs(A, seed=0, nrhs=1):

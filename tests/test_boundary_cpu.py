@@ -146,6 +146,37 @@ def test_setup_threads_argument_and_errors(pslr):
         assert e.value.status == pslr.PSLR_ERR_ZERO_PIVOT
 
 
+@pytest.mark.parametrize("graph,k", [("rgg2000", 7), ("rgg20000", 16), ("rgg20000", 5), ("grid2d", 4),
+                                     ("grid3d", 6), ("cd3d", 9)])
+def test_graph_partition_bit_exact_with_oracle(pslr, graph, k):
+    """The library's graph partition (nparts, no dims) and the oracle's
+    independent implementation give the same part of every vertex, and the
+    reordering built on it the same maps."""
+    if graph.startswith("rgg"):
+        A = G.random_geometric_laplacian(int(graph[3:]), 12.0, 0.0064, 0)
+    elif graph == "grid2d":
+        A = G.shifted_laplacian((13, 11), 0.1)
+    elif graph == "grid3d":
+        A = G.shifted_laplacian((9, 8, 7), 0.1)
+    else:
+        A = G.convection_diffusion((8, 7, 6), 50.0, 0.1)
+    info, part, iface, perm = pslr.plan(A, nparts=k)
+    po = O.graph_partition(A, k)
+    assert np.array_equal(part, po)
+    o = O.Oracle(A, part=po)
+    for a, b in zip((part, iface, perm), o.maps()):
+        assert np.array_equal(a, b)
+    assert info["s"] == k
+
+
+def test_graph_partition_arguments(pslr):
+    A = G.shifted_laplacian((4, 4), 0.0)
+    for k in (17, -1):
+        with pytest.raises(pslr.PslrError) as e:
+            pslr.plan(A, nparts=k)
+        assert e.value.status == pslr.PSLR_ERR_ARG
+
+
 @pytest.mark.parametrize("kind,dims,splits,tau", [("lap", (9, 8, 7), (2, 2, 2), 1e-2),
                                                   ("cd", (8, 7, 6), (2, 2, 1), 1e-2),
                                                   ("kappa", (7, 8, 6), (2, 1, 2), 3e-3)])

@@ -72,3 +72,23 @@ def test_rhs_is_A_times_uniform():
     b, xs = G.uniform_rhs(A, 0)
     assert xs.min() >= -1 and xs.max() <= 1
     np.testing.assert_allclose(b, G.dense_from_csr(A) @ xs, atol=1e-14)
+
+
+def test_random_geometric_workload():
+    """The matrix without a grid: symmetric, every diagonal stored, rows are
+    neighbour counts (+1 near the boundary) minus the shift, and the shift of
+    the 20,000-point workload leaves exactly one negative eigenvalue (shift-
+    invert Lanczos for the smallest eigenvalues)."""
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    import scipy.sparse as sp
+
+    w = C.rgg2d_20k()
+    A = w["A"]
+    M = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+    assert abs(M - M.T).max() == 0
+    d = M.diagonal()
+    off = np.asarray((M != 0).sum(axis=1)).ravel() - 1
+    assert np.all(np.isin(np.round(d + w["sigma"] - off, 12), (0.0, 1.0)))
+    assert 10.0 < off.mean() < 14.0
+    ev = np.sort(sla.eigsh(M, k=4, sigma=-0.01, which="LM", return_eigenvectors=False))
+    assert (ev < 0).sum() == w["nneg"] == 1
