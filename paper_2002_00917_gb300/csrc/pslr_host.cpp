@@ -63,7 +63,7 @@ void launch_grad_values(int n, const int32_t *rp, const int32_t *ci, const doubl
 using namespace pslr;
 
 namespace pslr_part {
-void graph_partition(int n, const int32_t *rowptr, const int32_t *colind, int nparts, int32_t *part);
+bool graph_partition(int n, const int32_t *rowptr, const int32_t *colind, int nparts, int32_t *part, int threads);
 }
 
 namespace {
@@ -888,7 +888,8 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
         c->s = mx + 1;
     } else if (opts->dims[0] == 0 && opts->dims[1] == 0 && opts->dims[2] == 0 && opts->nparts > 0) {
         if (opts->nparts > n) return bail(fail(c, PSLR_ERR_ARG, "nparts exceeds n"));
-        pslr_part::graph_partition(n, rowptr, colind, opts->nparts, c->part.data());
+        if (!pslr_part::graph_partition(n, rowptr, colind, opts->nparts, c->part.data(), threads))
+            return bail(fail(c, PSLR_ERR_ARG, "graph partition failed (out of host memory)"));
         c->s = opts->nparts;
     } else {
         const int64_t Nx = opts->dims[0], Ny = opts->dims[1], Nz = opts->dims[2];

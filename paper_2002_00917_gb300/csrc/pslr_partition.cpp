@@ -13,9 +13,16 @@
 // the first floor(|U| k1 / k) vertices of that order form U1, the rest U2
 // (both re-sorted ascending); U1 is cut into k1 parts numbered from the base,
 // U2 into k - k1 parts numbered after them.  Every step is deterministic, so
-// the result depends only on the pattern and k.
+// the result depends only on the pattern and k.  The two sides of a cut
+// touch disjoint vertices, so the upper levels of the recursion run on host
+// threads; the markers the searches share are relaxed atomics, and every
+// search compares them only against tags and stamps unique to itself, so the
+// result does not depend on the threads either.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
+#include <memory>
+#include <thread>
 #include <vector>
 
 namespace pslr_part {
@@ -59,22 +66,32 @@ Graph symmetric_pattern(int n, const int32_t *rowptr, const int32_t *colind) {
 
 class Bisector {
   public:
-    Bisector(const Graph &g, int n, int32_t *part) : g_(g), part_(part), inset_(n, 0), seen_(n, 0) {}
+    Bisector(const Graph &g, int n, int32_t *part)
+        : g_(g), part_(part), inset_(new std::atomic<int>[n]), seen_(new std::atomic<int>[n]) {
+        for (int v = 0; v < n; ++v) {
+            inset_[v].store(0, std::memory_order_relaxed);
+            seen_[v].store(0, std::memory_order_relaxed);
+        }
+    }
 
-    void cut(std::vector<int32_t> &U, int k, int base) {
+    // Cut U into k parts numbered from base; `threads` host threads may share
+    // the work below this cut.
+    void cut(std::vector<int32_t> &U, int k, int base, int threads) {
         if (k == 1) {
             for (int v : U) part_[v] = base;
             return;
         }
-        const int tag = ++tags_;
-        for (int v : U) inset_[v] = tag;
+        const int tag = tags_.fetch_add(1) + 1;
+        for (int v : U) set(inset_, v, tag);
         std::vector<int32_t> order;
         order.reserve(U.size());
-        const int done = ++stamps_;  // vertices already placed in `order`
+        const int done = stamps_.fetch_add(1) + 1;  // vertices already placed in `order`
+        std::vector<int32_t> seq;
         for (int c : U) {
-            if (seen_[c] == done) continue;
-            const int root = peripheral(c, tag, done);
-            bfs(root, tag, done, &order, nullptr);
+            if (get(seen_, c) == done) continue;
+            peripheral(c, tag, done, seq);  // the search from the vertex it picks
+            for (int v : seq) set(seen_, v, done);
+            order.insert(order.end(), seq.begin(), seq.end());
         }
         const int k1 = k / 2;
         const size_t n1 = (size_t)(((int64_t)U.size() * k1) / k);
@@ -83,21 +100,48 @@ class Bisector {
         std::vector<int32_t>().swap(U);
         std::sort(U1.begin(), U1.end());
         std::sort(U2.begin(), U2.end());
-        cut(U1, k1, base);
-        cut(U2, k - k1, base + k1);
+        std::thread side;
+        if (threads > 1) {
+            const int t1 = threads / 2;
+            try {
+                side = std::thread([&, t1]() {
+                    try {
+                        cut(U1, k1, base, t1);
+                    } catch (...) {
+                        failed_ = true;
+                    }
+                });
+            } catch (...) {  // no thread to be had: the same work on this one
+            }
+        }
+        try {
+            if (!side.joinable()) cut(U1, k1, base, 1);
+            cut(U2, k - k1, base + k1, side.joinable() ? threads - threads / 2 : 1);
+        } catch (...) {
+            failed_ = true;
+        }
+        if (side.joinable()) side.join();
     }
 
+    bool failed() const { return failed_; }
+
   private:
-    // Breadth-first search from root over vertices of the set `tag` that are
-    // not marked `done`.  With `out`, every reached vertex is appended to it and
-    // marked `done`; otherwise the search uses a fresh private stamp.  Returns
-    // the number of levels; `last` (optional) receives the last level.
-    int bfs(int root, int tag, int done, std::vector<int32_t> *out, std::vector<int32_t> *last) {
-        const int mark = out ? done : ++stamps_;
-        std::vector<int32_t> local;
-        std::vector<int32_t> &q = out ? *out : local;
-        size_t head = q.size();
-        seen_[root] = mark;
+    static int get(const std::unique_ptr<std::atomic<int>[]> &a, int v) {
+        return a[v].load(std::memory_order_relaxed);
+    }
+    static void set(std::unique_ptr<std::atomic<int>[]> &a, int v, int x) {
+        a[v].store(x, std::memory_order_relaxed);
+    }
+
+    // Breadth-first search from root over the vertices of the set `tag` not
+    // marked `done`, under a fresh private stamp; q receives the vertices in
+    // the order they are reached.  Returns the number of levels and the index
+    // in q where the last level begins.
+    int bfs(int root, int tag, int done, std::vector<int32_t> &q, size_t &last_begin) {
+        const int mark = stamps_.fetch_add(1) + 1;
+        q.clear();
+        size_t head = 0;
+        set(seen_, root, mark);
         q.push_back(root);
         int levels = 0;
         size_t level_begin = head;
@@ -109,59 +153,71 @@ class Bisector {
                 const int v = q[head];
                 for (int t = g_.rp[v]; t < g_.rp[v + 1]; ++t) {
                     const int w = g_.ci[t];
-                    if (inset_[w] != tag || seen_[w] == mark || seen_[w] == done) continue;
-                    seen_[w] = mark;
+                    if (get(inset_, w) != tag) continue;
+                    const int sw = get(seen_, w);
+                    if (sw == mark || sw == done) continue;
+                    set(seen_, w, mark);
                     q.push_back(w);
                 }
             }
         }
-        if (last) last->assign(q.begin() + level_begin, q.end());
+        last_begin = level_begin;
         return levels;
     }
 
     int degree(int v, int tag) const {
         int d = 0;
-        for (int t = g_.rp[v]; t < g_.rp[v + 1]; ++t) d += inset_[g_.ci[t]] == tag;
+        for (int t = g_.rp[v]; t < g_.rp[v + 1]; ++t) d += get(inset_, g_.ci[t]) == tag;
         return d;
     }
 
-    // George-Liu pseudo-peripheral vertex of the component of c.
-    int peripheral(int c, int tag, int done) {
-        int r = c;
-        std::vector<int32_t> last;
-        int ecc = bfs(r, tag, done, nullptr, &last);
+    // George-Liu pseudo-peripheral vertex of the component of c; seq
+    // receives the breadth-first search from it.
+    void peripheral(int c, int tag, int done, std::vector<int32_t> &seq) {
+        size_t lb = 0, lbx = 0;
+        int ecc = bfs(c, tag, done, seq, lb);
+        std::vector<int32_t> sx;
         for (;;) {
             int x = -1, dx = 0;
-            for (int v : last) {
+            for (size_t t = lb; t < seq.size(); ++t) {
+                const int v = seq[t];
                 const int d = degree(v, tag);
                 if (x < 0 || d < dx || (d == dx && v < x)) {
                     x = v;
                     dx = d;
                 }
             }
-            std::vector<int32_t> lx;
-            const int ex = bfs(x, tag, done, nullptr, &lx);
-            if (ex <= ecc) return r;
-            r = x;
+            const int ex = bfs(x, tag, done, sx, lbx);
+            if (ex <= ecc) return;
             ecc = ex;
-            last.swap(lx);
+            seq.swap(sx);
+            lb = lbx;
         }
     }
 
     const Graph &g_;
     int32_t *part_;
-    std::vector<int> inset_, seen_;
-    int tags_ = 0, stamps_ = 0;
+    std::unique_ptr<std::atomic<int>[]> inset_, seen_;
+    std::atomic<int> tags_{0}, stamps_{0};
+    std::atomic<bool> failed_{false};
 };
 
 }  // namespace
 
-// part[v] in 0..nparts-1 for every vertex; 1 <= nparts <= n.
-void graph_partition(int n, const int32_t *rowptr, const int32_t *colind, int nparts, int32_t *part) {
-    Graph g = symmetric_pattern(n, rowptr, colind);
-    std::vector<int32_t> U(n);
-    for (int v = 0; v < n; ++v) U[v] = v;
-    Bisector(g, n, part).cut(U, nparts, 0);
+// part[v] in 0..nparts-1 for every vertex; 1 <= nparts <= n; up to
+// `threads` host threads.  false if the host ran out of memory.
+bool graph_partition(int n, const int32_t *rowptr, const int32_t *colind, int nparts, int32_t *part,
+                     int threads) {
+    try {
+        Graph g = symmetric_pattern(n, rowptr, colind);
+        std::vector<int32_t> U(n);
+        for (int v = 0; v < n; ++v) U[v] = v;
+        Bisector b(g, n, part);
+        b.cut(U, nparts, 0, std::max(1, threads));
+        return !b.failed();
+    } catch (...) {
+        return false;
+    }
 }
 
 }  // namespace pslr_part

@@ -150,8 +150,8 @@ def test_setup_threads_argument_and_errors(pslr):
                                      ("grid3d", 6), ("cd3d", 9)])
 def test_graph_partition_bit_exact_with_oracle(pslr, graph, k):
     """The library's graph partition (nparts, no dims) and the oracle's
-    independent implementation give the same part of every vertex, and the
-    reordering built on it the same maps."""
+    independent implementation give the same part of every vertex, with any
+    number of set-up threads, and the reordering built on it the same maps."""
     if graph.startswith("rgg"):
         A = G.random_geometric_laplacian(int(graph[3:]), 12.0, 0.0064, 0)
     elif graph == "grid2d":
@@ -163,6 +163,8 @@ def test_graph_partition_bit_exact_with_oracle(pslr, graph, k):
     info, part, iface, perm = pslr.plan(A, nparts=k)
     po = O.graph_partition(A, k)
     assert np.array_equal(part, po)
+    for t in (1, 3):  # the cuts below the first run on host threads
+        assert np.array_equal(pslr.plan(A, nparts=k, setup_threads=t)[1], po)
     o = O.Oracle(A, part=po)
     for a, b in zip((part, iface, perm), o.maps()):
         assert np.array_equal(a, b)
