@@ -171,6 +171,23 @@ def test_graph_partition_bit_exact_with_oracle(pslr, graph, k):
     assert info["s"] == k
 
 
+def test_graph_partition_edge_cases(pslr):
+    """One part (no interface), one vertex per part (no interior), and a graph
+    with isolated vertices (components listed by their smallest vertex): the
+    library agrees with the oracle."""
+    A = G.shifted_laplacian((10, 9), 0.1)
+    for k, q in ((1, 0), (A.n, A.n)):
+        info, part, iface, perm = pslr.plan(A, nparts=k, m=2, rank=3)
+        assert np.array_equal(part, O.graph_partition(A, k)) and info["q"] == q
+    n = 30
+    rows = list(range(n)) + [0, 1, 5, 6]
+    cols = list(range(n)) + [1, 0, 6, 5]
+    B = G._assemble(n, np.array(rows), np.array(cols), np.array([2.0] * n + [-1.0] * 4), None)
+    for k in (3, 7):
+        part = pslr.plan(B, nparts=k, m=1, rank=2)[1]
+        assert np.array_equal(part, O.graph_partition(B, k))
+
+
 def test_graph_partition_arguments(pslr):
     A = G.shifted_laplacian((4, 4), 0.0)
     for k in (17, -1):
