@@ -670,7 +670,7 @@ void pack_subdomain(const Local &Lc, int npi, int nqi, bool transposed, int q, S
         // E-slot: F_i^T (interior rows <- interface cols); F-slot: E_i^T.
         k[kE] = pack_rows<T, uint16_t>(S, ell_rows(transpose(Lc.F)), false, nqi);
         k[kF] = pack_rows<T, uint16_t>(S, ell_rows(transpose(Lc.E)), false, npi);
-        k[kCg] = 0;  // filled by the caller (needs C_g of every subdomain)
+        k[kCg] = 0;  // C_g^T rows need C_g of every subdomain: packed by pack_direction
         // B^{-T} = U^{-T} L^{-T}: sweep 1 is U^T (lower, with diagonal), sweep 2 L^T (upper)
         Csr BUt = transpose(Lc.BU), BLt = transpose(Lc.BL);
         Csr CUt = transpose(Lc.CU), CLt = transpose(Lc.CL);
