@@ -6,6 +6,10 @@
  * Parity status of each part (what pins it is in tests/test_oracle_*.py):
  *   partition / reordering / blocks ..... pinned (brute force, reassembly)
  *   ILU(0), exact LU ..................... pinned (pattern identity, P L U = B)
+ *   ILUT(tau) ............................ pinned (tau = 0 is LU, tridiagonal = ILU(0),
+ *                                          thresholds, dense brute force)
+ *   graph partition ...................... pinned (paths cut into runs, grid
+ *                                          anti-diagonals, components, sizes)
  *   series, E_rr(m), Arnoldi, G ......... pinned (closed forms, Theorem 2)
  *   Algorithm 3 apply and transpose ...... pinned (dense formulas, identity case)
  *   FGMRES ............................... pinned (dense solve, M = I reduction)
