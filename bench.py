@@ -217,7 +217,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": w["name"], "m": w["m"], "rank": k,
-                                        "n": w["A"].n, "subdomains": int(np.prod(w["splits"]))},
+                                        "n": w["A"].n, "subdomains": orc.s},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} FP64 applies of {w['name']} in the C oracle"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -233,7 +233,8 @@ def reference_apply_bytes(w, rank):
     from paper_2002_00917_gb300 import pslr
 
     B.build()
-    info = pslr.plan(w["A"], w["dims"], w["splits"], factor=w["factor"], m=w["m"], rank=rank)[0]
+    info = pslr.plan(w["A"], w.get("dims", (0, 0, 0)), w.get("splits", (1, 1, 1)), factor=w["factor"], m=w["m"],
+                     rank=rank, drop_tol=w.get("drop_tol", 0.0), nparts=w.get("nparts", 0))[0]
     return info["apply_bytes_fp64"]
 
 
