@@ -225,6 +225,11 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def factor_name(w):
+    """Local factor kind of a workload, as the config names it."""
+    return {0: "ilu0", 1: "lu", 2: "ilut(%g)" % w.get("drop_tol", 0.0)}[w["factor"]]
+
+
 def reference_apply_bytes(w, rank):
     """Algorithmic bytes of one FP64 apply, the same count the GPU arm uses:
     pslr_plan runs the library's host-side set-up only (reordering and layout,
@@ -523,7 +528,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t64 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "n": w["A"].n, "subdomains": info["s"], "p": info["p"],
-                       "q": info["q"], "m": w["m"], "rank": k, "factor": "ilu0" if w["factor"] == 0 else "lu",
+                       "q": info["q"], "m": w["m"], "rank": k, "factor": factor_name(w),
                        "l2": "flushed between timed applies (512 MB write)",
                        "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
             "roofline": {"bound": "hbm", "achieved": value / world, "peak": peak, "unit": "GB/s",
