@@ -100,6 +100,11 @@ typedef struct {
                              layout (segments, descriptors and counts of both
                              directions and precisions); 0 from a device context  */
     int32_t setup_threads; /* host threads the set-up used                        */
+    int64_t layout_errors; /* pslr_plan only: violations a host-side decode of every
+                              packed segment found (indices out of range, a product
+                              writing a row twice, a sweep row reading a row not
+                              written at an earlier barrier step, a sweep missing
+                              or repeating a row); 0 for a sound layout           */
 } pslr_info;
 
 /*

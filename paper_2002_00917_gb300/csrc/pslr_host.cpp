@@ -532,6 +532,7 @@ struct pslr_ctx {
     int64_t nnz_A = 0, nnz_ilu = 0;
     int threads = 1;            // host threads of the set-up
     uint64_t layout_hash = 0;   // pslr_plan: hash of the packed device layout
+    int64_t layout_errors = 0;  // pslr_plan: violations found by check_layout
     std::vector<int32_t> h_rp, h_ci;
     std::vector<double> h_av;
     // device: maps and matrices
@@ -747,6 +748,122 @@ bool pack_direction(const std::vector<Local> &loc, const std::vector<int> &np, c
 
 }  // namespace
 
+// Host-side check of a packed layout (pslr_plan): it decodes every segment
+// the kernels will read and counts violations of what they rely on.
+//  - every header is consistent (rows <= kSegMaxRows, padding, encoding,
+//    byte size) and every row and column index is in range for its block
+//    (columns may name the zero slot: an unused entry);
+//  - an E, F or C_g product writes each output row at most once (its warps
+//    run through the segments without a barrier);
+//  - a triangular sweep writes every row of its block exactly once, and each
+//    row reads only rows written at an earlier barrier step of the same sweep
+//    (one segment is one barrier step), so no two threads race.
+template <class T>
+static int64_t check_layout(const pslr_ctx *c, const SegStore &S, const std::vector<int32_t> &sub_desc,
+                            const std::vector<int32_t> &cnt, std::string *first) {
+    int64_t bad = 0;
+    auto note = [&](const char *what, int i, int cat) {
+        if (bad++ == 0 && first) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "layout check: %s (subdomain %d, segment kind %d)", what, i, cat);
+            *first = buf;
+        }
+    };
+    std::vector<int> step;
+    for (int i = 0; i < c->s; ++i) {
+        const int np = c->ioff[i + 1] - c->ioff[i], nq = c->goff[i + 1] - c->goff[i];
+        int d = sub_desc[i];
+        for (int cat = 0; cat < kNCnt; ++cat) {
+            const bool sweep = cat >= kB1;
+            const int nrows = (cat == kE || cat == kB1 || cat == kB2) ? np : nq;
+            const int ncols = cat == kE ? nq : cat == kF ? np : cat == kCg ? c->q : nrows;  // also the zero slot
+            step.assign((size_t)nrows, -1);
+            const int nseg = cnt[(size_t)kNCnt * i + cat];
+            for (int t = 0; t < nseg; ++t, ++d) {
+                const SegDesc &sd = S.desc[d];
+                if (sd.off < 0 || sd.off + sd.bytes > (int64_t)S.bytes.size() || sd.bytes < (int)sizeof(SegHdr)) {
+                    note("segment outside the store", i, cat);
+                    continue;
+                }
+                const char *base = S.bytes.data() + sd.off;
+                SegHdr h;
+                std::memcpy(&h, base, sizeof h);
+                const bool global = (h.flags & kSegGlobalCols) != 0, diag = (h.flags & kSegDiag) != 0;
+                const int n = h.n, pn = h.np, fmt = h.fmt;
+                const int w = fmt == kTile ? h.w : fmt;
+                const int64_t want = global ? seg_bytes<T, int32_t>(n, w, diag) : seg_bytes<T, uint16_t>(n, w, diag);
+                if (n < 1 || n > kSegMaxRows || pn != seg_npad(n) || global != (cat == kCg) ||
+                    (fmt != kTile && fmt != kRec3 && fmt != kRec7) || seg_fmt_for(w) != fmt || want != sd.bytes) {
+                    note("inconsistent segment header", i, cat);
+                    continue;
+                }
+                auto idx = [&](size_t k) -> int {
+                    if (global) {
+                        int32_t x;
+                        std::memcpy(&x, base + sizeof(SegHdr) + 4 * k, 4);
+                        return x;
+                    }
+                    uint16_t x;
+                    std::memcpy(&x, base + sizeof(SegHdr) + 2 * k, 2);
+                    return x;
+                };
+                const size_t isz = global ? 4 : 2;
+                std::vector<std::pair<int, int>> writes;  // (row, step) applied after the segment
+                for (int j = 0; j < n; ++j) {
+                    int row;
+                    if (fmt != kTile) {
+                        row = idx((size_t)j * (w + 1));
+                    } else {
+                        const size_t roff = sizeof(SegHdr) + (size_t)pn * w * sizeof(T) + (diag ? pn * sizeof(T) : 0) +
+                                            (size_t)pn * w * isz;
+                        uint16_t r16;
+                        std::memcpy(&r16, base + roff + 2 * (size_t)j, 2);
+                        row = r16;
+                    }
+                    if (row < 0 || row >= nrows) {
+                        note("row out of range", i, cat);
+                        continue;
+                    }
+                    for (int k = 0; k < w; ++k) {
+                        int col;
+                        if (fmt != kTile) {
+                            col = idx((size_t)j * (w + 1) + 1 + k);
+                        } else {
+                            const size_t coff = sizeof(SegHdr) + (size_t)pn * w * sizeof(T) + (diag ? pn * sizeof(T) : 0);
+                            if (global) {
+                                int32_t x;
+                                std::memcpy(&x, base + coff + 4 * ((size_t)k * pn + j), 4);
+                                col = x;
+                            } else {
+                                uint16_t x;
+                                std::memcpy(&x, base + coff + 2 * ((size_t)k * pn + j), 2);
+                                col = x;
+                            }
+                        }
+                        if (col < 0 || col > ncols) {
+                            note("column out of range", i, cat);
+                        } else if (sweep && col < ncols && (step[col] < 0 || step[col] >= t)) {
+                            note("a sweep row reads a row not written at an earlier step", i, cat);
+                        }
+                    }
+                    writes.push_back({row, t});
+                }
+                for (auto &wr : writes) {
+                    if (step[wr.first] >= 0) note(sweep ? "a sweep writes a row twice" : "a product writes a row twice", i, cat);
+                    step[wr.first] = wr.second;
+                }
+            }
+            if (sweep)
+                for (int r = 0; r < nrows; ++r)
+                    if (step[r] < 0) {
+                        note("a sweep leaves a row unwritten", i, cat);
+                        break;
+                    }
+        }
+    }
+    return bad;
+}
+
 template <class T>
 static pslr_status finish_opset(pslr_ctx *c, OpSetHost &o, SegStore &S, const std::vector<int32_t> &sub_desc,
                                 const std::vector<int32_t> &cnt, bool fp32, bool plan_only) {
@@ -761,6 +878,9 @@ static pslr_status finish_opset(pslr_ctx *c, OpSetHost &o, SegStore &S, const st
     o.hsub = sub_desc;
     o.hcnt = cnt;
     if (plan_only) {
+        std::string first;
+        c->layout_errors += check_layout<T>(c, S, sub_desc, cnt, c->layout_errors ? nullptr : &first);
+        if (!first.empty()) fprintf(stderr, "pslr_plan: %s\n", first.c_str());
         uint64_t h = c->layout_hash ? c->layout_hash : 0xcbf29ce484222325ull;
         h = fnv1a(h, S.bytes.data(), S.bytes.size());
         for (const SegDesc &d : S.desc) {  // field by field: the struct has padding
@@ -1495,6 +1615,7 @@ pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info) {
     I.apply_bytes_fp32 = pslr_apply_bytes(c, 1);
     I.setup_threads = c->threads;
     I.layout_hash = c->layout_hash;
+    I.layout_errors = c->layout_errors;
     *info = I;
     return PSLR_OK;
 }

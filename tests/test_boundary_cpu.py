@@ -171,6 +171,28 @@ def test_graph_partition_bit_exact_with_oracle(pslr, graph, k):
     assert info["s"] == k
 
 
+@pytest.mark.parametrize("kind,dims,splits,factor", [("lap", (32, 32), (2, 2), 1), ("lap", (13, 11, 9), (3, 2, 2), 0),
+                                                     ("cd", (12, 10, 8), (3, 2, 2), 2), ("kappa", (10, 9, 11), (2, 3, 2), 0),
+                                                     ("lap", (40, 33), (3, 4), 0), ("cd", (9, 9, 9), (1, 1, 1), 0),
+                                                     ("lap", (7, 6, 5), (7, 6, 5), 0), ("lap", (13, 11, 9), (3, 2, 2), 2)])
+def test_layout_check_finds_no_violation(pslr, kind, dims, splits, factor):
+    """The host-side decode of every packed segment (both directions, both
+    precisions) finds every index in range, no product writing a row twice,
+    and every sweep row reading only rows written at an earlier barrier
+    step: the level schedules the kernels run are race-free."""
+    w = C.small_problem(kind, dims, splits, factor=factor, drop_tol=1e-2)
+    info = pslr.plan(w["A"], w["dims"], w["splits"], factor=factor, m=3, rank=4, drop_tol=1e-2)[0]
+    assert info["layout_errors"] == 0
+
+
+@pytest.mark.parametrize("name", ["lap3d_64_4x4x2_ilu0", "kappa3d_48_3x3x3", "lap3d_50_shift014", "rgg2d_20k"])
+def test_layout_check_full_size(pslr, name):
+    w = C.WORKLOADS[name]()
+    info = pslr.plan(w["A"], w.get("dims", (0, 0, 0)), w.get("splits", (1, 1, 1)), factor=w["factor"], m=w["m"],
+                     rank=w["rank"], drop_tol=w.get("drop_tol", 0.0), nparts=w.get("nparts", 0))[0]
+    assert info["layout_errors"] == 0
+
+
 def test_graph_partition_edge_cases(pslr):
     """One part (no interface), one vertex per part (no interior), and a graph
     with isolated vertices (components listed by their smallest vertex): the
