@@ -24,7 +24,7 @@ SOURCES = ["pslr_apply.cu", "pslr_krylov.cu", "pslr_host.cpp", "pslr_noalloc.cu"
            "pslr_partition.cpp"]
 HEADERS = [os.path.join(CSRC, "pslr_internal.h"), os.path.join(CSRC, "pslr_device.cuh"),
            os.path.join(CSRC, "pslr_sys.h"), os.path.join(CSRC, "pslr_batch.cuh"),
-           os.path.join(CSRC, "pslr_reduce.cuh"),
+           os.path.join(CSRC, "pslr_reduce.cuh"), os.path.join(CSRC, "pslr_trace.h"),
            os.path.join(ROOT, "include", "pslr.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

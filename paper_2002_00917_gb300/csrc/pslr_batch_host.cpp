@@ -20,6 +20,7 @@
 #include "pslr.h"
 #include "pslr_internal.h"
 #include "pslr_sys.h"
+#include "pslr_trace.h"
 
 namespace pslr {
 cudaError_t launch_batch_f64(const void *params, int smem, cudaStream_t st);
@@ -983,6 +984,7 @@ extern "C" {
 
 pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nrhs, int32_t group,
                               pslr_batch **out) {
+    TraceRange trace("pslr_batch_create");
     pslr_batch *bt = nullptr;
     if (out) *out = nullptr;
     if (!out || nsys < 1 || !systems || nrhs < 1 || nrhs > kMaxBatchRhs || group < 0 || group > kMaxGroup)
@@ -1039,6 +1041,7 @@ pslr_status pslr_batch_sync(pslr_batch *bt, void *stream) {
 
 pslr_status pslr_batch_solve(pslr_batch *bt, const double *b_dev, double *x_dev, double rtol, int32_t restart,
                              int32_t maxit, pslr_prec prec, int32_t *iters, double *relres, void *stream) {
+    TraceRange trace("pslr_batch_solve");
     if (!bt || !b_dev || !x_dev || restart < 1 || restart > 127 || maxit < 0 || !(rtol > 0.0) ||
         (prec != PSLR_FP64 && prec != PSLR_FP32))
         return bfail(bt, PSLR_ERR_ARG, "batch_solve: bad argument (restart must be 1..127)");

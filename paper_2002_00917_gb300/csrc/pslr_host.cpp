@@ -26,6 +26,7 @@
 #include "pslr.h"
 #include "pslr_internal.h"
 #include "pslr_sys.h"
+#include "pslr_trace.h"
 
 namespace pslr {
 // kernels (pslr_apply.cu, pslr_krylov.cu)
@@ -1256,6 +1257,7 @@ extern "C" {
 
 pslr_status pslr_setup(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *val,
                        const pslr_opts *opts, void *stream, pslr_ctx **out) {
+    TraceRange trace("pslr_setup");
     if (!out) return PSLR_ERR_ARG;
     *out = nullptr;
     if (n <= 0 || !rowptr || !colind || !val || !opts) return PSLR_ERR_ARG;
@@ -1623,6 +1625,7 @@ pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info) {
 pslr_status pslr_plan(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *val,
                       const pslr_opts *opts, int32_t m, int32_t rank, pslr_info *info, int32_t *part,
                       int32_t *is_interface, int32_t *perm) {
+    TraceRange trace("pslr_plan");
     if (n <= 0 || !rowptr || !colind || !val || !opts || m < 0 || rank < 0) return PSLR_ERR_ARG;
     pslr_ctx *c = new pslr_ctx();
     pslr_status st = setup_impl(c, n, rowptr, colind, val, opts, true);
@@ -1848,6 +1851,7 @@ static pslr_status launch_err(pslr_ctx *c, const double *vin, double *vout, int 
 extern "C" {
 
 pslr_status pslr_build_lowrank(pslr_ctx *c, int32_t m, int32_t rank, int32_t full_rank, void *stream) {
+    TraceRange trace("pslr_build_lowrank");
     if (!c || m < 0 || rank < 0) return fail(c, PSLR_ERR_ARG, "build_lowrank: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CK(cudaStreamSynchronize(st));
@@ -2031,6 +2035,7 @@ extern "C" {
 pslr_status pslr_solve(pslr_ctx *c, const double *b_dev, double *x_dev, double rtol, int32_t restart,
                        int32_t maxit, pslr_prec prec, int32_t transpose, int32_t *iters, double *relres,
                        void *stream) {
+    TraceRange trace("pslr_solve");
     if (!c || !b_dev || !x_dev || restart < 1 || restart > 127 || maxit < 0 || !(rtol > 0.0) ||
         (prec != PSLR_FP64 && prec != PSLR_FP32))
         return fail(c, PSLR_ERR_ARG, "solve: bad argument (restart must be 1..127)");
