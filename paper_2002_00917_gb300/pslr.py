@@ -11,6 +11,7 @@ class :class:`Pslr` owns one context.
 from __future__ import annotations
 
 import ctypes as C
+import hashlib
 import os
 
 import numpy as np
@@ -168,6 +169,7 @@ class Pslr:
         o.drop_tol = float(drop_tol)
         o.setup_threads = int(setup_threads)
         o.nparts = int(nparts)
+        self.factor, self.drop_tol = int(factor), float(drop_tol)
         h = C.c_void_p()
         st = lib.pslr_setup(self.n, self._rp.ctypes.data, self._ci.ctypes.data, self._av.ctypes.data,
                             C.byref(o), _stream(stream), C.byref(h))
@@ -233,6 +235,35 @@ class Pslr:
                                               H.ctypes.data if r else None,
                                               G.ctypes.data if r else None), "pslr_get_lowrank")
         return V, H, G
+
+    # -- checkpoint of the low-rank term
+    def fingerprint(self):
+        """Hex digest of what the low-rank term depends on: the matrix, the
+        local factor kind and threshold, and the reordering (Section 2)."""
+        h = hashlib.sha256()
+        for a in (self._rp, self._ci, self._av, *self.get_maps()):
+            h.update(np.ascontiguousarray(a).tobytes())
+        h.update(np.array([self.factor], np.int64).tobytes())
+        h.update(np.array([self.drop_tol], np.float64).tobytes())
+        return h.hexdigest()
+
+    def save_lowrank(self, path):
+        """Write the low-rank term (m, V, H, G of Algorithm 1, steps 6-8) with
+        this context's fingerprint to ``path`` (numpy .npz).  The local factors
+        are not saved: setting up the same matrix with the same options
+        rebuilds them bit for bit, so only the Arnoldi work is kept."""
+        V, H, G = self.get_lowrank()
+        np.savez(path, m=np.int64(self.info["m"]), V=V, H=H, G=G, fingerprint=np.array(self.fingerprint()))
+
+    def load_lowrank(self, path, stream=None):
+        """Install a term written by :meth:`save_lowrank` for the same matrix,
+        factor kind and reordering (ValueError otherwise); returns its rank."""
+        with np.load(path) as f:
+            if str(f["fingerprint"]) != self.fingerprint():
+                raise ValueError(f"{path}: low-rank term of another matrix, factor kind or reordering")
+            m, V, G = int(f["m"]), f["V"], f["G"]
+        self.set_lowrank(m, V if V.shape[1] else None, G if V.shape[1] else None, stream=stream)
+        return V.shape[1]
 
     # -- Algorithm 3 and its transpose
     def apply(self, b, z, transpose=False, stream=None):
