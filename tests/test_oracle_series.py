@@ -90,6 +90,35 @@ def test_lemma_spd_spectrum_inside_unit_interval():
     assert lam.real.max() < 1 and lam.real.min() > -1
 
 
+@pytest.mark.parametrize("dims,splits,K", [((10, 9, 8), (2, 2, 1), 7), ((12, 11), (3, 2), 5), ((9, 8, 7), (1, 2, 2), 12)])
+def test_eigenvalues_above_one_count_the_negative_eigenvalues_of_S(dims, splits, K):
+    """Sec. 3.1-3.2 on an indefinite problem (the setting of the spectra the
+    paper plots for a shifted 20^3 Laplacian): with exact local factors and C0
+    positive definite, E_s C0^{-1} is similar to C0^{-1/2} E_s C0^{-1/2}, whose
+    eigenvalues above 1 are those where S = C0 - E_s is negative (Sylvester's
+    law of inertia); by Haynsworth's inertia additivity S has neg(A) - neg(B)
+    negative eigenvalues.  The count is checked against dense eigenvalues of A
+    and B, so a sign or block mistake in E_s, E, F or C_g fails it."""
+    from pslr_inputs import generators as G
+    nd = len(dims)
+    d3 = tuple(dims) + (1,) * (3 - nd)
+    s3 = tuple(splits) + (1,) * (3 - nd)
+    sig, k = G.sigma_for_negative_count([G.laplacian_1d_eigs(d) for d in dims], K)
+    A = G.shifted_laplacian(dims, sig)
+    o = O.Oracle(A, dims=d3, splits=s3, factor=1)
+    D = dense_operators(o, 1)
+    assert np.linalg.eigvalsh(D["C0"]).min() > 0
+    Es = _columns(o.Es, o.q)
+    lam = np.linalg.eigvals(Es @ np.linalg.inv(D["C0"]))
+    assert np.abs(lam.imag).max() < 1e-9
+    neg_A = int((np.linalg.eigvalsh(G.dense_from_csr(A)) < 0).sum())
+    neg_B = int((np.linalg.eigvalsh(D["B"]) < 0).sum())
+    assert neg_A == k
+    above = int((lam.real > 1).sum())
+    assert above == neg_A - neg_B, (above, neg_A, neg_B)
+    assert np.abs(lam.real - 1).min() > 1e-8  # no eigenvalue at the boundary
+
+
 def test_proposition1_bound():
     """Proposition of Sec. 3.1 (Eq. 3.6): when ||C0^{-1}E_s|| < 1,
     ||S^{-1} - P_m|| <= ||C0^{-1}E_s||^{m+1} ||C0^{-1}|| / (1 - ||C0^{-1}E_s||)."""
