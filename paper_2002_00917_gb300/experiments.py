@@ -1,5 +1,5 @@
-"""The studies of Section 4.1 on the 50^3 shifted Laplacian, ILUT(1e-2) local
-factors, m = 3, through the library:
+"""The studies of Section 4.1 (the 50^3 shifted Laplacian and the meshes of
+Table 6), ILUT(1e-2) local factors, m = 3, through the library:
 
 * ``s``    - the number of subdomains (Table 1; r = 15, shift .05).  The
   geometric split stands in for METIS: 2x2x2, 4x2x2, 3x3x3, 3x3x4, 3x3x5 and
@@ -8,6 +8,9 @@ factors, m = 3, through the library:
 * ``m``    - the series order 0..5 (Table 2; 3x3x4, r = 15, shift .05).
 * ``rank`` - the rank 0, 15, ..., 75 (Tables 3 and 4; 3x3x4; shift .05 and
   .14 with ``--shift``).
+* ``lap``  - the meshes of Table 6 (32^3, 64^3, 128^3 at shifts .16, .08,
+  .03; m = 3, r = 15): 3x3x4 for the paper's s = 35 on the two smaller
+  meshes, 8x8x4 on 128^3 (35 parts of 128^3 do not fit one CTA each).
 
 Each run prints one JSON line: partition size, fill factors (Section 4's
 definitions), levels per sweep, and, unless ``--dry-run``, the FGMRES(127)
@@ -16,6 +19,7 @@ solve times on the current GPU.  ``--dry-run`` needs no GPU: it runs the
 host set-up only (``pslr.plan``) and reports the partition, fills and levels.
 
     python -m paper_2002_00917_gb300.experiments rank --shift 0.14
+    python -m paper_2002_00917_gb300.experiments lap --dry-run
 """
 from __future__ import annotations
 
@@ -26,28 +30,33 @@ import time
 from . import pslr
 
 DIMS = (50, 50, 50)
+LAP_MESHES = [(32, 0.16, (3, 3, 4)), (64, 0.08, (3, 3, 4)), (128, 0.03, (8, 8, 4))]
 S_SPLITS = [(2, 2, 2), (4, 2, 2), (3, 3, 3), (3, 3, 4), (3, 3, 5), (3, 3, 6)]
 PAPER_S = [5, 15, 25, 35, 45, 55]
 
 
 def runs(sweep, shift=None):
-    """(shift, splits, m, r) of every run of a sweep, in order."""
+    """(shift, splits, m, r) of every run of a sweep, in order; the ``lap``
+    runs add their mesh dimensions (the others use the 50^3 mesh)."""
     if sweep == "s":
         return [(0.05 if shift is None else shift, sp, 3, 15) for sp in S_SPLITS]
     if sweep == "m":
         return [(0.05 if shift is None else shift, (3, 3, 4), m, 15) for m in range(6)]
     if sweep == "rank":
         return [(0.05 if shift is None else shift, (3, 3, 4), 3, r) for r in range(0, 76, 15)]
+    if sweep == "lap":
+        return [(sh, sp, 3, 15, (N, N, N)) for N, sh, sp in LAP_MESHES]
     raise ValueError(f"unknown sweep {sweep!r}")
 
 
-def one(A, shift, splits, m, r, drop_tol=1e-2, restart=127, maxit=1500, dry_run=False, rhs_seed=0):
+def one(A, shift, splits, m, r, drop_tol=1e-2, restart=127, maxit=1500, dry_run=False, rhs_seed=0, dims=DIMS):
     """One run; returns its JSON record."""
-    rec = {"shift": shift, "splits": list(splits), "s": splits[0] * splits[1] * splits[2], "m": m, "r": r}
+    rec = {"shift": shift, "dims": list(dims), "splits": list(splits), "s": splits[0] * splits[1] * splits[2],
+           "m": m, "r": r}
     if dry_run:
-        info = pslr.plan(A, DIMS, splits, factor=2, m=m, rank=r, drop_tol=drop_tol)[0]
+        info = pslr.plan(A, dims, splits, factor=2, m=m, rank=r, drop_tol=drop_tol)[0]
         rec.update(q=info["q"], fill_ilu=round(info["fill_ilu"], 4), fill_lr=round(info["fill_lr"], 4),
-                   levels_B=info["levels_B"], levels_C0=info["levels_C0"])
+                   fill_total=round(info["fill_total"], 4), levels_B=info["levels_B"], levels_C0=info["levels_C0"])
         return rec
     import torch
 
@@ -57,7 +66,7 @@ def one(A, shift, splits, m, r, drop_tol=1e-2, restart=127, maxit=1500, dry_run=
     bd = torch.tensor(b, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctx = pslr.Pslr(A, dims=DIMS, splits=splits, factor=2, drop_tol=drop_tol)
+    ctx = pslr.Pslr(A, dims=dims, splits=splits, factor=2, drop_tol=drop_tol)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     try:
@@ -76,8 +85,10 @@ def one(A, shift, splits, m, r, drop_tol=1e-2, restart=127, maxit=1500, dry_run=
         torch.cuda.synchronize()
         t_solve = time.perf_counter() - t0
         info = ctx.info
-        rec.update(q=info["q"], fill_ilu=round(info["fill_ilu"], 4), fill_lr=round(ctx.get_info()["fill_lr"], 4),
-                   levels_B=info["levels_B"], levels_C0=info["levels_C0"], its=its, relres=rel,
+        full = ctx.get_info()
+        rec.update(q=info["q"], fill_ilu=round(info["fill_ilu"], 4), fill_lr=round(full["fill_lr"], 4),
+                   fill_total=round(full["fill_total"], 4), levels_B=info["levels_B"], levels_C0=info["levels_C0"],
+                   its=its, relres=rel,
                    converged=st == pslr.PSLR_OK, setup_s=round(t_setup, 4), lowrank_s=round(t_lr, 4),
                    solve_ms=round(1e3 * t_solve, 2))
     finally:
@@ -87,7 +98,7 @@ def one(A, shift, splits, m, r, drop_tol=1e-2, restart=127, maxit=1500, dry_run=
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("sweep", choices=["s", "m", "rank"])
+    ap.add_argument("sweep", choices=["s", "m", "rank", "lap"])
     ap.add_argument("--shift", type=float, default=None, help="shift of the Laplacian (default .05)")
     ap.add_argument("--drop-tol", type=float, default=1e-2)
     ap.add_argument("--restart", type=int, default=127)
@@ -96,11 +107,13 @@ def main(argv=None):
     from pslr_inputs import generators as G
 
     out = []
-    A = None
-    for shift, splits, m, r in runs(a.sweep, a.shift):
-        if A is None or A_shift != shift:
-            A, A_shift = G.shifted_laplacian(DIMS, shift), shift
-        rec = one(A, shift, splits, m, r, drop_tol=a.drop_tol, restart=a.restart, dry_run=a.dry_run)
+    A, key = None, None
+    for run in runs(a.sweep, a.shift):
+        shift, splits, m, r = run[:4]
+        dims = run[4] if len(run) > 4 else DIMS
+        if key != (dims, shift):
+            A, key = G.shifted_laplacian(dims, shift), (dims, shift)
+        rec = one(A, shift, splits, m, r, drop_tol=a.drop_tol, restart=a.restart, dry_run=a.dry_run, dims=dims)
         print(json.dumps(rec), flush=True)
         out.append(rec)
     return out
