@@ -105,6 +105,12 @@ typedef struct {
                               writing a row twice, a sweep row reading a row not
                               written at an earlier barrier step, a sweep missing
                               or repeating a row); 0 for a sound layout           */
+    int32_t grid[2];      /* launch shape of the persistent apply, [0] FP64, [1] FP32:
+                             CTAs of the cooperative grid (0 from pslr_plan)     */
+    int32_t ring[2];      /* shared-memory ring slots per CTA                       */
+    int32_t ctas_per_sm[2]; /* 1, or 2 when the FP32 form puts two subdomains' CTAs
+                               on one SM (more subdomains than SMs, and two CTAs'
+                               vectors and rings fit an SM's shared memory)       */
 } pslr_info;
 
 /*
@@ -236,10 +242,13 @@ pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info);
  * paper has no counterpart: this is an interface convenience.
  *
  * The call allocates nothing.  Its scratch (series iterates, accumulator,
- * partial sums, barrier and error words) is a 16 MiB array inside the
- * library, which every GPU that loads the library holds until the process
- * exits; it fits interface sizes up to q ~ 690,000 in FP64 (3*(q+1) + s*rank
- * values plus 256 bytes).  Larger contexts are rejected with
+ * partial sums, grid-barrier words) is a 16 MiB array inside the library,
+ * which every GPU that loads the library holds until the process exits; it
+ * fits interface sizes up to q ~ 690,000 in FP64 (3*(q+1) + s*rank values
+ * plus 256 bytes).  Device errors latch in the context's own error word, as
+ * for pslr_apply: pslr_sync reports them (a grid-barrier wait that gave up
+ * returns PSLR_ERR_TIMEOUT there), and until then later applies of the
+ * context do nothing.  Larger contexts are rejected with
  * PSLR_ERR_TOO_LARGE and a message.  The context, built by pslr_setup and
  * pslr_build_lowrank / pslr_set_lowrank beforehand, keeps everything else.
  * b_dev, z_dev: device vectors of n elements (double for PSLR_FP64, float for
@@ -250,7 +259,9 @@ pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info);
  * the GPU (different streams, or different contexts on concurrent streams)
  * race on the array: issue them in one stream or order them.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
+ * that device current; make that first call before any stream capture.  The
+ * library keeps that address for the rest of the process, so do not call
+ * this entry point again after a cudaDeviceReset of that device.
  */
 pslr_status pslr_apply_noalloc(pslr_ctx *c, const void *b_dev, void *z_dev, pslr_prec prec,
                                int32_t transpose, void *stream);

@@ -30,8 +30,12 @@ namespace pslr {
 
 // ------------------------------------------------------------------ the apply
 
-template <class T, class VT, class IO>
-__global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyParams<T, IO> P) {
+// MINB: CTAs per SM the instance is compiled for.  1 gives the kernel all the
+// registers it wants; 2 (FP32 forms, problems with more subdomains than SMs)
+// caps it so that two CTAs - two subdomains' level chains - share an SM and
+// hide each other's latencies instead of running one after the other.
+template <class T, class VT, class IO, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) pslr_apply_kernel(const ApplyParams<T, IO> P) {
     extern __shared__ __align__(128) char smem[];
     if (P.skip != nullptr && ld_volatile(P.skip) != 0) return;
     if (ld_volatile(P.err) != 0) return;
@@ -252,40 +256,46 @@ static cudaError_t launch_coop(K kern, const Prm &P, int grid, int smem, cudaStr
 }
 
 cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, cudaStream_t st) {
-    return launch_coop(pslr_apply_kernel<double, double, double>, P, P.grid, smem, st);
+    return launch_coop(pslr_apply_kernel<double, double, double, 1>, P, P.grid, smem, st);
 }
-cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, cudaStream_t st) {
-    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, float>, P, P.grid, smem, st);
+cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, bool dual, cudaStream_t st) {
+    if (dual) return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, float, 2>, P, P.grid, smem, st);
+    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, float, 1>, P, P.grid, smem, st);
 }
-cudaError_t launch_apply_f32d(const ApplyParams<float, double> &P, int smem, cudaStream_t st) {
-    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, double>, P, P.grid, smem, st);
+cudaError_t launch_apply_f32d(const ApplyParams<float, double> &P, int smem, bool dual, cudaStream_t st) {
+    if (dual) return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, double, 2>, P, P.grid, smem, st);
+    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, double, 1>, P, P.grid, smem, st);
 }
 cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, cudaStream_t st) {
     return launch_coop(pslr_err_kernel<double>, P, P.grid, smem, st);
 }
 
+template <class K>
+static cudaError_t blocks_per_sm(K kern, int smem, int *per) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, kern, kThreads, smem);
+    return e;
+}
+
 // Largest cooperative grid of the persistent kernels for a dynamic smem size
 // (the smallest occupancy of the kernels that launch with it: FP64 apply and
-// E_rr, or the two FP32 apply forms).
-int max_coresident_apply(int smem, bool fp32) {
-    int dev = 0, nsm = 0, per = 0, per2 = 1 << 30;
+// E_rr, or the two FP32 apply forms - their two-CTAs-per-SM instances when
+// dual is set).
+int max_coresident_apply(int smem, bool fp32, bool dual) {
+    int dev = 0, nsm = 0, per = 0, per2 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e;
-    if (fp32) {
-        auto k = pslr_apply_kernel<float, __nv_bfloat16, float>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreads, smem);
-        auto k2 = pslr_apply_kernel<float, __nv_bfloat16, double>;
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k2, kThreads, smem);
+    if (fp32 && dual) {
+        e = blocks_per_sm(pslr_apply_kernel<float, __nv_bfloat16, float, 2>, smem, &per);
+        if (e == cudaSuccess) e = blocks_per_sm(pslr_apply_kernel<float, __nv_bfloat16, double, 2>, smem, &per2);
+    } else if (fp32) {
+        e = blocks_per_sm(pslr_apply_kernel<float, __nv_bfloat16, float, 1>, smem, &per);
+        if (e == cudaSuccess) e = blocks_per_sm(pslr_apply_kernel<float, __nv_bfloat16, double, 1>, smem, &per2);
     } else {
-        auto k = pslr_apply_kernel<double, double, double>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreads, smem);
-        auto k2 = pslr_err_kernel<double>;
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k2, kThreads, smem);
+        if (dual) return 0;
+        e = blocks_per_sm(pslr_apply_kernel<double, double, double, 1>, smem, &per);
+        if (e == cudaSuccess) e = blocks_per_sm(pslr_err_kernel<double>, smem, &per2);
     }
     if (e != cudaSuccess) return 0;
     return (per < per2 ? per : per2) * nsm;

@@ -31,8 +31,8 @@
 namespace pslr {
 // kernels (pslr_apply.cu, pslr_krylov.cu)
 cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, cudaStream_t st);
-cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, cudaStream_t st);
-cudaError_t launch_apply_f32d(const ApplyParams<float, double> &P, int smem, cudaStream_t st);
+cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, bool dual, cudaStream_t st);
+cudaError_t launch_apply_f32d(const ApplyParams<float, double> &P, int smem, bool dual, cudaStream_t st);
 cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, cudaStream_t st);
 
 // The persistent kernels' launchers set the kernel's dynamic shared-memory
@@ -40,7 +40,7 @@ cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, cudaStream_t s
 // (the batched solve finishing problems on their systems) must not interleave
 // these two steps, or one launch can meet another context's smaller limit.
 static std::mutex g_launch_mutex;
-int max_coresident_apply(int smem, bool fp32);
+int max_coresident_apply(int smem, bool fp32, bool dual);
 int krylov_blocks(int n);
 size_t krylov_part_doubles(int nblk, int nres);
 int krylov_tickets();
@@ -513,6 +513,7 @@ struct OpSetHost {
     int64_t cat_bytes[kNCnt] = {0, 0, 0, 0, 0, 0, 0};  // segment bytes per category, all subdomains
     int smem = 0;
     int grid = 0;
+    bool dual = false;                   // two CTAs per SM (FP32 forms, more subdomains than SMs)
     std::map<std::string, StreamDev> streams;  // keyed by launch shape
 };
 
@@ -1213,11 +1214,37 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
     if (plan_only) return PSLR_OK;
     for (int prec = 0; prec < 2; ++prec) {
         int smem = std::max(c->ops[0][prec].smem, c->ops[1][prec].smem);
-        int cap = max_coresident_apply(smem, prec == 1);
+        int cap = max_coresident_apply(smem, prec == 1, false);
         if (cap <= 0) return bail(fail(c, PSLR_ERR_CUDA, "persistent kernel cannot be made resident"));
+        bool dual = false;
+        if (prec == 1 && s > cap) {
+            // More subdomains than resident CTAs: a CTA would sweep several
+            // subdomains one after the other.  If two CTAs fit an SM with a
+            // ring of kMinDualRing slots, use the two-CTAs-per-SM instances.
+            int dev = 0, per_sm = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+            const int avail = per_sm / 2 - 1024 - smem_fixed(c->max_p, c->max_q, 4, c->factor == 1);
+            int ring[2], smem2 = 0;
+            for (int dir = 0; dir < 2; ++dir) {
+                ring[dir] = std::min(kMaxRing, avail / c->ops[dir][prec].slot_bytes);
+                smem2 = std::max(smem2, smem_layout(c->ops[dir][prec].slot_bytes, ring[dir], c->max_p, c->max_q,
+                                                    4, c->factor == 1).total);
+            }
+            if (std::min(ring[0], ring[1]) >= kMinDualRing) {
+                const int cap2 = max_coresident_apply(smem2, true, true);
+                if (cap2 > cap) {
+                    dual = true;
+                    cap = cap2;
+                    smem = smem2;
+                    for (int dir = 0; dir < 2; ++dir) c->ops[dir][prec].ring = ring[dir];
+                }
+            }
+        }
         for (int dir = 0; dir < 2; ++dir) {
             c->ops[dir][prec].smem = smem;
             c->ops[dir][prec].grid = std::min(cap, s);
+            c->ops[dir][prec].dual = dual;
         }
     }
     CK(upload(&c->d_perm, c->perm));
@@ -1429,14 +1456,14 @@ static pslr_status apply_launch(pslr_ctx *c, const void *b, void *z, int form, i
         P.V = c->d_Vb;
         P.G = dir ? c->d_GTf : c->d_Gf;
         set_io(P, b, z, skip, scr);
-        e = launch_apply_fp32(P, o.smem, st);
+        e = launch_apply_fp32(P, o.smem, o.dual, st);
     } else {
         ApplyParams<float, double> P;
         fill_params(c, P, dir, prec, sd);
         P.V = c->d_Vb;
         P.G = dir ? c->d_GTf : c->d_Gf;
         set_io(P, b, z, skip, scr);
-        e = launch_apply_f32d(P, o.smem, st);
+        e = launch_apply_f32d(P, o.smem, o.dual, st);
     }
     if (e != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "apply launch: %s", cudaGetErrorString(e));
     return PSLR_OK;
@@ -1470,7 +1497,7 @@ pslr_status apply_with_scratch(pslr_ctx *c, const void *b, void *z, int prec, in
                                void *scratch, size_t scratch_bytes) {
     if (!c || !b || !z || !scratch || (prec != PSLR_FP64 && prec != PSLR_FP32))
         return fail(c, PSLR_ERR_ARG, "apply (no allocation): bad argument");
-    const size_t head = 256;  // barrier and error words
+    const size_t head = 256;  // grid-barrier words
     const size_t need = head + sizeof(double) * ((size_t)3 * (c->q + 1) + (size_t)c->s * c->r);
     if (need > scratch_bytes)
         return fail(c, PSLR_ERR_TOO_LARGE,
@@ -1480,12 +1507,16 @@ pslr_status apply_with_scratch(pslr_ctx *c, const void *b, void *z, int prec, in
     char *p = static_cast<char *>(scratch);
     ApplyScratch scr;
     scr.bar = reinterpret_cast<unsigned *>(p);
-    scr.err = reinterpret_cast<int *>(p + 16);
+    // the error word stays the context's own (allocated at set-up): pslr_sync
+    // reads and clears it, and a latched error stops later applies of this
+    // context, exactly as for pslr_apply
+    scr.err = c->d_err;
     scr.wbuf = p + head;
     scr.acc = p + head + sizeof(double) * 2 * (c->q + 1);
     scr.part = p + head + sizeof(double) * 3 * (c->q + 1);
-    // the shared array keeps the previous call's words: barrier and error start at zero
-    cudaError_t e = cudaMemsetAsync(p, 0, 32, st);
+    // the shared array keeps the previous call's words (a call that gave up
+    // leaves arrivals behind): the barrier starts at zero
+    cudaError_t e = cudaMemsetAsync(p, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     return apply_launch(c, b, z, prec, dir, nullptr, st, &scr, false);
 }
@@ -1618,6 +1649,11 @@ pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info) {
     I.setup_threads = c->threads;
     I.layout_hash = c->layout_hash;
     I.layout_errors = c->layout_errors;
+    for (int prec = 0; prec < 2; ++prec) {
+        I.grid[prec] = c->ops[0][prec].grid;
+        I.ring[prec] = c->ops[0][prec].ring;
+        I.ctas_per_sm[prec] = c->ops[0][prec].dual ? 2 : 1;
+    }
     *info = I;
     return PSLR_OK;
 }

@@ -39,6 +39,7 @@ constexpr int kThreads = kConsumers + 32;   // + one producer warp
 constexpr int kSegMaxRows = kConsumers;     // rows per segment
 constexpr int kSegBudget = 12 * 1024;       // bytes per segment (one ring slot at most)
 constexpr int kMaxRing = 32;                // ring slots at most
+constexpr int kMinDualRing = 4;             // ring slots at least when two CTAs share an SM
 constexpr int kMaxRank = 128;               // largest low-rank term
 
 enum SegFlags : uint32_t { kSegDiag = 1u, kSegGlobalCols = 2u };

@@ -13,6 +13,7 @@
 // library holds until the process exits.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "pslr.h"
@@ -33,10 +34,14 @@ constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // Device address of the array, looked up once per device (with that device
-// current).  In host code the array's name is only a host-side stand-in: a
-// kernel given &g_noalloc_scratch would address the wrong memory.
+// current) and kept for the life of the process.  In host code the array's
+// name is only a host-side stand-in: a kernel given &g_noalloc_scratch would
+// address the wrong memory.  The lookup takes the lock only to fill an empty
+// entry; later calls read the entry without it.  A cudaDeviceReset ends the
+// context the address belongs to, so the cached address must not be used
+// across one (documented in the header).
 constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {};
+std::atomic<void *> g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_lock;
 
 cudaError_t scratch_of_current_device(void **out) {
@@ -44,14 +49,17 @@ cudaError_t scratch_of_current_device(void **out) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_lock);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+    void *p = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lock(g_scratch_lock);
+        p = g_scratch_addr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return e;
+            g_scratch_addr[dev].store(p, std::memory_order_release);
+        }
     }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

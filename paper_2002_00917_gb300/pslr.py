@@ -47,10 +47,14 @@ class pslr_info(C.Structure):
                 ("fill_total", C.c_double), ("max_interior", C.c_int32),
                 ("max_interface", C.c_int32), ("levels_B", C.c_int32), ("levels_C0", C.c_int32),
                 ("apply_bytes_fp64", C.c_int64), ("apply_bytes_fp32", C.c_int64),
-                ("layout_hash", C.c_uint64), ("setup_threads", C.c_int32), ("layout_errors", C.c_int64)]
+                ("layout_hash", C.c_uint64), ("setup_threads", C.c_int32), ("layout_errors", C.c_int64),
+                ("grid", C.c_int32 * 2), ("ring", C.c_int32 * 2), ("ctas_per_sm", C.c_int32 * 2)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        for k in ("grid", "ring", "ctas_per_sm"):
+            d[k] = list(getattr(self, k))
+        return d
 
 
 class pslr_batch_info(C.Structure):
