@@ -30,17 +30,13 @@ namespace pslr {
 
 // ------------------------------------------------------------------ the apply
 
-// MINB: CTAs per SM the instance is compiled for.  1 gives the kernel all the
-// registers it wants; 2 (FP32 forms, problems with more subdomains than SMs)
-// caps it so that two CTAs - two subdomains' level chains - share an SM and
-// hide each other's latencies instead of running one after the other.
-template <class T, class VT, class IO, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) pslr_apply_kernel(const ApplyParams<T, IO> P) {
+template <class T, class VT, class IO>
+__device__ __forceinline__ void apply_body(const ApplyParams<T, IO> &P) {
     extern __shared__ __align__(128) char smem[];
     if (P.skip != nullptr && ld_volatile(P.skip) != 0) return;
     if (ld_volatile(P.err) != 0) return;
     const bool pivots = P.bpiv != nullptr;
-    const SmemLayout L = smem_layout(P.slot_bytes, P.ring, P.max_p, P.max_q, sizeof(T), pivots);
+    const SmemLayout L = smem_layout(P.slot_bytes, P.ring, P.max_p, P.max_q, sizeof(T), pivots, P.rs, true);
     Cta<T> c;
     if (!cta_start(c, smem, L, P.ring, P.slot_bytes, P.stream, P.stream_off, P.segbase)) return;
 
@@ -64,7 +60,7 @@ __global__ void __launch_bounds__(kThreads, MINB) pslr_apply_kernel(const ApplyP
         solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2], P.err);
         ell_op<T, false>(c, c.si, c.xi, true, k.n[kF], P.err);
         if (lr_before) {
-            lowrank_partial(c, V, P.ldv, r, go, nq, c.si, P.part + (int64_t)i * r);
+            lowrank_partial(c, V, P.ldv, r, go, nq, c.si, P.part + (int64_t)i * r, 1, P.rs);
             for (int j = tid; j < nq; j += kConsumers) P.acc[go + j] = c.si[j];
         } else {
             if (tid == 0) c.si[nq] = T(0);
@@ -87,14 +83,14 @@ __global__ void __launch_bounds__(kThreads, MINB) pslr_apply_kernel(const ApplyP
         grid_arrive(c, P.bar, P.grid);
         ok = grid_wait(c, P.bar, P.err, P.wait_limit);
         if (!ok) goto abort;
-        lowrank_coeffs(c, P.part, P.G, P.s, r);
+        lowrank_coeffs(c, P.part, P.G, P.s, r, P.rs);
         for (int i = blockIdx.x; i < P.s; i += gridDim.x) {
             const Counts k = counts_of(P.cnt, i);
             const int go = P.goff[i], nq = P.goff[i + 1] - go;
             for (int j = tid; j < nq; j += kConsumers) c.si[j] = __ldcg(P.acc + go + j);
             if (tid == 0) c.si[nq] = T(0);
             csync();
-            lowrank_update(c, V, P.ldv, r, go, nq, c.si);
+            lowrank_update(c, V, P.ldv, r, go, nq, c.si, 1, P.rs);
             solve_local(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1], k.n[kC2], P.err);
             for (int j = tid; j < nq; j += kConsumers) {
                 P.wbuf[go + j] = c.si[j];
@@ -150,12 +146,12 @@ __global__ void __launch_bounds__(kThreads, MINB) pslr_apply_kernel(const ApplyP
             const int go = P.goff[i], nq = P.goff[i + 1] - go;
             for (int j = tid; j < nq; j += kConsumers) c.si[j] = __ldcg(P.acc + go + j);
             csync();
-            lowrank_partial(c, V, P.ldv, r, go, nq, c.si, P.part + (int64_t)i * r);
+            lowrank_partial(c, V, P.ldv, r, go, nq, c.si, P.part + (int64_t)i * r, 1, P.rs);
         }
         grid_arrive(c, P.bar, P.grid);
         ok = grid_wait(c, P.bar, P.err, P.wait_limit);
         if (!ok) goto abort;
-        lowrank_coeffs(c, P.part, P.G, P.s, r);
+        lowrank_coeffs(c, P.part, P.G, P.s, r, P.rs);
     }
 
     // ---- y = acc; x = B^{-1}(f - E y); scatter (steps 5-6)
@@ -168,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, MINB) pslr_apply_kernel(const ApplyP
         for (int j = tid; j < np_; j += kConsumers) c.xi[j] = T(P.b[P.perm[io + j]]);
         if (tid == 0) c.xi[np_] = T(0);
         csync();
-        if (lr_after) lowrank_update(c, V, P.ldv, r, go, nq, c.wi);
+        if (lr_after) lowrank_update(c, V, P.ldv, r, go, nq, c.wi, 1, P.rs);
         ell_op<T, false>(c, c.xi, c.wi, true, k.n[kE], P.err);
         solve_local(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2], P.err);
         for (int j = tid; j < np_; j += kConsumers) P.z[P.perm[io + j]] = IO(c.xi[j]);
@@ -180,14 +176,30 @@ abort:
     consumers_abort_drain(c);
 }
 
+// Two instances of each persistent kernel: one CTA per SM with all the
+// registers it wants, and (suffix _x2) an instance of which two CTAs fit an
+// SM, for problems with more subdomains than SMs: two subdomains' level
+// chains then share an SM and hide each other's latencies instead of one CTA
+// sweeping them one after the other.  Two CTAs are 18 warps, so one SM
+// sub-partition holds five of them in its 16K registers: at most 96 registers
+// per thread, which is what the launch bound asks the compiler for.
+template <class T, class VT, class IO>
+__global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyParams<T, IO> P) {
+    apply_body<T, VT, IO>(P);
+}
+template <class T, class VT, class IO>
+__global__ void __launch_bounds__(kThreads, 2) pslr_apply_kernel_x2(const ApplyParams<T, IO> P) {
+    apply_body<T, VT, IO>(P);
+}
+
 // ------------------------------------------------------------ E_rr(m) matvec
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, 1) pslr_err_kernel(const ErrParams<T> P) {
+__device__ __forceinline__ void err_body(const ErrParams<T> &P) {
     extern __shared__ __align__(128) char smem[];
     if (ld_volatile(P.err) != 0) return;
     const bool pivots = P.bpiv != nullptr;
-    const SmemLayout L = smem_layout(P.slot_bytes, P.ring, P.max_p, P.max_q, sizeof(T), pivots);
+    const SmemLayout L = smem_layout(P.slot_bytes, P.ring, P.max_p, P.max_q, sizeof(T), pivots, P.rs, true);
     Cta<T> c;
     if (!cta_start(c, smem, L, P.ring, P.slot_bytes, P.stream, P.stream_off, P.segbase)) return;
     const int q = P.q, tid = threadIdx.x;
@@ -245,6 +257,15 @@ abort:
     consumers_abort_drain(c);
 }
 
+template <class T>
+__global__ void __launch_bounds__(kThreads, 1) pslr_err_kernel(const ErrParams<T> P) {
+    err_body<T>(P);
+}
+template <class T>
+__global__ void __launch_bounds__(kThreads, 2) pslr_err_kernel_x2(const ErrParams<T> P) {
+    err_body<T>(P);
+}
+
 // ------------------------------------------------------------- host launchers
 
 template <class K, class Prm>
@@ -255,18 +276,20 @@ static cudaError_t launch_coop(K kern, const Prm &P, int grid, int smem, cudaStr
     return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kThreads), args, smem, st);
 }
 
-cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, cudaStream_t st) {
-    return launch_coop(pslr_apply_kernel<double, double, double, 1>, P, P.grid, smem, st);
+cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, bool dual, cudaStream_t st) {
+    if (dual) return launch_coop(pslr_apply_kernel_x2<double, double, double>, P, P.grid, smem, st);
+    return launch_coop(pslr_apply_kernel<double, double, double>, P, P.grid, smem, st);
 }
 cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, bool dual, cudaStream_t st) {
-    if (dual) return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, float, 2>, P, P.grid, smem, st);
-    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, float, 1>, P, P.grid, smem, st);
+    if (dual) return launch_coop(pslr_apply_kernel_x2<float, __nv_bfloat16, float>, P, P.grid, smem, st);
+    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, float>, P, P.grid, smem, st);
 }
 cudaError_t launch_apply_f32d(const ApplyParams<float, double> &P, int smem, bool dual, cudaStream_t st) {
-    if (dual) return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, double, 2>, P, P.grid, smem, st);
-    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, double, 1>, P, P.grid, smem, st);
+    if (dual) return launch_coop(pslr_apply_kernel_x2<float, __nv_bfloat16, double>, P, P.grid, smem, st);
+    return launch_coop(pslr_apply_kernel<float, __nv_bfloat16, double>, P, P.grid, smem, st);
 }
-cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, cudaStream_t st) {
+cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, bool dual, cudaStream_t st) {
+    if (dual) return launch_coop(pslr_err_kernel_x2<double>, P, P.grid, smem, st);
     return launch_coop(pslr_err_kernel<double>, P, P.grid, smem, st);
 }
 
@@ -287,14 +310,16 @@ int max_coresident_apply(int smem, bool fp32, bool dual) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e;
     if (fp32 && dual) {
-        e = blocks_per_sm(pslr_apply_kernel<float, __nv_bfloat16, float, 2>, smem, &per);
-        if (e == cudaSuccess) e = blocks_per_sm(pslr_apply_kernel<float, __nv_bfloat16, double, 2>, smem, &per2);
+        e = blocks_per_sm(pslr_apply_kernel_x2<float, __nv_bfloat16, float>, smem, &per);
+        if (e == cudaSuccess) e = blocks_per_sm(pslr_apply_kernel_x2<float, __nv_bfloat16, double>, smem, &per2);
     } else if (fp32) {
-        e = blocks_per_sm(pslr_apply_kernel<float, __nv_bfloat16, float, 1>, smem, &per);
-        if (e == cudaSuccess) e = blocks_per_sm(pslr_apply_kernel<float, __nv_bfloat16, double, 1>, smem, &per2);
+        e = blocks_per_sm(pslr_apply_kernel<float, __nv_bfloat16, float>, smem, &per);
+        if (e == cudaSuccess) e = blocks_per_sm(pslr_apply_kernel<float, __nv_bfloat16, double>, smem, &per2);
+    } else if (dual) {
+        e = blocks_per_sm(pslr_apply_kernel_x2<double, double, double>, smem, &per);
+        if (e == cudaSuccess) e = blocks_per_sm(pslr_err_kernel_x2<double>, smem, &per2);
     } else {
-        if (dual) return 0;
-        e = blocks_per_sm(pslr_apply_kernel<double, double, double, 1>, smem, &per);
+        e = blocks_per_sm(pslr_apply_kernel<double, double, double>, smem, &per);
         if (e == cudaSuccess) e = blocks_per_sm(pslr_err_kernel<double>, smem, &per2);
     }
     if (e != cudaSuccess) return 0;

@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
     if (!cta_start(c, smem, L, P.ring, P.slot_bytes, P.stream, P.stream_off, P.segbase, P.active)) return;
     const int tid = threadIdx.x;
     const int gb = P.group_off[blockIdx.x], ge = P.group_off[blockIdx.x + 1];
-    T *const dsh = c.red + (kConsumers / 32) * kMaxRank + kMaxRank;  // where lowrank_coeffs leaves d
+    T *const dsh = c.red + red_u_off(kMaxRank) + kMaxRank;  // where lowrank_coeffs leaves d
     bool ok = true;
 
     // ---- phase 0: u = B^{-1} f, t = g - F u (Algorithm 3, step 2); a system
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
             if (S.r > 0)
                 for (int kr = 0; kr < nr; ++kr)
                     lowrank_partial(c, V, S.ldv, S.r, it.go, it.nq, y + kr, S.part + ((int64_t)kr * S.s + it.i) * S.r,
-                                    nr);
+                                    nr, kMaxRank);
             for (int j = tid; j < it.nq; j += kConsumers)
                 for (int kr = 0; kr < nr; ++kr) {
                     const T v = y[j * nr + kr];
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
             if (!on(P, P.pairs[2 * pi])) continue;
             const BatchSys<T> &S = P.sys[P.pairs[2 * pi]];
             const int kr = P.pairs[2 * pi + 1];
-            lowrank_coeffs(c, S.part + (int64_t)kr * S.s * S.r, S.G, S.s, S.r);
+            lowrank_coeffs(c, S.part + (int64_t)kr * S.s * S.r, S.G, S.s, S.r, kMaxRank);
             for (int j = tid; j < S.r; j += kConsumers) S.dco[(int64_t)kr * S.r + j] = dsh[j];
             csync();
         }
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
                 csync();
                 for (int t = 0; t < g.n; ++t) {
                     const ItemRange it = item_range(S, g, t);
-                    lowrank_update(c, V, S.ldv, S.r, it.go, it.nq, c.si + it.lo * nr + kr, nr);
+                    lowrank_update(c, V, S.ldv, S.r, it.go, it.nq, c.si + it.lo * nr + kr, nr, kMaxRank);
                 }
             }
             tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC1], P.err);

@@ -758,12 +758,12 @@ __device__ __forceinline__ Counts counts_of(const int32_t *cnt, int i) {
 }
 
 // Partial dots part[i*r + c] = sum_j V[go + j, c] * y[j * ys] over this
-// subdomain.  V is row-major with row stride ldv (a multiple of 8, zero
+// subdomain (c.red holds the 8 warps' sums at column stride rs >= r).  V is row-major with row stride ldv (a multiple of 8, zero
 // padded), so a thread reads eight columns of a row with vector loads; rows
 // are taken four at a time so that many loads are in flight.
 template <class T, class VT>
 __device__ void lowrank_partial(Cta<T> &c, const VT *V, int ldv, int r, int go, int nq, const T *y,
-                                T *part_i, int ys = 1) {
+                                T *part_i, int ys, int rs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const VT *Vs = V + (int64_t)go * ldv;
     for (int c0 = 0; c0 < r; c0 += 8) {
@@ -779,12 +779,12 @@ __device__ void lowrank_partial(Cta<T> &c, const VT *V, int ldv, int r, int go, 
             for (int k = 0; k < 8; ++k) a[k] = fma_t(v[k], yj, a[k]);
         }
         const T v = warp_reduce8(a);
-        if ((lane & 3) == 0 && c0 + (lane >> 2) < r) c.red[warp * kMaxRank + c0 + (lane >> 2)] = v;
+        if ((lane & 3) == 0 && c0 + (lane >> 2) < r) c.red[warp * rs + c0 + (lane >> 2)] = v;
     }
     csync();
     for (int col = threadIdx.x; col < r; col += kConsumers) {
         T a = T(0);
-        for (int w = 0; w < kConsumers / 32; ++w) a += c.red[w * kMaxRank + col];
+        for (int w = 0; w < kConsumers / 32; ++w) a += c.red[w * rs + col];
         part_i[col] = a;
     }
     csync();
@@ -794,9 +794,9 @@ __device__ void lowrank_partial(Cta<T> &c, const VT *V, int ldv, int r, int go, 
 // c.red.  Threads split as (column, group of subdomains); the group sums are
 // combined in a fixed order, so every CTA computes the same d.
 template <class T>
-__device__ void lowrank_coeffs(Cta<T> &c, const T *part, const T *G, int s, int r) {
-    T *u = c.red + (kConsumers / 32) * kMaxRank;
-    T *d = u + kMaxRank;
+__device__ void lowrank_coeffs(Cta<T> &c, const T *part, const T *G, int s, int r, int rs) {
+    T *u = c.red + red_u_off(rs);
+    T *d = u + rs;
     const int tpc = kConsumers / r;  // groups per column (r <= kMaxRank <= kConsumers)
     const int col = threadIdx.x % r, grp = threadIdx.x / r;
     if (grp < tpc) {
@@ -823,8 +823,8 @@ __device__ void lowrank_coeffs(Cta<T> &c, const T *part, const T *G, int s, int 
 // y[j * ys] += sum_c V[go + j, c] d[c] (V row-major with row stride ldv, as
 // in lowrank_partial; entries of d past r are not read).
 template <class T, class VT>
-__device__ void lowrank_update(Cta<T> &c, const VT *V, int ldv, int r, int go, int nq, T *y, int ys = 1) {
-    const T *d = c.red + (kConsumers / 32) * kMaxRank + kMaxRank;
+__device__ void lowrank_update(Cta<T> &c, const VT *V, int ldv, int r, int go, int nq, T *y, int ys, int rs) {
+    const T *d = c.red + red_u_off(rs) + rs;
     const VT *Vs = V + (int64_t)go * ldv;
 #pragma unroll 2
     for (int j = threadIdx.x; j < nq; j += kConsumers) {

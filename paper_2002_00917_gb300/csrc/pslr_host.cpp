@@ -30,10 +30,10 @@
 
 namespace pslr {
 // kernels (pslr_apply.cu, pslr_krylov.cu)
-cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, cudaStream_t st);
+cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, bool dual, cudaStream_t st);
 cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, bool dual, cudaStream_t st);
 cudaError_t launch_apply_f32d(const ApplyParams<float, double> &P, int smem, bool dual, cudaStream_t st);
-cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, cudaStream_t st);
+cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, bool dual, cudaStream_t st);
 
 // The persistent kernels' launchers set the kernel's dynamic shared-memory
 // limit and then launch; contexts applied from several host threads at once
@@ -527,6 +527,7 @@ struct KWork {
 
 struct pslr_ctx {
     int n = 0, s = 0, p = 0, q = 0, factor = 0;
+    int rs = 8;              // column stride of the kernels' low-rank scratch (red_stride(r))
     double drop_tol = 0.0;  // ILUT threshold (factor 2)
     uint64_t seed = 0;
     std::vector<int32_t> part, iface, perm, ioff, goff;
@@ -902,14 +903,16 @@ static pslr_status finish_opset(pslr_ctx *c, OpSetHost &o, SegStore &S, const st
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     }
-    // ring depth: as many slots as fit next to the vectors, 2 .. kMaxRing
-    const int avail = optin - 1024 - smem_fixed(c->max_p, c->max_q, fp32 ? 4 : 8, piv);
+    // ring depth: as many slots as fit next to the vectors, 2 .. kMaxRing; checked
+    // here for the largest rank, so that every later low-rank term fits (the
+    // launch shape itself is chosen by plan_launch for the current rank)
+    const int avail = optin - 1024 - smem_fixed(c->max_p, c->max_q, fp32 ? 4 : 8, piv, kMaxRank, true);
     o.ring = std::min(kMaxRing, avail / o.slot_bytes);
     if (o.ring < 2)
         return fail(c, PSLR_ERR_TOO_LARGE,
                     "a subdomain needs more shared memory than one CTA has (%d interior, %d interface "
                     "unknowns): use more subdomains", c->max_p, c->max_q);
-    o.smem = smem_layout(o.slot_bytes, o.ring, c->max_p, c->max_q, fp32 ? 4 : 8, piv).total;
+    o.smem = smem_layout(o.slot_bytes, o.ring, c->max_p, c->max_q, fp32 ? 4 : 8, piv, kMaxRank, true).total;
     o.grid = 0;
     return PSLR_OK;
 }
@@ -956,6 +959,75 @@ void pslr_destroy(pslr_ctx *c) {
 }  // extern "C"
 
 static pslr_status prebuild_streams(pslr_ctx *c);
+
+// Launch shape of the persistent kernels for the current rank: per precision
+// the ring depth, dynamic shared memory, cooperative grid and CTAs per SM
+// (both directions share one shape).  One CTA per SM takes the deepest ring
+// that fits; when the subdomains outnumber the resident CTAs and two CTAs fit
+// an SM with at least kMinDualRing slots each, the two-CTAs-per-SM instances
+// run instead, so that no CTA sweeps two subdomains in sequence.  The
+// low-rank scratch is sized for the current rank (red_stride), so the shape is
+// planned again whenever the low-rank term changes; segment streams built for
+// another grid are dropped.
+static pslr_status plan_launch(pslr_ctx *c) {
+    int dev = 0, optin = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    CK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    const int rs = red_stride(c->r);
+    const bool piv = c->factor == 1;
+    for (int prec = 0; prec < 2; ++prec) {
+        const int ts = prec == 0 ? 8 : 4;
+        auto shape = [&](int budget, int *ring, int *smem) {
+            const int avail = budget - 1024 - smem_fixed(c->max_p, c->max_q, ts, piv, rs, true);
+            *smem = 0;
+            for (int dir = 0; dir < 2; ++dir) {
+                ring[dir] = std::min(kMaxRing, avail / c->ops[dir][prec].slot_bytes);
+                *smem = std::max(*smem, smem_layout(c->ops[dir][prec].slot_bytes, ring[dir], c->max_p, c->max_q,
+                                                    ts, piv, rs, true).total);
+            }
+        };
+        int ring[2], smem = 0;
+        shape(optin, ring, &smem);
+        if (std::min(ring[0], ring[1]) < 2)
+            return fail(c, PSLR_ERR_TOO_LARGE, "a subdomain needs more shared memory than one CTA has");
+        int cap = max_coresident_apply(smem, prec == 1, false);
+        if (cap <= 0) return fail(c, PSLR_ERR_CUDA, "persistent kernel cannot be made resident");
+        bool dual = false;
+        if (c->s > cap) {
+            int ring2[2], smem2 = 0;
+            shape(per_sm / 2, ring2, &smem2);
+            if (std::min(ring2[0], ring2[1]) >= kMinDualRing) {
+                const int cap2 = max_coresident_apply(smem2, prec == 1, true);
+                if (cap2 > cap) {
+                    dual = true;
+                    cap = cap2;
+                    smem = smem2;
+                    ring[0] = ring2[0];
+                    ring[1] = ring2[1];
+                }
+            }
+        }
+        const int grid = std::min(cap, c->s);
+        for (int dir = 0; dir < 2; ++dir) {
+            OpSetHost &o = c->ops[dir][prec];
+            if (o.grid != grid) {  // streams partition the subdomains over the grid
+                for (auto &kv : o.streams) {
+                    cfree(kv.second.ent);
+                    cfree(kv.second.off);
+                }
+                o.streams.clear();
+            }
+            o.ring = ring[dir];
+            o.smem = smem;
+            o.grid = grid;
+            o.dual = dual;
+        }
+    }
+    c->rs = rs;
+    drop_graphs(c);
+    return PSLR_OK;
+}
 
 // Everything pslr_setup does; with plan_only the device is never touched (no
 // uploads, no allocations), which pslr_plan uses.
@@ -1212,40 +1284,9 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
             }
         }
     if (plan_only) return PSLR_OK;
-    for (int prec = 0; prec < 2; ++prec) {
-        int smem = std::max(c->ops[0][prec].smem, c->ops[1][prec].smem);
-        int cap = max_coresident_apply(smem, prec == 1, false);
-        if (cap <= 0) return bail(fail(c, PSLR_ERR_CUDA, "persistent kernel cannot be made resident"));
-        bool dual = false;
-        if (prec == 1 && s > cap) {
-            // More subdomains than resident CTAs: a CTA would sweep several
-            // subdomains one after the other.  If two CTAs fit an SM with a
-            // ring of kMinDualRing slots, use the two-CTAs-per-SM instances.
-            int dev = 0, per_sm = 0;
-            CK(cudaGetDevice(&dev));
-            CK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-            const int avail = per_sm / 2 - 1024 - smem_fixed(c->max_p, c->max_q, 4, c->factor == 1);
-            int ring[2], smem2 = 0;
-            for (int dir = 0; dir < 2; ++dir) {
-                ring[dir] = std::min(kMaxRing, avail / c->ops[dir][prec].slot_bytes);
-                smem2 = std::max(smem2, smem_layout(c->ops[dir][prec].slot_bytes, ring[dir], c->max_p, c->max_q,
-                                                    4, c->factor == 1).total);
-            }
-            if (std::min(ring[0], ring[1]) >= kMinDualRing) {
-                const int cap2 = max_coresident_apply(smem2, true, true);
-                if (cap2 > cap) {
-                    dual = true;
-                    cap = cap2;
-                    smem = smem2;
-                    for (int dir = 0; dir < 2; ++dir) c->ops[dir][prec].ring = ring[dir];
-                }
-            }
-        }
-        for (int dir = 0; dir < 2; ++dir) {
-            c->ops[dir][prec].smem = smem;
-            c->ops[dir][prec].grid = std::min(cap, s);
-            c->ops[dir][prec].dual = dual;
-        }
+    {
+        pslr_status ps = plan_launch(c);
+        if (ps != PSLR_OK) return bail(ps);
     }
     CK(upload(&c->d_perm, c->perm));
     CK(upload(&c->d_ioff, c->ioff));
@@ -1393,6 +1434,7 @@ static void fill_params(pslr_ctx *c, ApplyParams<T, IO> &P, int dir, int prec, c
     P.err = c->d_err;
     P.skip = nullptr;
     P.wait_limit = c->wait_limit;
+    P.rs = c->rs;
 }
 
 // Scratch of one apply launch: series iterates (2(q+1)), accumulator (q+1),
@@ -1449,7 +1491,7 @@ static pslr_status apply_launch(pslr_ctx *c, const void *b, void *z, int form, i
         P.V = c->d_Vr;
         P.G = dir ? c->d_GT : c->d_G;
         set_io(P, b, z, skip, scr);
-        e = launch_apply_fp64(P, o.smem, st);
+        e = launch_apply_fp64(P, o.smem, o.dual, st);
     } else if (form == PSLR_FP32) {
         ApplyParams<float> P;
         fill_params(c, P, dir, prec, sd);
@@ -1756,6 +1798,10 @@ static pslr_status install_lowrank(pslr_ctx *c, int m, int r, const std::vector<
     cudaFree(c->d_part);
     c->d_Vr = nullptr; c->d_Vb = nullptr; c->d_G = c->d_GT = nullptr; c->d_Gf = c->d_GTf = nullptr; c->d_part = nullptr;
     c->ldv = 0;
+    {
+        pslr_status ps = plan_launch(c);
+        if (ps != PSLR_OK) return ps;
+    }
     if (r == 0) return prebuild_streams(c);
     c->V.resize((size_t)q * r);
     CK(cudaMemcpy(c->V.data(), c->d_V, sizeof(double) * (size_t)q * r, cudaMemcpyDeviceToHost));
@@ -1875,10 +1921,11 @@ static pslr_status launch_err(pslr_ctx *c, const double *vin, double *vout, int 
     P.bar = c->d_bar;
     P.err = c->d_err;
     P.wait_limit = c->wait_limit;
+    P.rs = c->rs;
     cudaError_t e;
     {
         std::lock_guard<std::mutex> lock(g_launch_mutex);
-        e = launch_err_fp64(P, o.smem, st);
+        e = launch_err_fp64(P, o.smem, o.dual, st);
     }
     if (e != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "E_rr launch: %s", cudaGetErrorString(e));
     return PSLR_OK;

@@ -39,7 +39,7 @@ constexpr int kThreads = kConsumers + 32;   // + one producer warp
 constexpr int kSegMaxRows = kConsumers;     // rows per segment
 constexpr int kSegBudget = 12 * 1024;       // bytes per segment (one ring slot at most)
 constexpr int kMaxRing = 32;                // ring slots at most
-constexpr int kMinDualRing = 4;             // ring slots at least when two CTAs share an SM
+constexpr int kMinDualRing = 3;             // ring slots at least when two CTAs share an SM
 constexpr int kMaxRank = 128;               // largest low-rank term
 
 enum SegFlags : uint32_t { kSegDiag = 1u, kSegGlobalCols = 2u };
@@ -127,6 +127,7 @@ struct ApplyParams {
     int *err;                    // latched error (pslr_status)
     const int *skip;             // when *skip != 0 the launch does nothing (converged FGMRES cycle)
     long long wait_limit;        // polls before a grid-barrier wait gives up
+    int rs;                      // column stride of the low-rank reduction scratch (red_stride(r))
 };
 
 // E_rr(m) v for the Arnoldi process (Eq. 3.19): v <- (E_s C0^{-1})^{m+1} v.
@@ -147,6 +148,7 @@ struct ErrParams {
     unsigned *bar;
     int *err;
     long long wait_limit;
+    int rs;                      // as in ApplyParams (the layout must match the apply's)
 };
 
 // Batched apply (pslr_batch.cuh): per-system parameters and launch parameters.
@@ -256,19 +258,33 @@ struct SmemLayout {
 
 PSLR_HD inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-// Bytes of everything but the ring.
-PSLR_HD inline int smem_fixed(int max_p, int max_q, int tsize, bool pivots) {
+// Low-rank reduction scratch (8-byte entries) for a column stride rs >= rank:
+// 8 warps' partial sums of rs columns (or the kConsumers group sums of
+// lowrank_coeffs, whichever is larger), then u and d of rs entries each.
+PSLR_HD inline int red_u_off(int rs) { return 8 * rs > kConsumers ? 8 * rs : kConsumers; }
+PSLR_HD inline int red_bytes(int rs) { return align_up((red_u_off(rs) + 2 * rs) * 8, 128); }
+
+// Column stride of the reduction scratch for a rank r (kMaxRank for the
+// batched kernel, whose ranks differ per system).
+PSLR_HD inline int red_stride(int r) { return r < 8 ? 8 : (r + 7) / 8 * 8; }
+
+// alias_w: the interface vectors wi and si share one buffer.  The
+// single-system apply and E_rr kernels never hold both at once (wi only feeds
+// the E product that starts a series term, or the last phase, where si is
+// unused); the batched kernel does, and keeps them apart.
+PSLR_HD inline int smem_fixed(int max_p, int max_q, int tsize, bool pivots, int rs = kMaxRank,
+                              bool alias_w = false) {
     int o = 2 * align_up(kMaxRing * 8, 16) + 128;
     o = align_up(o, 128);
     o += align_up((max_p + 1) * tsize, 128);
-    o += 2 * align_up((max_q + 1) * tsize, 128);
+    o += (alias_w ? 1 : 2) * align_up((max_q + 1) * tsize, 128);
     o += pivots ? align_up(((max_p > max_q ? max_p : max_q) + 1) * tsize, 128) : 0;
-    o += align_up((kConsumers / 32 + 2) * kMaxRank * 8, 128);
+    o += red_bytes(rs);
     return o;
 }
 
 PSLR_HD inline SmemLayout smem_layout(int slot_bytes, int ring, int max_p, int max_q, int tsize,
-                                      bool pivots) {
+                                      bool pivots, int rs = kMaxRank, bool alias_w = false) {
     SmemLayout L;
     int o = 0;
     L.ring = o;  o += ring * slot_bytes;
@@ -277,10 +293,10 @@ PSLR_HD inline SmemLayout smem_layout(int slot_bytes, int ring, int max_p, int m
     L.ctl = o;   o += 128;
     o = align_up(o, 128);
     L.xi = o;    o += align_up((max_p + 1) * tsize, 128);
-    L.wi = o;    o += align_up((max_q + 1) * tsize, 128);
+    L.wi = o;    o += alias_w ? 0 : align_up((max_q + 1) * tsize, 128);
     L.si = o;    o += align_up((max_q + 1) * tsize, 128);
     L.tmp = o;   o += pivots ? align_up(((max_p > max_q ? max_p : max_q) + 1) * tsize, 128) : 0;
-    L.red = o;   o += align_up((kConsumers / 32 + 2) * kMaxRank * 8, 128);
+    L.red = o;   o += red_bytes(rs);
     L.total = o;
     return L;
 }
