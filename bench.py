@@ -2,15 +2,26 @@
 
 One step = one PSLR preconditioner apply (Algorithm 3) of the workload through
 the C ABI, with the input resident in HBM.  The metric is the apply's
-algorithmic bandwidth (bytes it must stream with this layout, see
-pslr_get_info().apply_bytes_*) over its device time, next to FGMRES time to a
-1e-8 relative residual with the FP64 and the FP32 preconditioner.
+algorithmic bandwidth over its device time, next to FGMRES time to a 1e-8
+relative residual with the FP64 and the FP32 preconditioner.
 
-Default workload: 3D 7-point shifted Laplacian 64^3 (sigma for 20 negative
-eigenvalues), 4x4x2 subdomains, ILU(0), m = 3, r = 16, FP64 apply, one
-uniform[-1,1] right-hand side.  Its operator (~28 MB) fits in L2, so L2 is
-flushed (a 512 MB write) between timed applies and only the apply itself is
-inside each CUDA-event pair.
+Algorithmic bytes of one apply (``apply_bytes_by_blocks``), counted from the
+blocks of the reordered system: every pass streams its matrix (values, int32
+column indices, int32 row pointers) and reads its input vector and writes its
+output vector once - m+2 solves with the local factors of B (an L and a U
+sweep, each with its row pointers), m+1 with those of C0, m+1 products with E
+and with F, m with C_g - plus two passes over V and the read of b and write
+of z.  The same count, from the oracle's own blocks, is used by the reference
+arm.  What the kernel actually streams with its device layout is reported as
+``bytes_streamed_per_launch``.
+
+Default workload: 3D 7-point upwinded convection-diffusion 128^3 (Pe = 50,
+shifted to make A indefinite), 8x8x4 subdomains, ILU(0), m = 5, r = 32, one
+uniform[-1,1] right-hand side: the largest single-GPU configuration.  Its
+operator is larger than L2, and L2 is also flushed (a 512 MB write) between
+timed applies; only the apply itself is inside each CUDA-event pair.  The
+line's "secondary" object covers the 3D shifted Laplacian 64^3 (20 negative
+eigenvalues, 4x4x2, ILU(0), m = 3, r = 16) the same way.
 
 The line's "batch" object covers the batched form on its own workload (64
 uneven 2D shifted Laplacians, sides 64..256, 4 right-hand sides each): the
@@ -161,22 +172,67 @@ def replica_aggregate(seconds, units_per_rank, dist=None, device=None):
     return [world * units_per_rank / t for t in ts], ts
 
 
-def time_oracle_applies(w, ctx_lowrank, budget_s):
-    """The FP64 C oracle as it stands, single-threaded, on a bounded number of
-    applies of the same workload.  Returns (seconds per apply, applies, the
-    oracle's z = M^{-1} b for the bench's right-hand side)."""
+def apply_bytes_by_blocks(n, p, q, m, r, nnz_fact_B, nnz_fact_C0, nnz_E, nnz_F, nnz_Cg, prec):
+    """Algorithmic bytes of one apply (Algorithm 3) from the block sizes.
+
+    Per pass over a matrix: its values, int32 column indices and int32 row
+    pointers, plus its input vector read and output vector written once.  A
+    local solve is an L and a U sweep (two sets of row pointers) in place on
+    one vector; the apply makes m+2 solves with the factors of B (p rows), m+1
+    with those of C0 (q rows), m+1 products with E (p x q) and F (q x p), m
+    with C_g (q x q), two passes over V (q x r: FP64, or BF16 in the FP32
+    form), and reads b and writes z (n each)."""
+    vs = 8 if prec == "fp64" else 4
+    vb = 8 if prec == "fp64" else 2
+
+    def solve(rows, nnz):
+        return (vs + 4) * nnz + 2 * 4 * (rows + 1) + 2 * vs * rows
+
+    def prod(rows, cols, nnz):
+        return (vs + 4) * nnz + 4 * (rows + 1) + vs * (rows + cols)
+
+    return ((m + 2) * solve(p, nnz_fact_B) + (m + 1) * solve(q, nnz_fact_C0) + (m + 1) * prod(p, q, nnz_E)
+            + (m + 1) * prod(q, p, nnz_F) + m * prod(q, q, nnz_Cg) + 2 * q * r * vb + 2 * n * vs)
+
+
+def bytes_of_info(info, prec):
+    """apply_bytes_by_blocks for a context's pslr_get_info()."""
+    return apply_bytes_by_blocks(info["n"], info["p"], info["q"], info["m"], info["rank"], info["nnz_fact_B"],
+                                 info["nnz_fact_C0"], info["nnz_E"], info["nnz_F"], info["nnz_Cg"], prec)
+
+
+def bytes_of_oracle(orc, n, m, rank, prec):
+    """apply_bytes_by_blocks from the oracle's own blocks (its stored local
+    factors L+U of B and C0, or the blocks where it keeps no factor)."""
+    fb = orc.block_nnz("LU_B")
+    fc = orc.block_nnz("LU_C0")
+    fb = fb if fb >= 0 else orc.block_nnz("B")
+    fc = fc if fc >= 0 else orc.block_nnz("C0")
+    return apply_bytes_by_blocks(n, orc.p, orc.q, m, rank, fb, fc, orc.block_nnz("E"), orc.block_nnz("F"),
+                                 orc.block_nnz("Cg"), prec)
+
+
+def bf16_round(x):
+    """Round to BF16 (nearest, ties to even) and widen back to FP64: the V the
+    FP32 form applies."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def oracle_check(w, lowrank, b, z64, z32, budget_s):
+    """The FP64 C oracle as it stands, single-threaded, on the bench's input:
+    its apply timed over a bounded number of calls (the CPU baseline), the
+    GPU FP64 result against it, and the GPU FP32 result against it and
+    against the oracle re-run on the inputs the FP32 form applies (BF16 V,
+    FP32 G)."""
     import oracle as O
 
     orc = O.from_workload(w)
-    V, H, G = ctx_lowrank
-    if V is not None and V.shape[1]:
-        orc.set_lowrank(w["m"], V, G)
-    else:
-        orc.set_lowrank(w["m"], None, None)
-    from pslr_inputs import generators as Gen
-
-    b, _ = Gen.uniform_rhs(w["A"], 0)
-    z = orc.apply(b)  # warm
+    V, H, G = lowrank
+    r = V.shape[1] if V is not None else 0
+    orc.set_lowrank(w["m"], V if r else None, G if r else None)
+    zo = orc.apply(b)  # also the warm-up
     t0 = time.perf_counter()
     k = 0
     while True:
@@ -184,7 +240,18 @@ def time_oracle_applies(w, ctx_lowrank, budget_s):
         k += 1
         if time.perf_counter() - t0 >= budget_s:
             break
-    return (time.perf_counter() - t0) / k, k, z
+    sec = (time.perf_counter() - t0) / k
+    nz = np.linalg.norm(zo)
+    out = {"sec_per_apply": sec, "applies": k,
+           "err64": float(np.linalg.norm(z64 - zo) / nz), "err32_vs_fp64_oracle": float(np.linalg.norm(z32 - zo) / nz)}
+    if r:
+        orc.set_lowrank(w["m"], bf16_round(V), G.astype(np.float32).astype(np.float64))
+        zs = orc.apply(b)
+        out["err32_vs_oracle_same_inputs"] = float(np.linalg.norm(z32 - zs) / np.linalg.norm(zs))
+    else:
+        out["err32_vs_oracle_same_inputs"] = out["err32_vs_fp64_oracle"]
+    out["bytes64"] = bytes_of_oracle(orc, w["A"].n, w["m"], r, "fp64")
+    return out
 
 
 def run_reference(args):
@@ -200,9 +267,9 @@ def run_reference(args):
     orc = O.from_workload(w)
     k, _ = orc.build_lowrank(w["m"], w["rank"], seed=0)
     b, _ = Gen.uniform_rhs(w["A"], 0)
-    # bytes of one apply: same accounting as the GPU arm (taken from the GPU
-    # library only if it can be loaded without a device; else recomputed)
-    nbytes = reference_apply_bytes(w, k)
+    # bytes of one apply: the block count of the GPU arm, from the oracle's own blocks
+    nbytes = bytes_of_oracle(orc, w["A"].n, w["m"], k, "fp64")
+    # each step: one apply (the 128^3 apply takes ~0.2 s in the oracle)
     for _ in range(args.warmup):
         orc.apply(b)
     times = []
@@ -216,11 +283,11 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": w["name"], "m": w["m"], "rank": k,
-                                        "n": w["A"].n, "subdomains": orc.s},
+        "data": "synthetic", "config": workload_config(w, k, orc.s, orc.p, orc.q),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} FP64 applies of {w['name']} in the C oracle"},
+                         "sample": f"{args.steps} FP64 applies of {w['name']} in the single-threaded C oracle"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "bytes_per_launch": nbytes,
     }
     print(json.dumps(line))
 
@@ -230,17 +297,11 @@ def factor_name(w):
     return {0: "ilu0", 1: "lu", 2: "ilut(%g)" % w.get("drop_tol", 0.0)}[w["factor"]]
 
 
-def reference_apply_bytes(w, rank):
-    """Algorithmic bytes of one FP64 apply, the same count the GPU arm uses:
-    pslr_plan runs the library's host-side set-up only (reordering and layout,
-    no device, no kernels) and reports it."""
-    from paper_2002_00917_gb300 import build as B
-    from paper_2002_00917_gb300 import pslr
-
-    B.build()
-    info = pslr.plan(w["A"], w.get("dims", (0, 0, 0)), w.get("splits", (1, 1, 1)), factor=w["factor"], m=w["m"],
-                     rank=rank, drop_tol=w.get("drop_tol", 0.0), nparts=w.get("nparts", 0))[0]
-    return info["apply_bytes_fp64"]
+def workload_config(w, rank, s, p, q, world=1):
+    return {"workload": w["name"], "n": w["A"].n, "subdomains": s, "p": p, "q": q, "m": w["m"], "rank": rank,
+            "factor": factor_name(w), "sigma": w.get("sigma"), "negative_eigenvalues": w.get("nneg"),
+            "l2": "operator larger than L2 for the 128^3 workload; L2 flushed (512 MB write) between timed applies",
+            "parallelism": f"replicas{world}" if world > 1 else "single-gpu"}
 
 
 # Nominal GB300 FP64 (non-tensor) rate; the Krylov work below is FP64 FMAs.
@@ -374,16 +435,116 @@ def run_batch(dev, flush, stream, steps, warmup, seq_stride, solve=True):
     return out
 
 
+def timed_applies(ctx, bin_, zout, steps, warmup, flush, stream, dist=None):
+    """Per-apply device times (ms): CUDA events on the launching stream around
+    each apply, L2 flushed before each (outside the events)."""
+    import torch
+
+    for _ in range(warmup):
+        ctx.apply(bin_, zout)
+    ctx.sync()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        flush.fill_(1.0)
+        e0.record(stream)
+        ctx.apply(bin_, zout)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.sync()
+    if dist:
+        dist.barrier()
+    return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+
+def fgmres_runs(ctx, w, bd, xs, restarts, stream, apply_ms):
+    """FGMRES to 1e-8 with the FP64 and the FP32 preconditioner for each
+    (restart, maxit); the time of each solve by CUDA events on the stream."""
+    import torch
+
+    from paper_2002_00917_gb300 import pslr
+
+    fg = {}
+    xs_d = torch.tensor(xs, device=bd.device)
+    nnz_a = int(w["A"].rowptr[-1])
+    for restart, maxit in restarts:
+        for name, prec in (("fp64", pslr.PSLR_FP64), ("fp32", pslr.PSLR_FP32)):
+            x = torch.empty_like(bd)
+            # untimed warm-up: one full restart cycle, which also captures the
+            # cycle's CUDA graph (a one-time cost per context and shape)
+            ctx.solve(bd, x, rtol=1e-8, restart=restart, maxit=restart, prec=prec, check=False)
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            its, rel, st = ctx.solve(bd, x, rtol=1e-8, restart=restart, maxit=maxit, prec=prec)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ms = s0.elapsed_time(s1)
+            fg[f"{name}_restart{restart}"] = {
+                "ms": ms, "iters": its, "relres": rel, "converged": st == 0, "status": "ok" if st == 0 else "F",
+                "rel_err_vs_xstar": float(torch.linalg.norm(x - xs_d) / np.linalg.norm(xs)),
+                "krylov": krylov_estimate(its, restart, w["A"].n, nnz_a, ms, apply_ms[name])}
+    return fg
+
+
+def apply_summary(info, ms64, ms32, peak, world=1):
+    """GB/s, roofline fraction and times of the two precision forms."""
+    b64, b32 = bytes_of_info(info, "fp64"), bytes_of_info(info, "fp32")
+    t64, t32 = sum(ms64) / len(ms64), sum(ms32) / len(ms32)
+    return {"fp64": {"GB/s": b64 / t64 / 1e6, "frac": b64 / t64 / 1e6 / peak, "launch_us": 1e3 * t64,
+                     "bytes_per_launch": b64, "bytes_streamed_per_launch": info["apply_bytes_fp64"]},
+            "fp32": {"GB/s": b32 / t32 / 1e6, "frac": b32 / t32 / 1e6 / peak, "launch_us": 1e3 * t32,
+                     "bytes_per_launch": b32, "bytes_streamed_per_launch": info["apply_bytes_fp32"],
+                     "dtype": "f32 (BF16 V)"},
+            "launch_shape": {"grid": info["grid"], "ring": info["ring"], "ctas_per_sm": info["ctas_per_sm"]}}
+
+
+def run_secondary(name, dev, flush, stream, steps, warmup, peak, budget_s, fgmres=True):
+    """The same measurements on a second workload (applies, errors against the
+    oracle, FGMRES), reported in the line's "secondary" object."""
+    import torch
+
+    from paper_2002_00917_gb300 import pslr
+    from pslr_inputs import generators as Gen
+
+    w = workload_by_name(name)
+    ctx = pslr.from_workload(w)
+    k, _ = ctx.build_lowrank(w["m"], w["rank"])
+    info = ctx.get_info()
+    b, xs = Gen.uniform_rhs(w["A"], 0)
+    bd = torch.tensor(b, device=dev)
+    zd, bf = torch.empty_like(bd), bd.float()
+    zf = torch.empty_like(bf)
+    ms64 = timed_applies(ctx, bd, zd, steps, warmup, flush, stream)
+    ms32 = timed_applies(ctx, bf, zf, steps, warmup, flush, stream)
+    out = {"config": workload_config(w, k, info["s"], info["p"], info["q"])}
+    out.update(apply_summary(info, ms64, ms32, peak))
+    orc = oracle_check(w, ctx.get_lowrank(), b, zd.cpu().numpy(), zf.double().cpu().numpy(), budget_s)
+    out["fp64"]["rel_err_vs_fp64_oracle"] = orc["err64"]
+    out["fp32"]["rel_err_vs_fp64_oracle"] = orc["err32_vs_fp64_oracle"]
+    out["fp32"]["rel_err_vs_oracle_same_inputs"] = orc["err32_vs_oracle_same_inputs"]
+    out["oracle_ms_per_apply"] = 1e3 * orc["sec_per_apply"]
+    if fgmres:
+        out["fgmres"] = fgmres_runs(ctx, w, bd, xs, ((40, 500), (120, 1500)), stream,
+                                    {"fp64": out["fp64"]["launch_us"] / 1e3, "fp32": out["fp32"]["launch_us"] / 1e3})
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="lap3d_64_4x4x2_ilu0")
+    ap.add_argument("--workload", default="cd3d_128_8x8x4_ilu0")
+    ap.add_argument("--secondary", default="lap3d_64_4x4x2_ilu0")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fgmres", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--batch-seq-stride", type=int, default=8)
     ap.add_argument("--no-batch-solve", action="store_true")
     args = ap.parse_args()
@@ -422,7 +583,7 @@ def main():
     torch.cuda.synchronize()
     lowrank_s = time.perf_counter() - t0
     info = ctx.get_info()
-    bytes64, bytes32 = info["apply_bytes_fp64"], info["apply_bytes_fp32"]
+    bytes64, bytes32 = bytes_of_info(info, "fp64"), bytes_of_info(info, "fp32")
     b, xs = Gen.uniform_rhs(w["A"], 0)
     bd = torch.tensor(b, device=dev)
     zd = torch.empty_like(bd)
@@ -430,41 +591,20 @@ def main():
     zf = torch.empty_like(bf)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-
-    def timed_applies(bin_, zout, steps, warmup):
-        for _ in range(warmup):
-            ctx.apply(bin_, zout)
-        ctx.sync()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(steps)]
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        for e0, e1 in evs:
-            flush.fill_(1.0)  # evict L2 between timed applies (not timed)
-            e0.record(stream)
-            ctx.apply(bin_, zout)
-            e1.record(stream)
-        torch.cuda.synchronize()
-        ctx.sync()
-        if dist:
-            dist.barrier()
-        return [e0.elapsed_time(e1) for e0, e1 in evs]
+    peak, peak_kind = measured_peaks()
 
     clk = ClockSampler(local).__enter__()  # sampled over every timed region of the line
-    ms64 = timed_applies(bd, zd, args.steps, args.warmup)
-    ms32 = timed_applies(bf, zf, args.steps, args.warmup)
+    ms64 = timed_applies(ctx, bd, zd, args.steps, args.warmup, flush, stream, dist)
+    ms32 = timed_applies(ctx, bf, zf, args.steps, args.warmup, flush, stream, dist)
     (runs64, runs32), (t64, t32) = replica_aggregate([sum(ms64) / 1e3, sum(ms32) / 1e3], args.steps, dist, dev)
     value = runs64 * bytes64 / 1e9
     value32 = runs32 * bytes32 / 1e9
-    peak, peak_kind = measured_peaks()
 
     # end to end: host (pinned) b -> device -> apply -> host z, through the C ABI
     bh = torch.tensor(b).pin_memory()
     zh = torch.empty_like(bh).pin_memory()
     for _ in range(3):
-        ctx.lib.pslr_apply_host(ctx.h, bh.data_ptr(), zh.data_ptr(), 1, 0, 0,
-                                pslr._stream(None))
+        ctx.lib.pslr_apply_host(ctx.h, bh.data_ptr(), zh.data_ptr(), 1, 0, 0, pslr._stream(None))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -481,32 +621,17 @@ def main():
     e2e_value = runs_e2e * bytes64 / 1e9
 
     # FGMRES to 1e-8 with the FP64 and the FP32 preconditioner: restart 40 (the
-    # workload's setting) and restart 120 (a longer Krylov space, for problems
+    # workloads' setting) and restart 120 (a longer Krylov space, for problems
     # whose restarted FGMRES(40) stalls, reported "F" as in Section 4)
     fg = {}
     if not args.no_fgmres:
-        xs_d = torch.tensor(xs, device=dev)
-        nnz_a = int(w["A"].rowptr[-1])
-        for restart, maxit in ((40, 500), (120, 1500)):
-            for name, prec in (("fp64", pslr.PSLR_FP64), ("fp32", pslr.PSLR_FP32)):
-                x = torch.empty_like(bd)
-                # untimed warm-up: one full restart cycle, which also captures the
-                # cycle's CUDA graph (a one-time cost per context and shape)
-                ctx.solve(bd, x, rtol=1e-8, restart=restart, maxit=restart, prec=prec, check=False)
-                torch.cuda.synchronize()
-                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                s0.record(stream)
-                its, rel, st = ctx.solve(bd, x, rtol=1e-8, restart=restart, maxit=maxit, prec=prec)
-                s1.record(stream)
-                torch.cuda.synchronize()
-                err = float(torch.linalg.norm(x - xs_d) / np.linalg.norm(xs))
-                ms = s0.elapsed_time(s1)
-                fg[f"{name}_restart{restart}"] = {
-                    "ms": ms, "iters": its, "relres": rel,
-                    "converged": st == 0, "status": "ok" if st == 0 else "F",
-                    "rel_err_vs_xstar": err,
-                    "krylov": krylov_estimate(its, restart, w["A"].n, nnz_a, ms,
-                                              1e3 * (t64 if prec == pslr.PSLR_FP64 else t32) / args.steps)}
+        fg = fgmres_runs(ctx, w, bd, xs, ((40, 500), (120, 1500)), stream,
+                         {"fp64": 1e3 * t64 / args.steps, "fp32": 1e3 * t32 / args.steps})
+
+    secondary = None
+    if not args.no_secondary and rank == 0 and args.secondary and args.secondary != args.workload:
+        secondary = run_secondary(args.secondary, dev, flush, stream, min(args.steps, 20), args.warmup, peak,
+                                  min(args.cpu_budget, 3.0), fgmres=not args.no_fgmres)
 
     batch = None
     if not args.no_batch and rank == 0:
@@ -515,36 +640,34 @@ def main():
 
     res = None
     if rank == 0:
-        V, H, G = ctx.get_lowrank()
-        sec, napp, z_orc = time_oracle_applies(w, (V, H, G), args.cpu_budget)
-        cpu_value = bytes64 / sec / 1e9
-        # every GPU apply above ran on the same b: its result against the FP64 oracle's
-        nz = np.linalg.norm(z_orc)
-        err64 = float(np.linalg.norm(zd.cpu().numpy() - z_orc) / nz)
-        err32 = float(np.linalg.norm(zf.double().cpu().numpy() - z_orc) / nz)
-        traffic = committed_traffic(w["name"], "fp64")
+        orc = oracle_check(w, ctx.get_lowrank(), b, zd.cpu().numpy(), zf.double().cpu().numpy(), args.cpu_budget)
+        cpu_value = orc["bytes64"] / orc["sec_per_apply"] / 1e9
+        summ = apply_summary(info, ms64, ms32, peak, world)
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t64 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "n": w["A"].n, "subdomains": info["s"], "p": info["p"],
-                       "q": info["q"], "m": w["m"], "rank": k, "factor": factor_name(w),
-                       "l2": "flushed between timed applies (512 MB write)",
-                       "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
+            "config": workload_config(w, k, info["s"], info["p"], info["q"], world),
             "roofline": {"bound": "hbm", "achieved": value / world, "peak": peak, "unit": "GB/s",
                          "frac": value / world / peak, "peak_kind": peak_kind + " (burst copy)",
-                         "traffic": traffic, "bytes_per_launch": bytes64,
-                         "launch_us": 1e6 * t64 / args.steps},
-            "rel_err_vs_fp64_oracle": err64,
+                         "traffic": committed_traffic(w["name"], "fp64"), "bytes_per_launch": bytes64,
+                         "bytes_streamed_per_launch": info["apply_bytes_fp64"], "launch_us": 1e6 * t64 / args.steps,
+                         "launch_shape": summ["launch_shape"]},
+            "rel_err_vs_fp64_oracle": orc["err64"],
             "fp32_apply": {"value": value32, "unit": UNIT, "frac": value32 / world / peak,
-                           "bytes_per_launch": bytes32, "launch_us": 1e6 * t32 / args.steps,
-                           "dtype": "f32 (BF16 V)", "rel_err_vs_fp64_oracle": err32},
+                           "bytes_per_launch": bytes32, "bytes_streamed_per_launch": info["apply_bytes_fp32"],
+                           "launch_us": 1e6 * t32 / args.steps, "dtype": "f32 (BF16 V)",
+                           "traffic": committed_traffic(w["name"], "fp32"),
+                           "rel_err_vs_fp64_oracle": orc["err32_vs_fp64_oracle"],
+                           "rel_err_vs_oracle_same_inputs": orc["err32_vs_oracle_same_inputs"]},
             "fgmres": fg,
+            "secondary": secondary,
             "batch": batch,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w["A"].n,
                     "d2h_bytes_per_step": 8 * w["A"].n},
             "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{napp} FP64 applies of {w['name']} in the single-threaded C oracle"},
+                             "sample": f"{orc['applies']} FP64 applies of {w['name']} in the single-threaded C "
+                                       f"oracle ({1e3 * orc['sec_per_apply']:.0f} ms each)"},
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "setup_s": setup_s, "build_lowrank_s": lowrank_s,

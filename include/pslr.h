@@ -108,9 +108,12 @@ typedef struct {
     int32_t grid[2];      /* launch shape of the persistent apply, [0] FP64, [1] FP32:
                              CTAs of the cooperative grid (0 from pslr_plan)     */
     int32_t ring[2];      /* shared-memory ring slots per CTA                       */
-    int32_t ctas_per_sm[2]; /* 1, or 2 when the FP32 form puts two subdomains' CTAs
-                               on one SM (more subdomains than SMs, and two CTAs'
-                               vectors and rings fit an SM's shared memory)       */
+    int32_t ctas_per_sm[2]; /* 1, or 2 when two subdomains' CTAs share an SM (more
+                               subdomains than SMs, and two CTAs' vectors and
+                               rings fit an SM's shared memory)                   */
+    int64_t nnz_fact_B, nnz_fact_C0; /* stored entries of the local factors L+U of
+                                        all B_i and all C_i (Algorithm 1, steps 3-4) */
+    int64_t nnz_E, nnz_F, nnz_Cg;    /* stored entries of E, F and C_g (Eq. 2.1, 3.1) */
 } pslr_info;
 
 /*

@@ -133,6 +133,10 @@ class Oracle:
         self._lib.orc_offsets(self.h, _p(io), _p(go))
         return io, go
 
+    def block_nnz(self, name):
+        """Stored entries of a block (-1 if not stored for this factor kind)."""
+        return int(self._lib.orc_block_nnz(self.h, BLOCKS[name]))
+
     def block(self, name):
         """(rowptr, col, val, shape) of a block in the reordered numbering."""
         w = BLOCKS[name]

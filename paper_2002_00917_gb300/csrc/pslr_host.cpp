@@ -533,6 +533,7 @@ struct pslr_ctx {
     std::vector<int32_t> part, iface, perm, ioff, goff;
     int max_p = 0, max_q = 0, levels_B = 0, levels_C = 0;
     int64_t nnz_A = 0, nnz_ilu = 0;
+    int64_t nnz_blk[5] = {0, 0, 0, 0, 0};  // local factors of B and C0 (L+U), E, F, C_g
     int threads = 1;            // host threads of the set-up
     uint64_t layout_hash = 0;   // pslr_plan: hash of the packed device layout
     int64_t layout_errors = 0;  // pslr_plan: violations found by check_layout
@@ -1193,7 +1194,7 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
     // index) is reported, as a serial loop would
     enum { kFacOk = 0, kFacZeroPivot, kFacTooLarge };
     std::vector<int> fac_st(s, kFacOk);
-    std::vector<int64_t> fac_nnz(s, 0);
+    std::vector<int64_t> fac_nnz(s, 0), fac_b(s, 0);
     bool fac_ok = parallel_for(s, threads, [&](int i) {
         Local &Lc = L[i];
         Csr fb, fc;
@@ -1222,6 +1223,7 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
             std::copy(Lc.cpiv.begin(), Lc.cpiv.end(), cpiv.begin() + c->goff[i]);
         }
         fac_nnz[i] = (int64_t)fb.ci.size() + (int64_t)fc.ci.size();
+        fac_b[i] = (int64_t)fb.ci.size();
         split_lu(fb, Lc.BL, Lc.BU);
         split_lu(fc, Lc.CL, Lc.CU);
     });
@@ -1235,6 +1237,11 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
             return bail(fail(c, PSLR_ERR_ZERO_PIVOT, "%s in subdomain %d", what, i));
         }
         c->nnz_ilu += fac_nnz[i];
+        c->nnz_blk[0] += fac_b[i];
+        c->nnz_blk[1] += fac_nnz[i] - fac_b[i];
+        c->nnz_blk[2] += (int64_t)L[i].E.ci.size();
+        c->nnz_blk[3] += (int64_t)L[i].F.ci.size();
+        c->nnz_blk[4] += (int64_t)L[i].Cg.ci.size();
     }
 
     // --- device layout: both directions, both precisions
@@ -1691,6 +1698,11 @@ pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info) {
     I.setup_threads = c->threads;
     I.layout_hash = c->layout_hash;
     I.layout_errors = c->layout_errors;
+    I.nnz_fact_B = c->nnz_blk[0];
+    I.nnz_fact_C0 = c->nnz_blk[1];
+    I.nnz_E = c->nnz_blk[2];
+    I.nnz_F = c->nnz_blk[3];
+    I.nnz_Cg = c->nnz_blk[4];
     for (int prec = 0; prec < 2; ++prec) {
         I.grid[prec] = c->ops[0][prec].grid;
         I.ring[prec] = c->ops[0][prec].ring;

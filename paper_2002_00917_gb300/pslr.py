@@ -48,7 +48,9 @@ class pslr_info(C.Structure):
                 ("max_interface", C.c_int32), ("levels_B", C.c_int32), ("levels_C0", C.c_int32),
                 ("apply_bytes_fp64", C.c_int64), ("apply_bytes_fp32", C.c_int64),
                 ("layout_hash", C.c_uint64), ("setup_threads", C.c_int32), ("layout_errors", C.c_int64),
-                ("grid", C.c_int32 * 2), ("ring", C.c_int32 * 2), ("ctas_per_sm", C.c_int32 * 2)]
+                ("grid", C.c_int32 * 2), ("ring", C.c_int32 * 2), ("ctas_per_sm", C.c_int32 * 2),
+                ("nnz_fact_B", C.c_int64), ("nnz_fact_C0", C.c_int64), ("nnz_E", C.c_int64),
+                ("nnz_F", C.c_int64), ("nnz_Cg", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -237,3 +237,57 @@ def test_full_gradient_kappa48(dev):
     fd = (Lp - Lm) / (2 * h)
     ad = float(gk @ delta)
     assert abs(fd - ad) <= 1e-4 * abs(ad), (fd, ad)
+
+
+def test_full_gradient_kappa48_entrywise_fd(dev):
+    """dL/dkappa_i of the 48^3 differentiable problem at central differences
+    with h = 1e-6, on a seeded subset of the entries whose gradient is at
+    least a tenth of the largest, to 1e-6 relative.
+
+    L(kappa +- h e_i) is not formed from two separately solved losses (their
+    difference, O(h), would drown in the solves' tolerance): with u0 the
+    forward solution, x = u0 + du solves A(kappa +- h e_i) x = b, where du
+    solves the perturbed system (its own PSLR context, FGMRES to 1e-12) for
+    the residual b - A(kappa +- h e_i) u0, and
+    L(x) - L(u0) = 2 (u0 - u_t) . du + du . du is accurate to the solves'
+    relative tolerance, so the difference of the two carries no
+    cancellation."""
+    from paper_2002_00917_gb300 import autograd as AG
+    from paper_2002_00917_gb300 import pslr
+
+    w = C.kappa3d_48_3x3x3()
+    dims, A, sigma, kap0 = w["dims"], w["A"], w["sigma"], w["kappa"]
+    b0, _ = G.uniform_rhs(A, 0)
+    utn = np.random.default_rng(1).uniform(-1, 1, A.n)
+    opts = dict(dims=dims, splits=w["splits"], m=w["m"], rank=w["rank"], rtol=1e-12, restart=127, maxit=6000)
+    kappa = torch.tensor(kap0, device=dev, requires_grad=True)
+    b = torch.tensor(b0, device=dev)
+    vals = G.variable_kappa_values(dims, A, kappa, sigma, xp=torch)
+    u = AG.solve(vals, b, A.rowptr, A.col, **opts)
+    torch.sum((u - torch.tensor(utn, device=dev)) ** 2).backward()
+    gk = kappa.grad.cpu().numpy()
+    u0 = u.detach().cpu().numpy()
+    d0 = u0 - utn
+    cand = np.flatnonzero(np.abs(gk) >= 0.1 * np.abs(gk).max())
+    idx = np.random.default_rng(4).choice(cand, 4, replace=False)
+    h = 1e-6
+    errs = []
+    for i in idx:
+        dL = []
+        for sgn in (1.0, -1.0):
+            kap = kap0.copy()
+            kap[i] += sgn * h
+            As = G.variable_kappa(dims, kap, sigma)
+            r = torch.tensor(b0 - G.csr_matvec(As, u0), device=dev)
+            ctx = pslr.Pslr(As, dims=dims, splits=w["splits"], factor=w["factor"])
+            ctx.build_lowrank(w["m"], w["rank"])
+            du = torch.zeros_like(r)
+            its, rel, st = ctx.solve(r, du, rtol=1e-12, restart=127, maxit=6000)
+            ctx.close()
+            assert st == pslr.PSLR_OK, (i, sgn, its, rel)
+            dun = du.cpu().numpy()
+            dL.append(2.0 * (d0 @ dun) + dun @ dun)
+        fd = (dL[0] - dL[1]) / (2 * h)
+        errs.append(abs(fd - gk[i]) / abs(gk[i]))
+    print("entrywise FD relative differences:", errs)
+    assert max(errs) <= 1e-6, errs
