@@ -72,6 +72,9 @@ def _load():
                 "orc_apply_T": (None, [P, P, P]),
                 "orc_fgmres": (I32, [P, I32, P, P, D, I32, I32, P, P]),
                 "orc_splitmix_uniform": (D, [U64, U64]),
+                "orc_neumann_series": (None, [P, I32, D, I32, P, P]),
+                "orc_neumann_apply": (None, [P, I32, D, I32, P, P]),
+                "orc_set_neumann": (None, [P, I32, D]),
                 "orc_graph_partition": (I32, [I32, P, P, I32, P]),
             }
             for name, (res, args) in sig.items():
@@ -226,6 +229,27 @@ class Oracle:
 
     def apply_T(self, b):
         return self._unary(self._lib.orc_apply_T, b, self.n)
+
+    def neumann_series(self, m, omega, t, transpose=False):
+        """Sec. 1 Neumann polynomial of the Schur complement applied to t
+        (interface numbering)."""
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        out = np.empty(self.q + 1)
+        self._lib.orc_neumann_series(self.h, int(m), float(omega), int(bool(transpose)), _p(t), _p(out))
+        return out[: self.q]
+
+    def neumann_apply(self, m, omega, b, transpose=False):
+        """Algorithm 3's block elimination with the Neumann polynomial in place
+        of the PSLR Schur approximation (original ordering)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        z = np.empty(self.n)
+        self._lib.orc_neumann_apply(self.h, int(m), float(omega), int(bool(transpose)), _p(b), _p(z))
+        return z
+
+    def set_neumann(self, m, omega):
+        """FGMRES preconditioned by the Neumann polynomial (omega > 0), or by
+        PSLR again (omega <= 0)."""
+        self._lib.orc_set_neumann(self.h, int(m), float(omega))
 
     def fgmres(self, b, rtol=1e-8, restart=40, maxit=500, precond=True, transpose=False):
         b = np.ascontiguousarray(b, dtype=np.float64)

@@ -13,6 +13,9 @@
  *   series, E_rr(m), Arnoldi, G ......... pinned (closed forms, Theorem 2)
  *   Algorithm 3 apply and transpose ...... pinned (dense formulas, identity case)
  *   FGMRES ............................... pinned (dense solve, M = I reduction)
+ *   Neumann polynomial (Sec. 1 foil) ..... pinned (omega = 1 is the series of Eq. 3.3,
+ *                                          dense closed form, limit S^{-1} when
+ *                                          rho(N) < 1, transpose by inner products)
  */
 #include "pslr_oracle.h"
 
@@ -36,6 +39,8 @@ struct orc_ctx {
     int32_t **pvB, **pvC;                 /* exact LU: row swap at each elimination step */
     int32_t m, r;
     double *V, *H, *G;                    /* q x r, r x r, r x r (column-major) */
+    int32_t nf_on, nf_m;                  /* FGMRES with the Sec. 1 Neumann foil instead of PSLR */
+    double nf_omega;
 };
 
 /* ------------------------------------------------------------------ helpers */
@@ -1082,6 +1087,131 @@ void orc_apply_T(const orc_ctx *c, const double *b, double *z) {
     free(f); free(u); free(h); free(w); free(x);
 }
 
+/* ------------------------------- Sec. 1: the classical Neumann polynomial */
+
+/* y = C0~ w (or C0~^T w): the matrix whose inverse the local C0 solves apply -
+ * L U of the incomplete factor (unit lower L, upper U, stored together), or
+ * C0 itself for the exact LU. */
+static void c0_mult(const orc_ctx *c, int transpose, const double *w, double *y) {
+    int32_t q = c->q;
+    if (c->factor == 1) {
+        if (transpose) spmv_t(&c->C0, w, y);
+        else spmv(&c->C0, w, y);
+        return;
+    }
+    const ocsr *LU = &c->luC;
+    double *u = calloc((size_t)q + 1, sizeof(double));
+    if (!transpose) { /* u = U w, y = L u */
+        for (int32_t i = 0; i < q; ++i)
+            for (int32_t k = LU->rp[i]; k < LU->rp[i + 1]; ++k)
+                if (LU->ci[k] >= i) u[i] += LU->v[k] * w[LU->ci[k]];
+        for (int32_t i = 0; i < q; ++i) {
+            double a = u[i];
+            for (int32_t k = LU->rp[i]; k < LU->rp[i + 1]; ++k)
+                if (LU->ci[k] < i) a += LU->v[k] * u[LU->ci[k]];
+            y[i] = a;
+        }
+    } else { /* (L U)^T w = U^T (L^T w) */
+        for (int32_t i = 0; i < q; ++i) u[i] = w[i];
+        for (int32_t i = 0; i < q; ++i)
+            for (int32_t k = LU->rp[i]; k < LU->rp[i + 1]; ++k)
+                if (LU->ci[k] < i) u[LU->ci[k]] += LU->v[k] * w[i];
+        for (int32_t i = 0; i < q; ++i) y[i] = 0.0;
+        for (int32_t i = 0; i < q; ++i)
+            for (int32_t k = LU->rp[i]; k < LU->rp[i + 1]; ++k)
+                if (LU->ci[k] >= i) y[LU->ci[k]] += LU->v[k] * u[i];
+    }
+    free(u);
+}
+
+/* S w = C0~ w - E_s w (Eq. 3.1 with the factored C0), or S^T w. */
+static void schur_mult(const orc_ctx *c, int transpose, const double *w, double *y) {
+    double *e = malloc(sizeof(double) * ((size_t)c->q + 1));
+    c0_mult(c, transpose, w, y);
+    if (transpose) orc_EsT(c, w, e);
+    else orc_Es(c, w, e);
+    for (int32_t i = 0; i < c->q; ++i) y[i] -= e[i];
+    free(e);
+}
+
+/*
+ * Sec. 1, the Neumann polynomial of the Schur complement that the paper
+ * contrasts with its method: N = I - omega D^{-1} S, with D the block
+ * diagonal of S taken as C0 (the splitting of Eq. 3.1; D^{-1} is the local
+ * factor solve and S = C0~ - E_s the matrix those solves make exact), and
+ *     S^{-1} ~ omega [I + N + N^2 + ... + N^m] D^{-1},
+ * the identity S^{-1} = omega (I - N)^{-1} D^{-1} truncated after m+1 terms
+ * (it converges only when rho(N) < 1).  Summed as v_0 = D^{-1} t,
+ * v_i = N v_{i-1} = v_{i-1} - omega D^{-1} (S v_{i-1}), out = omega sum v_i.
+ * The transpose, omega sum_i D^{-T} (N^T)^i t, runs v_0 = t,
+ * v_i = v_{i-1} - omega S^T D^{-T} v_{i-1}, out = omega sum D^{-T} v_i.
+ */
+void orc_neumann_series(const orc_ctx *c, int32_t m, double omega, int32_t transpose, const double *in,
+                        double *out) {
+    int32_t q = c->q;
+    double *v = malloc(sizeof(double) * ((size_t)q + 1)), *a = malloc(sizeof(double) * ((size_t)q + 1));
+    double *d = malloc(sizeof(double) * ((size_t)q + 1));
+    if (!transpose) {
+        orc_solve_C0(c, in, v);
+        for (int32_t k = 0; k < q; ++k) out[k] = v[k];
+        for (int32_t i = 1; i <= m; ++i) {
+            schur_mult(c, 0, v, a);
+            orc_solve_C0(c, a, d);
+            for (int32_t k = 0; k < q; ++k) {
+                v[k] -= omega * d[k];
+                out[k] += v[k];
+            }
+        }
+    } else {
+        for (int32_t k = 0; k < q; ++k) v[k] = in[k];
+        orc_solve_C0T(c, v, d);
+        for (int32_t k = 0; k < q; ++k) out[k] = d[k];
+        for (int32_t i = 1; i <= m; ++i) {
+            schur_mult(c, 1, d, a); /* S^T D^{-T} v_{i-1}, with d = D^{-T} v_{i-1} */
+            for (int32_t k = 0; k < q; ++k) v[k] -= omega * a[k];
+            orc_solve_C0T(c, v, d);
+            for (int32_t k = 0; k < q; ++k) out[k] += d[k];
+        }
+    }
+    for (int32_t k = 0; k < q; ++k) out[k] *= omega;
+    free(v); free(a); free(d);
+}
+
+/* The block elimination of Algorithm 3 with the Neumann polynomial in place of
+ * P_m (I + V G V^T) (no low-rank term): t = g - F B^{-1} f, y = the series of
+ * t, x = B^{-1}(f - E y); and its transpose, as orc_apply_T. */
+void orc_neumann_apply(const orc_ctx *c, int32_t m, double omega, int32_t transpose, const double *b, double *z) {
+    int32_t p = c->p, q = c->q;
+    double *f = malloc(sizeof(double) * (p + 1)), *u = malloc(sizeof(double) * (p + 1));
+    double *t = malloc(sizeof(double) * (q + 1)), *y = malloc(sizeof(double) * (q + 1));
+    double *x = malloc(sizeof(double) * (p + 1));
+    for (int32_t i = 0; i < p; ++i) f[i] = b[c->perm[i]];
+    if (!transpose) {
+        orc_solve_B(c, f, u);
+        spmv(&c->F, u, t);
+    } else {
+        orc_solve_BT(c, f, u);
+        spmv_t(&c->E, u, t);
+    }
+    for (int32_t i = 0; i < q; ++i) t[i] = b[c->perm[p + i]] - t[i];
+    orc_neumann_series(c, m, omega, transpose, t, y);
+    if (!transpose) spmv(&c->E, y, u);
+    else spmv_t(&c->F, y, u);
+    for (int32_t i = 0; i < p; ++i) u[i] = f[i] - u[i];
+    if (!transpose) orc_solve_B(c, u, x);
+    else orc_solve_BT(c, u, x);
+    for (int32_t i = 0; i < p; ++i) z[c->perm[i]] = x[i];
+    for (int32_t i = 0; i < q; ++i) z[c->perm[p + i]] = y[i];
+    free(f); free(u); free(t); free(y); free(x);
+}
+
+/* FGMRES with the foil (omega > 0) or with PSLR again (omega <= 0). */
+void orc_set_neumann(orc_ctx *c, int32_t m, double omega) {
+    c->nf_on = omega > 0.0;
+    c->nf_m = m;
+    c->nf_omega = omega;
+}
+
 /* -------------------------------------------------------------- FGMRES */
 
 static void op_A(const orc_ctx *c, int transpose, const double *x, double *y) {
@@ -1094,7 +1224,8 @@ static void op_M(const orc_ctx *c, int prec, int transpose, const double *x, dou
         memcpy(y, x, sizeof(double) * c->n);
         return;
     }
-    if (transpose) orc_apply_T(c, x, y);
+    if (c->nf_on) orc_neumann_apply(c, c->nf_m, c->nf_omega, transpose, x, y);
+    else if (transpose) orc_apply_T(c, x, y);
     else orc_apply(c, x, y);
 }
 

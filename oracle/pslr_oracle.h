@@ -83,6 +83,19 @@ int32_t orc_set_lowrank(orc_ctx *c, int32_t m, int32_t rank, const double *V, co
 void orc_apply(const orc_ctx *c, const double *b, double *z);
 void orc_apply_T(const orc_ctx *c, const double *b, double *z);
 
+/* Sec. 1: the classical Neumann polynomial of the Schur complement, the foil
+ * the paper contrasts PSLR with: S^{-1} ~ omega [I + N + ... + N^m] D^{-1},
+ * N = I - omega D^{-1} S, D = C0 (the factored block diagonal of Eq. 3.1),
+ * S = C0~ - E_s; interface numbering in and out (transpose: its transpose).
+ * orc_neumann_apply is Algorithm 3's block elimination with it in place of
+ * P_m (I + V G V^T), original ordering.  orc_set_neumann(c, m, omega > 0)
+ * makes orc_fgmres use it as the preconditioner (omega <= 0: PSLR again). */
+void orc_neumann_series(const orc_ctx *c, int32_t m, double omega, int32_t transpose, const double *in,
+                        double *out);
+void orc_neumann_apply(const orc_ctx *c, int32_t m, double omega, int32_t transpose, const double *b,
+                       double *z);
+void orc_set_neumann(orc_ctx *c, int32_t m, double omega);
+
 /* Right-preconditioned flexible GMRES(restart), x0 = 0, classical Gram-Schmidt
  * applied twice, Givens rotations.  prec bit 0: PSLR preconditioner
  * (Algorithm 3) instead of none; bit 1: solve with A^T and the transposed
