@@ -114,6 +114,8 @@ typedef struct {
     int64_t nnz_fact_B, nnz_fact_C0; /* stored entries of the local factors L+U of
                                         all B_i and all C_i (Algorithm 1, steps 3-4) */
     int64_t nnz_E, nnz_F, nnz_Cg;    /* stored entries of E, F and C_g (Eq. 2.1, 3.1) */
+    double omega;         /* 1: PSLR; otherwise the scaling of the Sec. 1 Neumann
+                             polynomial the context applies (pslr_set_neumann)    */
 } pslr_info;
 
 /*
@@ -230,6 +232,24 @@ pslr_status pslr_grad_values(pslr_ctx *c, const double *lambda_dev, const double
  * original index of reordered unknown t (interiors by subdomain, then
  * interfaces by subdomain, each in increasing original index). */
 pslr_status pslr_get_maps(const pslr_ctx *c, int32_t *part, int32_t *is_interface, int32_t *perm);
+
+/*
+ * The classical Neumann polynomial of Sec. 1, which the paper contrasts its
+ * method with, in place of the PSLR Schur complement approximation: from now
+ * on pslr_apply, pslr_apply_T, pslr_apply_noalloc and pslr_solve use
+ *     S^{-1} ~ omega [I + N + ... + N^m] D^{-1},   N = I - omega D^{-1} S,
+ * with D = C0, the block diagonal of the splitting S = C0 - E_s (Eq. 3.1),
+ * applied through the local factors (D^{-1} is the C0 solve), inside the same
+ * block elimination as Algorithm 3 and with no low-rank term.  The scalar is
+ * the one of the identity S^{-1} = omega (I - N)^{-1} D^{-1} (the series
+ * converges to S^{-1} only when the spectral radius of N is below 1); omega = 1
+ * gives exactly Algorithm 3 with rank 0 (N = C0^{-1} E_s, Eq. 3.3).  m >= 0,
+ * omega > 0 and finite, else PSLR_ERR_ARG.  Frees the low-rank term;
+ * pslr_build_lowrank or pslr_set_lowrank return the context to PSLR.  The
+ * batched calls reject a context in this state (PSLR_ERR_STATE).  Synchronises
+ * `stream` first.
+ */
+pslr_status pslr_set_neumann(pslr_ctx *c, int32_t m, double omega, void *stream);
 
 /* Copy V (q x rank), H and G (rank x rank), column-major FP64, to host
  * arrays sized for the current rank (pslr_get_info().rank); any may be NULL. */

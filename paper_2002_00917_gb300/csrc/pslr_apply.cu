@@ -44,6 +44,8 @@ __device__ __forceinline__ void apply_body(const ApplyParams<T, IO> &P) {
     const int q = P.q, p = P.p, r = P.r, m = P.m;
     const bool lr_before = r > 0 && !P.lowrank_after;
     const bool lr_after = r > 0 && P.lowrank_after;
+    const T om = P.omega;
+    const bool scaled = om != T(1);  // the Sec. 1 Neumann polynomial instead of Eq. 3.3
     const int tid = threadIdx.x;
     bool ok = true;
 
@@ -128,6 +130,9 @@ __device__ __forceinline__ void apply_body(const ApplyParams<T, IO> &P) {
             ell_op<T, true>(c, c.si, wprev, true, k.n[kCg], P.err);                      // - C_g w
             solve_local(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1], k.n[kC2],
                         P.err);                                                         // C0^{-1}
+            if (scaled)  // N w = (1 - omega) w + omega C0^{-1} E_s w, N = I - omega C0^{-1} S
+                for (int j = tid; j < nq; j += kConsumers)
+                    c.si[j] = fma_t(T(1) - om, __ldcg(wprev + go + j), om * c.si[j]);
             for (int j = tid; j < nq; j += kConsumers) {
                 wnext[go + j] = c.si[j];
                 P.acc[go + j] = __ldcg(P.acc + go + j) + c.si[j];
@@ -159,7 +164,7 @@ __device__ __forceinline__ void apply_body(const ApplyParams<T, IO> &P) {
         const Counts k = counts_of(P.cnt, i);
         const int io = P.ioff[i], np_ = P.ioff[i + 1] - io;
         const int go = P.goff[i], nq = P.goff[i + 1] - go;
-        for (int j = tid; j < nq; j += kConsumers) c.wi[j] = __ldcg(P.acc + go + j);
+        for (int j = tid; j < nq; j += kConsumers) c.wi[j] = scaled ? om * __ldcg(P.acc + go + j) : __ldcg(P.acc + go + j);
         if (tid == 0) c.wi[nq] = T(0);
         for (int j = tid; j < np_; j += kConsumers) c.xi[j] = T(P.b[P.perm[io + j]]);
         if (tid == 0) c.xi[np_] = T(0);

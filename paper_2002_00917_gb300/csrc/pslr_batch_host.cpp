@@ -997,6 +997,10 @@ pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nr
         if (sx[k].factor == 1)
             return bfail(nullptr, PSLR_ERR_ARG,
                          "batch_create: system %d uses exact LU factors; the batch takes ILU(0) and ILUT systems", k);
+        if (sx[k].omega != 1.0)
+            return bfail(nullptr, PSLR_ERR_STATE,
+                         "batch_create: system %d applies the Neumann polynomial (pslr_set_neumann); the batch "
+                         "applies PSLR", k);
         if (sx[k].r > 0 && (!sx[k].V || !sx[k].Vb || !sx[k].G || !sx[k].Gf))
             return bfail(nullptr, PSLR_ERR_STATE, "batch_create: system %d has no low-rank term on the device", k);
     }

@@ -548,6 +548,7 @@ struct pslr_ctx {
     // low-rank term
     int m = 0, r = 0;
     uint64_t lr_gen = 0;         // incremented whenever the low-rank term is replaced
+    double omega = 1.0;          // 1: PSLR; otherwise the Sec. 1 Neumann polynomial (pslr_set_neumann)
     std::vector<double> V, H, G;
     double *d_V = nullptr;       // q x r FP64 (leading dimension q)
     // the copies the apply reads: row-major, row stride ldv = r rounded up to 8, zero padded
@@ -1442,6 +1443,7 @@ static void fill_params(pslr_ctx *c, ApplyParams<T, IO> &P, int dir, int prec, c
     P.skip = nullptr;
     P.wait_limit = c->wait_limit;
     P.rs = c->rs;
+    P.omega = T(c->omega);
 }
 
 // Scratch of one apply launch: series iterates (2(q+1)), accumulator (q+1),
@@ -1698,6 +1700,7 @@ pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info) {
     I.setup_threads = c->threads;
     I.layout_hash = c->layout_hash;
     I.layout_errors = c->layout_errors;
+    I.omega = c->omega;
     I.nnz_fact_B = c->nnz_blk[0];
     I.nnz_fact_C0 = c->nnz_blk[1];
     I.nnz_E = c->nnz_blk[2];
@@ -1806,6 +1809,7 @@ static pslr_status install_lowrank(pslr_ctx *c, int m, int r, const std::vector<
     c->m = m;
     c->r = r;
     c->G = G;
+    c->omega = 1.0;
     cudaFree(c->d_Vr); cudaFree(c->d_Vb); cudaFree(c->d_G); cudaFree(c->d_GT); cudaFree(c->d_Gf); cudaFree(c->d_GTf);
     cudaFree(c->d_part);
     c->d_Vr = nullptr; c->d_Vb = nullptr; c->d_G = c->d_GT = nullptr; c->d_Gf = c->d_GTf = nullptr; c->d_part = nullptr;
@@ -1845,6 +1849,17 @@ static pslr_status install_lowrank(pslr_ctx *c, int m, int r, const std::vector<
 }
 
 extern "C" {
+
+pslr_status pslr_set_neumann(pslr_ctx *c, int32_t m, double omega, void *stream) {
+    if (!c || m < 0 || !(omega > 0.0) || !std::isfinite(omega))
+        return fail(c, PSLR_ERR_ARG, "set_neumann: bad argument (m >= 0, omega > 0)");
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    free_lowrank(c);
+    pslr_status st = install_lowrank(c, m, 0, {});
+    if (st != PSLR_OK) return st;
+    c->omega = omega;  // install_lowrank dropped the captured cycles
+    return PSLR_OK;
+}
 
 pslr_status pslr_set_lowrank(pslr_ctx *c, int32_t m, int32_t rank, const double *V, const double *G,
                              void *stream) {
@@ -2252,6 +2267,7 @@ bool sys_export(const pslr_ctx *c, SysExport *e) {
         e->seg_bytes[prec] = c->ops[0][prec].seg_total;
     }
     e->lr_gen = c->lr_gen;
+    e->omega = c->omega;
     e->ioff_h = c->ioff;
     e->goff_h = c->goff;
     return true;

@@ -128,6 +128,9 @@ struct ApplyParams {
     const int *skip;             // when *skip != 0 the launch does nothing (converged FGMRES cycle)
     long long wait_limit;        // polls before a grid-barrier wait gives up
     int rs;                      // column stride of the low-rank reduction scratch (red_stride(r))
+    T omega;                     // series scaling: 1 for PSLR (Eq. 3.3); otherwise the Sec. 1
+                                 // Neumann polynomial, w_k = (1-omega) w_{k-1} + omega C0^{-1} E_s w_{k-1},
+                                 // y = omega sum w_k (no low-rank term)
 };
 
 // E_rr(m) v for the Arnoldi process (Eq. 3.19): v <- (E_s C0^{-1})^{m+1} v.

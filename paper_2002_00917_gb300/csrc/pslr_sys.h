@@ -24,6 +24,7 @@ struct SysExport {
     const int32_t *cnt[2];                  // device kNCnt*s segment counts [FP64, FP32]
     int slot_bytes[2];
     uint64_t lr_gen;                        // changes whenever the low-rank term is replaced
+    double omega;                           // 1 unless the context applies the Neumann polynomial
     int64_t seg_bytes[2];                   // bytes of the forward segments
     std::vector<int32_t> ioff_h, goff_h;    // host copies of the s+1 interior / interface offsets
 };

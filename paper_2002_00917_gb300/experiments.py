@@ -11,6 +11,9 @@ Table 6), ILUT(1e-2) local factors, m = 3, through the library:
 * ``lap``  - the meshes of Table 6 (32^3, 64^3, 128^3 at shifts .16, .08,
   .03; m = 3, r = 15): 3x3x4 for the paper's s = 35 on the two smaller
   meshes, 8x8x4 on 128^3 (35 parts of 128^3 do not fit one CTA each).
+* ``neumann`` - the classical Neumann polynomial of Section 1 (the foil the
+  paper contrasts PSLR with; pslr_set_neumann) for omega = 0.5 .. 1.5 at
+  m = 3, next to PSLR with r = 0, 15 and 45 (3x3x4, shift .05 and .14).
 
 Each run prints one JSON line: partition size, fill factors (Section 4's
 definitions), levels per sweep, and, unless ``--dry-run``, the FGMRES(127)
@@ -33,6 +36,7 @@ DIMS = (50, 50, 50)
 LAP_MESHES = [(32, 0.16, (3, 3, 4)), (64, 0.08, (3, 3, 4)), (128, 0.03, (8, 8, 4))]
 S_SPLITS = [(2, 2, 2), (4, 2, 2), (3, 3, 3), (3, 3, 4), (3, 3, 5), (3, 3, 6)]
 PAPER_S = [5, 15, 25, 35, 45, 55]
+OMEGAS = [0.5, 0.75, 1.0, 1.25, 1.5]
 
 
 def runs(sweep, shift=None):
@@ -46,13 +50,23 @@ def runs(sweep, shift=None):
         return [(0.05 if shift is None else shift, (3, 3, 4), 3, r) for r in range(0, 76, 15)]
     if sweep == "lap":
         return [(sh, sp, 3, 15, (N, N, N)) for N, sh, sp in LAP_MESHES]
+    if sweep == "neumann":
+        out = []
+        for sh in ((0.05, 0.14) if shift is None else (shift,)):
+            out += [(sh, (3, 3, 4), 3, 0, DIMS, om) for om in OMEGAS]
+            out += [(sh, (3, 3, 4), 3, r) for r in (0, 15, 45)]
+        return out
     raise ValueError(f"unknown sweep {sweep!r}")
 
 
-def one(A, shift, splits, m, r, drop_tol=1e-2, restart=127, maxit=1500, dry_run=False, rhs_seed=0, dims=DIMS):
-    """One run; returns its JSON record."""
+def one(A, shift, splits, m, r, drop_tol=1e-2, restart=127, maxit=1500, dry_run=False, rhs_seed=0, dims=DIMS,
+        omega=None):
+    """One run; returns its JSON record.  omega: the Section 1 Neumann
+    polynomial with that scaling instead of PSLR (r is then 0)."""
     rec = {"shift": shift, "dims": list(dims), "splits": list(splits), "s": splits[0] * splits[1] * splits[2],
            "m": m, "r": r}
+    if omega is not None:
+        rec["preconditioner"] = f"neumann(omega={omega})"
     if dry_run:
         info = pslr.plan(A, dims, splits, factor=2, m=m, rank=r, drop_tol=drop_tol)[0]
         rec.update(q=info["q"], fill_ilu=round(info["fill_ilu"], 4), fill_lr=round(info["fill_lr"], 4),
@@ -71,7 +85,9 @@ def one(A, shift, splits, m, r, drop_tol=1e-2, restart=127, maxit=1500, dry_run=
     t_setup = time.perf_counter() - t0
     try:
         t0 = time.perf_counter()
-        if r:
+        if omega is not None:
+            ctx.set_neumann(m, omega)
+        elif r:
             ctx.build_lowrank(m, r)
         else:
             ctx.set_lowrank(m)
@@ -98,7 +114,7 @@ def one(A, shift, splits, m, r, drop_tol=1e-2, restart=127, maxit=1500, dry_run=
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("sweep", choices=["s", "m", "rank", "lap"])
+    ap.add_argument("sweep", choices=["s", "m", "rank", "lap", "neumann"])
     ap.add_argument("--shift", type=float, default=None, help="shift of the Laplacian (default .05)")
     ap.add_argument("--drop-tol", type=float, default=1e-2)
     ap.add_argument("--restart", type=int, default=127)
@@ -111,9 +127,11 @@ def main(argv=None):
     for run in runs(a.sweep, a.shift):
         shift, splits, m, r = run[:4]
         dims = run[4] if len(run) > 4 else DIMS
+        omega = run[5] if len(run) > 5 else None
         if key != (dims, shift):
             A, key = G.shifted_laplacian(dims, shift), (dims, shift)
-        rec = one(A, shift, splits, m, r, drop_tol=a.drop_tol, restart=a.restart, dry_run=a.dry_run, dims=dims)
+        rec = one(A, shift, splits, m, r, drop_tol=a.drop_tol, restart=a.restart, dry_run=a.dry_run, dims=dims,
+                  omega=omega)
         print(json.dumps(rec), flush=True)
         out.append(rec)
     return out

@@ -50,7 +50,7 @@ class pslr_info(C.Structure):
                 ("layout_hash", C.c_uint64), ("setup_threads", C.c_int32), ("layout_errors", C.c_int64),
                 ("grid", C.c_int32 * 2), ("ring", C.c_int32 * 2), ("ctas_per_sm", C.c_int32 * 2),
                 ("nnz_fact_B", C.c_int64), ("nnz_fact_C0", C.c_int64), ("nnz_E", C.c_int64),
-                ("nnz_F", C.c_int64), ("nnz_Cg", C.c_int64)]
+                ("nnz_F", C.c_int64), ("nnz_Cg", C.c_int64), ("omega", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,6 +80,7 @@ SIGNATURES = {
                          _P, _P, _P]),
     "pslr_build_lowrank": (_I32, [_P, _I32, _I32, _I32, _P]),
     "pslr_set_lowrank": (_I32, [_P, _I32, _I32, _P, _P, _P]),
+    "pslr_set_neumann": (_I32, [_P, _I32, _D, _P]),
     "pslr_apply": (_I32, [_P, _P, _P, _I32, _I32, _P]),
     "pslr_apply_T": (_I32, [_P, _P, _P, _I32, _I32, _P]),
     "pslr_apply_host": (_I32, [_P, _P, _P, _I32, _I32, _I32, _P]),
@@ -230,6 +231,13 @@ class Pslr:
         st = self.lib.pslr_set_lowrank(self.h, int(m), r, None if Vc is None else Vc.ctypes.data,
                                        None if Gc is None else Gc.ctypes.data, _stream(stream))
         self._check(st, "pslr_set_lowrank")
+        self.info = self.get_info()
+
+    def set_neumann(self, m, omega, stream=None):
+        """Apply the classical Neumann polynomial of Sec. 1 (scaling omega, m+1
+        terms, no low-rank term) instead of PSLR; build_lowrank/set_lowrank
+        return to PSLR."""
+        self._check(self.lib.pslr_set_neumann(self.h, int(m), float(omega), _stream(stream)), "pslr_set_neumann")
         self.info = self.get_info()
 
     def get_lowrank(self):

@@ -16,6 +16,7 @@ Workloads (names say what they are):
 ``cd3d_128_8x8x4_ilu0``   3D 128^3 upwinded convection-diffusion, Pe=50, sigma for
                           20 negative eigenvalues of the shifted operator, 8x8x4
                           split, ILU(0), m=5, r=32.
+``cd3d_128_8x8x4_ilu0_noshift``  the same operator without the shift (definite).
 ``lap3d_50_shift014``     3D 7-pt Laplacian 50^3 shifted by 0.14 (78 negative
                           eigenvalues: the strongly indefinite case of Section
                           4.1's rank study), 3x3x4 split (36 subdomains, near the
@@ -58,10 +59,20 @@ def lap3d_64_4x4x2_ilu0():
 def cd3d_128_8x8x4_ilu0(N=128, splits=(8, 8, 4), m=5, rank=32, K=20):
     pe = 50.0
     a = pe / (N + 1.0)
-    sig, k = G.sigma_for_negative_count([G.convdiff_1d_eigs(N, a)] * 3, K)
+    if K == 0:
+        sig, k = 0.0, 0
+    else:
+        sig, k = G.sigma_for_negative_count([G.convdiff_1d_eigs(N, a)] * 3, K)
     A = G.convection_diffusion((N, N, N), pe, sig)
-    return dict(name=f"cd3d_{N}_{splits[0]}x{splits[1]}x{splits[2]}_ilu0", A=A, sigma=sig, nneg=k,
-                ndim=3, dims=(N, N, N), splits=tuple(splits), factor=FACTOR_ILU0, m=m, rank=rank)
+    name = f"cd3d_{N}_{splits[0]}x{splits[1]}x{splits[2]}_ilu0" + ("_noshift" if K == 0 else "")
+    return dict(name=name, A=A, sigma=sig, nneg=k, ndim=3, dims=(N, N, N), splits=tuple(splits), factor=FACTOR_ILU0,
+                m=m, rank=rank)
+
+
+def cd3d_128_8x8x4_ilu0_noshift():
+    """The same upwinded operator without the shift (definite, nonsymmetric):
+    the 128^3 system on which restarted FGMRES reaches 1e-8."""
+    return cd3d_128_8x8x4_ilu0(K=0)
 
 
 def kappa3d_48_3x3x3(N=48, splits=(3, 3, 3), m=3, rank=16, K=10):
@@ -113,6 +124,7 @@ WORKLOADS = {
     "batch2d_64sys": batch2d_64sys,
     "kappa3d_48_3x3x3": kappa3d_48_3x3x3,
     "cd3d_128_8x8x4_ilu0": cd3d_128_8x8x4_ilu0,
+    "cd3d_128_8x8x4_ilu0_noshift": cd3d_128_8x8x4_ilu0_noshift,
     "lap3d_50_shift014": lap3d_50_shift014,
     "rgg2d_20k": rgg2d_20k,
 }
