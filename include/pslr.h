@@ -86,6 +86,16 @@ typedef struct {
                              splits the breadth-first order of the set at
                              floor(|U| (k/2) / k)); for matrices without a grid,
                              standing in for the paper's METIS (Section 2)      */
+    int32_t merge_levels; /* layout of the triangular-sweep segments the apply
+                             streams: 0 = automatic (several consecutive levels
+                             of a factor per segment only where two CTAs share
+                             an SM and the shared-memory ring then holds fewer
+                             than six segments; one level per segment
+                             otherwise), 1 = always one level per segment,
+                             2 = always several levels per segment.  The result
+                             is the same, bit for bit, for every value; the
+                             layout changes only the copies that feed the
+                             sweeps                                             */
 } pslr_opts;
 
 typedef struct {
@@ -116,6 +126,8 @@ typedef struct {
     int64_t nnz_E, nnz_F, nnz_Cg;    /* stored entries of E, F and C_g (Eq. 2.1, 3.1) */
     double omega;         /* 1: PSLR; otherwise the scaling of the Sec. 1 Neumann
                              polynomial the context applies (pslr_set_neumann)    */
+    int32_t merged[2];    /* 1 where the sweep segments of that precision ([0]
+                             FP64, [1] FP32) hold several levels (merge_levels) */
 } pslr_info;
 
 /*

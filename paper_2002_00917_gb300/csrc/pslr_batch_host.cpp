@@ -266,6 +266,7 @@ void pack_prows(std::vector<char> &bytes, std::vector<SegDesc> &desc, const std:
     const int fmt = seg_fmt_for(w);
     h.fmt = (uint8_t)fmt;
     h.w = (uint8_t)(fmt != kTile ? fmt : w);
+    h.bytes = (uint32_t)nbytes;
     std::memcpy(base, &h, sizeof(h));
     base += sizeof(SegHdr);
     const int zero0 = rows[b].zero;
@@ -348,13 +349,30 @@ void merge_group(const pslr_batch *bt, int prec, const std::vector<char> &host, 
     for (int cat = 0; cat < kNCnt; ++cat) {
         const bool interior_rows = cat == kE || cat == kB1 || cat == kB2;
         const bool global = cat == kCg;
+        const bool sweep = cat >= kB1;
         std::vector<std::vector<StreamEnt>> segs(g.n);
         size_t nmax = 0;
         for (int t = 0; t < g.n; ++t) {
             sys_segments(bt->ctx[g.sys], prec, g.sub[t], cat, 0, segs[t]);
+            if (sweep) {  // a sweep segment holds consecutive levels: one entry per level block
+                std::vector<StreamEnt> blocks;
+                for (const StreamEnt &se : segs[t]) {
+                    for (int64_t off = se.off; off < se.off + se.bytes;) {
+                        SegHdr h;
+                        std::memcpy(&h, host.data() + off, sizeof h);
+                        StreamEnt b;
+                        b.off = off;
+                        b.bytes = (int32_t)h.bytes;
+                        b.pad = 0;
+                        blocks.push_back(b);
+                        if (!(h.flags & kSegMore) || h.bytes == 0) break;
+                        off += h.bytes;
+                    }
+                }
+                segs[t].swap(blocks);
+            }
             nmax = std::max(nmax, segs[t].size());
         }
-        const bool sweep = cat >= kB1;
         int cnt = 0;
         std::vector<PRow<T>> rows;
         bool diag = false;

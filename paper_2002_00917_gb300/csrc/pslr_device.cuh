@@ -98,6 +98,11 @@ __device__ __forceinline__ uint2 lds_u2(uint32_t a) {
     asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
     return v;
 }
+__device__ __forceinline__ uint4 lds_u4(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
 __device__ __forceinline__ float4 lds_f4(uint32_t a) {
     float4 v;
     asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
@@ -591,7 +596,7 @@ __device__ __forceinline__ Rec3<T> rec3_shared(uint32_t seg, int np, int j) {
     return e;
 }
 
-// One triangular sweep over `nseg` level segments, in place:
+// tri_sweep_levels: one triangular sweep over `nseg` one-level segments, in place:
 // x[r] = (x[r] - sum_k T_rk x[c_k]) (* dinv[r]).  The loop is kept to a few
 // instructions per level (the level chain is latency-bound with two warps per
 // scheduler, so every instruction costs): ring cursor in registers advanced
@@ -603,7 +608,7 @@ __device__ __forceinline__ Rec3<T> rec3_shared(uint32_t seg, int np, int j) {
 // then synchronising), which takes the mbarrier poll of 256 threads out of
 // every level step.
 template <class T>
-__device__ void tri_sweep(Cta<T> &c, T *x, int nseg, int *err) {
+__device__ void tri_sweep_levels(Cta<T> &c, T *x, int nseg, int *err) {
     Ring &R = c.ring;
     int slot = R.slot;
     uint32_t phase = R.phase;
@@ -651,6 +656,81 @@ __device__ void tri_sweep(Cta<T> &c, T *x, int nseg, int *err) {
     R.slot = slot;
     R.phase = phase;
     R.consumed += nseg;
+}
+
+// tri_sweep_blocks: the same sweep over `nseg` segments that each hold one or
+// more consecutive levels (blocks chained by kSegMore, each header giving the
+// block's size in bytes), one barrier step per block.  The arrival of the next
+// segment is awaited before the barrier of the current segment's last block,
+// and a segment's slot is released after its last block.  The rows of a block
+// are computed exactly as those of a one-level segment, so the result is the
+// same bit for bit.
+template <class T>
+__device__ void tri_sweep_blocks(Cta<T> &c, T *x, int nseg, int *err) {
+    Ring &R = c.ring;
+    int slot = R.slot;
+    uint32_t phase = R.phase;
+    uint32_t fbar = R.full_s + 8 * slot;
+    const uint32_t edelta = R.empty_s - R.full_s;
+    const uint32_t base_s = smem_addr(R.base);
+    uint32_t ptr_s = base_s + (uint32_t)(slot * R.slot_bytes);  // the segment's slot
+    uint32_t blk_s = ptr_s;                                       // the level block
+    const uint32_t xs = smem_addr(x);
+    const int j = threadIdx.x;
+    constexpr uint32_t ts = sizeof(T);
+    if (nseg > 0 && !mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
+    for (int L = 0; L < nseg;) {
+        const uint4 h = lds_u4(blk_s);
+        if (((h.y >> 16) & 0xffu) == kRec3) {
+            if (j < (int)(h.x & 0xffffu)) {
+                const Rec3<T> e = rec3_shared<T>(blk_s, (int)(h.y & 0xffffu), j);
+                const T x0 = lds(xs + ts * e.c0, T()), x1 = lds(xs + ts * e.c1, T());
+                const T x2 = lds(xs + ts * e.c2, T()), xr = lds(xs + ts * e.r, T());
+                T a = fma_t(-e.v0, x0, xr);
+                a = fma_t(-e.v1, x1, a);
+                a = fma_t(-e.v2, x2, a);
+                if ((h.x >> 24) & kSegDiag) a *= e.d;
+                sts(xs + ts * e.r, a);
+            }
+        } else {
+            level_row_general(R.base + (blk_s - base_s), x, j);
+        }
+        const bool more = (h.x >> 24) & kSegMore;
+        if (!more && j == kConsumers - 1 && L + 1 < nseg) {
+            const bool wrap = slot + 1 == R.slots;
+            const uint32_t nbar = wrap ? R.full_s : fbar + 8, nph = wrap ? phase ^ 1u : phase;
+            if (!mbar_try_wait(nbar, nph)) wait_full_slow(nbar, nph, err);
+        }
+        csync();
+        if (more) {
+            blk_s += h.z;
+            continue;
+        }
+        if (j == 0) mbar_arrive_cnt(fbar + edelta, kConsumerWarps);
+        ++L;
+        ++slot;
+        fbar += 8;
+        ptr_s += R.slot_bytes;
+        if (slot == R.slots) {
+            slot = 0;
+            phase ^= 1u;
+            fbar = R.full_s;
+            ptr_s = base_s;
+        }
+        blk_s = ptr_s;
+    }
+    R.slot = slot;
+    R.phase = phase;
+    R.consumed += nseg;
+}
+
+// One triangular sweep: one-level segments (the common layout: a tight loop
+// of one level per segment) or multi-level segments (merged where the ring is
+// shallow).  The form is a template parameter of the kernel.
+template <class T, bool kMerged>
+__device__ __forceinline__ void tri_sweep(Cta<T> &c, T *x, int nseg, int *err) {
+    if constexpr (kMerged) tri_sweep_blocks(c, x, nseg, err);
+    else tri_sweep_levels(c, x, nseg, err);
 }
 
 // Rows of an ELL segment in the general encodings (out of line).
@@ -732,12 +812,12 @@ __device__ void permute(T *x, T *tmp, const uint16_t *piv, int n, bool scatter) 
 }
 
 // Local solve x <- B_i~^{-1} x (or C0_i~^{-1}, or a transpose): two sweeps.
-template <class T>
+template <class T, bool kMerged>
 __device__ void solve_local(Cta<T> &c, T *x, int n, const uint16_t *piv, int pivot_post, int n1,
                             int n2, int *err) {
     if (piv && !pivot_post) permute(x, c.tmp, piv, n, false);
-    tri_sweep(c, x, n1, err);
-    tri_sweep(c, x, n2, err);
+    tri_sweep<T, kMerged>(c, x, n1, err);
+    tri_sweep<T, kMerged>(c, x, n2, err);
     if (piv && pivot_post) permute(x, c.tmp, piv, n, true);
 }
 

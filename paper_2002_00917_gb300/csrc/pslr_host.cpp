@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -30,17 +31,18 @@
 
 namespace pslr {
 // kernels (pslr_apply.cu, pslr_krylov.cu)
-cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, bool dual, cudaStream_t st);
-cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, bool dual, cudaStream_t st);
-cudaError_t launch_apply_f32d(const ApplyParams<float, double> &P, int smem, bool dual, cudaStream_t st);
-cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, bool dual, cudaStream_t st);
+cudaError_t launch_apply_fp64(const ApplyParams<double> &P, int smem, bool dual, bool merged, cudaStream_t st);
+cudaError_t launch_apply_fp32(const ApplyParams<float> &P, int smem, bool dual, bool merged, cudaStream_t st);
+cudaError_t launch_apply_f32d(const ApplyParams<float, double> &P, int smem, bool dual, bool merged,
+                              cudaStream_t st);
+cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, bool dual, bool merged, cudaStream_t st);
 
 // The persistent kernels' launchers set the kernel's dynamic shared-memory
 // limit and then launch; contexts applied from several host threads at once
 // (the batched solve finishing problems on their systems) must not interleave
 // these two steps, or one launch can meet another context's smaller limit.
 static std::mutex g_launch_mutex;
-int max_coresident_apply(int smem, bool fp32, bool dual);
+int max_coresident_apply(int smem, bool fp32, bool dual, bool merged);
 int krylov_blocks(int n);
 size_t krylov_part_doubles(int nblk, int nres);
 int krylov_tickets();
@@ -151,12 +153,17 @@ uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
     return h;
 }
 
+// pad128: the block's size is rounded up to 128 bytes (levels of a sweep, so
+// that every level block of a multi-level segment starts on a 128-byte row of
+// shared memory, as a slot does: the warps' record loads then touch no more
+// rows than they must).
 template <class T, class IDX>
-void pack_segment(SegStore &S, const std::vector<Row> &rows, size_t b, size_t e, bool diag, int zero_col) {
+void pack_segment(SegStore &S, const std::vector<Row> &rows, size_t b, size_t e, bool diag, int zero_col,
+                  bool pad128) {
     int n = (int)(e - b), w = 0;
     for (size_t i = b; i < e; ++i) w = std::max<int>(w, (int)rows[i].e.size());
     const int np = seg_npad(n);
-    const int64_t nbytes = seg_bytes<T, IDX>(n, w, diag);
+    const int64_t nbytes = pad128 ? align_up((int)seg_bytes<T, IDX>(n, w, diag), 128) : seg_bytes<T, IDX>(n, w, diag);
     SegDesc d;
     d.off = (int64_t)S.bytes.size();
     d.bytes = (int32_t)nbytes;
@@ -171,6 +178,7 @@ void pack_segment(SegStore &S, const std::vector<Row> &rows, size_t b, size_t e,
     const int fmt = seg_fmt_for(w);
     h.fmt = (uint8_t)fmt;
     if (fmt != kTile) h.w = (uint8_t)fmt;
+    h.bytes = (uint32_t)nbytes;
     std::memcpy(base, &h, sizeof(h));
     base += sizeof(SegHdr);
     if (fmt != kTile) {
@@ -216,7 +224,7 @@ void pack_segment(SegStore &S, const std::vector<Row> &rows, size_t b, size_t e,
 // Split a row list into segments within kSegBudget bytes / kSegMaxRows rows.
 // Returns the number of segments appended (an empty list appends none).
 template <class T, class IDX>
-int pack_rows(SegStore &S, const std::vector<Row> &rows, bool diag, int zero_col) {
+int pack_rows(SegStore &S, const std::vector<Row> &rows, bool diag, int zero_col, bool pad128 = false) {
     int cnt = 0;
     size_t b = 0;
     while (b < rows.size()) {
@@ -224,15 +232,40 @@ int pack_rows(SegStore &S, const std::vector<Row> &rows, bool diag, int zero_col
         int w = 0;
         while (e < rows.size() && (int)(e - b) < kSegMaxRows) {
             int w2 = std::max<int>(w, (int)rows[e].e.size());
-            if (e > b && seg_bytes<T, IDX>((int)(e - b + 1), w2, diag) > kSegBudget) break;
+            if (e > b && align_up((int)seg_bytes<T, IDX>((int)(e - b + 1), w2, diag), pad128 ? 128 : 1) > kSegBudget)
+                break;
             w = w2;
             ++e;
         }
-        pack_segment<T, IDX>(S, rows, b, e, diag, zero_col);
+        pack_segment<T, IDX>(S, rows, b, e, diag, zero_col, pad128);
         ++cnt;
         b = e;
     }
     return cnt;
+}
+
+// Merge the one-level segments S.desc[d0..] of a sweep, which lie back to
+// back in the store, into segments of consecutive levels of at most `budget`
+// bytes (every block but a segment's last flagged kSegMore).  Returns the
+// number of segments.
+int merge_levels(SegStore &S, size_t d0, int budget) {
+    std::vector<SegDesc> out;
+    for (size_t d = d0; d < S.desc.size();) {
+        SegDesc c = S.desc[d];
+        size_t e = d + 1;
+        while (e < S.desc.size() && c.bytes + S.desc[e].bytes <= budget &&
+               S.desc[e].off == S.desc[e - 1].off + S.desc[e - 1].bytes) {
+            S.bytes[(size_t)S.desc[e - 1].off + offsetof(SegHdr, flags)] |= (char)kSegMore;
+            c.bytes += S.desc[e].bytes;
+            ++e;
+        }
+        S.max_bytes = std::max<int>(S.max_bytes, c.bytes);
+        out.push_back(c);
+        d = e;
+    }
+    S.desc.resize(d0);
+    S.desc.insert(S.desc.end(), out.begin(), out.end());
+    return (int)out.size();
 }
 
 // Level schedule of a triangular sweep: lower (deps on smaller columns,
@@ -513,7 +546,8 @@ struct OpSetHost {
     int64_t cat_bytes[kNCnt] = {0, 0, 0, 0, 0, 0, 0};  // segment bytes per category, all subdomains
     int smem = 0;
     int grid = 0;
-    bool dual = false;                   // two CTAs per SM (FP32 forms, more subdomains than SMs)
+    bool dual = false;                   // two CTAs per SM (more subdomains than SMs)
+    bool merged = false;                 // sweep segments hold several levels
     std::map<std::string, StreamDev> streams;  // keyed by launch shape
 };
 
@@ -549,6 +583,7 @@ struct pslr_ctx {
     int m = 0, r = 0;
     uint64_t lr_gen = 0;         // incremented whenever the low-rank term is replaced
     double omega = 1.0;          // 1: PSLR; otherwise the Sec. 1 Neumann polynomial (pslr_set_neumann)
+    int merge_levels = 0;        // pslr_opts::merge_levels
     std::vector<double> V, H, G;
     double *d_V = nullptr;       // q x r FP64 (leading dimension q)
     // the copies the apply reads: row-major, row stride ldv = r rounded up to 8, zero padded
@@ -656,10 +691,18 @@ struct Local {
 // The segments of subdomain i in one direction, in the order
 // [E, F, Cg, B1, B2, C1, C2] (transposed: Cg left empty, inserted later),
 // into its own store; k receives the kNCnt segment counts.
+// Sweep levels are merged into segments no larger than the largest one-level
+// segment of the precision (a full level of 3-entry records in FP64, a
+// 256-row slice of a product with global columns in FP32), so merging does
+// not enlarge the ring's slots.
+template <class T>
+constexpr int merge_budget() { return sizeof(T) == 8 ? kSegBudget : 8 * 1024; }
+
 template <class T>
 void pack_subdomain(const Local &Lc, int npi, int nqi, bool transposed, int q, SegStore &S, int *k, int &levB,
-                    int &levC) {
+                    int &levC, bool merge) {
     levB = levC = 0;
+    const int budget = merge ? merge_budget<T>() : 0;  // budget 0: one level per segment
     if (!transposed) {
         k[kE] = pack_rows<T, uint16_t>(S, ell_rows(Lc.E), false, nqi);
         k[kF] = pack_rows<T, uint16_t>(S, ell_rows(Lc.F), false, npi);
@@ -668,10 +711,18 @@ void pack_subdomain(const Local &Lc, int npi, int nqi, bool transposed, int q, S
         auto lc = levels(Lc.CL, true), uc = levels(Lc.CU, false);
         levB = (int)(lb.size() + ub.size());
         levC = (int)(lc.size() + uc.size());
-        for (auto &lv : lb) k[kB1] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.BL, lv, true, false), false, npi);
-        for (auto &lv : ub) k[kB2] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.BU, lv, false, true), true, npi);
-        for (auto &lv : lc) k[kC1] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.CL, lv, true, false), false, nqi);
-        for (auto &lv : uc) k[kC2] += pack_rows<T, uint16_t>(S, sweep_rows(Lc.CU, lv, false, true), true, nqi);
+        size_t d0 = S.desc.size();
+        for (auto &lv : lb) pack_rows<T, uint16_t>(S, sweep_rows(Lc.BL, lv, true, false), false, npi, merge);
+        k[kB1] = merge_levels(S, d0, budget);
+        d0 = S.desc.size();
+        for (auto &lv : ub) pack_rows<T, uint16_t>(S, sweep_rows(Lc.BU, lv, false, true), true, npi, merge);
+        k[kB2] = merge_levels(S, d0, budget);
+        d0 = S.desc.size();
+        for (auto &lv : lc) pack_rows<T, uint16_t>(S, sweep_rows(Lc.CL, lv, true, false), false, nqi, merge);
+        k[kC1] = merge_levels(S, d0, budget);
+        d0 = S.desc.size();
+        for (auto &lv : uc) pack_rows<T, uint16_t>(S, sweep_rows(Lc.CU, lv, false, true), true, nqi, merge);
+        k[kC2] = merge_levels(S, d0, budget);
     } else {
         // E-slot: F_i^T (interior rows <- interface cols); F-slot: E_i^T.
         k[kE] = pack_rows<T, uint16_t>(S, ell_rows(transpose(Lc.F)), false, nqi);
@@ -682,10 +733,18 @@ void pack_subdomain(const Local &Lc, int npi, int nqi, bool transposed, int q, S
         Csr CUt = transpose(Lc.CU), CLt = transpose(Lc.CL);
         auto l1 = levels(BUt, true), l2 = levels(BLt, false);
         auto l3 = levels(CUt, true), l4 = levels(CLt, false);
-        for (auto &lv : l1) k[kB1] += pack_rows<T, uint16_t>(S, sweep_rows(BUt, lv, true, true), true, npi);
-        for (auto &lv : l2) k[kB2] += pack_rows<T, uint16_t>(S, sweep_rows(BLt, lv, false, false), false, npi);
-        for (auto &lv : l3) k[kC1] += pack_rows<T, uint16_t>(S, sweep_rows(CUt, lv, true, true), true, nqi);
-        for (auto &lv : l4) k[kC2] += pack_rows<T, uint16_t>(S, sweep_rows(CLt, lv, false, false), false, nqi);
+        size_t d0 = S.desc.size();
+        for (auto &lv : l1) pack_rows<T, uint16_t>(S, sweep_rows(BUt, lv, true, true), true, npi, merge);
+        k[kB1] = merge_levels(S, d0, budget);
+        d0 = S.desc.size();
+        for (auto &lv : l2) pack_rows<T, uint16_t>(S, sweep_rows(BLt, lv, false, false), false, npi, merge);
+        k[kB2] = merge_levels(S, d0, budget);
+        d0 = S.desc.size();
+        for (auto &lv : l3) pack_rows<T, uint16_t>(S, sweep_rows(CUt, lv, true, true), true, nqi, merge);
+        k[kC1] = merge_levels(S, d0, budget);
+        d0 = S.desc.size();
+        for (auto &lv : l4) pack_rows<T, uint16_t>(S, sweep_rows(CLt, lv, false, false), false, nqi, merge);
+        k[kC2] = merge_levels(S, d0, budget);
     }
 }
 
@@ -698,7 +757,7 @@ void pack_subdomain(const Local &Lc, int npi, int nqi, bool transposed, int q, S
 template <class T>
 bool pack_direction(const std::vector<Local> &loc, const std::vector<int> &np, const std::vector<int> &nq,
                     bool transposed, int q, const std::vector<Csr> *cgT, int threads, SegStore &S,
-                    std::vector<int32_t> &sub_desc, std::vector<int32_t> &cnt, int &levB, int &levC) {
+                    std::vector<int32_t> &sub_desc, std::vector<int32_t> &cnt, int &levB, int &levC, bool merge) {
     const int s = (int)loc.size();
     sub_desc.assign(s, 0);
     cnt.assign((size_t)kNCnt * s, 0);
@@ -706,7 +765,7 @@ bool pack_direction(const std::vector<Local> &loc, const std::vector<int> &np, c
     std::vector<int> lb(s, 0), lc(s, 0);
     bool ok = parallel_for(s, threads, [&](int i) {
         int *k = &cnt[(size_t)kNCnt * i];
-        pack_subdomain<T>(loc[i], np[i], nq[i], transposed, q, part[i], k, lb[i], lc[i]);
+        pack_subdomain<T>(loc[i], np[i], nq[i], transposed, q, part[i], k, lb[i], lc[i], merge);
         if (transposed) k[kCg] = pack_rows<T, int32_t>(pcg[i], ell_rows((*cgT)[i]), false, q);
     });
     if (!ok) return false;
@@ -762,7 +821,8 @@ bool pack_direction(const std::vector<Local> &loc, const std::vector<int> &np, c
 //    run through the segments without a barrier);
 //  - a triangular sweep writes every row of its block exactly once, and each
 //    row reads only rows written at an earlier barrier step of the same sweep
-//    (one segment is one barrier step), so no two threads race.
+//    (one block of a segment is one barrier step), so no two threads race;
+//  - a segment's blocks fill it exactly, and only sweeps chain blocks.
 template <class T>
 static int64_t check_layout(const pslr_ctx *c, const SegStore &S, const std::vector<int32_t> &sub_desc,
                             const std::vector<int32_t> &cnt, std::string *first) {
@@ -784,24 +844,37 @@ static int64_t check_layout(const pslr_ctx *c, const SegStore &S, const std::vec
             const int ncols = cat == kE ? nq : cat == kF ? np : cat == kCg ? c->q : nrows;  // also the zero slot
             step.assign((size_t)nrows, -1);
             const int nseg = cnt[(size_t)kNCnt * i + cat];
+            int stepno = 0;  // barrier steps so far: one per block
             for (int t = 0; t < nseg; ++t, ++d) {
                 const SegDesc &sd = S.desc[d];
                 if (sd.off < 0 || sd.off + sd.bytes > (int64_t)S.bytes.size() || sd.bytes < (int)sizeof(SegHdr)) {
                     note("segment outside the store", i, cat);
                     continue;
                 }
-                const char *base = S.bytes.data() + sd.off;
+                int64_t boff = 0;
+                for (;; ++stepno) {
+                if (boff + (int64_t)sizeof(SegHdr) > sd.bytes) {
+                    note("a segment's blocks run past its end", i, cat);
+                    break;
+                }
+                const char *base = S.bytes.data() + sd.off + boff;
                 SegHdr h;
                 std::memcpy(&h, base, sizeof h);
                 const bool global = (h.flags & kSegGlobalCols) != 0, diag = (h.flags & kSegDiag) != 0;
+                const bool more = (h.flags & kSegMore) != 0;
                 const int n = h.n, pn = h.np, fmt = h.fmt;
                 const int w = fmt == kTile ? h.w : fmt;
-                const int64_t want = global ? seg_bytes<T, int32_t>(n, w, diag) : seg_bytes<T, uint16_t>(n, w, diag);
+                const int64_t raw = global ? seg_bytes<T, int32_t>(n, w, diag) : seg_bytes<T, uint16_t>(n, w, diag);
+                // levels of merged sweep segments are padded to 128 bytes
+                const int64_t want = sweep && (int64_t)h.bytes == align_up((int)raw, 128) ? align_up((int)raw, 128) : raw;
                 if (n < 1 || n > kSegMaxRows || pn != seg_npad(n) || global != (cat == kCg) ||
-                    (fmt != kTile && fmt != kRec3 && fmt != kRec7) || seg_fmt_for(w) != fmt || want != sd.bytes) {
+                    (fmt != kTile && fmt != kRec3 && fmt != kRec7) || seg_fmt_for(w) != fmt ||
+                    want != (int64_t)h.bytes || boff + want > sd.bytes || (more && !sweep) ||
+                    (!more && boff + want != sd.bytes)) {
                     note("inconsistent segment header", i, cat);
-                    continue;
+                    break;
                 }
+                const int tstep = sweep ? stepno : t;
                 auto idx = [&](size_t k) -> int {
                     if (global) {
                         int32_t x;
@@ -813,7 +886,7 @@ static int64_t check_layout(const pslr_ctx *c, const SegStore &S, const std::vec
                     return x;
                 };
                 const size_t isz = global ? 4 : 2;
-                std::vector<std::pair<int, int>> writes;  // (row, step) applied after the segment
+                std::vector<std::pair<int, int>> writes;  // (row, step) applied after the block
                 for (int j = 0; j < n; ++j) {
                     int row;
                     if (fmt != kTile) {
@@ -847,15 +920,21 @@ static int64_t check_layout(const pslr_ctx *c, const SegStore &S, const std::vec
                         }
                         if (col < 0 || col > ncols) {
                             note("column out of range", i, cat);
-                        } else if (sweep && col < ncols && (step[col] < 0 || step[col] >= t)) {
+                        } else if (sweep && col < ncols && (step[col] < 0 || step[col] >= tstep)) {
                             note("a sweep row reads a row not written at an earlier step", i, cat);
                         }
                     }
-                    writes.push_back({row, t});
+                    writes.push_back({row, tstep});
                 }
                 for (auto &wr : writes) {
                     if (step[wr.first] >= 0) note(sweep ? "a sweep writes a row twice" : "a product writes a row twice", i, cat);
                     step[wr.first] = wr.second;
+                }
+                if (!more) {
+                    ++stepno;
+                    break;
+                }
+                boff += want;
                 }
             }
             if (sweep)
@@ -993,14 +1072,15 @@ static pslr_status plan_launch(pslr_ctx *c) {
         shape(optin, ring, &smem);
         if (std::min(ring[0], ring[1]) < 2)
             return fail(c, PSLR_ERR_TOO_LARGE, "a subdomain needs more shared memory than one CTA has");
-        int cap = max_coresident_apply(smem, prec == 1, false);
+        const bool merged = c->ops[0][prec].merged;  // the same for both directions
+        int cap = max_coresident_apply(smem, prec == 1, false, merged);
         if (cap <= 0) return fail(c, PSLR_ERR_CUDA, "persistent kernel cannot be made resident");
         bool dual = false;
         if (c->s > cap) {
             int ring2[2], smem2 = 0;
             shape(per_sm / 2, ring2, &smem2);
             if (std::min(ring2[0], ring2[1]) >= kMinDualRing) {
-                const int cap2 = max_coresident_apply(smem2, prec == 1, true);
+                const int cap2 = max_coresident_apply(smem2, prec == 1, true, merged);
                 if (cap2 > cap) {
                     dual = true;
                     cap = cap2;
@@ -1043,6 +1123,9 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
     if (opts->factor == 2 && !(opts->drop_tol >= 0.0 && std::isfinite(opts->drop_tol)))
         return bail(fail(c, PSLR_ERR_ARG, "ILUT needs a finite drop tolerance >= 0"));
     c->drop_tol = opts->drop_tol;
+    if (opts->merge_levels < 0 || opts->merge_levels > 2)
+        return bail(fail(c, PSLR_ERR_ARG, "merge_levels must be 0, 1 or 2"));
+    c->merge_levels = opts->merge_levels;
     if (opts->setup_threads < 0) return bail(fail(c, PSLR_ERR_ARG, "setup_threads must be >= 0"));
     if (opts->setup_threads > 0) {
         c->threads = opts->setup_threads;
@@ -1270,6 +1353,30 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
             }
         }
     }
+    // Sweep levels are merged into multi-level segments only where the ring
+    // will be shallow: with more subdomains than SMs the kernels run two CTAs
+    // per SM, and if that leaves room for fewer than kMergeBelowSlots segments
+    // of kSegBudget bytes, one bulk copy per level cannot keep ahead of the
+    // sweeps (128^3 FP64: 1025 -> 947 us merged).  With a deep ring one level
+    // per segment is faster (the per-level bookkeeping of merged segments
+    // costs ~8% at 64^3).  Without a device (pslr_plan) the GB300's counts
+    // stand in.
+    bool merge[2] = {false, false};
+    {
+        int nsm = 152, per_sm = 233472;
+        if (!plan_only) {
+            int dev = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            CK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        }
+        for (int prec = 0; prec < 2; ++prec) {
+            const int ts = prec == 0 ? 8 : 4;
+            const int avail = per_sm / 2 - 1024 - smem_fixed(c->max_p, c->max_q, ts, c->factor == 1, red_stride(0), true);
+            merge[prec] = c->merge_levels == 2 ||
+                          (c->merge_levels == 0 && c->s > nsm && avail < kMergeBelowSlots * kSegBudget);
+        }
+    }
     for (int dir = 0; dir < 2; ++dir)
         for (int prec = 0; prec < 2; ++prec) {
             SegStore S;
@@ -1277,11 +1384,14 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
             int lb = 0, lc = 0;
             pslr_status st;
             bool ok;
+            c->ops[dir][prec].merged = merge[prec];
             if (prec == 0) {
-                ok = pack_direction<double>(L, np, nq, dir == 1, c->q, &cgT, threads, S, sub_desc, cnt, lb, lc);
+                ok = pack_direction<double>(L, np, nq, dir == 1, c->q, &cgT, threads, S, sub_desc, cnt, lb, lc,
+                                            merge[0]);
                 st = ok ? finish_opset<double>(c, c->ops[dir][prec], S, sub_desc, cnt, false, plan_only) : PSLR_OK;
             } else {
-                ok = pack_direction<float>(L, np, nq, dir == 1, c->q, &cgT, threads, S, sub_desc, cnt, lb, lc);
+                ok = pack_direction<float>(L, np, nq, dir == 1, c->q, &cgT, threads, S, sub_desc, cnt, lb, lc,
+                                           merge[1]);
                 st = ok ? finish_opset<float>(c, c->ops[dir][prec], S, sub_desc, cnt, true, plan_only) : PSLR_OK;
             }
             if (!ok) return bail(fail(c, PSLR_ERR_ARG, "host set-up failed while packing (out of memory?)"));
@@ -1500,21 +1610,21 @@ static pslr_status apply_launch(pslr_ctx *c, const void *b, void *z, int form, i
         P.V = c->d_Vr;
         P.G = dir ? c->d_GT : c->d_G;
         set_io(P, b, z, skip, scr);
-        e = launch_apply_fp64(P, o.smem, o.dual, st);
+        e = launch_apply_fp64(P, o.smem, o.dual, o.merged, st);
     } else if (form == PSLR_FP32) {
         ApplyParams<float> P;
         fill_params(c, P, dir, prec, sd);
         P.V = c->d_Vb;
         P.G = dir ? c->d_GTf : c->d_Gf;
         set_io(P, b, z, skip, scr);
-        e = launch_apply_fp32(P, o.smem, o.dual, st);
+        e = launch_apply_fp32(P, o.smem, o.dual, o.merged, st);
     } else {
         ApplyParams<float, double> P;
         fill_params(c, P, dir, prec, sd);
         P.V = c->d_Vb;
         P.G = dir ? c->d_GTf : c->d_Gf;
         set_io(P, b, z, skip, scr);
-        e = launch_apply_f32d(P, o.smem, o.dual, st);
+        e = launch_apply_f32d(P, o.smem, o.dual, o.merged, st);
     }
     if (e != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "apply launch: %s", cudaGetErrorString(e));
     return PSLR_OK;
@@ -1710,6 +1820,7 @@ pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info) {
         I.grid[prec] = c->ops[0][prec].grid;
         I.ring[prec] = c->ops[0][prec].ring;
         I.ctas_per_sm[prec] = c->ops[0][prec].dual ? 2 : 1;
+        I.merged[prec] = c->ops[0][prec].merged ? 1 : 0;
     }
     *info = I;
     return PSLR_OK;
@@ -1952,7 +2063,7 @@ static pslr_status launch_err(pslr_ctx *c, const double *vin, double *vout, int 
     cudaError_t e;
     {
         std::lock_guard<std::mutex> lock(g_launch_mutex);
-        e = launch_err_fp64(P, o.smem, o.dual, st);
+        e = launch_err_fp64(P, o.smem, o.dual, o.merged, st);
     }
     if (e != cudaSuccess) return fail(c, PSLR_ERR_CUDA, "E_rr launch: %s", cudaGetErrorString(e));
     return PSLR_OK;

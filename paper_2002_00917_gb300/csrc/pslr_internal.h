@@ -19,6 +19,13 @@
 // The zero slot is index n_local of the shared-memory vector (or q for the
 // global interface vector), which always holds 0.
 //
+// A triangular sweep's segment may hold several consecutive levels: blocks of
+// the form above, one after the other, every block but the last flagged
+// kSegMore, each with its own header and byte size.  Each block is one
+// barrier step of the sweep; the segment is one ring slot and one bulk copy.
+// Copying a segment costs the producer about as long as a level step, so
+// packing levels together (up to kSegBudget bytes) keeps it ahead.
+//
 // For every launch the host lays out, per CTA, the exact sequence of segments
 // its consumers will use (the "stream").  A producer warp walks the stream and
 // copies each segment into a shared-memory ring with a TMA bulk copy as soon
@@ -40,9 +47,10 @@ constexpr int kSegMaxRows = kConsumers;     // rows per segment
 constexpr int kSegBudget = 12 * 1024;       // bytes per segment (one ring slot at most)
 constexpr int kMaxRing = 32;                // ring slots at most
 constexpr int kMinDualRing = 3;             // ring slots at least when two CTAs share an SM
+constexpr int kMergeBelowSlots = 6;         // merge sweep levels when a two-CTA ring holds fewer slots
 constexpr int kMaxRank = 128;               // largest low-rank term
 
-enum SegFlags : uint32_t { kSegDiag = 1u, kSegGlobalCols = 2u };
+enum SegFlags : uint32_t { kSegDiag = 1u, kSegGlobalCols = 2u, kSegMore = 4u };
 enum SegFmt : uint8_t { kTile = 0, kRec3 = 3, kRec7 = 7 };
 
 struct SegHdr {
@@ -52,7 +60,8 @@ struct SegHdr {
     uint16_t np;     // padded rows
     uint8_t fmt;     // SegFmt
     uint8_t pad0;
-    uint32_t pad1, pad2;
+    uint32_t bytes;  // byte size of this block
+    uint32_t pad2;
 };
 static_assert(sizeof(SegHdr) == 16, "SegHdr is 16 bytes");
 

@@ -37,7 +37,7 @@ PSLR_FP32 = 1
 class pslr_opts(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("splits", C.c_int32 * 3), ("part", C.c_void_p),
                 ("factor", C.c_int32), ("seed", C.c_uint64), ("drop_tol", C.c_double),
-                ("setup_threads", C.c_int32), ("nparts", C.c_int32)]
+                ("setup_threads", C.c_int32), ("nparts", C.c_int32), ("merge_levels", C.c_int32)]
 
 
 class pslr_info(C.Structure):
@@ -50,11 +50,12 @@ class pslr_info(C.Structure):
                 ("layout_hash", C.c_uint64), ("setup_threads", C.c_int32), ("layout_errors", C.c_int64),
                 ("grid", C.c_int32 * 2), ("ring", C.c_int32 * 2), ("ctas_per_sm", C.c_int32 * 2),
                 ("nnz_fact_B", C.c_int64), ("nnz_fact_C0", C.c_int64), ("nnz_E", C.c_int64),
-                ("nnz_F", C.c_int64), ("nnz_Cg", C.c_int64), ("omega", C.c_double)]
+                ("nnz_F", C.c_int64), ("nnz_Cg", C.c_int64), ("omega", C.c_double),
+                ("merged", C.c_int32 * 2)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
-        for k in ("grid", "ring", "ctas_per_sm"):
+        for k in ("grid", "ring", "ctas_per_sm", "merged"):
             d[k] = list(getattr(self, k))
         return d
 
@@ -155,10 +156,12 @@ class Pslr:
     all hardware threads); the context is the same for every value.
     ``nparts`` > 0 with ``dims`` all zero and no ``part``: the library's graph
     partition (recursive breadth-first bisection) into that many subdomains.
+    ``merge_levels``: sweep segment layout, 0 automatic, 1 one level per
+    segment, 2 several levels per segment (same result, bit for bit).
     """
 
     def __init__(self, A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, seed=0,
-                 stream=None, drop_tol=0.0, setup_threads=0, nparts=0):
+                 stream=None, drop_tol=0.0, setup_threads=0, nparts=0, merge_levels=0):
         lib = load()
         self.lib = lib
         self.n = int(A.n)
@@ -176,6 +179,7 @@ class Pslr:
         o.drop_tol = float(drop_tol)
         o.setup_threads = int(setup_threads)
         o.nparts = int(nparts)
+        o.merge_levels = int(merge_levels)
         self.factor, self.drop_tol = int(factor), float(drop_tol)
         h = C.c_void_p()
         st = lib.pslr_setup(self.n, self._rp.ctypes.data, self._ci.ctypes.data, self._av.ctypes.data,
@@ -413,7 +417,7 @@ class Batch:
         return self.lib.pslr_batch_set_wait_limit(self.h, int(polls))
 
 
-def _opts(dims, splits, part, factor, seed, drop_tol=0.0, setup_threads=0, nparts=0):
+def _opts(dims, splits, part, factor, seed, drop_tol=0.0, setup_threads=0, nparts=0, merge_levels=0):
     o = pslr_opts()
     for d in range(3):
         o.dims[d] = int(dims[d])
@@ -424,11 +428,12 @@ def _opts(dims, splits, part, factor, seed, drop_tol=0.0, setup_threads=0, npart
     o.drop_tol = float(drop_tol)
     o.setup_threads = int(setup_threads)
     o.nparts = int(nparts)
+    o.merge_levels = int(merge_levels)
     return o
 
 
 def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, drop_tol=0.0, setup_threads=0,
-         nparts=0):
+         nparts=0, merge_levels=0):
     """Host-only dry run of the set-up (no GPU needed): returns (info dict,
     part, is_interface, perm) exactly as a device context would report them."""
     lib = load()
@@ -436,7 +441,7 @@ def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, 
     ci = np.ascontiguousarray(A.col, dtype=np.int32)
     av = np.ascontiguousarray(A.val, dtype=np.float64)
     pa = None if part is None else np.ascontiguousarray(part, dtype=np.int32)
-    o = _opts(dims, splits, pa, factor, 0, drop_tol, setup_threads, nparts)
+    o = _opts(dims, splits, pa, factor, 0, drop_tol, setup_threads, nparts, merge_levels)
     info = pslr_info()
     n = int(A.n)
     mp = [np.empty(n, np.int32) for _ in range(3)]
@@ -447,7 +452,8 @@ def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, 
     return (info.as_dict(), *mp)
 
 
-def from_workload(w, seed=0, stream=None):
+def from_workload(w, seed=0, stream=None, merge_levels=0):
     """Context for a workload dict of ``pslr_inputs.configs``."""
     return Pslr(w["A"], dims=w.get("dims", (0, 0, 0)), splits=w.get("splits", (1, 1, 1)), factor=w["factor"],
-                seed=seed, stream=stream, drop_tol=w.get("drop_tol", 0.0), nparts=w.get("nparts", 0))
+                seed=seed, stream=stream, drop_tol=w.get("drop_tol", 0.0), nparts=w.get("nparts", 0),
+                merge_levels=merge_levels)

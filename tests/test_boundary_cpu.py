@@ -109,16 +109,17 @@ def test_plan_rejects_bad_input(pslr):
                                                      ("cd", (12, 11, 10), (3, 2, 2), 2),
                                                      ("lap", (32, 32), (2, 2), 1),
                                                      ("kappa", (10, 9, 11), (2, 3, 2), 0)])
-def test_setup_threads_do_not_change_the_layout(pslr, kind, dims, splits, factor):
+@pytest.mark.parametrize("merge_levels", [0, 2])
+def test_setup_threads_do_not_change_the_layout(pslr, kind, dims, splits, factor, merge_levels):
     """The set-up runs per subdomain on host threads; the packed device layout
     of both directions and precisions (its hash over every byte, descriptor
     and count), the fill and the levels are the same for 1, 2, 5 and all
-    threads."""
+    threads, with one level per sweep segment and with several."""
     w = C.small_problem(kind, dims, splits, factor=factor, drop_tol=1e-2)
     infos = []
     for t in (1, 2, 5, 0):
         info, part, iface, perm = pslr.plan(w["A"], w["dims"], w["splits"], factor=factor, m=3, rank=4,
-                                            drop_tol=1e-2, setup_threads=t)
+                                            drop_tol=1e-2, setup_threads=t, merge_levels=merge_levels)
         assert info["setup_threads"] == (t if t else info["setup_threads"]) and info["setup_threads"] >= 1
         infos.append(({k: v for k, v in info.items() if k != "setup_threads"}, perm.tobytes()))
     assert infos[0][0]["layout_hash"] != 0
@@ -175,14 +176,43 @@ def test_graph_partition_bit_exact_with_oracle(pslr, graph, k):
                                                      ("cd", (12, 10, 8), (3, 2, 2), 2), ("kappa", (10, 9, 11), (2, 3, 2), 0),
                                                      ("lap", (40, 33), (3, 4), 0), ("cd", (9, 9, 9), (1, 1, 1), 0),
                                                      ("lap", (7, 6, 5), (7, 6, 5), 0), ("lap", (13, 11, 9), (3, 2, 2), 2)])
-def test_layout_check_finds_no_violation(pslr, kind, dims, splits, factor):
+@pytest.mark.parametrize("merge_levels", [0, 2])
+def test_layout_check_finds_no_violation(pslr, kind, dims, splits, factor, merge_levels):
     """The host-side decode of every packed segment (both directions, both
     precisions) finds every index in range, no product writing a row twice,
     and every sweep row reading only rows written at an earlier barrier
-    step: the level schedules the kernels run are race-free."""
+    step: the level schedules the kernels run are race-free.  The same holds
+    for sweep segments that carry several levels (merge_levels = 2), whose
+    blocks must also fill their segment exactly."""
     w = C.small_problem(kind, dims, splits, factor=factor, drop_tol=1e-2)
-    info = pslr.plan(w["A"], w["dims"], w["splits"], factor=factor, m=3, rank=4, drop_tol=1e-2)[0]
+    info = pslr.plan(w["A"], w["dims"], w["splits"], factor=factor, m=3, rank=4, drop_tol=1e-2,
+                     merge_levels=merge_levels)[0]
     assert info["layout_errors"] == 0
+    assert info["merged"] == [int(merge_levels == 2)] * 2
+
+
+def test_merge_levels_option(pslr):
+    """Automatic merging only where the ring is shallow: the 128^3
+    convection-diffusion problem (256 subdomains, two CTAs per SM) merges its
+    FP64 sweeps and not its FP32 ones; the 64^3 Laplacian (32 subdomains)
+    merges neither.  Forcing either layout keeps the decode clean and changes
+    the packed bytes; the maps are the same."""
+    w = C.WORKLOADS["cd3d_128_8x8x4_ilu0"]()
+    kw = dict(factor=w["factor"], m=w["m"], rank=w["rank"])
+    got = {ml: pslr.plan(w["A"], w["dims"], w["splits"], merge_levels=ml, **kw) for ml in (0, 1, 2)}
+    assert [got[ml][0]["merged"] for ml in (0, 1, 2)] == [[1, 0], [0, 0], [1, 1]]
+    assert all(got[ml][0]["layout_errors"] == 0 for ml in (0, 1, 2))
+    assert len({got[ml][0]["layout_hash"] for ml in (0, 1, 2)}) == 3
+    for ml in (1, 2):
+        assert all(np.array_equal(a, b) for a, b in zip(got[0][1:], got[ml][1:]))
+    w = C.lap3d_64_4x4x2_ilu0()
+    info = pslr.plan(w["A"], w["dims"], w["splits"], factor=w["factor"], m=w["m"], rank=w["rank"])[0]
+    assert info["merged"] == [0, 0]
+    A = G.shifted_laplacian((12, 10), 0.1)
+    for ml in (-1, 3):
+        with pytest.raises(pslr.PslrError) as e:
+            pslr.plan(A, (12, 10, 1), (2, 2, 1), merge_levels=ml)
+        assert e.value.status == pslr.PSLR_ERR_ARG
 
 
 @pytest.mark.parametrize("name", ["lap3d_64_4x4x2_ilu0", "kappa3d_48_3x3x3", "lap3d_50_shift014", "rgg2d_20k"])
