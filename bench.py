@@ -534,6 +534,124 @@ def run_secondary(name, dev, flush, stream, steps, warmup, peak, budget_s, fgmre
     return out
 
 
+def run_lowrank_phase(args):
+    """Apply times with the low-rank term of Eq. 3.18 as built (the batch:
+    ranks 8/16/32 from the Arnoldi process; 128^3: r = 32), replaced by a
+    seeded orthonormal V of rank 32 and of rank 1, and removed (r = 0).  r = 1
+    keeps the phase's grid barriers and reductions with almost no arithmetic,
+    so (r32 - r1) is the part a faster product (tensor cores) could shorten and
+    (r1 - r0) the synchronisation.  L2 flushed before each timed apply."""
+    import numpy as np
+    import torch
+
+    from paper_2002_00917_gb300 import build as B
+    from paper_2002_00917_gb300 import pslr
+    from pslr_inputs import configs as C
+
+    B.build()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps=15):
+        ts = []
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        return round(float(np.median(ts)), 1)
+
+    rng = np.random.default_rng(1)
+
+    def set_rank(ctx, m, r):
+        if r:
+            q = ctx.info["q"]
+            ctx.set_lowrank(m, np.linalg.qr(rng.standard_normal((q, r)))[0], rng.uniform(-0.01, 0.01, (r, r)))
+        else:
+            ctx.set_lowrank(m)
+
+    out = {"probe": "lowrank_phase", "unit": "us per apply"}
+    w = C.batch2d_64sys()
+    ctxs, ms = [], []
+    for sy in w["systems"]:
+        c = pslr.Pslr(sy["A"], dims=sy["dims"], splits=sy["splits"], factor=sy["factor"])
+        c.build_lowrank(sy["m"], sy["rank"])
+        ctxs.append(c)
+        ms.append(sy["m"])
+    res = {}
+    for tag, r in (("built", None), ("r32", 32), ("r1", 1), ("r0", 0)):
+        if r is not None:
+            for c, m in zip(ctxs, ms):
+                set_rank(c, m, r)
+        bt = pslr.Batch(ctxs, w["nrhs"])
+        b = torch.tensor(np.random.default_rng(0).uniform(-1, 1, bt.info["n_total"]), device="cuda")
+        row = {}
+        for prec, bb in (("fp64", b), ("fp32", b.float())):
+            z = torch.empty_like(bb)
+            row[prec] = timed(lambda: bt.apply(bb, z))
+            bt.sync()
+        res[tag] = row
+        bt.close()
+    out["batch2d_64sys_4rhs"] = res
+    for c in ctxs:
+        c.close()
+    w1 = workload_by_name("cd3d_128_8x8x4_ilu0")
+    c1 = pslr.from_workload(w1)
+    bd = torch.tensor(np.random.default_rng(2).uniform(-1, 1, w1["A"].n), device="cuda")
+    res = {}
+    for tag, r in (("r32", 32), ("r1", 1), ("r0", 0)):
+        set_rank(c1, w1["m"], r)
+        row = {}
+        for prec, bb in (("fp64", bd), ("fp32", bd.float())):
+            z = torch.empty_like(bb)
+            row[prec] = timed(lambda: c1.apply(bb, z))
+            c1.sync()
+        res[tag] = row
+    out["cd3d_128_8x8x4_ilu0"] = res
+    c1.close()
+    print(json.dumps(out))
+
+
+def run_cgs_probe(args):
+    """FGMRES(120) for K iterations with a seeded random low-rank term (no
+    Arnoldi launches, so the k_cgs_pass launches are the solve's own: one for
+    ||b||, then three per iteration with k = 1, 2, ... basis columns).  The
+    first solve of each form is the one to capture; the second is timed."""
+    import numpy as np
+    import torch
+
+    from paper_2002_00917_gb300 import build as B
+    from paper_2002_00917_gb300 import pslr
+    from pslr_inputs import generators as Gen
+
+    B.build()
+    w = workload_by_name(args.workload)
+    ctx = pslr.from_workload(w)
+    rng = np.random.default_rng(0)
+    q, r = ctx.info["q"], w["rank"]
+    ctx.set_lowrank(w["m"], np.linalg.qr(rng.standard_normal((q, r)))[0], rng.uniform(-0.01, 0.01, (r, r)))
+    b, _ = Gen.uniform_rhs(w["A"], 0)
+    bd = torch.tensor(b, device="cuda")
+    out = {"probe": "cgs", "workload": w["name"], "iters": args.cgs_probe, "restart": 120}
+    for prec, tag in ((pslr.PSLR_FP64, "fp64"), (pslr.PSLR_FP32, "fp32")):
+        x = torch.zeros_like(bd)
+        ctx.solve(bd, x, rtol=1e-30, restart=120, maxit=args.cgs_probe, prec=prec)
+        x.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        its, rel, st = ctx.solve(bd, x, rtol=1e-30, restart=120, maxit=args.cgs_probe, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        out[tag] = {"iters": its, "ms": e0.elapsed_time(e1), "ms_per_iter": e0.elapsed_time(e1) / max(its, 1)}
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -548,11 +666,23 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--batch-seq-stride", type=int, default=8)
     ap.add_argument("--no-batch-solve", action="store_true")
+    ap.add_argument("--lowrank-phase", action="store_true",
+                    help="only time the batched apply (64 systems x 4 rhs) and the 128^3 apply with the workloads' "
+                         "low-rank terms, with r = 32, r = 1 and r = 0 (Eq. 3.18's share of the apply) and print "
+                         "one JSON line")
+    ap.add_argument("--cgs-probe", type=int, default=0, metavar="K",
+                    help="only run FGMRES(120) for K iterations on --workload (for ncu captures of k_cgs_pass at "
+                         "k basis columns: its launch 1 + 3 (k - 1) is the first pass of iteration k) and print "
+                         "the time per iteration")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.cgs_probe:
+        return run_cgs_probe(args)
+    if args.lowrank_phase:
+        return run_lowrank_phase(args)
 
     import torch
 
