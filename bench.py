@@ -348,12 +348,15 @@ def run_batch(dev, flush, stream, steps, warmup, seq_stride, solve=True):
         ctxs.append(c)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    # group size: the autotuner times the FP32 batched apply for a few
-    # requests (0 = the largest group that fits) and keeps the fastest
+    # launch shape: the autotuner times the batched apply over group size and
+    # ring depth per precision and the FP64 thread mapping of the rhs, then
+    # one FGMRES cycle per Krylov chunk length, and keeps the fastest
     from paper_2002_00917_gb300 import autotune
 
-    group, tune = autotune.tune_group(ctxs, nr, prec=pslr.PSLR_FP32, candidates=(0, 2, 4, 6), steps=3, warmup=2)
-    bt = pslr.Batch(ctxs, nr, group=group)
+    t_tune = time.perf_counter()
+    best, tune = autotune.tune_batch(ctxs, nr, steps=3, warmup=2)
+    t_tune = time.perf_counter() - t_tune
+    bt = pslr.Batch(ctxs, nr, **best)
     info = bt.info
     rng = np.random.default_rng(0)
     bs, xs = [], []
@@ -383,7 +386,10 @@ def run_batch(dev, flush, stream, steps, warmup, seq_stride, solve=True):
     out = {"workload": w["name"], "nsys": info["nsys"], "nrhs": nr, "problems": info["nprob"],
            "n_total": info["n_total"], "work_items": info["items"], "grid": info["grid"],
            "group": info["group"], "groups": info["groups"],
-           "autotune_fp32_ms": {str(k): round(v[1], 3) for k, v in tune.items()}, "setup_s": setup_s}
+           "launch_options": {k: (list(v) if isinstance(v, tuple) else v) for k, v in best.items()},
+           "autotune": {"s": round(t_tune, 1),
+                        "table": [{k: (round(v, 3) if k == "ms" else v) for k, v in row.items()} for row in tune]},
+           "setup_s": setup_s}
     for name, bin_ in (("apply_fp64", b), ("apply_fp32", b.float())):
         ms = timed(bin_, torch.empty_like(bin_))
         nb = info["apply_bytes_fp64" if name == "apply_fp64" else "apply_bytes_fp32"]

@@ -345,7 +345,27 @@ typedef struct {
     int64_t apply_bytes_fp32;
     int32_t graph;                  /* 1: the last solve replayed its cycles as CUDA graphs */
     int32_t handoff;                /* problems the last solve finished one by one (pslr_solve) */
+    int32_t krylov_chunk;           /* rows per chunk of the batched Krylov kernels   */
+    int32_t pair_rhs;               /* FP64 apply with nrhs > 1: 1 = a thread per (row, rhs)
+                                       pair, 0 = a thread per row                      */
 } pslr_batch_info;
+
+/* Launch-shape options of a batch (pslr_batch_create_opts).  None changes a
+ * result, only the speed; pslr_batch_create(group) is group = {group, group},
+ * pair_rhs = 1 and zero elsewhere.  They have no counterpart in the paper: they are
+ * the autotuner's knobs (paper_2002_00917_gb300.autotune.tune_batch). */
+typedef struct {
+    int32_t group[2];     /* subdomains of one system a CTA sweeps in lockstep, [FP64, FP32]:
+                             1..8, 0 = the largest that fits shared memory (as
+                             pslr_batch_create)                                              */
+    int32_t ring_max[2];  /* cap on the apply's shared-memory ring slots, [FP64, FP32]:
+                             0 = as many as fit, else >= 2                                  */
+    int32_t krylov_chunk; /* rows per chunk of the batched FGMRES kernels (one CTA per
+                             chunk): 0 = 1024, else 64..2^20                                */
+    int32_t pair_rhs;     /* FP64 apply with nrhs > 1: 1 = one thread per (row, rhs) pair in
+                             the level sweeps and products, 0 = one thread per row with its
+                             right-hand sides (the same operations either way)              */
+} pslr_batch_opts;
 
 /*
  * Build a batch over nsys contexts that pslr_setup made and whose low-rank
@@ -363,6 +383,12 @@ typedef struct {
  */
 pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nrhs, int32_t group,
                               pslr_batch **out);
+
+/* pslr_batch_create with every launch-shape option of pslr_batch_opts (no
+ * counterpart in the paper).  opts must not be NULL; a bad option returns
+ * PSLR_ERR_ARG.  Everything else as pslr_batch_create. */
+pslr_status pslr_batch_create_opts(int32_t nsys, pslr_ctx *const *systems, int32_t nrhs,
+                                   const pslr_batch_opts *opts, pslr_batch **out);
 
 /* z = M_k^{-1} b for every system k and right-hand side (Algorithm 3), one
  * launch.  b_dev, z_dev: batched device vectors of n_total doubles

@@ -147,7 +147,7 @@ __device__ __noinline__ void ell_row_general_rhs(const char *seg, T *out, int nr
 // arrival of each segment after the first is awaited by the last consumer
 // thread before the level barrier.
 template <class T, int NR>
-__device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int nseg, int *err) {
+__device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int nseg, int *err, bool pair) {
     constexpr int nr = NR;
     Ring &R = c.ring;
     int slot = R.slot;
@@ -163,7 +163,7 @@ __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int nseg, int *err
     if (nseg > 0 && !mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
     for (int L = 0; L < nseg; ++L) {
         const uint2 h = lds_u2(ptr_s);
-        if (sizeof(T) == 8 && nr > 1 && ((h.y >> 16) & 0xffu) == kRec3) {
+        if (sizeof(T) == 8 && nr > 1 && pair && ((h.y >> 16) & 0xffu) == kRec3) {
             const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu);
             const bool diag = (h.x >> 24) & kSegDiag;
             for (PairWalk u(j, nr); u.row < n; u.next()) {
@@ -229,7 +229,7 @@ __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int nseg, int *err
 // no CTA barrier between segments, one at the end.
 template <class T, bool GLOBAL, int NR>
 __device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, const T *src, int64_t ss, bool subtract, int nseg,
-                                          int *err) {
+                                          int *err, bool pair) {
     constexpr int nr = NR;
     Ring &R = c.ring;
     int slot = R.slot;
@@ -244,7 +244,7 @@ __device__ __noinline__ void ell_op_multi(Cta<T> &c, T *out, const T *src, int64
     for (int kseg = 0; kseg < nseg; ++kseg) {
         if (!mbar_try_wait(fbar, phase)) wait_full_slow(fbar, phase, err);
         const uint2 h = lds_u2(ptr_s);
-        if (!GLOBAL && sizeof(T) == 8 && nr > 1 && ((h.y >> 16) & 0xffu) == kRec3) {
+        if (!GLOBAL && sizeof(T) == 8 && nr > 1 && pair && ((h.y >> 16) & 0xffu) == kRec3) {
             const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu);
             const uint32_t o0 = smem_addr(out), s0 = smem_addr(src);
             for (PairWalk u(j, nr); u.row < n; u.next()) {
@@ -364,12 +364,12 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
             }
         }
         csync();
-        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB1], P.err);
-        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB2], P.err);
-        ell_op_multi<T, false, NR>(c, c.si, c.xi, 0, true, g.cnt[kF], P.err);
+        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB1], P.err, P.pair64 != 0);
+        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB2], P.err, P.pair64 != 0);
+        ell_op_multi<T, false, NR>(c, c.si, c.xi, 0, true, g.cnt[kF], P.err, P.pair64 != 0);
         if (S.r == 0) {
-            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC1], P.err);
-            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC2], P.err);
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC1], P.err, P.pair64 != 0);
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC2], P.err, P.pair64 != 0);
         }
         const VT *V = reinterpret_cast<const VT *>(S.V);
         for (int t = 0; t < g.n; ++t) {
@@ -431,8 +431,8 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
                     lowrank_update(c, V, S.ldv, S.r, it.go, it.nq, c.si + it.lo * nr + kr, nr, kMaxRank);
                 }
             }
-            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC1], P.err);
-            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC2], P.err);
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC1], P.err, P.pair64 != 0);
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC2], P.err, P.pair64 != 0);
             for (int t = 0; t < g.n; ++t) {
                 const ItemRange it = item_range(S, g, t);
                 const T *y = c.si + it.lo * nr;
@@ -470,18 +470,18 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
                 for (int kr = tid; kr < nr; kr += kConsumers) w[it.nq * nr + kr] = T(0);
             }
             csync();
-            ell_op_multi<T, false, NR>(c, c.xi, c.wi, 0, false, g.cnt[kE], P.err);   // E w
-            tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB1], P.err);                       // B^{-1}
-            tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB2], P.err);
-            ell_op_multi<T, false, NR>(c, c.si, c.xi, 0, false, g.cnt[kF], P.err);   // F
+            ell_op_multi<T, false, NR>(c, c.xi, c.wi, 0, false, g.cnt[kE], P.err, P.pair64 != 0);   // E w
+            tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB1], P.err, P.pair64 != 0);                       // B^{-1}
+            tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB2], P.err, P.pair64 != 0);
+            ell_op_multi<T, false, NR>(c, c.si, c.xi, 0, false, g.cnt[kF], P.err, P.pair64 != 0);   // F
             if (!waited) {
                 ok = grid_wait(c, P.bar, P.err, P.wait_limit);
                 waited = true;
                 if (!ok) goto abort;
             }
-            ell_op_multi<T, true, NR>(c, c.si, wprev, wst, true, g.cnt[kCg], P.err);  // - C_g w
-            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC1], P.err);                       // C0^{-1}
-            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC2], P.err);
+            ell_op_multi<T, true, NR>(c, c.si, wprev, wst, true, g.cnt[kCg], P.err, P.pair64 != 0);  // - C_g w
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC1], P.err, P.pair64 != 0);                       // C0^{-1}
+            tri_sweep_multi<T, NR>(c, c.si, g.cnt[kC2], P.err, P.pair64 != 0);
             for (int t = 0; t < g.n; ++t) {
                 const ItemRange it = item_range(S, g, t);
                 const T *y = c.si + it.lo * nr;
@@ -522,9 +522,9 @@ __global__ void __launch_bounds__(kThreads, 1) pslr_batch_apply_kernel(const Bat
             }
         }
         csync();
-        ell_op_multi<T, false, NR>(c, c.xi, c.wi, 0, true, g.cnt[kE], P.err);
-        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB1], P.err);
-        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB2], P.err);
+        ell_op_multi<T, false, NR>(c, c.xi, c.wi, 0, true, g.cnt[kE], P.err, P.pair64 != 0);
+        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB1], P.err, P.pair64 != 0);
+        tri_sweep_multi<T, NR>(c, c.xi, g.cnt[kB2], P.err, P.pair64 != 0);
         IO *zs = P.z + S.voff;
         for (int t = 0; t < g.n; ++t) {
             const ItemRange it = item_range(S, g, t);

@@ -76,7 +76,10 @@ struct pslr_batch {
     std::vector<SysExport> sx;
     std::vector<int64_t> voff;
     int max_p = 0, max_q = 0, max_m = 0, any_lr = 0, items = 0, grid = 0;
-    int group_req = 0;                         // requested items per group (0: largest that fits)
+    int group_req[2] = {0, 0};                 // requested items per group, [FP64, FP32] (0: largest that fits)
+    int ring_max[2] = {0, 0};                  // cap on the apply's ring slots (0: as many as fit)
+    int kchunk = kBkChunk;                     // rows per chunk of the batched Krylov kernels
+    int pair64 = 1;                            // FP64 with several rhs: a thread per (row, rhs) pair
     int group[2] = {0, 0}, ngroups[2] = {0, 0};  // items per group and groups, [FP64, FP32]
     int xs[2] = {0, 0}, gs[2] = {0, 0};        // group vector strides
     int ring[2] = {0, 0}, slot_bytes[2] = {0, 0}, smem[2] = {0, 0};
@@ -486,7 +489,7 @@ static pslr_status batch_build(pslr_batch *bt) {
         int item_slot = 128;
         for (int k = 0; k < nsys; ++k) item_slot = std::max(item_slot, bt->sx[k].slot_bytes[prec]);
         // largest group size whose vectors and a 4-slot ring of merged segments fit
-        int G = bt->group_req > 0 ? std::min(bt->group_req, kMaxGroup) : kMaxGroup, xs = 1, gs = 1;
+        int G = bt->group_req[prec] > 0 ? std::min(bt->group_req[prec], kMaxGroup) : kMaxGroup, xs = 1, gs = 1;
         for (; G >= 1; --G) {
             groups[prec] = form_groups(bt, G, &xs, &gs);
             const int slot_est = std::min(kSegBudget, align_up(G * item_slot, 128));
@@ -515,6 +518,7 @@ static pslr_status batch_build(pslr_batch *bt) {
         bt->slot_bytes[prec] = sb;
         const int avail = optin - 1024 - smem_fixed(nr * xs - 1, nr * gs - 1, ts, false);
         bt->ring[prec] = std::min(kMaxRing, avail / sb);
+        if (bt->ring_max[prec] > 0) bt->ring[prec] = std::min(bt->ring[prec], bt->ring_max[prec]);
         if (bt->ring[prec] < 2)
             return bfail(bt, PSLR_ERR_TOO_LARGE, "batch: no room for the segment ring (%d-byte slots)", sb);
         bt->smem[prec] = smem_layout(sb, bt->ring[prec], nr * xs - 1, nr * gs - 1, ts, false).total;
@@ -704,7 +708,7 @@ static pslr_status batch_build(pslr_batch *bt) {
             p.off = bt->voff[k] + (int64_t)j * bt->sx[k].n;
             p.n = bt->sx[k].n;
             p.sys = k;
-            p.nc = std::max(1, (p.n + kBkChunk - 1) / kBkChunk);
+            p.nc = std::max(1, (p.n + bt->kchunk - 1) / bt->kchunk);
             p.c0 = (int32_t)chunks.size();
             for (int c = 0; c < p.nc; ++c) {
                 BkChunk ch;
@@ -762,6 +766,7 @@ static pslr_status batch_launch(pslr_batch *bt, int form, const void *b, void *z
         P.nrhs = bt->nrhs;
         P.grid = bt->grid;
         P.any_lr = bt->any_lr;
+        P.pair64 = bt->pair64;
         P.bar = bt->d_bar;
         P.err = bt->d_err;
         P.skip = skip;
@@ -1002,12 +1007,29 @@ extern "C" {
 
 pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nrhs, int32_t group,
                               pslr_batch **out) {
+    pslr_batch_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.group[0] = o.group[1] = group;
+    o.pair_rhs = 1;
+    return pslr_batch_create_opts(nsys, systems, nrhs, &o, out);
+}
+
+pslr_status pslr_batch_create_opts(int32_t nsys, pslr_ctx *const *systems, int32_t nrhs, const pslr_batch_opts *opts,
+                                   pslr_batch **out) {
     TraceRange trace("pslr_batch_create");
     pslr_batch *bt = nullptr;
     if (out) *out = nullptr;
-    if (!out || nsys < 1 || !systems || nrhs < 1 || nrhs > kMaxBatchRhs || group < 0 || group > kMaxGroup)
+    const bool gok = opts && opts->group[0] >= 0 && opts->group[0] <= kMaxGroup && opts->group[1] >= 0 &&
+                     opts->group[1] <= kMaxGroup;
+    if (!out || nsys < 1 || !systems || nrhs < 1 || nrhs > kMaxBatchRhs || !gok)
         return bfail(nullptr, PSLR_ERR_ARG, "batch_create: bad argument (nsys >= 1, nrhs 1..%d, group 0..%d)",
                      kMaxBatchRhs, kMaxGroup);
+    if (opts->ring_max[0] < 0 || opts->ring_max[1] < 0 || (opts->ring_max[0] > 0 && opts->ring_max[0] < 2) ||
+        (opts->ring_max[1] > 0 && opts->ring_max[1] < 2) || opts->krylov_chunk < 0 ||
+        (opts->krylov_chunk > 0 && (opts->krylov_chunk < 64 || opts->krylov_chunk > (1 << 20))) ||
+        (opts->pair_rhs != 0 && opts->pair_rhs != 1))
+        return bfail(nullptr, PSLR_ERR_ARG,
+                     "batch_create: bad option (ring_max 0 or >= 2, krylov_chunk 0 or 64..2^20, pair_rhs 0 or 1)");
     std::vector<SysExport> sx(nsys);
     for (int k = 0; k < nsys; ++k) {
         if (!systems[k] || !sys_export(systems[k], &sx[k]))
@@ -1025,7 +1047,12 @@ pslr_status pslr_batch_create(int32_t nsys, pslr_ctx *const *systems, int32_t nr
     bt = new pslr_batch();
     bt->nsys = nsys;
     bt->nrhs = nrhs;
-    bt->group_req = group;
+    bt->group_req[0] = opts->group[0];
+    bt->group_req[1] = opts->group[1];
+    bt->ring_max[0] = opts->ring_max[0];
+    bt->ring_max[1] = opts->ring_max[1];
+    bt->kchunk = opts->krylov_chunk > 0 ? opts->krylov_chunk : kBkChunk;
+    bt->pair64 = opts->pair_rhs;
     bt->ctx.assign(systems, systems + nsys);
     bt->sx = sx;
     pslr_status st = batch_build(bt);
@@ -1148,6 +1175,8 @@ pslr_status pslr_batch_get_info(const pslr_batch *bt, pslr_batch_info *info) {
     info->apply_bytes_fp32 = bt->apply_bytes[1];
     info->graph = bt->graph_used;
     info->handoff = bt->handoff;
+    info->krylov_chunk = bt->kchunk;
+    info->pair_rhs = bt->pair64;
     return PSLR_OK;
 }
 

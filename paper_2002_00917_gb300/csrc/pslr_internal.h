@@ -209,6 +209,7 @@ struct BatchParams {
     int ring, slot_bytes;
     int xs, gs;                 // per-rhs strides of a group's interior / interface vectors in shared memory
     int max_m, nrhs, grid, any_lr;
+    int pair64;                 // FP64, nrhs > 1: one thread per (row, rhs) pair (else one per row)
     unsigned *bar;
     int *err;
     const int *skip;            // when *skip != 0 the launch does nothing

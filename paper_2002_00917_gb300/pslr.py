@@ -65,13 +65,19 @@ class pslr_batch_info(C.Structure):
                 ("items", C.c_int32), ("grid", C.c_int32), ("ring", C.c_int32 * 2),
                 ("group", C.c_int32 * 2), ("groups", C.c_int32 * 2), ("max_m", C.c_int32),
                 ("max_p", C.c_int32), ("max_q", C.c_int32), ("apply_bytes_fp64", C.c_int64),
-                ("apply_bytes_fp32", C.c_int64), ("graph", C.c_int32), ("handoff", C.c_int32)]
+                ("apply_bytes_fp32", C.c_int64), ("graph", C.c_int32), ("handoff", C.c_int32),
+                ("krylov_chunk", C.c_int32), ("pair_rhs", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         for k in ("ring", "group", "groups"):
             d[k] = list(getattr(self, k))
         return d
+
+
+class pslr_batch_opts(C.Structure):
+    _fields_ = [("group", C.c_int32 * 2), ("ring_max", C.c_int32 * 2), ("krylov_chunk", C.c_int32),
+                ("pair_rhs", C.c_int32)]
 
 
 _P, _I32, _I64, _D, _U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint64
@@ -99,6 +105,7 @@ SIGNATURES = {
     "pslr_status_string": (C.c_char_p, [_I32]),
     "pslr_destroy": (None, [_P]),
     "pslr_batch_create": (_I32, [_I32, _P, _I32, _I32, C.POINTER(_P)]),
+    "pslr_batch_create_opts": (_I32, [_I32, _P, _I32, _P, C.POINTER(_P)]),
     "pslr_batch_apply": (_I32, [_P, _P, _P, _I32, _P]),
     "pslr_batch_solve": (_I32, [_P, _P, _P, _D, _I32, _I32, _I32, _P, _P, _P]),
     "pslr_batch_get_info": (_I32, [_P, C.POINTER(pslr_batch_info)]),
@@ -341,17 +348,28 @@ class Batch:
     the systems in order, each an n_k x nrhs column-major block;
     :meth:`offsets` gives the blocks' starts.  The contexts must outlive the
     batch; the batch keeps references to them.  ``group``: subdomains of one
-    system a CTA sweeps in lockstep (0: the largest that fits; see
-    :func:`paper_2002_00917_gb300.autotune.tune_group`)."""
+    system a CTA sweeps in lockstep (0: the largest that fits; an int, or a
+    pair (FP64, FP32)); ``ring_max``
+    (FP64, FP32) caps the apply's ring slots (0: as many as fit);
+    ``krylov_chunk``: rows per chunk of the batched FGMRES kernels (0: 1024);
+    ``pair_rhs``: in the FP64 apply with several right-hand sides, one thread
+    per (row, rhs) pair (1) or per row (0).  None changes a result; see
+    :func:`paper_2002_00917_gb300.autotune.tune_batch`."""
 
-    def __init__(self, systems, nrhs, group=0):
+    def __init__(self, systems, nrhs, group=0, ring_max=(0, 0), krylov_chunk=0, pair_rhs=1):
         lib = load()
         self.lib = lib
         self.systems = list(systems)
         self.nrhs = int(nrhs)
         arr = (C.c_void_p * len(self.systems))(*[p.h for p in self.systems])
+        o = pslr_batch_opts()
+        g = (group, group) if isinstance(group, int) else tuple(group)
+        o.group[0], o.group[1] = int(g[0]), int(g[1])
+        o.ring_max[0], o.ring_max[1] = int(ring_max[0]), int(ring_max[1])
+        o.krylov_chunk = int(krylov_chunk)
+        o.pair_rhs = int(pair_rhs)
         h = C.c_void_p()
-        st = lib.pslr_batch_create(len(self.systems), arr, self.nrhs, int(group), C.byref(h))
+        st = lib.pslr_batch_create_opts(len(self.systems), arr, self.nrhs, C.byref(o), C.byref(h))
         if st != PSLR_OK:
             raise PslrError(st, f"pslr_batch_create: {lib.pslr_batch_last_error(None).decode()}")
         self.h = h

@@ -413,3 +413,94 @@ def test_autotune_group_picks_a_candidate_and_stays_exact(dev):
         for j in range(2):
             r2, rinf = _rel(zk[:, j], orc.apply(np.ascontiguousarray(bk[:, j])))
             assert r2 <= TOL64 and rinf <= TOL64
+
+
+def test_launch_options_change_speed_not_results(dev):
+    """pslr_batch_create_opts: the FP64 (row, rhs) mapping and a cap on the
+    ring depth leave every applied value unchanged, bit for bit, in both
+    precisions; per-precision group requests are honoured (reduced to fit)."""
+    from paper_2002_00917_gb300 import pslr
+
+    sy = _systems(SYSTEMS)
+    ctxs = [c for _, c, _ in sy]
+    ref = pslr.Batch(ctxs, 3, group=(2, 4))
+    assert ref.info["group"][0] <= 2 and ref.info["group"][1] <= 4 and ref.info["pair_rhs"] == 1
+    b = torch.tensor(np.random.default_rng(23).uniform(-1, 1, ref.info["n_total"]), device=dev)
+    outs = {}
+    for key, kw in (("ref", None), ("rows", dict(pair_rhs=0)), ("ring3", dict(ring_max=(3, 3))),
+                    ("both", dict(pair_rhs=0, ring_max=(2, 2)))):
+        bt = ref if kw is None else pslr.Batch(ctxs, 3, group=(2, 4), **kw)
+        if kw and "ring_max" in kw:
+            assert bt.info["ring"][0] <= kw["ring_max"][0] and bt.info["ring"][1] <= kw["ring_max"][1]
+        if kw and "pair_rhs" in kw:
+            assert bt.info["pair_rhs"] == kw["pair_rhs"]
+        res = []
+        for dt in (torch.float64, torch.float32):
+            bb = b.to(dt)
+            z = torch.full_like(bb, float("nan"))
+            bt.apply(bb, z)
+            bt.sync()
+            res.append(z)
+        outs[key] = res
+        if bt is not ref:
+            bt.close()
+    for key in ("rows", "ring3", "both"):
+        for a, c in zip(outs["ref"], outs[key]):
+            assert torch.equal(a, c), key
+    ref.close()
+
+
+def test_krylov_chunk_option_and_bad_options(dev):
+    """A shorter Krylov chunk changes only the order of the per-problem
+    partial sums: the batched FGMRES still reaches 1e-8 on every problem in
+    about the same iterations.  Out-of-range options are rejected."""
+    from paper_2002_00917_gb300 import pslr
+
+    sy = _systems(SYSTEMS[:3])
+    ctxs = [c for _, c, _ in sy]
+    its = []
+    for ch in (0, 256):
+        bt = pslr.Batch(ctxs, 2, krylov_chunk=ch)
+        assert bt.info["krylov_chunk"] == (ch or 1024)
+        b = torch.tensor(np.random.default_rng(29).uniform(-1, 1, bt.info["n_total"]), device=dev)
+        x = torch.zeros_like(b)
+        it, rel, st = bt.solve(b, x, rtol=1e-8, restart=40, maxit=800)
+        assert st == pslr.PSLR_OK and (rel <= 1e-8).all()
+        its.append(it)
+        bt.close()
+    assert np.abs(its[0].astype(int) - its[1].astype(int)).max() <= 2, (its[0], its[1])
+    for kw in (dict(ring_max=(1, 0)), dict(ring_max=(0, -1)), dict(krylov_chunk=32), dict(pair_rhs=2),
+               dict(group=(9, 0)), dict(group=(0, -1))):
+        with pytest.raises(pslr.PslrError) as e:
+            pslr.Batch(ctxs, 2, **kw)
+        assert e.value.status == pslr.PSLR_ERR_ARG, kw
+
+
+def test_tune_batch_searches_every_knob(dev):
+    """The autotuner times every apply candidate per precision and every
+    Krylov chunk length, and returns options of the candidates it timed; a
+    batch built with them matches the oracle."""
+    from paper_2002_00917_gb300 import autotune, pslr
+
+    sy = _systems(SYSTEMS)
+    ctxs = [c for _, c, _ in sy]
+    best, table = autotune.tune_batch(ctxs, 2, groups=((0, 2), (0, 4)), rings=(0, 3), pairs=(1, 0),
+                                      chunks=(512, 1024), restart=20, steps=2, warmup=1)
+    applies64 = [r for r in table if r["what"] == "apply_fp64"]
+    applies32 = [r for r in table if r["what"] == "apply_fp32"]
+    cycles = [r for r in table if r["what"].startswith("fgmres")]
+    assert len(applies64) == 2 * 2 * 2 and len(applies32) == 2 * 2 and len(cycles) == 2
+    assert all(r["ms"] > 0 for r in table)
+    assert best["group"][0] in (0, 2) and best["group"][1] in (0, 4) and best["pair_rhs"] in (0, 1)
+    assert best["krylov_chunk"] in (512, 1024) and all(v in (0, 3) for v in best["ring_max"])
+    bt = pslr.Batch(ctxs, 2, **best)
+    b = np.random.default_rng(31).uniform(-1, 1, bt.info["n_total"])
+    bd = torch.tensor(b, device=dev)
+    zd = torch.zeros_like(bd)
+    bt.apply(bd, zd)
+    bt.sync()
+    for (w, ctx, orc), bk, zk in zip(sy, _split(bt, b), _split(bt, zd.cpu().numpy())):
+        for j in range(2):
+            r2, rinf = _rel(zk[:, j], orc.apply(np.ascontiguousarray(bk[:, j])))
+            assert r2 <= TOL64 and rinf <= TOL64
+    bt.close()
