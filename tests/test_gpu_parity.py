@@ -138,6 +138,31 @@ def test_apply_host_matches_device(dev):
     np.testing.assert_allclose(z, orc.apply(b), rtol=0, atol=TOL64 * np.abs(z).max())
 
 
+def test_apply_host_pinned_and_pageable_equal_device(dev):
+    """pslr_apply_host with page-locked (pinned) and with pageable host
+    buffers gives the device apply's result bit for bit (both precisions,
+    both directions, two right-hand sides)."""
+    from paper_2002_00917_gb300 import pslr
+
+    w, ctx, orc = _setup(CASES[2])
+    n = w["A"].n
+    rng = np.random.default_rng(17)
+    for dt in (torch.float64, torch.float32):
+        prec = pslr.PSLR_FP64 if dt == torch.float64 else pslr.PSLR_FP32
+        for tr in (0, 1):
+            b = torch.tensor(rng.uniform(-1, 1, 2 * n), dtype=dt)
+            zd = torch.empty(2 * n, dtype=dt, device=dev)
+            bd = b.to(dev)
+            f = ctx.lib.pslr_apply_T if tr else ctx.lib.pslr_apply
+            assert f(ctx.h, bd.data_ptr(), zd.data_ptr(), 2, prec, pslr._stream(None)) == 0
+            ctx.sync()
+            bp, zp = b.pin_memory(), torch.full((2 * n,), float("nan"), dtype=dt).pin_memory()
+            zq = torch.full((2 * n,), float("nan"), dtype=dt)
+            assert ctx.lib.pslr_apply_host(ctx.h, bp.data_ptr(), zp.data_ptr(), 2, prec, tr, pslr._stream(None)) == 0
+            assert ctx.lib.pslr_apply_host(ctx.h, b.data_ptr(), zq.data_ptr(), 2, prec, tr, pslr._stream(None)) == 0
+            assert torch.equal(zp, zd.cpu()) and torch.equal(zq, zd.cpu()), (dt, tr)
+
+
 @pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[5]], ids=["lap3d", "cd3d", "lap3d_r16"])
 def test_build_lowrank_matches_oracle(dev, case):
     """Device Arnoldi (Algorithm 1, steps 6-8) against the oracle's from the same
