@@ -326,7 +326,7 @@ def krylov_estimate(iters, restart, n, nnz, ms, apply_ms):
             "frac_of_fp64_nominal": tflops / FP64_NOMINAL_TFLOPS, "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS}
 
 
-def run_batch(dev, flush, stream, steps, warmup, seq_stride, solve=True):
+def run_batch(dev, flush, stream, steps, warmup, seq_stride, solve=True, tune=True):
     """The batched workload (64 uneven 2D shifted Laplacians x 4 rhs): batched
     apply bandwidth (one launch for all systems and rhs), batched FGMRES to
     1e-8 with the FP32 and the FP64 preconditioner, and the plain FP64 form -
@@ -354,7 +354,10 @@ def run_batch(dev, flush, stream, steps, warmup, seq_stride, solve=True):
     from paper_2002_00917_gb300 import autotune
 
     t_tune = time.perf_counter()
-    best, tune = autotune.tune_batch(ctxs, nr, steps=3, warmup=2)
+    if tune:
+        best, tune = autotune.tune_batch(ctxs, nr, steps=3, warmup=2)
+    else:  # the library's defaults (pslr_batch_create)
+        best, tune = {"group": (0, 0), "ring_max": (0, 0), "pair_rhs": 1, "krylov_chunk": 0}, []
     t_tune = time.perf_counter() - t_tune
     bt = pslr.Batch(ctxs, nr, **best)
     info = bt.info
@@ -672,6 +675,7 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--batch-seq-stride", type=int, default=8)
     ap.add_argument("--no-batch-solve", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="batch with the default launch options, no autotuning")
     ap.add_argument("--lowrank-phase", action="store_true",
                     help="only time the batched apply (64 systems x 4 rhs) and the 128^3 apply with the workloads' "
                          "low-rank terms, with r = 32, r = 1 and r = 0 (Eq. 3.18's share of the apply) and print "
@@ -787,7 +791,7 @@ def main():
     batch = None
     if not args.no_batch and rank == 0:
         batch = run_batch(dev, flush, stream, min(args.steps, 20), args.warmup, args.batch_seq_stride,
-                          solve=not args.no_batch_solve)
+                          solve=not args.no_batch_solve, tune=not args.no_tune)
 
     res = None
     if rank == 0:

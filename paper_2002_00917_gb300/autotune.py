@@ -8,7 +8,7 @@ times the batched apply with CUDA events (L2 flushed between launches, as the
 bench does) and returns the fastest.  ``tune_batch`` searches every knob of
 pslr_batch_opts: group size and ring depth per precision, the FP64 thread
 mapping of the right-hand sides ((row, rhs) pairs or rows), and the chunk
-length of the batched Krylov kernels (timed on one FGMRES restart cycle).
+length of the batched Krylov kernels (timed on a batched FGMRES solve).
 Every candidate computes the same result; only the speed differs.  The
 number of consumer warps per CTA is not a knob: the level-sweep barriers,
 the ring protocol and the shared-memory layout are built for eight.
@@ -62,27 +62,30 @@ def tune_group(systems, nrhs, prec=pslr.PSLR_FP32, candidates=(1, 2, 4, 6, 8), s
     return best, table
 
 
-def _time_solve(bt, b, restart, prec):
+def _time_solve(bt, b, restart, prec, rtol, maxit):
     x = torch.zeros_like(b)
-    bt.solve(b, x, rtol=1e-30, restart=restart, maxit=restart, prec=prec, check=False)  # captures the cycle
+    bt.solve(b, x, rtol=rtol, restart=restart, maxit=1, prec=prec, check=False)  # workspace, cycle graph
     torch.cuda.synchronize()
     x.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    bt.solve(b, x, rtol=1e-30, restart=restart, maxit=restart, prec=prec, check=False)
+    bt.solve(b, x, rtol=rtol, restart=restart, maxit=maxit, prec=prec, check=False)
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1)
 
 
 def tune_batch(systems, nrhs, groups=((0, 2, 3), (0, 2, 4, 6)), rings=(0, 3), pairs=(1, 0),
-               chunks=(512, 1024, 2048), restart=127, steps=3, warmup=2, flush_bytes=512 << 20):
+               chunks=(512, 1024, 2048), restart=127, rtol=1e-8, maxit=2000, steps=3, warmup=2,
+               flush_bytes=512 << 20):
     """Search the launch-shape knobs of a batch over ``systems`` (set-up
     :class:`pslr.Pslr` contexts with their low-rank terms), ``nrhs``
     right-hand sides each.  The applies are timed per precision over
     ``groups[prec]`` x ``rings`` (x ``pairs`` in FP64, where it applies);
-    then, with the best FP32 apply, one FGMRES(``restart``) cycle of the
-    FP32 form per Krylov chunk length.  Returns ``(best, table)``: ``best``
+    then, with the best FP32 apply, a batched FGMRES(``restart``) solve of
+    the FP32 form to ``rtol`` (a seeded random right-hand side; the late
+    cycles, with few problems left, favour other chunk lengths than the
+    first) per Krylov chunk length.  Returns ``(best, table)``: ``best``
     holds the keyword arguments of :class:`pslr.Batch` (group and ring_max
     per precision, pair_rhs, krylov_chunk); ``table`` is one dict per timed
     candidate: the request, what the library made of it (effective group,
@@ -117,11 +120,13 @@ def tune_batch(systems, nrhs, groups=((0, 2, 3), (0, 2, 4, 6)), rings=(0, 3), pa
         bt = pslr.Batch(systems, nrhs, group=best["group"], ring_max=best["ring_max"], pair_rhs=best["pair_rhs"],
                         krylov_chunk=ch)
         try:
-            b = torch.rand(bt.info["n_total"], dtype=torch.float64, device="cuda")
-            ms = _time_solve(bt, b, restart, pslr.PSLR_FP32)
+            gen = torch.Generator(device="cuda")
+            gen.manual_seed(7)
+            b = torch.rand(bt.info["n_total"], dtype=torch.float64, device="cuda", generator=gen)
+            ms = _time_solve(bt, b, restart, pslr.PSLR_FP32, rtol, maxit)
         finally:
             bt.close()
-        table.append({"what": f"fgmres{restart}_cycle_fp32", "krylov_chunk": ch, "ms": ms})
+        table.append({"what": f"fgmres{restart}_solve_fp32", "krylov_chunk": ch, "ms": ms})
         if best_ms is None or ms < best_ms:
             best_ms, best["krylov_chunk"] = ms, ch
     return best, table

@@ -485,7 +485,7 @@ def test_tune_batch_searches_every_knob(dev):
     sy = _systems(SYSTEMS)
     ctxs = [c for _, c, _ in sy]
     best, table = autotune.tune_batch(ctxs, 2, groups=((0, 2), (0, 4)), rings=(0, 3), pairs=(1, 0),
-                                      chunks=(512, 1024), restart=20, steps=2, warmup=1)
+                                      chunks=(512, 1024), restart=20, maxit=200, steps=2, warmup=1)
     applies64 = [r for r in table if r["what"] == "apply_fp64"]
     applies32 = [r for r in table if r["what"] == "apply_fp32"]
     cycles = [r for r in table if r["what"].startswith("fgmres")]
