@@ -67,8 +67,8 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-APPLY_SOURCES = ("pslr_apply.cu", "pslr_apply_ml.cu", "pslr_kernels.cuh", "pslr_device.cuh", "pslr_internal.h",
-                 "pslr_reduce.cuh")  # the kernels, their device code, their layout
+APPLY_SOURCES = ("pslr_apply.cu", "pslr_apply_ml.cu", "pslr_apply_unit.cu", "pslr_kernels.cuh", "pslr_device.cuh",
+                 "pslr_internal.h", "pslr_reduce.cuh")  # the kernels, their device code, their layout
 BATCH_SOURCES = ("pslr_batch.cuh", "pslr_device.cuh", "pslr_internal.h", "pslr_reduce.cuh")
 
 

@@ -128,6 +128,12 @@ typedef struct {
                              polynomial the context applies (pslr_set_neumann)    */
     int32_t merged[2];    /* 1 where the sweep segments of that precision ([0]
                              FP64, [1] FP32) hold several levels (merge_levels) */
+    int32_t unit_sweeps;  /* 1: forward FP64 applies run both sweeps of every local
+                             solve with unit diagonals (L~ = D L D^-1, U^ = D U,
+                             D = diag(1/u_rr); the right-hand sides scaled by D),
+                             the form used whenever the factors have no row
+                             pivots (factor 0 and 2); same solves in exact
+                             arithmetic                                          */
 } pslr_info;
 
 /*

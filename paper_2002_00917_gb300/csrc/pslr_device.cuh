@@ -606,8 +606,10 @@ __device__ __forceinline__ Rec3<T> rec3_shared(uint32_t seg, int np, int j) {
 // thread just before the level barrier, and the barrier passes it on to the
 // others (the same ordering as waiting for one's own asynchronous copies and
 // then synchronising), which takes the mbarrier poll of 256 threads out of
-// every level step.
-template <class T>
+// every level step.  kUnit: the sweep's 3-entry rows have a unit diagonal
+// (no scaling multiply in the code at all: on GB300 an FP64 instruction holds
+// the FP64 unit for its full time even when predicated off).
+template <class T, bool kUnit = false>
 __device__ void tri_sweep_levels(Cta<T> &c, T *x, int nseg, int *err) {
     Ring &R = c.ring;
     int slot = R.slot;
@@ -630,7 +632,8 @@ __device__ void tri_sweep_levels(Cta<T> &c, T *x, int nseg, int *err) {
                 T a = fma_t(-e.v0, x0, xr);
                 a = fma_t(-e.v1, x1, a);
                 a = fma_t(-e.v2, x2, a);
-                if ((h.x >> 24) & kSegDiag) a *= e.d;
+                if constexpr (!kUnit)
+                    if ((h.x >> 24) & kSegDiag) a *= e.d;
                 sts(xs + ts * e.r, a);
             }
         } else {
@@ -665,7 +668,7 @@ __device__ void tri_sweep_levels(Cta<T> &c, T *x, int nseg, int *err) {
 // and a segment's slot is released after its last block.  The rows of a block
 // are computed exactly as those of a one-level segment, so the result is the
 // same bit for bit.
-template <class T>
+template <class T, bool kUnit = false>
 __device__ void tri_sweep_blocks(Cta<T> &c, T *x, int nseg, int *err) {
     Ring &R = c.ring;
     int slot = R.slot;
@@ -689,7 +692,8 @@ __device__ void tri_sweep_blocks(Cta<T> &c, T *x, int nseg, int *err) {
                 T a = fma_t(-e.v0, x0, xr);
                 a = fma_t(-e.v1, x1, a);
                 a = fma_t(-e.v2, x2, a);
-                if ((h.x >> 24) & kSegDiag) a *= e.d;
+                if constexpr (!kUnit)
+                    if ((h.x >> 24) & kSegDiag) a *= e.d;
                 sts(xs + ts * e.r, a);
             }
         } else {
@@ -727,10 +731,10 @@ __device__ void tri_sweep_blocks(Cta<T> &c, T *x, int nseg, int *err) {
 // One triangular sweep: one-level segments (the common layout: a tight loop
 // of one level per segment) or multi-level segments (merged where the ring is
 // shallow).  The form is a template parameter of the kernel.
-template <class T, bool kMerged>
+template <class T, bool kMerged, bool kUnit = false>
 __device__ __forceinline__ void tri_sweep(Cta<T> &c, T *x, int nseg, int *err) {
-    if constexpr (kMerged) tri_sweep_blocks(c, x, nseg, err);
-    else tri_sweep_levels(c, x, nseg, err);
+    if constexpr (kMerged) tri_sweep_blocks<T, kUnit>(c, x, nseg, err);
+    else tri_sweep_levels<T, kUnit>(c, x, nseg, err);
 }
 
 // Rows of an ELL segment in the general encodings (out of line).
@@ -811,13 +815,14 @@ __device__ void permute(T *x, T *tmp, const uint16_t *piv, int n, bool scatter) 
     csync();
 }
 
-// Local solve x <- B_i~^{-1} x (or C0_i~^{-1}, or a transpose): two sweeps.
-template <class T, bool kMerged>
+// Local solve x <- B_i~^{-1} x (or C0_i~^{-1}, or a transpose): two sweeps
+// (kUnit: both with unit-diagonal 3-entry rows).
+template <class T, bool kMerged, bool kUnit = false>
 __device__ void solve_local(Cta<T> &c, T *x, int n, const uint16_t *piv, int pivot_post, int n1,
                             int n2, int *err) {
     if (piv && !pivot_post) permute(x, c.tmp, piv, n, false);
-    tri_sweep<T, kMerged>(c, x, n1, err);
-    tri_sweep<T, kMerged>(c, x, n2, err);
+    tri_sweep<T, kMerged, kUnit>(c, x, n1, err);
+    tri_sweep<T, kMerged, kUnit>(c, x, n2, err);
     if (piv && pivot_post) permute(x, c.tmp, piv, n, true);
 }
 

@@ -43,6 +43,7 @@ cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, bool dual, boo
 // these two steps, or one launch can meet another context's smaller limit.
 static std::mutex g_launch_mutex;
 int max_coresident_apply(int smem, bool fp32, bool dual, bool merged);
+cudaError_t launch_apply_fp64_unit(const ApplyParams<double> &P, int smem, bool dual, bool merged, cudaStream_t st);
 int krylov_blocks(int n);
 size_t krylov_part_doubles(int nblk, int nres);
 int krylov_tickets();
@@ -577,6 +578,13 @@ struct pslr_ctx {
     int32_t *d_perm = nullptr, *d_ioff = nullptr, *d_goff = nullptr;
     uint16_t *d_bpiv = nullptr, *d_cpiv = nullptr;
     OpSetHost ops[2][2];  // [direction: 0 forward, 1 transposed][precision]
+    // forward FP64 applies without row pivots: the unit-diagonal operator set
+    // (E rows and both sweeps scaled, see unit_rows) and the inverse U
+    // diagonals by which the kernel scales the other solve right-hand sides
+    bool has_unit = false;
+    OpSetHost ops_unit;
+    std::vector<double> h_dB, h_dC;
+    double *d_dB = nullptr, *d_dC = nullptr;
     int32_t *d_rp = nullptr, *d_ci = nullptr, *d_rpT = nullptr, *d_ciT = nullptr;
     double *d_av = nullptr, *d_avT = nullptr;
     // low-rank term
@@ -698,30 +706,63 @@ struct Local {
 template <class T>
 constexpr int merge_budget() { return sizeof(T) == 8 ? kSegBudget : 8 * 1024; }
 
+// The diagonal of an upper factor, row by row.
+std::vector<double> upper_diag(const Csr &U) {
+    std::vector<double> d(U.nr, 1.0);
+    for (int r = 0; r < U.nr; ++r)
+        for (int k = U.rp[r]; k < U.rp[r + 1]; ++k)
+            if (U.ci[k] == r) d[r] = U.v[k];
+    return d;
+}
+
+// Unit-diagonal form of the forward solves (no row pivots): with D =
+// diag(1/u_rr) of the local U factor, L~ = D L D^{-1} (entries l_rk u_kk /
+// u_rr) and U^ = D U (entries u_rk / u_rr, diagonal 1) give L U = D^{-1} L~ U^,
+// so x = U^{-1} L^{-1} b = U^^{-1} L~^{-1} (D b): the same solve with the
+// right-hand side scaled by D and no scaling multiply in either sweep.
+void unit_rows(std::vector<Row> &rows, const std::vector<double> &u, bool lower) {
+    for (Row &R : rows) {
+        for (auto &e : R.e) e.second = lower ? e.second * u[e.first] / u[R.row] : e.second / u[R.row];
+        R.diag = 1.0;
+    }
+}
+
 template <class T>
 void pack_subdomain(const Local &Lc, int npi, int nqi, bool transposed, int q, SegStore &S, int *k, int &levB,
-                    int &levC, bool merge) {
+                    int &levC, bool merge, bool unit = false) {
     levB = levC = 0;
     const int budget = merge ? merge_budget<T>() : 0;  // budget 0: one level per segment
     if (!transposed) {
-        k[kE] = pack_rows<T, uint16_t>(S, ell_rows(Lc.E), false, nqi);
+        // unit: E's rows feed the B solves' right-hand sides, so they carry D_B
+        const std::vector<double> uB = unit ? upper_diag(Lc.BU) : std::vector<double>();
+        const std::vector<double> uC = unit ? upper_diag(Lc.CU) : std::vector<double>();
+        std::vector<Row> er = ell_rows(Lc.E);
+        if (unit)
+            for (Row &R : er)
+                for (auto &e : R.e) e.second /= uB[R.row];
+        k[kE] = pack_rows<T, uint16_t>(S, er, false, nqi);
         k[kF] = pack_rows<T, uint16_t>(S, ell_rows(Lc.F), false, npi);
         k[kCg] = pack_rows<T, int32_t>(S, ell_rows(Lc.Cg), false, q);
         auto lb = levels(Lc.BL, true), ub = levels(Lc.BU, false);
         auto lc = levels(Lc.CL, true), uc = levels(Lc.CU, false);
         levB = (int)(lb.size() + ub.size());
         levC = (int)(lc.size() + uc.size());
+        auto sweep = [&](const Csr &Tm, const std::vector<int> &lv, bool lower, const std::vector<double> &u) {
+            std::vector<Row> rows = sweep_rows(Tm, lv, lower, !lower);
+            if (unit) unit_rows(rows, u, lower);
+            return rows;
+        };
         size_t d0 = S.desc.size();
-        for (auto &lv : lb) pack_rows<T, uint16_t>(S, sweep_rows(Lc.BL, lv, true, false), false, npi, merge);
+        for (auto &lv : lb) pack_rows<T, uint16_t>(S, sweep(Lc.BL, lv, true, uB), false, npi, merge);
         k[kB1] = merge_levels(S, d0, budget);
         d0 = S.desc.size();
-        for (auto &lv : ub) pack_rows<T, uint16_t>(S, sweep_rows(Lc.BU, lv, false, true), true, npi, merge);
+        for (auto &lv : ub) pack_rows<T, uint16_t>(S, sweep(Lc.BU, lv, false, uB), !unit, npi, merge);
         k[kB2] = merge_levels(S, d0, budget);
         d0 = S.desc.size();
-        for (auto &lv : lc) pack_rows<T, uint16_t>(S, sweep_rows(Lc.CL, lv, true, false), false, nqi, merge);
+        for (auto &lv : lc) pack_rows<T, uint16_t>(S, sweep(Lc.CL, lv, true, uC), false, nqi, merge);
         k[kC1] = merge_levels(S, d0, budget);
         d0 = S.desc.size();
-        for (auto &lv : uc) pack_rows<T, uint16_t>(S, sweep_rows(Lc.CU, lv, false, true), true, nqi, merge);
+        for (auto &lv : uc) pack_rows<T, uint16_t>(S, sweep(Lc.CU, lv, false, uC), !unit, nqi, merge);
         k[kC2] = merge_levels(S, d0, budget);
     } else {
         // E-slot: F_i^T (interior rows <- interface cols); F-slot: E_i^T.
@@ -757,7 +798,8 @@ void pack_subdomain(const Local &Lc, int npi, int nqi, bool transposed, int q, S
 template <class T>
 bool pack_direction(const std::vector<Local> &loc, const std::vector<int> &np, const std::vector<int> &nq,
                     bool transposed, int q, const std::vector<Csr> *cgT, int threads, SegStore &S,
-                    std::vector<int32_t> &sub_desc, std::vector<int32_t> &cnt, int &levB, int &levC, bool merge) {
+                    std::vector<int32_t> &sub_desc, std::vector<int32_t> &cnt, int &levB, int &levC, bool merge,
+                    bool unit = false) {
     const int s = (int)loc.size();
     sub_desc.assign(s, 0);
     cnt.assign((size_t)kNCnt * s, 0);
@@ -765,7 +807,7 @@ bool pack_direction(const std::vector<Local> &loc, const std::vector<int> &np, c
     std::vector<int> lb(s, 0), lc(s, 0);
     bool ok = parallel_for(s, threads, [&](int i) {
         int *k = &cnt[(size_t)kNCnt * i];
-        pack_subdomain<T>(loc[i], np[i], nq[i], transposed, q, part[i], k, lb[i], lc[i], merge);
+        pack_subdomain<T>(loc[i], np[i], nq[i], transposed, q, part[i], k, lb[i], lc[i], merge, unit);
         if (transposed) k[kCg] = pack_rows<T, int32_t>(pcg[i], ell_rows((*cgT)[i]), false, q);
     });
     if (!ok) return false;
@@ -1025,6 +1067,9 @@ void pslr_destroy(pslr_ctx *c) {
     if (!c) return;
     for (auto &d : c->ops)
         for (auto &o : d) free_opset(o);
+    free_opset(c->ops_unit);
+    cfree(c->d_dB);
+    cfree(c->d_dC);
     free_krylov(c);
     free_lowrank(c);
     if (c->kcap) cudaStreamDestroy(c->kcap);
@@ -1059,40 +1104,48 @@ static pslr_status plan_launch(pslr_ctx *c) {
     const bool piv = c->factor == 1;
     for (int prec = 0; prec < 2; ++prec) {
         const int ts = prec == 0 ? 8 : 4;
+        // the operator sets launched with this precision's kernels share one shape
+        std::vector<OpSetHost *> sets = {&c->ops[0][prec], &c->ops[1][prec]};
+        if (prec == 0 && c->has_unit) sets.push_back(&c->ops_unit);
+        const int ns = (int)sets.size();
         auto shape = [&](int budget, int *ring, int *smem) {
             const int avail = budget - 1024 - smem_fixed(c->max_p, c->max_q, ts, piv, rs, true);
             *smem = 0;
-            for (int dir = 0; dir < 2; ++dir) {
-                ring[dir] = std::min(kMaxRing, avail / c->ops[dir][prec].slot_bytes);
-                *smem = std::max(*smem, smem_layout(c->ops[dir][prec].slot_bytes, ring[dir], c->max_p, c->max_q,
-                                                    ts, piv, rs, true).total);
+            for (int d = 0; d < ns; ++d) {
+                ring[d] = std::min(kMaxRing, avail / sets[d]->slot_bytes);
+                *smem = std::max(*smem, smem_layout(sets[d]->slot_bytes, ring[d], c->max_p, c->max_q, ts, piv, rs,
+                                                    true).total);
             }
         };
-        int ring[2], smem = 0;
+        auto min_ring = [&](const int *ring) {
+            int m = ring[0];
+            for (int d = 1; d < ns; ++d) m = std::min(m, ring[d]);
+            return m;
+        };
+        int ring[3], smem = 0;
         shape(optin, ring, &smem);
-        if (std::min(ring[0], ring[1]) < 2)
+        if (min_ring(ring) < 2)
             return fail(c, PSLR_ERR_TOO_LARGE, "a subdomain needs more shared memory than one CTA has");
-        const bool merged = c->ops[0][prec].merged;  // the same for both directions
+        const bool merged = c->ops[0][prec].merged;  // the same for every set of the precision
         int cap = max_coresident_apply(smem, prec == 1, false, merged);
         if (cap <= 0) return fail(c, PSLR_ERR_CUDA, "persistent kernel cannot be made resident");
         bool dual = false;
         if (c->s > cap) {
-            int ring2[2], smem2 = 0;
+            int ring2[3], smem2 = 0;
             shape(per_sm / 2, ring2, &smem2);
-            if (std::min(ring2[0], ring2[1]) >= kMinDualRing) {
+            if (min_ring(ring2) >= kMinDualRing) {
                 const int cap2 = max_coresident_apply(smem2, prec == 1, true, merged);
                 if (cap2 > cap) {
                     dual = true;
                     cap = cap2;
                     smem = smem2;
-                    ring[0] = ring2[0];
-                    ring[1] = ring2[1];
+                    for (int d = 0; d < ns; ++d) ring[d] = ring2[d];
                 }
             }
         }
         const int grid = std::min(cap, c->s);
-        for (int dir = 0; dir < 2; ++dir) {
-            OpSetHost &o = c->ops[dir][prec];
+        for (int d = 0; d < ns; ++d) {
+            OpSetHost &o = *sets[d];
             if (o.grid != grid) {  // streams partition the subdomains over the grid
                 for (auto &kv : o.streams) {
                     cfree(kv.second.ent);
@@ -1100,7 +1153,7 @@ static pslr_status plan_launch(pslr_ctx *c) {
                 }
                 o.streams.clear();
             }
-            o.ring = ring[dir];
+            o.ring = ring[d];
             o.smem = smem;
             o.grid = grid;
             o.dual = dual;
@@ -1401,6 +1454,25 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
                 c->levels_C = lc;
             }
         }
+    if (c->factor != 1) {  // the unit-diagonal forward FP64 set (no row pivots to respect)
+        SegStore S;
+        std::vector<int32_t> sub_desc, cnt;
+        int lb = 0, lc = 0;
+        c->ops_unit.merged = merge[0];
+        const bool ok = pack_direction<double>(L, np, nq, false, c->q, &cgT, threads, S, sub_desc, cnt, lb, lc,
+                                               merge[0], true);
+        if (!ok) return bail(fail(c, PSLR_ERR_ARG, "host set-up failed while packing (out of memory?)"));
+        pslr_status st = finish_opset<double>(c, c->ops_unit, S, sub_desc, cnt, false, plan_only);
+        if (st != PSLR_OK) return bail(st);
+        c->h_dB.assign(c->p, 1.0);
+        c->h_dC.assign(c->q, 1.0);
+        for (int i = 0; i < c->s; ++i) {
+            const std::vector<double> uB = upper_diag(L[i].BU), uC = upper_diag(L[i].CU);
+            for (int r = 0; r < (int)uB.size(); ++r) c->h_dB[c->ioff[i] + r] = 1.0 / uB[r];
+            for (int r = 0; r < (int)uC.size(); ++r) c->h_dC[c->goff[i] + r] = 1.0 / uC[r];
+        }
+        c->has_unit = true;
+    }
     if (plan_only) return PSLR_OK;
     {
         pslr_status ps = plan_launch(c);
@@ -1412,6 +1484,10 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
     if (c->factor == 1) {
         CK(upload(&c->d_bpiv, bpiv));
         CK(upload(&c->d_cpiv, cpiv));
+    }
+    if (c->has_unit) {
+        CK(upload(&c->d_dB, c->h_dB));
+        CK(upload(&c->d_dC, c->h_dC));
     }
     CK(upload(&c->d_rp, c->h_rp));
     CK(upload(&c->d_ci, c->h_ci));
@@ -1521,8 +1597,7 @@ static pslr_status get_stream(pslr_ctx *c, OpSetHost &o, int kind, int m, bool l
 }
 
 template <class T, class IO>
-static void fill_params(pslr_ctx *c, ApplyParams<T, IO> &P, int dir, int prec, const StreamDev *sd) {
-    const OpSetHost &o = c->ops[dir][prec];
+static void fill_params(pslr_ctx *c, ApplyParams<T, IO> &P, const OpSetHost &o, int dir, const StreamDev *sd) {
     P.segbase = o.seg;
     P.stream = sd->ent;
     P.stream_off = sd->off;
@@ -1554,6 +1629,8 @@ static void fill_params(pslr_ctx *c, ApplyParams<T, IO> &P, int dir, int prec, c
     P.wait_limit = c->wait_limit;
     P.rs = c->rs;
     P.omega = T(c->omega);
+    P.dB = nullptr;
+    P.dC = nullptr;
 }
 
 // Scratch of one apply launch: series iterates (2(q+1)), accumulator (q+1),
@@ -1590,10 +1667,17 @@ static void set_io(ApplyParams<T, IO> &P, const void *b, void *z, const int *ski
     }
 }
 
+// The operator set an apply of this precision and direction runs on: the
+// unit-diagonal set for forward FP64 applies where there is one.
+static OpSetHost &apply_opset(pslr_ctx *c, int dir, int prec) {
+    return dir == 0 && prec == 0 && c->has_unit ? c->ops_unit : c->ops[dir][prec];
+}
+
 static pslr_status apply_launch(pslr_ctx *c, const void *b, void *z, int form, int dir, const int *skip,
                                 cudaStream_t st, const ApplyScratch *scr, bool may_allocate) {
     const int prec = form == PSLR_FP64 ? 0 : 1;  // operator set: FP64 or FP32 segments
-    OpSetHost &o = c->ops[dir][prec];
+    OpSetHost &o = apply_opset(c, dir, prec);
+    const bool unit = &o == &c->ops_unit;
     const bool lr_before = c->r > 0 && dir == 0;
     const StreamDev *sd = find_stream(o, 0, c->m, lr_before);
     if (!sd) {
@@ -1606,21 +1690,27 @@ static pslr_status apply_launch(pslr_ctx *c, const void *b, void *z, int form, i
     std::lock_guard<std::mutex> lock(g_launch_mutex);
     if (form == PSLR_FP64) {
         ApplyParams<double> P;
-        fill_params(c, P, dir, prec, sd);
+        fill_params(c, P, o, dir, sd);
         P.V = c->d_Vr;
         P.G = dir ? c->d_GT : c->d_G;
         set_io(P, b, z, skip, scr);
-        e = launch_apply_fp64(P, o.smem, o.dual, o.merged, st);
+        if (unit) {
+            P.dB = c->d_dB;
+            P.dC = c->d_dC;
+            e = launch_apply_fp64_unit(P, o.smem, o.dual, o.merged, st);
+        } else {
+            e = launch_apply_fp64(P, o.smem, o.dual, o.merged, st);
+        }
     } else if (form == PSLR_FP32) {
         ApplyParams<float> P;
-        fill_params(c, P, dir, prec, sd);
+        fill_params(c, P, o, dir, sd);
         P.V = c->d_Vb;
         P.G = dir ? c->d_GTf : c->d_Gf;
         set_io(P, b, z, skip, scr);
         e = launch_apply_fp32(P, o.smem, o.dual, o.merged, st);
     } else {
         ApplyParams<float, double> P;
-        fill_params(c, P, dir, prec, sd);
+        fill_params(c, P, o, dir, sd);
         P.V = c->d_Vb;
         P.G = dir ? c->d_GTf : c->d_Gf;
         set_io(P, b, z, skip, scr);
@@ -1641,7 +1731,7 @@ static pslr_status prebuild_streams(pslr_ctx *c) {
     for (int dir = 0; dir < 2; ++dir)
         for (int prec = 0; prec < 2; ++prec) {
             const StreamDev *sd = nullptr;
-            pslr_status st = get_stream(c, c->ops[dir][prec], 0, c->m, c->r > 0 && dir == 0, &sd);
+            pslr_status st = get_stream(c, apply_opset(c, dir, prec), 0, c->m, c->r > 0 && dir == 0, &sd);
             if (st != PSLR_OK) return st;
         }
     return PSLR_OK;
@@ -1822,6 +1912,7 @@ pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info) {
         I.ctas_per_sm[prec] = c->ops[0][prec].dual ? 2 : 1;
         I.merged[prec] = c->ops[0][prec].merged ? 1 : 0;
     }
+    I.unit_sweeps = c->has_unit ? 1 : 0;
     *info = I;
     return PSLR_OK;
 }
@@ -2235,7 +2326,9 @@ static cudaGraphExec_t arnoldi_graph(pslr_ctx *c, int prec, int dir) {
     if (it != c->kgraphs.end()) return it->second;
     // the apply's segment stream must exist before capture: building it allocates
     const StreamDev *sd = nullptr;
-    if (get_stream(c, c->ops[dir][prec], 0, c->m, c->r > 0 && dir == 0, &sd) != PSLR_OK) return nullptr;
+    if (get_stream(c, apply_opset(c, dir, prec == PSLR_FP64 ? 0 : 1), 0, c->m, c->r > 0 && dir == 0, &sd) !=
+        PSLR_OK)
+        return nullptr;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t x = nullptr;
     if (cudaStreamBeginCapture(c->kcap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {

@@ -140,6 +140,9 @@ struct ApplyParams {
     T omega;                     // series scaling: 1 for PSLR (Eq. 3.3); otherwise the Sec. 1
                                  // Neumann polynomial, w_k = (1-omega) w_{k-1} + omega C0^{-1} E_s w_{k-1},
                                  // y = omega sum w_k (no low-rank term)
+    const T *dB, *dC;            // unit-diagonal form (the kernels' kUnit instances): p and q inverse
+                                 // diagonals of the U factors of B_i and C0_i, reordered order, by
+                                 // which every sweep's right-hand side is scaled; nullptr otherwise
 };
 
 // E_rr(m) v for the Arnoldi process (Eq. 3.19): v <- (E_s C0^{-1})^{m+1} v.

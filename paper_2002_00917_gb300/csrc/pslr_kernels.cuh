@@ -35,7 +35,14 @@ namespace pslr {
 
 // ------------------------------------------------------------------ the apply
 
-template <class T, class VT, class IO, bool kMerged>
+// kUnit: the forward apply on the unit-diagonal operator set (no row
+// pivots): L~ = D L D^{-1} and U^ = D U with D = diag(1/u_rr) of each local
+// factor, so both sweeps have unit diagonals, E's rows are scaled by D_B when
+// packed, and the two other right-hand sides of a solve are scaled here: f by
+// D_B where it is gathered, and the C0 right-hand side by D_C0 before each C0
+// solve.  Same solves as B~^{-1} and C0~^{-1} in exact arithmetic, one FP64
+// instruction less per U row.
+template <class T, class VT, class IO, bool kMerged, bool kUnit = false>
 __device__ __forceinline__ void apply_body(const ApplyParams<T, IO> &P) {
     extern __shared__ __align__(128) char smem[];
     if (P.skip != nullptr && ld_volatile(P.skip) != 0) return;
@@ -60,19 +67,27 @@ __device__ __forceinline__ void apply_body(const ApplyParams<T, IO> &P) {
         const Counts k = counts_of(P.cnt, i);
         const int io = P.ioff[i], np_ = P.ioff[i + 1] - io;
         const int go = P.goff[i], nq = P.goff[i + 1] - go;
-        for (int j = tid; j < np_; j += kConsumers) c.xi[j] = T(P.b[P.perm[io + j]]);
+        for (int j = tid; j < np_; j += kConsumers) {
+            T f = T(P.b[P.perm[io + j]]);
+            if constexpr (kUnit) f *= __ldg(P.dB + io + j);
+            c.xi[j] = f;
+        }
         if (tid == 0) c.xi[np_] = T(0);
         for (int j = tid; j < nq; j += kConsumers) c.si[j] = T(P.b[P.perm[p + go + j]]);
         csync();
-        solve_local<T, kMerged>(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2], P.err);
+        solve_local<T, kMerged, kUnit>(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1],
+                                       k.n[kB2], P.err);
         ell_op<T, false>(c, c.si, c.xi, true, k.n[kF], P.err);
         if (lr_before) {
             lowrank_partial(c, V, P.ldv, r, go, nq, c.si, P.part + (int64_t)i * r, 1, P.rs);
             for (int j = tid; j < nq; j += kConsumers) P.acc[go + j] = c.si[j];
         } else {
             if (tid == 0) c.si[nq] = T(0);
+            if constexpr (kUnit)
+                for (int j = tid; j < nq; j += kConsumers) c.si[j] *= __ldg(P.dC + go + j);
             csync();
-            solve_local<T, kMerged>(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1], k.n[kC2], P.err);
+            solve_local<T, kMerged, kUnit>(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1],
+                                           k.n[kC2], P.err);
             for (int j = tid; j < nq; j += kConsumers) {
                 P.wbuf[go + j] = c.si[j];
                 P.acc[go + j] = c.si[j];
@@ -98,7 +113,12 @@ __device__ __forceinline__ void apply_body(const ApplyParams<T, IO> &P) {
             if (tid == 0) c.si[nq] = T(0);
             csync();
             lowrank_update(c, V, P.ldv, r, go, nq, c.si, 1, P.rs);
-            solve_local<T, kMerged>(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1], k.n[kC2], P.err);
+            if constexpr (kUnit) {
+                for (int j = tid; j < nq; j += kConsumers) c.si[j] *= __ldg(P.dC + go + j);
+                csync();
+            }
+            solve_local<T, kMerged, kUnit>(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1],
+                                           k.n[kC2], P.err);
             for (int j = tid; j < nq; j += kConsumers) {
                 P.wbuf[go + j] = c.si[j];
                 P.acc[go + j] = c.si[j];
@@ -122,8 +142,8 @@ __device__ __forceinline__ void apply_body(const ApplyParams<T, IO> &P) {
             fill(c.xi, np_ + 1, T(0));
             csync();
             ell_op<T, false>(c, c.xi, c.wi, false, k.n[kE], P.err);                      // E w
-            solve_local<T, kMerged>(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2],
-                        P.err);                                                         // B^{-1}
+            solve_local<T, kMerged, kUnit>(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1],
+                                           k.n[kB2], P.err);                            // B^{-1}
             fill(c.si, nq + 1, T(0));
             csync();
             ell_op<T, false>(c, c.si, c.xi, false, k.n[kF], P.err);                      // F
@@ -133,8 +153,12 @@ __device__ __forceinline__ void apply_body(const ApplyParams<T, IO> &P) {
                 if (!ok) goto abort;
             }
             ell_op<T, true>(c, c.si, wprev, true, k.n[kCg], P.err);                      // - C_g w
-            solve_local<T, kMerged>(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1], k.n[kC2],
-                        P.err);                                                         // C0^{-1}
+            if constexpr (kUnit) {
+                for (int j = tid; j < nq; j += kConsumers) c.si[j] *= __ldg(P.dC + go + j);
+                csync();
+            }
+            solve_local<T, kMerged, kUnit>(c, c.si, nq, pivots ? P.cpiv + go : nullptr, P.pivot_post, k.n[kC1],
+                                           k.n[kC2], P.err);                            // C0^{-1}
             if (scaled)  // N w = (1 - omega) w + omega C0^{-1} E_s w, N = I - omega C0^{-1} S
                 for (int j = tid; j < nq; j += kConsumers)
                     c.si[j] = fma_t(T(1) - om, __ldcg(wprev + go + j), om * c.si[j]);
@@ -171,12 +195,17 @@ __device__ __forceinline__ void apply_body(const ApplyParams<T, IO> &P) {
         const int go = P.goff[i], nq = P.goff[i + 1] - go;
         for (int j = tid; j < nq; j += kConsumers) c.wi[j] = scaled ? om * __ldcg(P.acc + go + j) : __ldcg(P.acc + go + j);
         if (tid == 0) c.wi[nq] = T(0);
-        for (int j = tid; j < np_; j += kConsumers) c.xi[j] = T(P.b[P.perm[io + j]]);
+        for (int j = tid; j < np_; j += kConsumers) {
+            T f = T(P.b[P.perm[io + j]]);
+            if constexpr (kUnit) f *= __ldg(P.dB + io + j);
+            c.xi[j] = f;
+        }
         if (tid == 0) c.xi[np_] = T(0);
         csync();
         if (lr_after) lowrank_update(c, V, P.ldv, r, go, nq, c.wi, 1, P.rs);
         ell_op<T, false>(c, c.xi, c.wi, true, k.n[kE], P.err);
-        solve_local<T, kMerged>(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1], k.n[kB2], P.err);
+        solve_local<T, kMerged, kUnit>(c, c.xi, np_, pivots ? P.bpiv + io : nullptr, P.pivot_post, k.n[kB1],
+                                       k.n[kB2], P.err);
         for (int j = tid; j < np_; j += kConsumers) P.z[P.perm[io + j]] = IO(c.xi[j]);
         for (int j = tid; j < nq; j += kConsumers) P.z[P.perm[p + go + j]] = IO(c.wi[j]);
         csync();
@@ -193,13 +222,13 @@ abort:
 // sweeping them one after the other.  Two CTAs are 18 warps, so one SM
 // sub-partition holds five of them in its 16K registers: at most 96 registers
 // per thread, which is what the launch bound asks the compiler for.
-template <class T, class VT, class IO, bool kMerged>
+template <class T, class VT, class IO, bool kMerged, bool kUnit = false>
 __global__ void __launch_bounds__(kThreads, 1) pslr_apply_kernel(const ApplyParams<T, IO> P) {
-    apply_body<T, VT, IO, kMerged>(P);
+    apply_body<T, VT, IO, kMerged, kUnit>(P);
 }
-template <class T, class VT, class IO, bool kMerged>
+template <class T, class VT, class IO, bool kMerged, bool kUnit = false>
 __global__ void __launch_bounds__(kThreads, 2) pslr_apply_kernel_x2(const ApplyParams<T, IO> P) {
-    apply_body<T, VT, IO, kMerged>(P);
+    apply_body<T, VT, IO, kMerged, kUnit>(P);
 }
 
 // ------------------------------------------------------------ E_rr(m) matvec

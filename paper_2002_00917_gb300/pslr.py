@@ -51,7 +51,7 @@ class pslr_info(C.Structure):
                 ("grid", C.c_int32 * 2), ("ring", C.c_int32 * 2), ("ctas_per_sm", C.c_int32 * 2),
                 ("nnz_fact_B", C.c_int64), ("nnz_fact_C0", C.c_int64), ("nnz_E", C.c_int64),
                 ("nnz_F", C.c_int64), ("nnz_Cg", C.c_int64), ("omega", C.c_double),
-                ("merged", C.c_int32 * 2)]
+                ("merged", C.c_int32 * 2), ("unit_sweeps", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -189,6 +189,7 @@ def test_layout_check_finds_no_violation(pslr, kind, dims, splits, factor, merge
                      merge_levels=merge_levels)[0]
     assert info["layout_errors"] == 0
     assert info["merged"] == [int(merge_levels == 2)] * 2
+    assert info["unit_sweeps"] == int(factor != 1)  # no row pivots: the unit-diagonal forward FP64 set
 
 
 def test_merge_levels_option(pslr):
