@@ -29,6 +29,20 @@ constexpr int kBkThreads = 256;
 constexpr int kBkCols = 8;      // basis columns per register block
 constexpr int kBkMaxK = 128;    // restart length + 1 at most
 
+// a[u] += sum_i V[c0 + u, i] w[i] for u < U over rows sb + lane, sb + lane +
+// 32, ... < se, U a compile-time width (an FP64 FMA that is predicated off
+// still takes the FP64 unit's time on GB300).
+template <int U>
+__device__ __forceinline__ void bk_chunk_dots(double (&a)[kBkCols], const double *__restrict__ V, int64_t ldv, int c0,
+                                              int64_t sb, int64_t se, int lane, const double *__restrict__ w) {
+#pragma unroll 4
+    for (int64_t i = sb + lane; i < se; i += 32) {
+        const double wi = w[i];
+#pragma unroll
+        for (int u = 0; u < U; ++u) a[u] = fma(V[(int64_t)(c0 + u) * ldv + i], wi, a[u]);
+    }
+}
+
 // part[blk * ldp + t] = V(:, t)^T w over the chunk [b, e), t = 0..k-1.  The
 // rows of w were written by this block just before.  Column-wise: a warp
 // takes a chunk of eight columns and a subset of the rows, lanes stride over
@@ -49,12 +63,15 @@ __device__ void bk_dots(int k, const double *__restrict__ V, int64_t ldv, const 
         double a[kBkCols];
 #pragma unroll
         for (int u = 0; u < kBkCols; ++u) a[u] = 0.0;
-#pragma unroll 4
-        for (int64_t i = sb + lane; i < se; i += 32) {
-            const double wi = w[i];
-#pragma unroll
-            for (int u = 0; u < kBkCols; ++u)
-                if (c0 + u < k) a[u] = fma(V[(int64_t)(c0 + u) * ldv + i], wi, a[u]);
+        switch (min(kBkCols, k - c0)) {  // the chunk's own width: no predicated-off FMAs
+        case 8: bk_chunk_dots<8>(a, V, ldv, c0, sb, se, lane, w); break;
+        case 7: bk_chunk_dots<7>(a, V, ldv, c0, sb, se, lane, w); break;
+        case 6: bk_chunk_dots<6>(a, V, ldv, c0, sb, se, lane, w); break;
+        case 5: bk_chunk_dots<5>(a, V, ldv, c0, sb, se, lane, w); break;
+        case 4: bk_chunk_dots<4>(a, V, ldv, c0, sb, se, lane, w); break;
+        case 3: bk_chunk_dots<3>(a, V, ldv, c0, sb, se, lane, w); break;
+        case 2: bk_chunk_dots<2>(a, V, ldv, c0, sb, se, lane, w); break;
+        default: bk_chunk_dots<1>(a, V, ldv, c0, sb, se, lane, w); break;
         }
         const double v = warp_reduce8(a);
         if ((lane & 3) == 0 && c0 + (lane >> 2) < k) sh[sub * kBkMaxK + c0 + (lane >> 2)] = v;

@@ -89,6 +89,22 @@ __device__ __forceinline__ double block_reduce1(double v, double *sh) {
     return a;
 }
 
+// Column sums a[u] += sum_i V[c0 + u, i] w[i], u < U, over the rows sb + lane,
+// sb + lane + 32, ... < se.  U is the chunk's width as a compile-time
+// constant: on GB300 an FP64 instruction holds the FP64 unit for its full
+// time even when predicated off, so a chunk narrower than eight columns must
+// not issue the other FMAs.
+template <int U>
+__device__ __forceinline__ void chunk_dots(double (&a)[kChunk], const double *__restrict__ V, int64_t ld, int c0,
+                                           int sb, int se, int lane, const double *__restrict__ w) {
+#pragma unroll 4
+    for (int i = sb + lane; i < se; i += 32) {
+        const double wi = w[i];
+#pragma unroll
+        for (int u = 0; u < U; ++u) a[u] = fma(V[(int64_t)(c0 + u) * ld + i], wi, a[u]);
+    }
+}
+
 // One CGS pass.  If rp != nullptr: w = A z first (CSR, FP64).  If hsub !=
 // nullptr: w -= V(:, 0:k) hsub.  Then either h = V(:, 0:k)^T w (norm == 0) or
 // res[0] = ||w||^2 (norm != 0).
@@ -147,12 +163,15 @@ __global__ void __launch_bounds__(kKThreads) k_cgs_pass(
             double a[kChunk];
 #pragma unroll
             for (int u = 0; u < kChunk; ++u) a[u] = 0.0;
-#pragma unroll 4
-            for (int i = sb + lane; i < se; i += 32) {
-                const double wi = w[i];
-#pragma unroll
-                for (int u = 0; u < kChunk; ++u)
-                    if (c0 + u < k) a[u] = fma(V[(int64_t)(c0 + u) * ld + i], wi, a[u]);
+            switch (min(kChunk, k - c0)) {  // the chunk's own width: no predicated-off FMAs
+            case 8: chunk_dots<8>(a, V, ld, c0, sb, se, lane, w); break;
+            case 7: chunk_dots<7>(a, V, ld, c0, sb, se, lane, w); break;
+            case 6: chunk_dots<6>(a, V, ld, c0, sb, se, lane, w); break;
+            case 5: chunk_dots<5>(a, V, ld, c0, sb, se, lane, w); break;
+            case 4: chunk_dots<4>(a, V, ld, c0, sb, se, lane, w); break;
+            case 3: chunk_dots<3>(a, V, ld, c0, sb, se, lane, w); break;
+            case 2: chunk_dots<2>(a, V, ld, c0, sb, se, lane, w); break;
+            default: chunk_dots<1>(a, V, ld, c0, sb, se, lane, w); break;
             }
             const double v = warp_reduce8(a);
             if ((lane & 3) == 0 && c0 + (lane >> 2) < k) sh[sub * kMaxK + c0 + (lane >> 2)] = v;
