@@ -146,6 +146,49 @@ __device__ __noinline__ void ell_row_general_rhs(const char *seg, T *out, int nr
 // x_k[r] = (x_k[r] - sum_e T_re x_k[c_e]) (* dinv[r]).  As in tri_sweep, the
 // arrival of each segment after the first is awaited by the last consumer
 // thread before the level barrier.
+// The 3-entry rows of one sweep level for the nr interleaved right-hand
+// sides, one thread per (row, rhs) pair (FP64) or per row with all its rhs;
+// DIAG: rows scaled by 1/diag.  Separate loops for the two, because an FP64
+// multiply that is predicated off still holds the FP64 unit on GB300.
+template <class T, int NR, bool DIAG>
+__device__ __forceinline__ void sweep_pairs(uint32_t ptr_s, int n, int np, uint32_t x0s, int j) {
+    constexpr uint32_t ts = sizeof(T);
+    const uint32_t es = ts * (uint32_t)NR;
+    for (PairWalk u(j, NR); u.row < n; u.next()) {
+        const Rec3<T> e = rec3_shared<T>(ptr_s, np, u.row);
+        const uint32_t b = x0s + ts * u.k;
+        const T x0 = lds(b + es * e.c0, T()), x1 = lds(b + es * e.c1, T());
+        const T x2 = lds(b + es * e.c2, T()), xr = lds(b + es * e.r, T());
+        T a = fma_t(-e.v0, x0, xr);
+        a = fma_t(-e.v1, x1, a);
+        a = fma_t(-e.v2, x2, a);
+        if constexpr (DIAG) a *= e.d;
+        sts(b + es * e.r, a);
+    }
+}
+template <class T, int NR, bool DIAG>
+__device__ __forceinline__ void sweep_rows_rhs(uint32_t ptr_s, int n, int np, uint32_t x0s, int j, bool scale = true) {
+    constexpr uint32_t es = sizeof(T) * (uint32_t)NR;
+    if (j < n) {
+        const Rec3<T> e = rec3_shared<T>(ptr_s, np, j);
+        T a0[kMaxBatchRhs], a1[kMaxBatchRhs], a2[kMaxBatchRhs], ar[kMaxBatchRhs];
+        lds_rhs<NR>(x0s + es * e.c0, a0);
+        lds_rhs<NR>(x0s + es * e.c1, a1);
+        lds_rhs<NR>(x0s + es * e.c2, a2);
+        lds_rhs<NR>(x0s + es * e.r, ar);
+#pragma unroll
+        for (int k = 0; k < kMaxBatchRhs; ++k)
+            if (k < NR) {
+                T a = fma_t(-e.v0, a0[k], ar[k]);
+                a = fma_t(-e.v1, a1[k], a);
+                a = fma_t(-e.v2, a2[k], a);
+                if constexpr (DIAG) ar[k] = scale ? a * e.d : a;
+                else ar[k] = a;
+            }
+        sts_rhs<NR>(x0s + es * e.r, ar);
+    }
+}
+
 template <class T, int NR>
 __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int nseg, int *err, bool pair) {
     constexpr int nr = NR;
@@ -165,36 +208,15 @@ __device__ __noinline__ void tri_sweep_multi(Cta<T> &c, T *x, int nseg, int *err
         const uint2 h = lds_u2(ptr_s);
         if (sizeof(T) == 8 && nr > 1 && pair && ((h.y >> 16) & 0xffu) == kRec3) {
             const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu);
-            const bool diag = (h.x >> 24) & kSegDiag;
-            for (PairWalk u(j, nr); u.row < n; u.next()) {
-                const Rec3<T> e = rec3_shared<T>(ptr_s, np, u.row);
-                const uint32_t b = x0s + ts * u.k;
-                const T x0 = lds(b + es * e.c0, T()), x1 = lds(b + es * e.c1, T());
-                const T x2 = lds(b + es * e.c2, T()), xr = lds(b + es * e.r, T());
-                T a = fma_t(-e.v0, x0, xr);
-                a = fma_t(-e.v1, x1, a);
-                a = fma_t(-e.v2, x2, a);
-                if (diag) a *= e.d;
-                sts(b + es * e.r, a);
-            }
+            if ((h.x >> 24) & kSegDiag) sweep_pairs<T, NR, true>(ptr_s, n, np, x0s, j);
+            else sweep_pairs<T, NR, false>(ptr_s, n, np, x0s, j);
         } else if (((h.y >> 16) & 0xffu) == kRec3) {
-            if (j < (int)(h.x & 0xffffu)) {
-                const Rec3<T> e = rec3_shared<T>(ptr_s, (int)(h.y & 0xffffu), j);
-                const bool diag = (h.x >> 24) & kSegDiag;
-                T a0[kMaxBatchRhs], a1[kMaxBatchRhs], a2[kMaxBatchRhs], ar[kMaxBatchRhs];
-                lds_rhs<NR>(x0s + es * e.c0, a0);
-                lds_rhs<NR>(x0s + es * e.c1, a1);
-                lds_rhs<NR>(x0s + es * e.c2, a2);
-                lds_rhs<NR>(x0s + es * e.r, ar);
-#pragma unroll
-                for (int k = 0; k < kMaxBatchRhs; ++k)
-                    if (k < nr) {
-                        T a = fma_t(-e.v0, a0[k], ar[k]);
-                        a = fma_t(-e.v1, a1[k], a);
-                        a = fma_t(-e.v2, a2[k], a);
-                        ar[k] = diag ? a * e.d : a;
-                    }
-                sts_rhs<NR>(x0s + es * e.r, ar);
+            const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu);
+            if constexpr (sizeof(T) == 8) {  // FP64: rows without a diagonal issue no multiply
+                if ((h.x >> 24) & kSegDiag) sweep_rows_rhs<T, NR, true>(ptr_s, n, np, x0s, j);
+                else sweep_rows_rhs<T, NR, false>(ptr_s, n, np, x0s, j);
+            } else {
+                sweep_rows_rhs<T, NR, true>(ptr_s, n, np, x0s, j, (h.x >> 24) & kSegDiag);
             }
         } else {
             const char *seg = R.base + (ptr_s - base_s);

@@ -596,6 +596,26 @@ __device__ __forceinline__ Rec3<T> rec3_shared(uint32_t seg, int np, int j) {
     return e;
 }
 
+// One 3-entry row of a sweep level per thread j < n: x[r] = (x[r] - v0 x[c0]
+// - v1 x[c1] - v2 x[c2]) (* 1/diag where DIAG and scale).  FP64 rows without
+// a diagonal use DIAG = false, so that no multiply is issued: on GB300 an FP64
+// instruction holds the FP64 unit for its full time even when predicated off.
+template <class T, bool DIAG>
+__device__ __forceinline__ void sweep_row3(uint32_t seg_s, int n, int np, uint32_t xs, int j, bool scale = true) {
+    constexpr uint32_t ts = sizeof(T);
+    if (j < n) {
+        const Rec3<T> e = rec3_shared<T>(seg_s, np, j);
+        const T x0 = lds(xs + ts * e.c0, T()), x1 = lds(xs + ts * e.c1, T());
+        const T x2 = lds(xs + ts * e.c2, T()), xr = lds(xs + ts * e.r, T());
+        T a = fma_t(-e.v0, x0, xr);
+        a = fma_t(-e.v1, x1, a);
+        a = fma_t(-e.v2, x2, a);
+        if constexpr (DIAG)
+            if (scale) a *= e.d;
+        sts(xs + ts * e.r, a);
+    }
+}
+
 // tri_sweep_levels: one triangular sweep over `nseg` one-level segments, in place:
 // x[r] = (x[r] - sum_k T_rk x[c_k]) (* dinv[r]).  The loop is kept to a few
 // instructions per level (the level chain is latency-bound with two warps per
@@ -625,16 +645,14 @@ __device__ void tri_sweep_levels(Cta<T> &c, T *x, int nseg, int *err) {
     for (int L = 0; L < nseg; ++L) {
         const uint2 h = lds_u2(ptr_s);
         if (((h.y >> 16) & 0xffu) == kRec3) {
-            if (j < (int)(h.x & 0xffffu)) {
-                const Rec3<T> e = rec3_shared<T>(ptr_s, (int)(h.y & 0xffffu), j);
-                const T x0 = lds(xs + ts * e.c0, T()), x1 = lds(xs + ts * e.c1, T());
-                const T x2 = lds(xs + ts * e.c2, T()), xr = lds(xs + ts * e.r, T());
-                T a = fma_t(-e.v0, x0, xr);
-                a = fma_t(-e.v1, x1, a);
-                a = fma_t(-e.v2, x2, a);
-                if constexpr (!kUnit)
-                    if ((h.x >> 24) & kSegDiag) a *= e.d;
-                sts(xs + ts * e.r, a);
+            const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu);
+            if constexpr (kUnit) {
+                sweep_row3<T, false>(ptr_s, n, np, xs, j);
+            } else if constexpr (sizeof(T) == 8) {  // no FP64 multiply issued in rows without a diagonal
+                if ((h.x >> 24) & kSegDiag) sweep_row3<T, true>(ptr_s, n, np, xs, j);
+                else sweep_row3<T, false>(ptr_s, n, np, xs, j);
+            } else {
+                sweep_row3<T, true>(ptr_s, n, np, xs, j, (h.x >> 24) & kSegDiag);
             }
         } else {
             level_row_general(R.base + (ptr_s - base_s), x, j);
@@ -685,16 +703,14 @@ __device__ void tri_sweep_blocks(Cta<T> &c, T *x, int nseg, int *err) {
     for (int L = 0; L < nseg;) {
         const uint4 h = lds_u4(blk_s);
         if (((h.y >> 16) & 0xffu) == kRec3) {
-            if (j < (int)(h.x & 0xffffu)) {
-                const Rec3<T> e = rec3_shared<T>(blk_s, (int)(h.y & 0xffffu), j);
-                const T x0 = lds(xs + ts * e.c0, T()), x1 = lds(xs + ts * e.c1, T());
-                const T x2 = lds(xs + ts * e.c2, T()), xr = lds(xs + ts * e.r, T());
-                T a = fma_t(-e.v0, x0, xr);
-                a = fma_t(-e.v1, x1, a);
-                a = fma_t(-e.v2, x2, a);
-                if constexpr (!kUnit)
-                    if ((h.x >> 24) & kSegDiag) a *= e.d;
-                sts(xs + ts * e.r, a);
+            const int n = (int)(h.x & 0xffffu), np = (int)(h.y & 0xffffu);
+            if constexpr (kUnit) {
+                sweep_row3<T, false>(blk_s, n, np, xs, j);
+            } else if constexpr (sizeof(T) == 8) {  // no FP64 multiply issued in rows without a diagonal
+                if ((h.x >> 24) & kSegDiag) sweep_row3<T, true>(blk_s, n, np, xs, j);
+                else sweep_row3<T, false>(blk_s, n, np, xs, j);
+            } else {
+                sweep_row3<T, true>(blk_s, n, np, xs, j, (h.x >> 24) & kSegDiag);
             }
         } else {
             level_row_general(R.base + (blk_s - base_s), x, j);
