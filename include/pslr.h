@@ -96,6 +96,12 @@ typedef struct {
                              is the same, bit for bit, for every value; the
                              layout changes only the copies that feed the
                              sweeps                                             */
+    int32_t device_factor; /* 1: the ILU(0) local factors (factor 0) are computed
+                              on the GPU (pslr_ilu0_device on all B_i and C_i
+                              at once) instead of on the host; the same factors
+                              up to the rounding of a fused multiply-add.
+                              0: on the host.  Needs factor 0; pslr_plan, which
+                              touches no GPU, factors on the host regardless */
 } pslr_opts;
 
 typedef struct {
@@ -134,6 +140,8 @@ typedef struct {
                              the form used whenever the factors have no row
                              pivots (factor 0 and 2); same solves in exact
                              arithmetic                                          */
+    int32_t device_factor; /* 1 when the set-up factored on the GPU               */
+    double factor_ms;      /* device_factor: time of the factorization kernel     */
 } pslr_info;
 
 /*
@@ -149,6 +157,29 @@ typedef struct {
  */
 pslr_status pslr_setup(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *val,
                        const pslr_opts *opts, void *stream, pslr_ctx **out);
+
+/*
+ * ILU(0) on the device of a block-diagonal sparse matrix M = blockdiag(M_0,
+ * ..., M_{nb-1}), the form of B and C0 (Eq. 2.1, Eq. 3.1): Algorithm 1, steps
+ * 3-4, with ILU(0) as the local factorization, in the IKJ order of Saad,
+ * Iterative Methods, Sec. 10.3.2 (natural order, no pivoting).  block_ptr
+ * (host, nb+1 entries, block_ptr[0] = 0, block_ptr[nb] = n, non-decreasing)
+ * gives the first row of each block; rowptr (n+1) and colind (host, 0-based)
+ * are M's pattern: columns strictly ascending within a row, every row holding
+ * its diagonal, no entry outside its row's diagonal block.  val_dev (device,
+ * rowptr[n] doubles, owned by the caller) holds M's values on entry and the
+ * factor on return, on M's pattern: the strictly lower part is L (unit
+ * diagonal implied), the rest U.  The pattern is checked on the host before
+ * any device work; one CTA per block walks the block's level sets (the rows
+ * whose stored columns below the diagonal lie in earlier levels), one thread
+ * per row.  Synchronous with respect to the host (stream: cudaStream_t as
+ * void*).  Errors: PSLR_ERR_ARG (pattern or sizes; nothing was touched),
+ * PSLR_ERR_ZERO_PIVOT (a pivot is zero; val_dev is partly factored),
+ * PSLR_ERR_CUDA.  No counterpart call in the paper, whose set-up factors each
+ * subdomain on its own processor.
+ */
+pslr_status pslr_ilu0_device(int32_t n, int32_t nb, const int32_t *block_ptr, const int32_t *rowptr,
+                             const int32_t *colind, double *val_dev, void *stream);
 
 /*
  * Host-only dry run of pslr_setup: the same validation, reordering (Section 2),

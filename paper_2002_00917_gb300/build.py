@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpslr.so")
 SOURCES = ["pslr_apply.cu", "pslr_apply_ml.cu", "pslr_apply_unit.cu", "pslr_krylov.cu", "pslr_host.cpp", "pslr_noalloc.cu", "pslr_batch_f64.cu",
            "pslr_batch_f32.cu", "pslr_batch_f32d.cu", "pslr_bkrylov.cu", "pslr_batch_host.cpp",
-           "pslr_partition.cpp"]
+           "pslr_partition.cpp", "pslr_ilu0.cu"]
 HEADERS = [os.path.join(CSRC, "pslr_internal.h"), os.path.join(CSRC, "pslr_device.cuh"),
            os.path.join(CSRC, "pslr_kernels.cuh"),
            os.path.join(CSRC, "pslr_sys.h"), os.path.join(CSRC, "pslr_batch.cuh"),

@@ -44,6 +44,9 @@ cudaError_t launch_err_fp64(const ErrParams<double> &P, int smem, bool dual, boo
 static std::mutex g_launch_mutex;
 int max_coresident_apply(int smem, bool fp32, bool dual, bool merged);
 cudaError_t launch_apply_fp64_unit(const ApplyParams<double> &P, int smem, bool dual, bool merged, cudaStream_t st);
+// device ILU(0) of a block-diagonal matrix (pslr_ilu0.cu)
+pslr_status ilu0_device_blocks(int n, int nb, const int32_t *bptr, const int32_t *rp, const int32_t *ci,
+                               double *val_dev, cudaStream_t st, float *kernel_ms, int *bad_row, std::string &why);
 int krylov_blocks(int n);
 size_t krylov_part_doubles(int nblk, int nres);
 int krylov_tickets();
@@ -562,6 +565,8 @@ struct KWork {
 
 struct pslr_ctx {
     int n = 0, s = 0, p = 0, q = 0, factor = 0;
+    int device_factor = 0;   // ILU(0) factors computed on the GPU
+    float factor_ms = 0.f;   // time of that factorization kernel
     int rs = 8;              // column stride of the kernels' low-rank scratch (red_stride(r))
     double drop_tol = 0.0;  // ILUT threshold (factor 2)
     uint64_t seed = 0;
@@ -1179,6 +1184,11 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
     if (opts->merge_levels < 0 || opts->merge_levels > 2)
         return bail(fail(c, PSLR_ERR_ARG, "merge_levels must be 0, 1 or 2"));
     c->merge_levels = opts->merge_levels;
+    if (opts->device_factor < 0 || opts->device_factor > 1)
+        return bail(fail(c, PSLR_ERR_ARG, "device_factor must be 0 or 1"));
+    if (opts->device_factor == 1 && opts->factor != 0)
+        return bail(fail(c, PSLR_ERR_ARG, "device_factor needs ILU(0) local factors (factor 0)"));
+    c->device_factor = plan_only ? 0 : opts->device_factor;
     if (opts->setup_threads < 0) return bail(fail(c, PSLR_ERR_ARG, "setup_threads must be >= 0"));
     if (opts->setup_threads > 0) {
         c->threads = opts->setup_threads;
@@ -1322,6 +1332,56 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
     if (!blocks_ok) return bail(fail(c, PSLR_ERR_ARG, "host set-up failed while extracting the blocks (out of memory?)"));
 
     // --- Algorithm 1, steps 2-5: local factors
+    // With device_factor, all B_i and C_i are factored at once on the GPU as
+    // one block-diagonal matrix (B_0 .. B_{s-1}, then C_0 .. C_{s-1}); dev_v
+    // receives the factored values in that order.
+    std::vector<double> dev_v;
+    // offsets of each block's rows and stored entries in that matrix
+    std::vector<int32_t> bptr(2 * s + 1, 0);
+    std::vector<int64_t> dev_off(2 * s + 1, 0);
+    for (int b = 0; b < 2 * s; ++b) {
+        const Csr &M = b < s ? L[b].B : L[b - s].C0;
+        bptr[b + 1] = bptr[b] + M.nr;
+        dev_off[b + 1] = dev_off[b] + (int64_t)M.v.size();
+    }
+    if (c->device_factor) {
+        if (dev_off[2 * s] > INT32_MAX)
+            return bail(fail(c, PSLR_ERR_TOO_LARGE, "device factor: more than 2^31 stored entries in B and C0"));
+        std::vector<int32_t> rp(bptr[2 * s] + 1, 0), ci(dev_off[2 * s]);
+        dev_v.resize(dev_off[2 * s]);
+        parallel_for(2 * s, threads, [&](int b) {
+            const Csr &M = b < s ? L[b].B : L[b - s].C0;
+            const int r0 = bptr[b];
+            const int64_t e0 = dev_off[b];
+            for (int r = 0; r < M.nr; ++r) rp[r0 + r + 1] = (int32_t)(e0 + M.rp[r + 1]);
+            for (size_t k = 0; k < M.v.size(); ++k) {
+                ci[e0 + k] = r0 + M.ci[k];
+                dev_v[e0 + k] = M.v[k];
+            }
+        });
+        double *d_v = nullptr;
+        cudaError_t e = cudaMalloc(&d_v, std::max<size_t>(1, dev_v.size()) * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d_v, dev_v.data(), dev_v.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d_v);
+            return bail(fail(c, PSLR_ERR_CUDA, "device factor: %s", cudaGetErrorString(e)));
+        }
+        int bad = -1;
+        std::string why;
+        const pslr_status fst = ilu0_device_blocks(bptr.back(), 2 * s, bptr.data(), rp.data(), ci.data(), d_v,
+                                                   nullptr, &c->factor_ms, &bad, why);
+        if (fst == PSLR_OK)
+            e = cudaMemcpy(dev_v.data(), d_v, dev_v.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaFree(d_v);
+        if (fst == PSLR_ERR_ZERO_PIVOT) {
+            // the block of the first failing row: B_i for rows below p, else C_i
+            const int blk = (int)(std::upper_bound(bptr.begin(), bptr.end(), bad) - bptr.begin()) - 1;
+            return bail(fail(c, PSLR_ERR_ZERO_PIVOT, "ILU(0) met a zero pivot in subdomain %d", blk % s));
+        }
+        if (fst != PSLR_OK) return bail(fail(c, fst, "device factor: %s", why.c_str()));
+        if (e != cudaSuccess) return bail(fail(c, PSLR_ERR_CUDA, "device factor: %s", cudaGetErrorString(e)));
+    }
     std::vector<uint16_t> bpiv, cpiv;
     if (c->factor == 1) {
         bpiv.resize(c->p);
@@ -1335,7 +1395,12 @@ static pslr_status setup_impl(pslr_ctx *c, int32_t n, const int32_t *rowptr, con
     bool fac_ok = parallel_for(s, threads, [&](int i) {
         Local &Lc = L[i];
         Csr fb, fc;
-        if (c->factor == 0) {
+        if (c->factor == 0 && c->device_factor) {
+            fb = Lc.B;
+            fc = Lc.C0;
+            std::copy(dev_v.begin() + dev_off[i], dev_v.begin() + dev_off[i + 1], fb.v.begin());
+            std::copy(dev_v.begin() + dev_off[s + i], dev_v.begin() + dev_off[s + i + 1], fc.v.begin());
+        } else if (c->factor == 0) {
             fb = Lc.B;
             fc = Lc.C0;
             if (!ilu0_inplace(fb) || !ilu0_inplace(fc)) {
@@ -1913,6 +1978,8 @@ pslr_status pslr_get_info(const pslr_ctx *c, pslr_info *info) {
         I.merged[prec] = c->ops[0][prec].merged ? 1 : 0;
     }
     I.unit_sweeps = c->has_unit ? 1 : 0;
+    I.device_factor = c->device_factor;
+    I.factor_ms = c->factor_ms;
     *info = I;
     return PSLR_OK;
 }

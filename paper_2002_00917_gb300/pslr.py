@@ -37,7 +37,8 @@ PSLR_FP32 = 1
 class pslr_opts(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("splits", C.c_int32 * 3), ("part", C.c_void_p),
                 ("factor", C.c_int32), ("seed", C.c_uint64), ("drop_tol", C.c_double),
-                ("setup_threads", C.c_int32), ("nparts", C.c_int32), ("merge_levels", C.c_int32)]
+                ("setup_threads", C.c_int32), ("nparts", C.c_int32), ("merge_levels", C.c_int32),
+                ("device_factor", C.c_int32)]
 
 
 class pslr_info(C.Structure):
@@ -51,7 +52,8 @@ class pslr_info(C.Structure):
                 ("grid", C.c_int32 * 2), ("ring", C.c_int32 * 2), ("ctas_per_sm", C.c_int32 * 2),
                 ("nnz_fact_B", C.c_int64), ("nnz_fact_C0", C.c_int64), ("nnz_E", C.c_int64),
                 ("nnz_F", C.c_int64), ("nnz_Cg", C.c_int64), ("omega", C.c_double),
-                ("merged", C.c_int32 * 2), ("unit_sweeps", C.c_int32)]
+                ("merged", C.c_int32 * 2), ("unit_sweeps", C.c_int32), ("device_factor", C.c_int32),
+                ("factor_ms", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,6 +99,7 @@ SIGNATURES = {
     "pslr_matvec": (_I32, [_P, _P, _P, _I32, _P]),
     "pslr_grad_values": (_I32, [_P, _P, _P, _P, _P]),
     "pslr_get_maps": (_I32, [_P, _P, _P, _P]),
+    "pslr_ilu0_device": (_I32, [_I32, _I32, _P, _P, _P, _P, _P]),
     "pslr_get_lowrank": (_I32, [_P, _P, _P, _P]),
     "pslr_get_info": (_I32, [_P, C.POINTER(pslr_info)]),
     "pslr_sync": (_I32, [_P, _P]),
@@ -165,10 +168,12 @@ class Pslr:
     partition (recursive breadth-first bisection) into that many subdomains.
     ``merge_levels``: sweep segment layout, 0 automatic, 1 one level per
     segment, 2 several levels per segment (same result, bit for bit).
+    ``device_factor``: compute the ILU(0) local factors (``factor`` 0) on
+    the GPU instead of on the host.
     """
 
     def __init__(self, A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, seed=0,
-                 stream=None, drop_tol=0.0, setup_threads=0, nparts=0, merge_levels=0):
+                 stream=None, drop_tol=0.0, setup_threads=0, nparts=0, merge_levels=0, device_factor=False):
         lib = load()
         self.lib = lib
         self.n = int(A.n)
@@ -187,6 +192,7 @@ class Pslr:
         o.setup_threads = int(setup_threads)
         o.nparts = int(nparts)
         o.merge_levels = int(merge_levels)
+        o.device_factor = int(bool(device_factor))
         self.factor, self.drop_tol = int(factor), float(drop_tol)
         h = C.c_void_p()
         st = lib.pslr_setup(self.n, self._rp.ctypes.data, self._ci.ctypes.data, self._av.ctypes.data,
@@ -435,7 +441,8 @@ class Batch:
         return self.lib.pslr_batch_set_wait_limit(self.h, int(polls))
 
 
-def _opts(dims, splits, part, factor, seed, drop_tol=0.0, setup_threads=0, nparts=0, merge_levels=0):
+def _opts(dims, splits, part, factor, seed, drop_tol=0.0, setup_threads=0, nparts=0, merge_levels=0,
+          device_factor=0):
     o = pslr_opts()
     for d in range(3):
         o.dims[d] = int(dims[d])
@@ -447,11 +454,12 @@ def _opts(dims, splits, part, factor, seed, drop_tol=0.0, setup_threads=0, npart
     o.setup_threads = int(setup_threads)
     o.nparts = int(nparts)
     o.merge_levels = int(merge_levels)
+    o.device_factor = int(device_factor)
     return o
 
 
 def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, drop_tol=0.0, setup_threads=0,
-         nparts=0, merge_levels=0):
+         nparts=0, merge_levels=0, device_factor=0):
     """Host-only dry run of the set-up (no GPU needed): returns (info dict,
     part, is_interface, perm) exactly as a device context would report them."""
     lib = load()
@@ -459,7 +467,7 @@ def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, 
     ci = np.ascontiguousarray(A.col, dtype=np.int32)
     av = np.ascontiguousarray(A.val, dtype=np.float64)
     pa = None if part is None else np.ascontiguousarray(part, dtype=np.int32)
-    o = _opts(dims, splits, pa, factor, 0, drop_tol, setup_threads, nparts, merge_levels)
+    o = _opts(dims, splits, pa, factor, 0, drop_tol, setup_threads, nparts, merge_levels, device_factor)
     info = pslr_info()
     n = int(A.n)
     mp = [np.empty(n, np.int32) for _ in range(3)]
@@ -470,8 +478,28 @@ def plan(A, dims=(0, 0, 0), splits=(1, 1, 1), part=None, factor=0, m=0, rank=0, 
     return (info.as_dict(), *mp)
 
 
-def from_workload(w, seed=0, stream=None, merge_levels=0):
+def from_workload(w, seed=0, stream=None, merge_levels=0, device_factor=False):
     """Context for a workload dict of ``pslr_inputs.configs``."""
     return Pslr(w["A"], dims=w.get("dims", (0, 0, 0)), splits=w.get("splits", (1, 1, 1)), factor=w["factor"],
                 seed=seed, stream=stream, drop_tol=w.get("drop_tol", 0.0), nparts=w.get("nparts", 0),
-                merge_levels=merge_levels)
+                merge_levels=merge_levels, device_factor=device_factor)
+
+
+def ilu0_device(block_ptr, rowptr, col, val, stream=None):
+    """ILU(0) on the device of the block-diagonal CSR matrix (``block_ptr``
+    the first row of each diagonal block, plus n; ``rowptr``/``col`` the
+    host pattern); ``val`` is a CUDA float64 tensor, factored in place (L
+    strictly lower with unit diagonal, U the rest).  See pslr_ilu0_device."""
+    lib = load()
+    bp = np.ascontiguousarray(block_ptr, dtype=np.int32)
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    n = len(rp) - 1
+    import torch
+    if val.dtype != torch.float64 or not val.is_cuda or not val.is_contiguous() or val.numel() != int(rp[-1]):
+        raise ValueError("val must be a contiguous CUDA float64 tensor with rowptr[-1] entries")
+    st = lib.pslr_ilu0_device(n, len(bp) - 1, bp.ctypes.data, rp.ctypes.data, ci.ctypes.data, _ptr(val),
+                              _stream(stream))
+    if st != PSLR_OK:
+        raise PslrError(st, f"pslr_ilu0_device: {lib.pslr_status_string(st).decode()}")
+    return val

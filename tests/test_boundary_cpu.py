@@ -264,3 +264,54 @@ def test_ilut_factors_have_the_oracles_pattern(kind, dims, splits, tau):
     assert info["nnz_ilu"] == nnz
     o0 = O.from_workload(dict(w, factor=0))
     assert nnz > sum(np.count_nonzero(o0.dense_block(f)) for f in ("LU_B", "LU_C0"))
+
+
+def test_device_factor_option(pslr):
+    """pslr_opts.device_factor: ILU(0) only, 0 or 1; the host-only dry run
+    factors on the host and reports device_factor 0 with the same layout."""
+    A = G.shifted_laplacian((12, 10), 0.1)
+    base = pslr.plan(A, (12, 10, 1), (2, 2, 1))
+    info, *maps = pslr.plan(A, (12, 10, 1), (2, 2, 1), device_factor=1)
+    assert info["device_factor"] == 0 and info["layout_hash"] == base[0]["layout_hash"]
+    for bad in (dict(device_factor=2), dict(device_factor=-1), dict(device_factor=1, factor=2, drop_tol=0.01),
+                dict(device_factor=1, factor=1)):
+        with pytest.raises(pslr.PslrError) as e:
+            pslr.plan(A, (12, 10, 1), (2, 2, 1), **bad)
+        assert e.value.status == pslr.PSLR_ERR_ARG
+
+
+def test_ilu0_device_rejects_bad_patterns_before_any_device_work(pslr):
+    """pslr_ilu0_device checks the block-diagonal pattern on the host and
+    returns PSLR_ERR_ARG without touching the device (so this runs without a
+    GPU): bad block pointers, a column outside its row's block, columns out
+    of order, a missing diagonal, negative sizes."""
+    lib = pslr.load()
+    val = np.ones(16)  # never read: every case fails on the host
+
+    def call(n, bptr, rp, ci):
+        bp = np.ascontiguousarray(bptr, np.int32)
+        r = np.ascontiguousarray(rp, np.int32)
+        c = np.ascontiguousarray(ci if len(ci) else [0], np.int32)
+        return lib.pslr_ilu0_device(n, len(bp) - 1, bp.ctypes.data, r.ctypes.data, c.ctypes.data,
+                                    val.ctypes.data, None)
+
+    # two 2x2 blocks, full within each block: a valid pattern for reference
+    rp, ci = [0, 2, 4, 6, 8], [0, 1, 0, 1, 2, 3, 2, 3]
+    cases = [
+        (4, [0, 2], rp, ci),              # block_ptr does not end at n
+        (4, [0, 3, 2, 4], rp, ci),        # block_ptr not monotone
+        (4, [1, 2, 4], rp, ci),           # block_ptr does not start at 0
+        (4, [0, 1, 4], rp, ci),           # row 0 reaches column 1 in the next block
+        (4, [0, 2, 4], rp, [1, 0, 0, 1, 2, 3, 2, 3]),   # row 0's columns descending
+        (4, [0, 2, 4], [0, 1, 3, 5, 7], [1, 0, 1, 2, 3, 2, 3]),  # row 0 without its diagonal
+        (4, [0, 2, 4], [0, 2, 4, 3, 8], ci),  # rowptr not monotone
+    ]
+    for n, bptr, r, c in cases:
+        assert call(n, bptr, r, c) == pslr.PSLR_ERR_ARG, (bptr, r, c)
+    assert lib.pslr_ilu0_device(-1, 1, val.ctypes.data, val.ctypes.data, val.ctypes.data, val.ctypes.data,
+                                None) == pslr.PSLR_ERR_ARG
+    assert lib.pslr_ilu0_device(4, 2, None, val.ctypes.data, val.ctypes.data, val.ctypes.data,
+                                None) == pslr.PSLR_ERR_ARG
+    # an empty matrix is a valid (empty) factorization
+    z = np.zeros(1, np.int32)
+    assert lib.pslr_ilu0_device(0, 0, z.ctypes.data, z.ctypes.data, None, None, None) == pslr.PSLR_OK
