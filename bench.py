@@ -661,6 +661,70 @@ def run_cgs_probe(args):
     print(json.dumps(out))
 
 
+def run_autograd_probe(args):
+    """The differentiable solve u = solve(A(kappa), b) on the 48^3 variable-
+    coefficient workload: forward (set-up, Arnoldi, FGMRES to 1e-12) and
+    backward (the adjoint FGMRES with pslr_apply_T, then dL/da_ij =
+    -lambda_i u_j and torch's chain rule to kappa), each timed on its own, and
+    the two solves and the gradient kernel timed separately with CUDA events
+    (their iteration counts beside them).  A second call is timed; the first
+    builds and warms up."""
+    import numpy as np
+    import torch
+
+    from paper_2002_00917_gb300 import autograd as AG
+    from paper_2002_00917_gb300 import build as B
+    from paper_2002_00917_gb300 import pslr
+    from pslr_inputs import configs as Cfg
+    from pslr_inputs import generators as Gen
+
+    B.build()
+    w = Cfg.kappa3d_48_3x3x3()
+    dims, A, sigma, kap0 = w["dims"], w["A"], w["sigma"], w["kappa"]
+    b0, _ = Gen.uniform_rhs(A, 0)
+    ut = torch.tensor(np.random.default_rng(1).uniform(-1, 1, A.n), device="cuda")
+    opts = dict(dims=dims, splits=w["splits"], m=w["m"], rank=w["rank"], rtol=1e-12, restart=127, maxit=6000)
+    b = torch.tensor(b0, device="cuda")
+    out = {"probe": "autograd", "workload": w["name"], "n": A.n, "nnz": int(A.rowptr[-1]), "rtol": 1e-12,
+           "restart": 127}
+    for rep in range(2):
+        kappa = torch.tensor(kap0, device="cuda", requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vals = Gen.variable_kappa_values(dims, A, kappa, sigma, xp=torch)
+        u = AG.solve(vals, b, A.rowptr, A.col, **opts)
+        loss = torch.sum((u - ut) ** 2)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out["forward_s"], out["backward_s"] = t1 - t0, t2 - t1
+    # the pieces, on one context
+    ctx = pslr.Pslr(A, dims=dims, splits=w["splits"], factor=w["factor"])
+    ctx.build_lowrank(w["m"], w["rank"])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    u = torch.zeros_like(b)
+    lam = torch.zeros_like(b)
+    g = torch.empty(int(A.rowptr[-1]), dtype=torch.float64, device="cuda")
+    ev[0].record()
+    its_f, rel_f, _ = ctx.solve(b, u, rtol=1e-12, restart=127, maxit=6000)
+    ev[1].record()
+    gu = 2 * (u - ut)  # dL/du of the probe's loss
+    ev[2].record()
+    its_b, rel_b, _ = ctx.solve(gu, lam, rtol=1e-12, restart=127, maxit=6000, transpose=True)
+    ev[3].record()
+    ev[4].record()
+    ctx.grad_values(lam, u, g)
+    ev[5].record()
+    torch.cuda.synchronize()
+    out["forward_solve"] = {"iters": its_f, "relres": rel_f, "ms": ev[0].elapsed_time(ev[1])}
+    out["adjoint_solve"] = {"iters": its_b, "relres": rel_b, "ms": ev[2].elapsed_time(ev[3])}
+    out["grad_values_us"] = 1e3 * ev[4].elapsed_time(ev[5])
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -684,6 +748,10 @@ def main():
                     help="only run FGMRES(120) for K iterations on --workload (for ncu captures of k_cgs_pass at "
                          "k basis columns: its launch 1 + 3 (k - 1) is the first pass of iteration k) and print "
                          "the time per iteration")
+    ap.add_argument("--autograd-probe", action="store_true",
+                    help="only time the differentiable solve on the 48^3 variable-coefficient workload (forward, "
+                         "backward, and the forward, adjoint and gradient kernels on their own) and print one "
+                         "JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -693,6 +761,8 @@ def main():
         return run_cgs_probe(args)
     if args.lowrank_phase:
         return run_lowrank_phase(args)
+    if args.autograd_probe:
+        return run_autograd_probe(args)
 
     import torch
 
